@@ -1,0 +1,161 @@
+"""FP64 CPU oracle — TEST INFRASTRUCTURE ONLY.
+
+A plain, slow restatement of the sharp-interface VOF phase-change hot path (liboracle.so, from
+oracle.cpp) plus an FP64 NumPy restatement of the isovalue-guess MLP (oracle.mlp). It exists to
+check the CUDA library: only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import it. It shares no code with the library.
+
+Parity unpinned (no independent reference exists, only invariants): the inverse-distance vertex
+field on general meshes, the one-sweep per-side gradient, and the rule for faces whose two cells
+are both interface cells.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+ST_DEGENERATE = 1
+ST_NOT_CONVERGED = 2
+ST_SINGULAR_LSQ = 8
+ST_NO_SIDE = 16
+
+XF_RECON, XF_LINEAR, XF_AS_PRINTED = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    so = os.path.join(_HERE, "liboracle.so")
+    src = os.path.join(_HERE, "oracle.cpp")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
+        os.replace(tmp, so)
+    return so
+
+
+class _OrcMesh(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_verts", ctypes.c_int64),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
+                ("face_vert_off", ctypes.c_void_p), ("face_vert", ctypes.c_void_p),
+                ("face_owner", ctypes.c_void_p), ("face_neigh", ctypes.c_void_p),
+                ("cell_face_off", ctypes.c_void_p), ("cell_face", ctypes.c_void_p)]
+
+
+class _OrcProps(ctypes.Structure):
+    _fields_ = [("k_l", ctypes.c_double), ("k_v", ctypes.c_double), ("h_lv", ctypes.c_double),
+                ("T_sat", ctypes.c_double)]
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = ctypes.CDLL(build())
+        _LIB.orc_liquid_volume.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.c_void_p, ctypes.c_void_p]
+        _LIB.orc_reconstruct.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 7)
+        _LIB.orc_phase_change.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 6
+                                          + [ctypes.c_int] + [ctypes.c_void_p] * 15)
+        _LIB.orc_vertex_field.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
+        _LIB.orc_geometry.argtypes = [ctypes.c_void_p] * 5
+        _LIB.orc_pairwise_sum.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    return _LIB
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+class Oracle:
+    """Oracle bound to one mesh (any object with the synth.Mesh arrays)."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        self._keep = [np.ascontiguousarray(a) for a in (mesh.vx, mesh.vy, mesh.vz, mesh.face_vert_off,
+                                                          mesh.face_vert, mesh.face_owner, mesh.face_neigh,
+                                                          mesh.cell_face_off, mesh.cell_face)]
+        k = self._keep
+        self.c = _OrcMesh(len(mesh.cell_face_off) - 1, len(mesh.face_owner), len(mesh.vx),
+                          *[a.ctypes.data for a in k])
+        self.ref = ctypes.byref(self.c)
+        self._geo = None
+
+    @property
+    def n_cells(self):
+        return self.c.n_cells
+
+    def geometry(self) -> dict:
+        """face_area (outward from owner) [nf,3], face_cen [nf,3], cell_vol [nc], cell_cen [nc,3]."""
+        if self._geo is None:
+            nf, nc = self.c.n_faces, self.c.n_cells
+            g = dict(face_area=np.empty((nf, 3)), face_cen=np.empty((nf, 3)), cell_vol=np.empty(nc),
+                     cell_cen=np.empty((nc, 3)))
+            _lib().orc_geometry(self.ref, *[_p(g[k]) for k in ("face_area", "face_cen", "cell_vol", "cell_cen")])
+            self._geo = g
+        return self._geo
+
+    def vertex_field(self, alpha: np.ndarray, mode: int = 0) -> np.ndarray:
+        """R1: mode 0 inverse distance to cell centroids, mode 1 plain average."""
+        phi = np.empty(self.c.n_verts)
+        a = np.ascontiguousarray(alpha, np.float64)
+        _lib().orc_vertex_field(self.ref, _p(self.geometry()["cell_cen"]), _p(a), mode, _p(phi))
+        return phi
+
+    def liquid_volume(self, cell: int, phi: np.ndarray, c: float, x0=None) -> dict:
+        """R2 for one cell at isovalue c."""
+        out = np.empty(9)
+        x = None if x0 is None else np.ascontiguousarray(x0, np.float64)
+        _lib().orc_liquid_volume(self.ref, int(cell), _p(phi), float(c), _p(x), _p(out))
+        return dict(VL=out[0], area=out[1], vec_area=out[2:5].copy(), centroid=out[5:8].copy(), nloops=int(out[8]))
+
+    def reconstruct(self, alpha, phi, eps=1e-12, tol=1e-12, max_iter=100, cells=None) -> dict:
+        """R0 + R3 (+ geometry at the root). Arrays over all cells; untouched cells hold nan/0."""
+        nc = self.c.n_cells
+        a = np.ascontiguousarray(alpha, np.float64)
+        r = dict(iso=np.full(nc, np.nan), status=np.zeros(nc, np.int32), evals=np.zeros(nc, np.int32),
+                 A_int=np.zeros(nc), n_int=np.zeros((nc, 3)), x_gamma=np.zeros((nc, 3)),
+                 nloops=np.zeros(nc, np.int32))
+        cl = None if cells is None else np.ascontiguousarray(cells, np.int64)
+        _lib().orc_reconstruct(self.ref, _p(a), _p(phi), _p(self.geometry()["cell_vol"]), eps, tol, max_iter,
+                               _p(cl), 0 if cl is None else len(cl),
+                               *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
+        return r
+
+    def phase_change(self, alpha, recon: dict, T, T_bnd, props: dict, eps=1e-12, xf_mode=XF_RECON) -> dict:
+        """R4-R8 given a reconstruction (oracle's own, or another one to be judged)."""
+        g = self.geometry()
+        nc, nf = self.c.n_cells, self.c.n_faces
+        o = dict(in_band=np.zeros(nc, np.uint8), grad=np.zeros((nc, 3)), grad_l=np.zeros((nc, 3)),
+                 grad_v=np.zeros((nc, 3)), q_l=np.zeros(nc), q_v=np.zeros(nc), mdot=np.zeros(nc), Q=np.zeros(nc),
+                 status=np.array(recon["status"], np.int32, copy=True), crossing=np.zeros(nf, np.uint8),
+                 x_f=np.zeros((nf, 3)), d_own=np.zeros(nf), d_neigh=np.zeros(nf), A_int_f=np.zeros(nf),
+                 totals=np.zeros(2))
+        pr = _OrcProps(props["k_l"], props["k_v"], props["h_lv"], props["T_sat"])
+        arr = lambda x: np.ascontiguousarray(x, np.float64)
+        _lib().orc_phase_change(self.ref, _p(g["face_area"]), _p(g["face_cen"]), _p(g["cell_vol"]),
+                                _p(g["cell_cen"]), _p(arr(alpha)), eps, _p(arr(recon["A_int"])),
+                                _p(arr(recon["n_int"])), _p(arr(recon["x_gamma"])), _p(arr(T)),
+                                None if T_bnd is None else _p(arr(T_bnd)), ctypes.byref(pr), xf_mode,
+                                *[_p(o[k]) for k in ("in_band", "grad", "grad_l", "grad_v", "q_l", "q_v", "mdot", "Q",
+                                                     "status", "crossing", "x_f", "d_own", "d_neigh", "A_int_f",
+                                                     "totals")])
+        return o
+
+    def run(self, alpha, T, T_bnd, props, eps=1e-12, tol=1e-12, vertex_mode=0, xf_mode=XF_RECON) -> dict:
+        """The whole path: R0-R8."""
+        phi = self.vertex_field(alpha, vertex_mode)
+        rec = self.reconstruct(alpha, phi, eps, tol)
+        pc = self.phase_change(alpha, rec, T, T_bnd, props, eps, xf_mode)
+        return dict(phi=phi, recon=rec, pc=pc)
+
+
+def pairwise_sum(a: np.ndarray) -> float:
+    out = np.zeros(1)
+    x = np.ascontiguousarray(a, np.float64)
+    _lib().orc_pairwise_sum(_p(x), len(x), _p(out))
+    return float(out[0])
