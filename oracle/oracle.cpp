@@ -9,9 +9,9 @@
 // (interface_htc); Appendix B least squares):
 //   R0  interface cells: eps < alpha < 1 - eps
 //   R1  vertex field: inverse-distance (or plain) average of the alpha of the cells around a vertex
-//   R2  liquid sub-volume V_L(c) of a cell: the cell split into tetrahedra (cell centre, face
-//       centre, two consecutive face vertices; the centres carry the mean vertex value), phi
-//       linear on each; the wet part of each tetrahedron by clipping with the plane phi = c
+//   R2  liquid sub-volume V_L(c) of a cell: the cell split into tetrahedra of its own vertices
+//       (faces fanned from their lowest-id vertex, the cell fanned from its lowest-id vertex),
+//       phi linear on each; the wet part of each tetrahedron by clipping with the plane phi = c
 //       through the cuts of Eq. edge_intersection
 //   R3  isovalue by bisection on V_L(c)/V - alpha
 //   R4  crossing point x_f on faces with (alpha_P - 1/2)(alpha_Q - 1/2) < 0
@@ -232,32 +232,27 @@ void clip_tet(const VPt* T, double c, const V3& x0, IsoGeom& g, V3& moment) {
   }
 }
 
-// R2. The cell is split into tetrahedra (cell centre, face centre, v_i, v_{i+1}); the cell centre
-// and each face centre are vertex means and carry the mean of the vertex values of the cell and
-// of the face. phi is linear on each tetrahedron, so its iso-surface there is planar and passes
-// through the cuts of Eq. edge_intersection on the tetrahedron's edges (the cell's own edges
-// included). V_L(c) is the volume of the wet parts. It is continuous and non-increasing in c,
-// exact for a linear field, and resolves faces whose crossings are ambiguous (saddle faces).
+// R2. The cell is split into tetrahedra using only its own vertices: each face is fanned from
+// its lowest-id vertex, and the cell is fanned from its lowest-id vertex (the apex) over every
+// face triangle that does not contain the apex (a convex cell is star-shaped from any vertex).
+// phi is linear on each tetrahedron, so its iso-surface there is planar and passes through the cuts
+// of Eq. edge_intersection on the tetrahedron's edges, the cell's own edges included. V_L(c) is the
+// volume of the wet parts: continuous and non-increasing in c, exact for a linear field, and the
+// faces whose four crossings are ambiguous for straight chords (saddle faces) are resolved.
 IsoGeom liquid_volume(const OrcMesh& m, int64_t cell, const double* phi, double c, const V3* x0_in) {
   const std::vector<int32_t> vs = cell_vertices(m, cell);
-  VPt ctr;
-  ctr.x = mean_point(m, vs);
-  ctr.phi = 0;
-  for (int32_t v : vs) ctr.phi += phi[v];
-  ctr.phi /= (double)vs.size();
-  const V3 x0 = x0_in ? *x0_in : ctr.x;
+  const int32_t apex = vs[0];
+  const V3 x0 = x0_in ? *x0_in : mean_point(m, vs);
   IsoGeom g;
   V3 moment = {0, 0, 0};
   for (int64_t k = m.cell_face_off[cell]; k < m.cell_face_off[cell + 1]; ++k) {
     const std::vector<int32_t> L = loop_of(m, m.cell_face[k]);
     const size_t n = L.size();
-    VPt fc;
-    fc.x = mean_point(m, L);
-    fc.phi = 0;
-    for (int32_t v : L) fc.phi += phi[v];
-    fc.phi /= (double)n;
-    for (size_t i = 0; i < n; ++i) {
-      const VPt T[4] = {ctr, fc, {vert(m, L[i]), phi[L[i]]}, {vert(m, L[(i + 1) % n]), phi[L[(i + 1) % n]]}};
+    const size_t s = std::min_element(L.begin(), L.end()) - L.begin();
+    for (size_t i = 1; i + 1 < n; ++i) {
+      const int32_t t0 = L[s], t1 = L[(s + i) % n], t2 = L[(s + i + 1) % n];
+      if (t0 == apex || t1 == apex || t2 == apex) continue;
+      const VPt T[4] = {{vert(m, apex), phi[apex]}, {vert(m, t0), phi[t0]}, {vert(m, t1), phi[t1]}, {vert(m, t2), phi[t2]}};
       clip_tet(T, c, x0, g, moment);
     }
   }
