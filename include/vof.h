@@ -1,0 +1,213 @@
+/* vof.h — C ABI of the GB300 (sm_103a) sharp-interface VOF phase-change hot path.
+ *
+ * What the calls compute (paper: arXiv 2604.14938, Sec. 2.1 "Interface capturing method",
+ * Eq. (edge_intersection) and the isoap steps; Sec. 2.3 "Energy specific terms", Eqs.
+ * (mass_transfer), (front_interpolation), (extrapolation), (latent_source), (interface_htc);
+ * Appendix B "Least Squares Gradient Reconstruction"):
+ *
+ *   vof_reconstruct          per interface cell (eps < alpha < 1 - eps): the vertex field
+ *                            (inverse-distance average of alpha), the isovalue c whose liquid
+ *                            sub-volume {phi >= c} equals alpha V, and the interface area A_int,
+ *                            unit normal n_int (vapour -> liquid) and centroid x_gamma.
+ *   vof_phase_change_source  interface-modified least-squares temperature gradient on the band
+ *                            (interface cells and their face neighbours) with T_sat imposed at the
+ *                            crossing point x_f of every face with (alpha_P-1/2)(alpha_Q-1/2) < 0;
+ *                            per-side gradients; q_l = k_l (grad T_l . n) A_int,
+ *                            q_v = -k_v (grad T_v . n) A_int; mdot = (q_l + q_v)/(h_lv V);
+ *                            Q = -mdot h_lv; totals sum(mdot V), sum(Q V) by a fixed pairwise tree.
+ *
+ * The cut volume of a polyhedron is taken on its tetrahedralisation by its own vertices (faces
+ * fanned from their lowest-id vertex, the cell fanned from its lowest-id vertex), phi linear per
+ * tetrahedron: continuous and non-increasing in c, exact for linear fields.
+ *
+ * Conventions
+ *   - Every function returns a vof_status; no exception or abort crosses the ABI. A non-zero
+ *     status means malformed input, allocation failure or a CUDA error; vof_last_error() gives a
+ *     thread-local message. Per-cell conditions (degenerate range, not converged, fallback,
+ *     singular least squares, no neighbour on the other side) are status bits in arrays plus
+ *     counters, never errors.
+ *   - "stream" is a cudaStream_t passed as void*; all device work is ordered on it. Calls return
+ *     without synchronising unless stated.
+ *   - Device pointers are caller-owned unless stated; the library never frees them.
+ *   - The mesh's faces must be planar (all generated meshes are) and its cells convex; at most
+ *     VOF_MAX_CELL_VERTS vertices and VOF_MAX_CELL_TETS tetrahedra per cell.
+ *   - Memory: vof_mesh_create allocates everything the mesh's steps need (geometry tables and a
+ *     workspace sized for the mesh); the step calls allocate nothing.
+ */
+#ifndef VOF_H
+#define VOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOF_MAX_CELL_VERTS 64
+#define VOF_MAX_CELL_TETS 192
+
+typedef enum {
+  VOF_OK = 0,
+  VOF_EINVAL = 1, /* bad argument (null pointer, size out of range, bad option) */
+  VOF_ENOMEM = 2, /* device or host allocation failed */
+  VOF_ECUDA = 3,  /* a CUDA call failed; see vof_last_error() */
+  VOF_EMESH = 4,  /* malformed mesh (offsets, ids, face/cell lists disagree, cell too large) */
+  VOF_ESTATE = 5  /* call out of order (e.g. source before reconstruct, no MLP loaded) */
+} vof_status;
+
+/* Per-cell status bits (int32 arrays). */
+#define VOF_ST_DEGENERATE 1    /* phi_max - phi_min < 1e-14: c = phi_min, A_int = 0, mdot = 0 */
+#define VOF_ST_NOT_CONVERGED 2 /* |V_L(c)/V - alpha| > tol after the iteration cap */
+#define VOF_ST_FALLBACK 4      /* learned guess + secant missed tol; bisection finished it */
+#define VOF_ST_SINGULAR_LSQ 8  /* det(G) <= 1e-12 (tr G / 3)^3: gradient set to 0 */
+#define VOF_ST_NO_SIDE 16      /* no face neighbour looks into the other phase: its gradient is 0 */
+#define VOF_ST_MLP_SKIPPED 32  /* more than 32 vertices: learned guess not used */
+
+/* Crossing-point modes (Eq. front_interpolation). */
+#define VOF_XF_RECON 0      /* x_f on the reconstructed interface plane (x_gamma, n_int) */
+#define VOF_XF_LINEAR 1     /* x_f = x_o + t (x_n - x_o), t = (alpha_o - 1/2)/(alpha_o - alpha_n) */
+#define VOF_XF_AS_PRINTED 2 /* t = |alpha_n - 1/2| / |alpha_o - alpha_n|, the equation as printed */
+
+/* Root-search modes. */
+#define VOF_ROOT_BISECT 0  /* plain FP64 bisection on [phi_min, phi_max] */
+#define VOF_ROOT_LEARNED 1 /* BF16 MLP guess, <= max_secant FP64 secant steps, bracketed bisection fallback */
+
+typedef struct vof_mesh vof_mesh; /* opaque, library-owned */
+
+/* Mesh description: HOST pointers, read only during vof_mesh_create. Faces are vertex loops
+ * oriented outward from their owner; cell_face entries have bit 31 set when the cell is the
+ * face's neighbour (its loop is inward for that cell); face_neigh = -1 on the boundary. */
+typedef struct {
+  int64_t n_cells, n_faces, n_verts;
+  const int64_t* cell_face_off; /* [n_cells + 1] */
+  const int32_t* cell_face;     /* [cell_face_off[n_cells]] */
+  const int64_t* face_vert_off; /* [n_faces + 1] */
+  const int32_t* face_vert;     /* [face_vert_off[n_faces]] */
+  const int32_t* face_owner;    /* [n_faces] */
+  const int32_t* face_neigh;    /* [n_faces] */
+  const double *vx, *vy, *vz;   /* [n_verts] */
+} vof_mesh_desc;
+
+typedef struct {
+  double k_l, k_v; /* thermal conductivities of liquid and vapour, W/(m K) */
+  double h_lv;     /* latent heat, J/kg */
+  double T_sat;    /* saturation temperature, K */
+} vof_props;
+
+typedef struct {
+  double alpha_eps;  /* interface cells: alpha_eps < alpha < 1 - alpha_eps (default 1e-12) */
+  double tol_alpha;  /* root accepted when |V_L(c)/V - alpha| <= tol_alpha (default 1e-12) */
+  int max_bisect;    /* bisection iteration cap (default 100) */
+  int root_mode;     /* VOF_ROOT_BISECT or VOF_ROOT_LEARNED */
+  int max_secant;    /* secant steps after the learned guess (default 2) */
+  int xf_mode;       /* VOF_XF_* (default VOF_XF_RECON) */
+  int vertex_mode;   /* 0 inverse distance to cell centroids (default), 1 plain average */
+  int group_size;    /* lanes per cell in the root search: 0 = auto, else 1, 2, 4, 8, 16 or 32 */
+} vof_options;
+
+/* Fills *o with the defaults above. */
+void vof_default_options(vof_options* o);
+
+/* Builds a mesh: validates the arrays (VOF_EMESH on any inconsistency), derives the cell
+ * tetrahedralisations, vertex->cell table and inverse-distance weights on the host, uploads
+ * them, computes geometry (face area vectors and centroids, cell volumes and centroids,
+ * tetrahedron volumes) on the device and allocates the step workspace. Synchronises the stream.
+ * *out is library-owned; release it with vof_mesh_destroy. */
+vof_status vof_mesh_create(const vof_mesh_desc* desc, void* stream, vof_mesh** out);
+vof_status vof_mesh_destroy(vof_mesh* mesh);
+
+/* Reconstruction. d_alpha: device [n_cells] liquid volume fractions. Results stay in the
+ * mesh's workspace (see vof_copy_field). With VOF_ROOT_LEARNED an MLP must have been set with
+ * vof_mlp_set_weights, else VOF_ESTATE. */
+vof_status vof_reconstruct(vof_mesh* mesh, const double* d_alpha, const vof_options* opt, void* stream);
+
+/* Phase-change source after vof_reconstruct with the same d_alpha. d_T: device [n_cells] cell
+ * temperatures; d_T_bnd: device [n_faces] temperatures read at boundary faces (virtual
+ * neighbours at the face centroid), or NULL to leave boundary faces out of the stencil.
+ * d_mdot, d_Q: device [n_cells], written everywhere (zero outside interface cells).
+ * d_totals: device [2] = {sum mdot V, sum Q V} over interface cells (pairwise tree in cell order). */
+vof_status vof_phase_change_source(vof_mesh* mesh, const double* d_alpha, const double* d_T, const double* d_T_bnd,
+                                   const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q,
+                                   double* d_totals, void* stream);
+
+/* One whole step: vof_reconstruct followed by vof_phase_change_source. */
+vof_status vof_step(vof_mesh* mesh, const double* d_alpha, const double* d_T, const double* d_T_bnd,
+                    const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q, double* d_totals,
+                    void* stream);
+
+/* The same step from HOST buffers: copies h_alpha, h_T [n_cells] (and h_T_bnd [n_faces] when
+ * non-NULL) to the device on the stream, runs vof_step, copies mdot [n_cells] into h_mdot and
+ * the totals into h_totals [2], and synchronises. Pinned host memory makes the copies
+ * asynchronous. */
+vof_status vof_step_host(vof_mesh* mesh, const double* h_alpha, const double* h_T, const double* h_T_bnd,
+                         const vof_props* props, const vof_options* opt, double* h_mdot, double* h_totals,
+                         void* stream);
+
+/* Workspace fields, copied with vof_copy_field into caller device memory (count = elements). */
+typedef enum {
+  VOF_F_IFACE_IDX = 0, /* int32 [n_iface]: interface cells in increasing cell order */
+  VOF_F_PHI_V = 1,     /* double [n_verts]: vertex field (valid on vertices of interface cells) */
+  VOF_F_ISO = 2,       /* double [n_cells]: isovalue c (interface cells) */
+  VOF_F_A_INT = 3,     /* double [n_cells] */
+  VOF_F_N_INT = 4,     /* double [n_cells][3] */
+  VOF_F_X_GAMMA = 5,   /* double [n_cells][3] */
+  VOF_F_STATUS = 6,    /* int32 [n_cells]: VOF_ST_* bits (interface and band cells) */
+  VOF_F_EVALS = 7,     /* int32 [n_cells]: FP64 cut-volume evaluations of the root search */
+  VOF_F_GRAD = 8,      /* double [n_cells][3]: modified least-squares grad T (band cells) */
+  VOF_F_GRAD_L = 9,    /* double [n_cells][3]: liquid-side gradient (interface cells) */
+  VOF_F_GRAD_V = 10,   /* double [n_cells][3]: vapour-side gradient (interface cells) */
+  VOF_F_Q_L = 11,      /* double [n_cells] */
+  VOF_F_Q_V = 12,      /* double [n_cells] */
+  VOF_F_X_F = 13,      /* double [n_faces][3]: crossing point (crossing faces next to the band) */
+  VOF_F_D_OWN = 14,    /* double [n_faces]: |x_f - x_owner| */
+  VOF_F_D_NEIGH = 15,  /* double [n_faces]: |x_f - x_neigh| */
+  VOF_F_A_INT_F = 16,  /* double [n_faces]: |A_int n_int . n_f| of the interface cell used */
+  VOF_F_FACE_STAMP = 17, /* uint32 [n_faces]: equals the step stamp on crossing faces of this step */
+  VOF_F_CELL_VOL = 18, /* double [n_cells] */
+  VOF_F_CELL_CEN = 19, /* double [n_cells][3] */
+  VOF_F_FACE_AREA = 20,/* double [n_faces][3], outward from the owner */
+  VOF_F_FACE_CEN = 21, /* double [n_faces][3] */
+  VOF_F_IFACE_STAMP = 22, /* uint32 [n_cells]: equals the step stamp on interface cells */
+  VOF_F_BAND_STAMP = 23,  /* uint32 [n_cells]: equals the step stamp on band cells */
+  VOF_F_N = 24
+} vof_field;
+
+/* Element count of a field in the current state (n_iface for the interface list). */
+vof_status vof_field_size(vof_mesh* mesh, int field, int64_t* count, int* elem_bytes);
+/* Copies a field into d_dst (device, at least count * elem_bytes bytes) on the stream; d_dst may be
+ * NULL when count is 0. */
+vof_status vof_copy_field(vof_mesh* mesh, int field, void* d_dst, int64_t count, void* stream);
+
+/* Counters of the last step, read back synchronously. */
+typedef struct {
+  int64_t step;  /* stamp of the last step (see the *_STAMP fields) */
+  int64_t n_iface, n_band, n_crossing;
+  int64_t n_degenerate, n_not_converged, n_fallback, n_singular, n_no_side, n_mlp_skipped;
+  int64_t evals_total; /* FP64 cut-volume evaluations summed over interface cells */
+  /* algorithmic work of the root search (roofline accounting): tetrahedron evaluations (sum over
+   * interface cells of evaluations x tetrahedra), tetrahedra prepared, tetrahedra cut by the final
+   * interface */
+  int64_t tet_evals, tets_prepared, tets_sectioned;
+} vof_counts;
+vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
+
+/* Mesh sizes and limits: n_cells, n_faces, n_verts, max vertices per cell, max tets per cell. */
+vof_status vof_mesh_info(const vof_mesh* mesh, int64_t* out5);
+
+/* Per-kernel device time, measured with pairs of CUDA events recorded on the launch stream
+ * around each kernel group (off by default; measurement support, not part of the method).
+ * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
+ * vof_timing_read synchronises the stream and returns, per kernel class, the summed
+ * milliseconds and the launch count since the last read (at most 8192 records are kept).
+ * Classes: 0 selection, 1 vertex field, 2 root search + geometry, 3 least squares,
+ * 4 per-side gradients + source, 5 totals, 6 learned guess. */
+vof_status vof_timing_enable(vof_mesh* mesh, int on);
+vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
+
+const char* vof_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOF_H */

@@ -1,0 +1,219 @@
+"""GB300 (sm_103a) sharp-interface VOF phase-change hot path — Python binding.
+
+Argument marshalling over the C ABI of ``libvof_gb300.so`` (include/vof.h): every step of the
+path runs in the library's CUDA kernels; PyTorch supplies device memory and the stream. If the
+library is missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvof_gb300.so")
+_LIB = None
+
+VOF_ST_DEGENERATE, VOF_ST_NOT_CONVERGED, VOF_ST_FALLBACK = 1, 2, 4
+VOF_ST_SINGULAR_LSQ, VOF_ST_NO_SIDE, VOF_ST_MLP_SKIPPED = 8, 16, 32
+XF_RECON, XF_LINEAR, XF_AS_PRINTED = 0, 1, 2
+ROOT_BISECT, ROOT_LEARNED = 0, 1
+
+FIELDS = {
+    "iface_idx": (0, np.int32, 1), "phi_v": (1, np.float64, 1), "iso": (2, np.float64, 1),
+    "A_int": (3, np.float64, 1), "n_int": (4, np.float64, 3), "x_gamma": (5, np.float64, 3),
+    "status": (6, np.int32, 1), "evals": (7, np.int32, 1), "grad": (8, np.float64, 3),
+    "grad_l": (9, np.float64, 3), "grad_v": (10, np.float64, 3), "q_l": (11, np.float64, 1),
+    "q_v": (12, np.float64, 1), "x_f": (13, np.float64, 3), "d_own": (14, np.float64, 1),
+    "d_neigh": (15, np.float64, 1), "A_int_f": (16, np.float64, 1), "face_stamp": (17, np.int32, 1),
+    "cell_vol": (18, np.float64, 1), "cell_cen": (19, np.float64, 3), "face_area": (20, np.float64, 3),
+    "face_cen": (21, np.float64, 3), "iface_stamp": (22, np.int32, 1), "band_stamp": (23, np.int32, 1),
+}
+
+
+class VofError(RuntimeError):
+    pass
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_verts", ctypes.c_int64),
+                ("cell_face_off", ctypes.c_void_p), ("cell_face", ctypes.c_void_p),
+                ("face_vert_off", ctypes.c_void_p), ("face_vert", ctypes.c_void_p),
+                ("face_owner", ctypes.c_void_p), ("face_neigh", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p)]
+
+
+class Props(ctypes.Structure):
+    _fields_ = [("k_l", ctypes.c_double), ("k_v", ctypes.c_double), ("h_lv", ctypes.c_double),
+                ("T_sat", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("alpha_eps", ctypes.c_double), ("tol_alpha", ctypes.c_double), ("max_bisect", ctypes.c_int),
+                ("root_mode", ctypes.c_int), ("max_secant", ctypes.c_int), ("xf_mode", ctypes.c_int),
+                ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int)]
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("step", "n_iface", "n_band", "n_crossing", "n_degenerate",
+                                               "n_not_converged", "n_fallback", "n_singular", "n_no_side",
+                                               "n_mlp_skipped", "evals_total", "tet_evals", "tets_prepared",
+                                               "tets_sectioned")]
+
+
+def lib():
+    """The loaded library; raises VofError when it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise VofError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, st = ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "vof_mesh_create": [vp, vp, vp], "vof_mesh_destroy": [vp], "vof_reconstruct": [vp, vp, vp, vp],
+            "vof_phase_change_source": [vp] * 10, "vof_step": [vp] * 10, "vof_step_host": [vp] * 9,
+            "vof_field_size": [vp, ctypes.c_int, vp, vp], "vof_copy_field": [vp, ctypes.c_int, vp, ctypes.c_int64, vp],
+            "vof_get_counts": [vp, vp, vp], "vof_mesh_info": [vp, vp],
+            "vof_timing_enable": [vp, ctypes.c_int], "vof_timing_read": [vp, vp, vp, ctypes.c_int, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = st
+        L.vof_last_error.restype = ctypes.c_char_p
+        L.vof_default_options.argtypes = [vp]
+        L.vof_default_options.restype = None
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise VofError(f"{what} failed with status {status}: {lib().vof_last_error().decode()}")
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().vof_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def props_of(d: dict) -> Props:
+    return Props(d["k_l"], d["k_v"], d["h_lv"], d["T_sat"])
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A mesh uploaded to the GPU (library-owned). `m` is any object with the primitive arrays
+    of the mesh format (vx, vy, vz, face_vert_off, face_vert, face_owner, face_neigh,
+    cell_face_off, cell_face)."""
+
+    def __init__(self, m, stream=None):
+        keep = [np.ascontiguousarray(a, dt) for a, dt in (
+            (m.cell_face_off, np.int64), (m.cell_face, np.int32), (m.face_vert_off, np.int64),
+            (m.face_vert, np.int32), (m.face_owner, np.int32), (m.face_neigh, np.int32),
+            (m.vx, np.float64), (m.vy, np.float64), (m.vz, np.float64))]
+        d = _Desc(len(keep[0]) - 1, len(keep[4]), len(keep[6]), *[a.ctypes.data for a in keep])
+        h = ctypes.c_void_p()
+        _check(lib().vof_mesh_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)), "vof_mesh_create")
+        self.h = h
+        info = (ctypes.c_int64 * 5)()
+        _check(lib().vof_mesh_info(h, info), "vof_mesh_info")
+        self.n_cells, self.n_faces, self.n_verts, self.max_cell_verts, self.max_cell_tets = list(info)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vof_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the hot path
+    def reconstruct(self, alpha, opt: Options | None = None, stream=None):
+        """vof_reconstruct: alpha is a CUDA float64 tensor [n_cells]."""
+        o = opt or default_options()
+        _check(lib().vof_reconstruct(self.h, _ptr(alpha), ctypes.byref(o), _stream(stream)), "vof_reconstruct")
+
+    def phase_change_source(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: Options | None = None,
+                            stream=None):
+        """vof_phase_change_source: all tensors CUDA float64 (T_bnd may be None)."""
+        o = opt or default_options()
+        p = props_of(props)
+        _check(lib().vof_phase_change_source(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p),
+                                             ctypes.byref(o), _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)),
+               "vof_phase_change_source")
+
+    def step(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: Options | None = None, stream=None):
+        """vof_step: reconstruct + phase-change source in one call."""
+        o = opt or default_options()
+        p = props_of(props)
+        _check(lib().vof_step(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p), ctypes.byref(o),
+                              _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)), "vof_step")
+
+    def step_host(self, h_alpha, h_T, h_T_bnd, props: dict, h_mdot, h_totals, opt: Options | None = None,
+                  stream=None):
+        """vof_step_host: host tensors (pinned for asynchronous copies); synchronises."""
+        o = opt or default_options()
+        p = props_of(props)
+        _check(lib().vof_step_host(self.h, _ptr(h_alpha), _ptr(h_T), _ptr(h_T_bnd), ctypes.byref(p), ctypes.byref(o),
+                                   _ptr(h_mdot), _ptr(h_totals), _stream(stream)), "vof_step_host")
+
+    # ---- results
+    def field(self, name: str, stream=None):
+        """A copy of a workspace field as a CUDA tensor."""
+        import torch
+        fid, dt, width = FIELDS[name]
+        cnt, eb = ctypes.c_int64(), ctypes.c_int()
+        _check(lib().vof_field_size(self.h, fid, ctypes.byref(cnt), ctypes.byref(eb)), "vof_field_size")
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[dt]
+        out = torch.empty(cnt.value, dtype=tdt, device="cuda")
+        _check(lib().vof_copy_field(self.h, fid, _ptr(out), cnt.value, _stream(stream)), "vof_copy_field")
+        return out.view(-1, width) if width > 1 else out
+
+    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp")
+
+    def timing_enable(self, on: bool = True):
+        _check(lib().vof_timing_enable(self.h, int(on)), "vof_timing_enable")
+
+    def timing_read(self, stream=None) -> dict:
+        """{kernel class: (milliseconds summed, launches)} since the last read (synchronises)."""
+        n = len(self.KERNEL_CLASSES)
+        ms, nl = (ctypes.c_double * n)(), (ctypes.c_int64 * n)()
+        _check(lib().vof_timing_read(self.h, ms, nl, n, _stream(stream)), "vof_timing_read")
+        return {k: (ms[i], nl[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    # FP64 flops per unit of the root search's algorithmic work (see the kernel header):
+    # one tetrahedron evaluation = x = ref - c, three FMAs, one add (8 flops); preparing one
+    # tetrahedron = 6 differences, 12 products, 3 divisions, 3 sums (24); cutting one in the
+    # final geometry = 3-4 edge cuts, cross products, norms and moments (60); 2 per evaluation.
+    FLOPS_TET_EVAL, FLOPS_TET_PREP, FLOPS_TET_SECTION, FLOPS_EVAL = 8, 24, 60, 2
+
+    def root_flops(self, counts: dict) -> int:
+        """Algorithmic FP64 flops of the root-search launches summed in `counts`."""
+        return (self.FLOPS_TET_EVAL * counts["tet_evals"] + self.FLOPS_TET_PREP * counts["tets_prepared"]
+                + self.FLOPS_TET_SECTION * counts["tets_sectioned"] + self.FLOPS_EVAL * counts["evals_total"])
+
+    def counts(self, stream=None) -> dict:
+        c = Counts()
+        _check(lib().vof_get_counts(self.h, ctypes.byref(c), _stream(stream)), "vof_get_counts")
+        return {n: getattr(c, n) for n, _ in Counts._fields_}

@@ -1,0 +1,162 @@
+// C ABI: field access, counters and the host-buffer step.
+#include <cstring>
+
+#include "vof_internal.cuh"
+
+using namespace vof;
+
+namespace {
+
+struct FieldDesc {
+  const void* ptr;
+  int64_t count;
+  int bytes;
+};
+
+FieldDesc field_of(vof_mesh* m, int f, int64_t n_iface) {
+  const Workspace& W = m->ws;
+  const MeshView& M = m->view;
+  const int64_t nc = m->n_cells, nf = m->n_faces, nv = m->n_verts;
+  switch (f) {
+    case VOF_F_IFACE_IDX: return {W.iface_idx, n_iface, 4};
+    case VOF_F_PHI_V: return {W.phi_v, nv, 8};
+    case VOF_F_ISO: return {W.iso, nc, 8};
+    case VOF_F_A_INT: return {W.A_int, nc, 8};
+    case VOF_F_N_INT: return {W.n_int, 3 * nc, 8};
+    case VOF_F_X_GAMMA: return {W.x_gamma, 3 * nc, 8};
+    case VOF_F_STATUS: return {W.status, nc, 4};
+    case VOF_F_EVALS: return {W.evals, nc, 4};
+    case VOF_F_GRAD: return {W.grad, 3 * nc, 8};
+    case VOF_F_GRAD_L: return {W.grad_l, 3 * nc, 8};
+    case VOF_F_GRAD_V: return {W.grad_v, 3 * nc, 8};
+    case VOF_F_Q_L: return {W.q_l, nc, 8};
+    case VOF_F_Q_V: return {W.q_v, nc, 8};
+    case VOF_F_X_F: return {W.x_f, 3 * nf, 8};
+    case VOF_F_D_OWN: return {W.d_own, nf, 8};
+    case VOF_F_D_NEIGH: return {W.d_neigh, nf, 8};
+    case VOF_F_A_INT_F: return {W.A_int_f, nf, 8};
+    case VOF_F_FACE_STAMP: return {W.face_stamp, nf, 4};
+    case VOF_F_CELL_VOL: return {M.cell_vol, nc, 8};
+    case VOF_F_CELL_CEN: return {M.cell_cen, 3 * nc, 8};
+    case VOF_F_FACE_AREA: return {M.face_area, 3 * nf, 8};
+    case VOF_F_FACE_CEN: return {M.face_cen, 3 * nf, 8};
+    case VOF_F_IFACE_STAMP: return {W.iface_stamp, nc, 4};
+    case VOF_F_BAND_STAMP: return {W.band_stamp, nc, 4};
+    default: return {nullptr, 0, 0};
+  }
+}
+
+vof_status read_counters(vof_mesh* m, Counters* c, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(c, m->ws.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "counter readback");
+  return VOF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vof_status vof_field_size(vof_mesh* m, int field, int64_t* count, int* elem_bytes) {
+  if (!m || !count || !elem_bytes || field < 0 || field >= VOF_F_N) { set_error("bad argument"); return VOF_EINVAL; }
+  int64_t n_iface = 0;
+  if (field == VOF_F_IFACE_IDX) {
+    Counters c;
+    if (vof_status st = read_counters(m, &c, 0)) return st;
+    n_iface = c.n_iface;
+  }
+  const FieldDesc d = field_of(m, field, n_iface);
+  *count = d.count;
+  *elem_bytes = d.bytes;
+  return VOF_OK;
+}
+
+vof_status vof_copy_field(vof_mesh* m, int field, void* d_dst, int64_t count, void* stream) {
+  if (!m || field < 0 || field >= VOF_F_N || count < 0) { set_error("bad argument"); return VOF_EINVAL; }
+  const FieldDesc d = field_of(m, field, m->n_cells);
+  if (count > d.count) { set_error("count exceeds the field size"); return VOF_EINVAL; }
+  if (count == 0) return VOF_OK;
+  if (!d_dst) { set_error("null destination"); return VOF_EINVAL; }
+  cudaError_t e = cudaMemcpyAsync(d_dst, d.ptr, (size_t)count * d.bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vof_copy_field");
+  return VOF_OK;
+}
+
+vof_status vof_get_counts(vof_mesh* m, vof_counts* out, void* stream) {
+  if (!m || !out) { set_error("null argument"); return VOF_EINVAL; }
+  Counters c;
+  if (vof_status st = read_counters(m, &c, (cudaStream_t)stream)) return st;
+  out->step = c.step;
+  out->n_iface = c.n_iface;
+  out->n_band = c.n_band;
+  out->n_crossing = c.n_crossing;
+  out->n_degenerate = c.n_degenerate;
+  out->n_not_converged = c.n_not_converged;
+  out->n_fallback = c.n_fallback;
+  out->n_singular = c.n_singular;
+  out->n_no_side = c.n_no_side;
+  out->n_mlp_skipped = c.n_mlp_skipped;
+  out->evals_total = c.evals_total;
+  out->tet_evals = c.tet_evals;
+  out->tets_prepared = c.tets_prepared;
+  out->tets_sectioned = c.tets_sectioned;
+  return VOF_OK;
+}
+
+vof_status vof_timing_enable(vof_mesh* m, int on) {
+  if (!m) { set_error("null argument"); return VOF_EINVAL; }
+  Timing& t = m->timing;
+  if (on && t.ev.empty()) {
+    t.cap = 8192;
+    t.ev.resize(2 * (size_t)t.cap);
+    t.cls.resize(t.cap);
+    for (auto& e : t.ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+    }
+  }
+  t.on = on != 0;
+  t.used = 0;
+  return VOF_OK;
+}
+
+vof_status vof_timing_read(vof_mesh* m, double* ms, int64_t* launches, int n, void* stream) {
+  if (!m || !ms || !launches || n < 1) { set_error("bad argument"); return VOF_EINVAL; }
+  Timing& t = m->timing;
+  for (int k = 0; k < n; ++k) { ms[k] = 0; launches[k] = 0; }
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vof_timing_read");
+  for (int i = 0; i < t.used; ++i) {
+    if (t.cls[i] >= n) continue;
+    float f = 0;
+    e = cudaEventElapsedTime(&f, t.ev[2 * i], t.ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ms[t.cls[i]] += f;
+    launches[t.cls[i]] += 1;
+  }
+  t.used = 0;
+  return VOF_OK;
+}
+
+vof_status vof_step_host(vof_mesh* m, const double* h_alpha, const double* h_T, const double* h_T_bnd,
+                         const vof_props* props, const vof_options* opt, double* h_mdot, double* h_totals,
+                         void* stream) {
+  if (!m || !h_alpha || !h_T || !h_mdot || !h_totals) { set_error("null argument"); return VOF_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& W = m->ws;
+  const size_t nc = (size_t)m->n_cells, nf = (size_t)m->n_faces;
+  cudaError_t e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && h_T_bnd) e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  vof_status st = vof_step(m, W.io_alpha, W.io_T, h_T_bnd ? W.io_Tb : nullptr, props, opt, W.io_mdot, W.io_Q,
+                           W.io_totals, stream);
+  if (st) return st;
+  e = cudaMemcpyAsync(h_mdot, W.io_mdot, nc * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_totals, W.io_totals, 2 * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  return VOF_OK;
+}
+
+}  // extern "C"

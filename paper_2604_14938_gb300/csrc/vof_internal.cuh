@@ -1,0 +1,145 @@
+// Library-internal declarations shared by the CUDA sources of libvof_gb300.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "vof.h"
+
+namespace vof {
+
+// Device counters of one step; reset by the step's first kernel.
+struct Counters {
+  uint32_t step;        // incremented on the device every step (membership stamps)
+  uint32_t reduce_done; // blocks finished in the totals reduction
+  int64_t n_iface, n_band, n_crossing;
+  int64_t n_uvert;  // distinct vertices of interface cells
+  int64_t n_degenerate, n_not_converged, n_fallback, n_singular, n_no_side, n_mlp_skipped;
+  int64_t evals_total;
+  // algorithmic work of the root search: tetrahedron evaluations (sum of evals x tets per cell),
+  // tetrahedra prepared, tetrahedra cut in the final geometry
+  int64_t tet_evals, tets_prepared, tets_sectioned;
+};
+
+// Everything a step kernel reads or writes, by value (device pointers).
+struct MeshView {
+  int64_t n_cells, n_faces, n_verts;
+  const int64_t* cell_face_off;
+  const int32_t* cell_face;
+  const int32_t* face_owner;
+  const int32_t* face_neigh;
+  const double *vx, *vy, *vz;
+  const int64_t* cell_vert_off;
+  const int32_t* cell_vert;  // sorted unique vertex ids per cell; local 0 is the apex
+  const int64_t* cell_tet_off;
+  const uint32_t* cell_tet;  // three local vertex indices (8 bits each) of the base triangle
+  const double* tet_vol;     // positive volumes, apex = local vertex 0
+  const int64_t* vert_cell_off;
+  const int32_t* vert_cell;
+  const double* vert_w;      // inverse-distance weights, normalised per vertex
+  const double* cell_vol;
+  const double* cell_cen;    // [n][3]
+  const double* face_area;   // [n][3] outward from owner
+  const double* face_cen;    // [n][3]
+};
+
+struct Workspace {
+  Counters* counters;
+  int32_t* iface_idx;      // [n_cells]
+  uint32_t* iface_stamp;   // [n_cells]
+  uint32_t* band_stamp;    // [n_cells]
+  uint32_t* vert_stamp;    // [n_verts]
+  uint32_t* face_stamp;    // [n_faces]
+  int64_t* blk_count;      // [n_sel_blocks]
+  int64_t* blk_off;        // [n_sel_blocks]
+  int64_t* blk_count2;     // [n_sel_blocks + n_vert_blocks] band cells, then vertices
+  int64_t* blk_off2;
+  int32_t* band_idx;       // [n_cells] band cells in increasing order
+  int32_t* vert_idx;       // [n_verts] vertices of interface cells in increasing order
+  double* phi_v;           // [n_verts]
+  double* iso;             // [n_cells]
+  double* A_int;           // [n_cells]
+  double* n_int;           // [n_cells][3]
+  double* x_gamma;         // [n_cells][3]
+  int32_t* status;         // [n_cells]
+  int32_t* evals;          // [n_cells]
+  double* grad;            // [n_cells][3]
+  double* grad_l;          // [n_cells][3]
+  double* grad_v;          // [n_cells][3]
+  double* q_l;             // [n_cells]
+  double* q_v;             // [n_cells]
+  double* x_f;             // [n_faces][3]
+  double* d_own;           // [n_faces]
+  double* d_neigh;         // [n_faces]
+  double* A_int_f;         // [n_faces]
+  double* mdotV;           // [n_cells] in interface-list order
+  double* QV;              // [n_cells]
+  double* partial;         // [4][kMaxPartials]: two ping-pong buffers per total
+  float* mlp_out;          // [n_cells] learned guesses (normalised position in the range)
+  // device staging for the host-buffer step
+  double *io_alpha, *io_T, *io_Tb, *io_mdot, *io_Q, *io_totals;
+};
+
+constexpr int kSelTile = 2048;      // cells per selection block
+constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
+constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
+
+struct StepArgs {
+  const double* alpha;
+  const double* T;
+  const double* T_bnd;
+  double* mdot;
+  double* Q;
+  double* totals;
+  vof_props props;
+  vof_options opt;
+};
+
+}  // namespace vof
+
+namespace vof {
+// Optional per-kernel device timing: pairs of CUDA events recorded on the launch stream.
+enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_N };
+struct Timing {
+  bool on = false;
+  int cap = 0, used = 0;
+  std::vector<cudaEvent_t> ev;  // 2 per record
+  std::vector<int> cls;
+  void start(int k, cudaStream_t s) {
+    if (!on || used >= cap) return;
+    cls[used] = k;
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void stop(cudaStream_t s) {
+    if (!on || used >= cap) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+  }
+};
+}  // namespace vof
+
+struct vof_mesh {
+  int64_t n_cells = 0, n_faces = 0, n_verts = 0;
+  int max_cv = 0, max_ct = 0;
+  double mean_ct = 0;  // tetrahedra per cell, mean
+  int n_sel_blocks = 0, n_vert_blocks = 0;
+  int num_sms = 0;
+  vof::MeshView view{};
+  vof::Workspace ws{};
+  std::vector<void*> allocs;
+  // learned isovalue guess (BF16 weights, device), see vof_mlp.cu
+  void* mlp = nullptr;
+  bool recon_done = false;
+  vof::Timing timing;
+};
+
+namespace vof {
+void set_error(const std::string& msg);
+vof_status cuda_fail(cudaError_t e, const char* what);
+
+// step kernels (vof_step.cu)
+vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s);
+vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s);
+}  // namespace vof

@@ -1,0 +1,879 @@
+// Step kernels of the hot path: interface selection, vertex field, isovalue root search with the
+// interface geometry, interface-modified least squares, per-side gradients and phase-change
+// source, deterministic totals.
+//
+// Cut volume (paper Sec. 2.1, Eq. edge_intersection; reading: tetrahedralisation by the cell's
+// own vertices, phi linear per tetrahedron): for a tetrahedron with corner values p_i and k corners
+// at or above c the wet fraction is
+//   k = 1 (wet a):         (p_a - c)^3 / prod_{j != a} (p_a - p_j)
+//   k = 3 (dry d):     1 - (c - p_d)^3 / prod_{j != d} (p_j - p_d)
+//   k = 2 (wet a, b):  [wa^2 wb^2 + (uc + ud) wa wb (wa + wb) + uc ud (wa^2 + wa wb + wb^2)]
+//                       / [(p_a - p_c)(p_a - p_d)(p_b - p_c)(p_b - p_d)]
+// with w = p - c on wet corners and u = c - p on dry corners: every denominator is a product of
+// (wet - dry) differences, so no term is singular and nothing cancels.
+#include <cstring>
+
+#include "vof_internal.cuh"
+
+namespace vof {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint64_t okey(double x) {
+  // order-preserving map of a double onto uint64 (-0.0 folded onto +0.0), integer operations
+  // only, so that the wet test phi >= c stays off the FP64 pipe
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  b = b == 0x8000000000000000ull ? 0ull : b;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <int G>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ double group_min(double v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(mask, v, o));
+  return v;
+}
+template <int G>
+__device__ __forceinline__ double group_max(double v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double pick(int i, double a, double b, double c, double d) {
+  return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
+}
+
+struct Vec3 {
+  double x, y, z;
+};
+__device__ __forceinline__ Vec3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ Vec3 operator-(Vec3 a, Vec3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ Vec3 operator+(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ Vec3 operator*(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ Vec3 cross(Vec3 a, Vec3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(Vec3 a) { return sqrt(dot(a, a)); }
+__device__ __forceinline__ Vec3 pickv(int i, Vec3 a, Vec3 b, Vec3 c, Vec3 d) {
+  return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
+}
+// point where phi = c on the edge from corner i (value pi) to corner j (value pj)
+__device__ __forceinline__ Vec3 cutp(Vec3 Pi, double pi, Vec3 Pj, double pj, double c) {
+  return Pi + (Pj - Pi) * ((pi - c) / (pi - pj));
+}
+
+// Section of one tetrahedron by phi = c: vector area (oriented from wet to dry), area, area moment.
+__device__ void tet_section(Vec3 P0, Vec3 P1, Vec3 P2, Vec3 P3, double p0, double p1, double p2, double p3, unsigned m,
+                            double c, Vec3& A, double& ar, Vec3& mom) {
+  const int k = __popc(m);
+  A = v3(0, 0, 0);
+  ar = 0;
+  mom = v3(0, 0, 0);
+  if (k == 0 || k == 4) return;
+  if (k == 1 || k == 3) {
+    const int i = k == 1 ? __ffs(m) - 1 : __ffs(~m & 15u) - 1;  // the lone corner
+    const Vec3 X = pickv(i, P0, P1, P2, P3);
+    const double x = pick(i, p0, p1, p2, p3);
+    Vec3 q[3];
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j == i) continue;
+      q[n++] = cutp(X, x, pickv(j, P0, P1, P2, P3), pick(j, p0, p1, p2, p3), c);
+    }
+    A = cross(q[1] - q[0], q[2] - q[0]) * 0.5;
+    const Vec3 g = (q[0] + q[1] + q[2]) * (1.0 / 3.0);
+    // wet -> dry: away from a lone wet corner, towards a lone dry corner
+    const double s = dot(A, g - X);
+    if ((k == 1 && s < 0) || (k == 3 && s > 0)) A = A * -1.0;
+    ar = norm(A);
+    mom = g * ar;
+    return;
+  }
+  const unsigned dm = ~m & 15u;
+  const int ia = __ffs(m) - 1, ib = 31 - __clz(m), ic = __ffs(dm) - 1, id = 31 - __clz(dm);
+  const Vec3 Pa = pickv(ia, P0, P1, P2, P3), Pb = pickv(ib, P0, P1, P2, P3);
+  const Vec3 Pc = pickv(ic, P0, P1, P2, P3), Pd = pickv(id, P0, P1, P2, P3);
+  const double pa = pick(ia, p0, p1, p2, p3), pb = pick(ib, p0, p1, p2, p3);
+  const double pc = pick(ic, p0, p1, p2, p3), pd = pick(id, p0, p1, p2, p3);
+  const Vec3 q1 = cutp(Pa, pa, Pc, pc, c), q2 = cutp(Pa, pa, Pd, pd, c);
+  const Vec3 q3 = cutp(Pb, pb, Pd, pd, c), q4 = cutp(Pb, pb, Pc, pc, c);
+  A = cross(q3 - q1, q4 - q2) * 0.5;
+  if (dot(A, (Pc + Pd) - (Pa + Pb)) < 0) A = A * -1.0;
+  const double a1 = 0.5 * norm(cross(q2 - q1, q3 - q1)), a2 = 0.5 * norm(cross(q3 - q1, q4 - q1));
+  ar = norm(A);
+  if (a1 + a2 > 0) {
+    const Vec3 g = ((q1 + q2 + q3) * (a1 / 3.0) + (q1 + q3 + q4) * (a2 / 3.0)) * (1.0 / (a1 + a2));
+    mom = g * ar;
+  }
+}
+
+__global__ void k_begin(Counters* cn) {
+  cn->step += 1;
+  cn->reduce_done = 0;
+  cn->n_iface = cn->n_band = cn->n_crossing = cn->n_uvert = 0;
+  cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
+  cn->evals_total = 0;
+  cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = 0;
+}
+
+__device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
+
+// ---- selection: per-tile counts, scan, order-preserving scatter -------------------------------
+__global__ void k_sel_count(int64_t nc, const double* alpha, double eps, int64_t* blk_count) {
+  const int64_t base = (int64_t)blockIdx.x * kSelTile;
+  int cnt = 0;
+  for (int64_t c = base + threadIdx.x; c < min(nc, base + kSelTile); c += blockDim.x) cnt += is_iface(alpha[c], eps);
+  __shared__ int s[kThreads / 32];
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += s[w];
+    blk_count[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sel_scan(int nb, const int64_t* cnt, int64_t* off, Counters* cn) {
+  __shared__ int64_t s[1024];
+  int64_t carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int64_t v = i < nb ? cnt[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) off[i] = carry + s[threadIdx.x] - v;
+    carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cn->n_iface = carry;
+}
+
+__global__ void k_sel_scatter(MeshView M, const double* alpha, double eps, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t base = (int64_t)blockIdx.x * kSelTile;
+  const int64_t end = min(M.n_cells, base + kSelTile);
+  int64_t pos = W.blk_off[blockIdx.x];
+  __shared__ int wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t r = base; r < end; r += blockDim.x) {
+    const int64_t c = r + threadIdx.x;
+    const bool f = c < end && is_iface(alpha[c], eps);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      before += w < wid ? wsum[w] : 0;
+      total += wsum[w];
+    }
+    if (f) {
+      const int64_t p = pos + before + __popc(bal & ((1u << lane) - 1));
+      W.iface_idx[p] = (int32_t)c;
+      W.iface_stamp[c] = step;
+    }
+    pos += total;
+    __syncthreads();
+  }
+}
+
+// Band and vertex stamps of the interface cells: 8 lanes per cell over its faces and vertices.
+__global__ void k_mark(MeshView M, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t n = W.counters->n_iface;
+  const int lane = threadIdx.x & 7;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / 8);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 8) + threadIdx.x / 8; i < n; i += groups) {
+    const int32_t c = W.iface_idx[i];
+    if (lane == 0) atomicMax(&W.band_stamp[c], step);
+    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += 8) {
+      const int32_t fc = M.cell_face[k] & 0x7fffffff;
+      const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
+      if (q >= 0) atomicMax(&W.band_stamp[q], step);
+    }
+    for (int64_t k = M.cell_vert_off[c] + lane; k < M.cell_vert_off[c + 1]; k += 8)
+      atomicMax(&W.vert_stamp[M.cell_vert[k]], step);
+  }
+}
+
+// ---- band cells and interface vertices: the same count / scan / scatter over the stamps -------
+// Blocks [0, nbc) cover cells (band stamp), blocks [nbc, nbc + nbv) cover vertices.
+__global__ void k_bv_count(int64_t nc, int64_t nv, int nbc, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const bool cells = blockIdx.x < (unsigned)nbc;
+  const int64_t base = (int64_t)(cells ? blockIdx.x : blockIdx.x - nbc) * kSelTile;
+  const int64_t n = cells ? nc : nv;
+  const uint32_t* st = cells ? W.band_stamp : W.vert_stamp;
+  int cnt = 0;
+  for (int64_t i = base + threadIdx.x; i < min(n, base + kSelTile); i += blockDim.x) cnt += st[i] == step;
+  __shared__ int s[kThreads / 32];
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += s[w];
+    W.blk_count2[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_bv_scan(int nbc, int nbv, Workspace W) {
+  __shared__ int64_t s[1024];
+  for (int seg = 0; seg < 2; ++seg) {
+    const int off = seg ? nbc : 0, nb = seg ? nbv : nbc;
+    int64_t carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+      const int i = base + threadIdx.x;
+      const int64_t v = i < nb ? W.blk_count2[off + i] : 0;
+      s[threadIdx.x] = v;
+      __syncthreads();
+      for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+      }
+      if (i < nb) W.blk_off2[off + i] = carry + s[threadIdx.x] - v;
+      carry += s[1023];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (seg) W.counters->n_uvert = carry;
+      else W.counters->n_band = carry;
+    }
+  }
+}
+
+__global__ void k_bv_scatter(int64_t nc, int64_t nv, int nbc, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const bool cells = blockIdx.x < (unsigned)nbc;
+  const int64_t base = (int64_t)(cells ? blockIdx.x : blockIdx.x - nbc) * kSelTile;
+  const int64_t n = cells ? nc : nv;
+  const int64_t end = min(n, base + kSelTile);
+  const uint32_t* st = cells ? W.band_stamp : W.vert_stamp;
+  int32_t* out = cells ? W.band_idx : W.vert_idx;
+  int64_t pos = W.blk_off2[blockIdx.x];
+  __shared__ int wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t r = base; r < end; r += blockDim.x) {
+    const int64_t i = r + threadIdx.x;
+    const bool f = i < end && st[i] == step;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      before += w < wid ? wsum[w] : 0;
+      total += wsum[w];
+    }
+    if (f) out[pos + before + __popc(bal & ((1u << lane) - 1))] = (int32_t)i;
+    pos += total;
+    __syncthreads();
+  }
+}
+
+// ---- vertex field (R1) --------------------------------------------------------------------------
+__global__ void k_vertex(MeshView M, const double* alpha, int mode, Workspace W) {
+  const int64_t n = W.counters->n_uvert;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = W.vert_idx[j];
+    const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
+    double s = 0;
+    if (mode == 0) {
+      for (int64_t k = k0; k < k1; ++k) s = fma(M.vert_w[k], alpha[M.vert_cell[k]], s);
+    } else {
+      for (int64_t k = k0; k < k1; ++k) s += alpha[M.vert_cell[k]];
+      s /= (double)(k1 - k0);
+    }
+    W.phi_v[v] = s;
+  }
+}
+
+// ---- isovalue root search + interface geometry (R2, R3) ------------------------------------------
+// Once per cell and step every tetrahedron's corner values are sorted (s0 >= s1 >= s2 >= s3) and
+// its wet volume is written, for each number k of corners at or above c, as a cubic in a local
+// variable x = ref_k - c:
+//   k = 1: x = s0 - c,  V x^3 / (d01 d02 d03)
+//   k = 2: x = s1 - c,  V [a^2 e f + 3 a e f x + 3 e f x^2 - (a + e + f) x^3] / [e f (a + e)(a + f)]
+//          with a = s0 - s1, e = s1 - s2, f = s1 - s3 (the expansion of the bracket in the header)
+//   k = 3: x = s3 - c,  V + V x^3 / (d03 d13 d23)
+//   k = 0: 0, k = 4: V
+// so an evaluation is one integer classification, selects, and the same three FMAs (Horner) in
+// every lane: no division and no divergent FP64 code. Every term is bounded by V.
+struct TetRow {
+  double s0, s1, s2, s3;      // corner values, descending
+  double a2, b2, c2, d2;      // k = 2 cubic (times V)
+  double d1, d3, v;           // k = 1 and k = 3 cubic coefficients, V
+};
+
+__device__ __forceinline__ void cswap(uint64_t& ka, double& va, uint64_t& kb, double& vb) {
+  // descending order by key
+  const bool sw = ka < kb;
+  const uint64_t tk = sw ? kb : ka;
+  kb = sw ? ka : kb;
+  ka = tk;
+  const double tv = sw ? vb : va;
+  vb = sw ? va : vb;
+  va = tv;
+}
+
+__device__ __forceinline__ TetRow tet_prepare(double p0, double p1, double p2, double p3, double vt) {
+  uint64_t k0 = okey(p0), k1 = okey(p1), k2 = okey(p2), k3 = okey(p3);
+  cswap(k0, p0, k1, p1);
+  cswap(k2, p2, k3, p3);
+  cswap(k0, p0, k2, p2);
+  cswap(k1, p1, k3, p3);
+  cswap(k1, p1, k2, p2);
+  const double d01 = p0 - p1, d02 = p0 - p2, d03 = p0 - p3, d12 = p1 - p2, d13 = p1 - p3, d23 = p2 - p3;
+  TetRow r;
+  r.s0 = p0; r.s1 = p1; r.s2 = p2; r.s3 = p3;
+  r.v = vt;
+  // a zero denominator means the case cannot occur (its interval is empty)
+  const double P1 = d01 * (d02 * d03), P3 = d03 * (d13 * d23), K = d02 * d03, EF = d12 * d13;
+  r.d1 = P1 > 0 ? vt / P1 : 0.0;
+  r.d3 = P3 > 0 ? vt / P3 : 0.0;
+  if (K > 0 && EF > 0) {
+    const double vk = vt / K;
+    r.a2 = vk * (d01 * d01);
+    r.b2 = 3.0 * vk * d01;
+    r.c2 = 3.0 * vk;
+    r.d2 = -(vk / EF) * (d01 + d12 + d13);
+  } else {
+    r.a2 = r.b2 = r.c2 = r.d2 = 0.0;
+  }
+  return r;
+}
+
+// Wet volume of a prepared tetrahedron at c (kc = okey(c)).
+__device__ __forceinline__ double tet_wet_volume(const TetRow& r, uint64_t kc, double c) {
+  const int k = (okey(r.s0) >= kc) + (okey(r.s1) >= kc) + (okey(r.s2) >= kc) + (okey(r.s3) >= kc);
+  const double ref = k == 1 ? r.s0 : (k == 2 ? r.s1 : r.s3);
+  const double A = k == 2 ? r.a2 : (k >= 3 ? r.v : 0.0);
+  const double B = k == 2 ? r.b2 : 0.0;
+  const double C = k == 2 ? r.c2 : 0.0;
+  const double D = k == 1 ? r.d1 : (k == 2 ? r.d2 : (k == 3 ? r.d3 : 0.0));
+  const double x = ref - c;
+  return fma(fma(fma(D, x, C), x, B), x, A);
+}
+
+template <int G>
+__device__ __forceinline__ double liquid_volume(const TetRow* rows, int nt, int lane, unsigned mask, double c) {
+  const uint64_t kc = okey(c);
+  double part = 0;
+  for (int t = lane; t < nt; t += G) part += tet_wet_volume(rows[t], kc, c);
+  return group_sum<G>(part, mask);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
+                                                   int max_ct, int learned) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int kGroups = blockDim.x / G;
+  const int gib = threadIdx.x / G;  // group in block
+  const int lane = threadIdx.x % G;
+  const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  TetRow* rows = reinterpret_cast<TetRow*>(smem) + (size_t)gib * max_ct;
+  const int64_t n_iface = W.counters->n_iface;
+  const int64_t n_groups = (int64_t)gridDim.x * kGroups;
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, sect_acc = 0;
+  // cells interleaved over blocks first, so that a short list still spreads over every SM
+  for (int64_t i = (int64_t)gib * gridDim.x + blockIdx.x; i < n_iface; i += n_groups) {
+    const int32_t cell = W.iface_idx[i];
+    const int64_t v0 = M.cell_vert_off[cell];
+    const int nv = (int)(M.cell_vert_off[cell + 1] - v0);
+    const int64_t t0 = M.cell_tet_off[cell];
+    const int nt = (int)(M.cell_tet_off[cell + 1] - t0);
+    const int32_t* cv = M.cell_vert + v0;
+    double lo = 1e300, hi = -1e300;
+    for (int j = lane; j < nv; j += G) {
+      const double p = W.phi_v[cv[j]];
+      lo = fmin(lo, p);
+      hi = fmax(hi, p);
+    }
+    lo = group_min<G>(lo, mask);
+    hi = group_max<G>(hi, mask);
+    const double p_apex = W.phi_v[cv[0]];
+    for (int t = lane; t < nt; t += G) {
+      const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+      rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]], W.phi_v[cv[(pk >> 16) & 255]],
+                            __ldg(M.tet_vol + t0 + t));
+    }
+    __syncwarp(mask);
+    const double a = alpha[cell];
+    const double V = M.cell_vol[cell];
+    const double invV = 1.0 / V;
+    int status = 0, evals = 0;
+    double c_best;
+    if (hi - lo < 1e-14) {
+      status = VOF_ST_DEGENERATE;
+      c_best = lo;
+    } else {
+      // f(lo) = 1 - alpha (everything wet), f(hi) = -alpha
+      double f_best = fmin(1.0 - a, a);
+      c_best = (1.0 - a) <= a ? lo : hi;
+      double L = lo, H = hi;
+      bool done = false;
+      if (learned) {
+        // learned guess (normalised position in the range) + secant steps, then bracketed bisection
+        const float t = W.mlp_out[i];
+        if (t >= 0.0f) {
+          double c1 = lo + (double)t * (hi - lo);
+          c1 = fmin(fmax(c1, lo), hi);
+          double f1 = liquid_volume<G>(rows, nt, lane, mask, c1) * invV - a;
+          ++evals;
+          if (fabs(f1) < f_best) { f_best = fabs(f1); c_best = c1; }
+          if (f1 > 0) L = c1; else H = c1;
+          if (fabs(f1) <= opt.tol_alpha) done = true;
+          // second point: a small step towards the root inside the bracket
+          double c0 = c1, f0 = f1;
+          if (!done && opt.max_secant > 0) {
+            const double step = 1e-3 * (hi - lo);
+            double c2 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+            double f2 = liquid_volume<G>(rows, nt, lane, mask, c2) * invV - a;
+            ++evals;
+            if (fabs(f2) < f_best) { f_best = fabs(f2); c_best = c2; }
+            if (f2 > 0) L = fmax(L, c2); else H = fmin(H, c2);
+            if (fabs(f2) <= opt.tol_alpha) done = true;
+            c0 = c2; f0 = f2;
+            for (int s = 0; s < opt.max_secant && !done; ++s) {
+              if (f0 == f1) break;
+              double c3 = c0 - f0 * (c0 - c1) / (f0 - f1);
+              if (!(c3 > L && c3 < H)) c3 = 0.5 * (L + H);
+              const double f3 = liquid_volume<G>(rows, nt, lane, mask, c3) * invV - a;
+              ++evals;
+              if (fabs(f3) < f_best) { f_best = fabs(f3); c_best = c3; }
+              if (f3 > 0) L = fmax(L, c3); else H = fmin(H, c3);
+              if (fabs(f3) <= opt.tol_alpha) done = true;
+              c1 = c0; f1 = f0; c0 = c3; f0 = f3;
+            }
+          }
+          if (!done) status |= VOF_ST_FALLBACK;
+        } else {
+          status |= VOF_ST_MLP_SKIPPED;
+        }
+      }
+      for (int it = 0; it < opt.max_bisect && !done; ++it) {
+        const double mid = 0.5 * (L + H);
+        const double f = liquid_volume<G>(rows, nt, lane, mask, mid) * invV - a;
+        ++evals;
+        if (fabs(f) < f_best) { f_best = fabs(f); c_best = mid; }
+        if (fabs(f) <= opt.tol_alpha) break;
+        if (f > 0) L = mid; else H = mid;
+        const double scale = fmax(fabs(L), fabs(H));
+        if (H - L <= 4.0 * (nextafter(scale, 2.0 * scale + 1.0) - scale)) break;
+      }
+      if (f_best > opt.tol_alpha) status |= VOF_ST_NOT_CONVERGED;
+    }
+    // interface geometry at c_best
+    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
+    double area = 0;
+    if (!(status & VOF_ST_DEGENERATE)) {
+      const uint64_t kc = okey(c_best);
+      const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
+      for (int t = lane; t < nt; t += G) {
+        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+        const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
+        const double q1 = W.phi_v[g1], q2 = W.phi_v[g2], q3 = W.phi_v[g3];
+        const unsigned m = (unsigned)(okey(p_apex) >= kc) | ((unsigned)(okey(q1) >= kc) << 1) |
+                           ((unsigned)(okey(q2) >= kc) << 2) | ((unsigned)(okey(q3) >= kc) << 3);
+        if (m == 0 || m == 15u) continue;
+        ++sect_acc;
+        const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
+        const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
+        const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
+        Vec3 tA, tm;
+        double ta;
+        tet_section(P0, P1, P2, P3, p_apex, q1, q2, q3, m, c_best, tA, ta, tm);
+        A = A + tA;
+        area += ta;
+        mom = mom + tm;
+      }
+      A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
+      area = group_sum<G>(area, mask);
+      mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
+    }
+    if (lane == 0) {
+      W.iso[cell] = c_best;
+      W.status[cell] = status;
+      W.evals[cell] = evals;
+      W.A_int[cell] = area;
+      const double an = norm(A);
+      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
+      W.n_int[3 * cell] = A.x * inv;
+      W.n_int[3 * cell + 1] = A.y * inv;
+      W.n_int[3 * cell + 2] = A.z * inv;
+      const double ia = area > 0 ? 1.0 / area : 0.0;
+      W.x_gamma[3 * cell] = mom.x * ia;
+      W.x_gamma[3 * cell + 1] = mom.y * ia;
+      W.x_gamma[3 * cell + 2] = mom.z * ia;
+      evals_acc += evals;
+      tetev_acc += (int64_t)evals * nt;
+      prep_acc += nt;
+      if (status & VOF_ST_DEGENERATE) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
+      if (status & VOF_ST_NOT_CONVERGED) atomicAdd((unsigned long long*)&W.counters->n_not_converged, 1ull);
+      if (status & VOF_ST_FALLBACK) atomicAdd((unsigned long long*)&W.counters->n_fallback, 1ull);
+      if (status & VOF_ST_MLP_SKIPPED) atomicAdd((unsigned long long*)&W.counters->n_mlp_skipped, 1ull);
+    }
+    __syncwarp(mask);
+  }
+  if (lane == 0 && evals_acc) {
+    atomicAdd((unsigned long long*)&W.counters->evals_total, (unsigned long long)evals_acc);
+    atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
+    atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
+  }
+  if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
+}
+
+// ---- crossing point (R4) -----------------------------------------------------------------------
+__device__ __forceinline__ bool has_plane(const Workspace& W, int32_t c, uint32_t step) {
+  return W.iface_stamp[c] == step && W.A_int[c] > 0;
+}
+
+// t along x_owner -> x_neigh; *src = the interface cell whose plane gave it, or -1
+__device__ double crossing_t(const MeshView& M, const Workspace& W, const double* alpha, int32_t f, int xf_mode,
+                             uint32_t step, int32_t* src) {
+  const int32_t o = M.face_owner[f], n = M.face_neigh[f];
+  *src = -1;
+  if (xf_mode == VOF_XF_AS_PRINTED) return fabs(alpha[n] - 0.5) / fabs(alpha[o] - alpha[n]);
+  const double t_lin = (alpha[o] - 0.5) / (alpha[o] - alpha[n]);
+  if (xf_mode == VOF_XF_LINEAR) return t_lin;
+  const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
+  const Vec3 xn = v3(M.cell_cen[3 * n], M.cell_cen[3 * n + 1], M.cell_cen[3 * n + 2]);
+  const Vec3 xfc = v3(M.face_cen[3 * f], M.face_cen[3 * f + 1], M.face_cen[3 * f + 2]);
+  double best_t = 0, best_d = 0;
+  const int32_t cand[2] = {o, n};
+  for (int q = 0; q < 2; ++q) {
+    const int32_t c = cand[q];
+    if (!has_plane(W, c, step)) continue;
+    const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+    const Vec3 xg = v3(W.x_gamma[3 * c], W.x_gamma[3 * c + 1], W.x_gamma[3 * c + 2]);
+    const double den = dot(nn, xn - xo);
+    if (den == 0) continue;
+    const double t = dot(nn, xg - xo) / den;
+    if (!(t >= 0 && t <= 1)) continue;
+    const double d = norm(xo + (xn - xo) * t - xfc);
+    if (*src < 0 || d < best_d) { best_t = t; best_d = d; *src = c; }
+  }
+  return *src >= 0 ? best_t : t_lin;
+}
+
+// ---- interface-modified least squares (R7) on band cells, crossing-face outputs -----------------
+// 8 lanes per band cell over its faces; the nine sums of G and b are reduced across the lanes.
+constexpr int kLsqLanes = 8;
+
+__global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t nb = W.counters->n_band;
+  const int lane = threadIdx.x % kLsqLanes;
+  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
+  int ncross = 0, nsing = 0;
+  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + threadIdx.x / kLsqLanes; j < nb; j += groups) {
+    const int32_t c = W.band_idx[j];
+    const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
+    const double TP = a.T[c], aP = a.alpha[c];
+    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+      const int32_t q = o == c ? nbr : o;
+      Vec3 r;
+      double dT;
+      if (q >= 0) {
+        const double aQ = a.alpha[q];
+        if ((aP - 0.5) * (aQ - 0.5) < 0) {
+          int32_t src;
+          const double t = crossing_t(M, W, a.alpha, f, a.opt.xf_mode, step, &src);
+          const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
+          const Vec3 xn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]);
+          const Vec3 xf = xo + (xn - xo) * t;
+          r = xf - xP;
+          dT = a.props.T_sat - TP;
+          // crossing-face outputs, written once: by the owner if it is in the band
+          if (o == c || W.band_stamp[o] != step) {
+            W.x_f[3 * f] = xf.x; W.x_f[3 * f + 1] = xf.y; W.x_f[3 * f + 2] = xf.z;
+            W.d_own[f] = norm(xf - xo);
+            W.d_neigh[f] = norm(xf - xn);
+            const int32_t sc = src >= 0 ? src : (has_plane(W, o, step) ? o : (has_plane(W, nbr, step) ? nbr : -1));
+            double af = 0;
+            if (sc >= 0) {
+              const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
+              const Vec3 nn = v3(W.n_int[3 * sc], W.n_int[3 * sc + 1], W.n_int[3 * sc + 2]);
+              af = fabs(W.A_int[sc] * dot(nn, Af) / norm(Af));
+            }
+            W.A_int_f[f] = af;
+            W.face_stamp[f] = step;
+            ++ncross;
+          }
+        } else {
+          r = v3(M.cell_cen[3 * q], M.cell_cen[3 * q + 1], M.cell_cen[3 * q + 2]) - xP;
+          dT = a.T[q] - TP;
+        }
+      } else {
+        if (!a.T_bnd) continue;
+        r = v3(M.face_cen[3 * f], M.face_cen[3 * f + 1], M.face_cen[3 * f + 2]) - xP;
+        dT = a.T_bnd[f] - TP;
+      }
+      g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
+      g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
+      b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+    }
+    g00 = group_sum<kLsqLanes>(g00, mask); g01 = group_sum<kLsqLanes>(g01, mask);
+    g02 = group_sum<kLsqLanes>(g02, mask); g11 = group_sum<kLsqLanes>(g11, mask);
+    g12 = group_sum<kLsqLanes>(g12, mask); g22 = group_sum<kLsqLanes>(g22, mask);
+    b0 = group_sum<kLsqLanes>(b0, mask); b1 = group_sum<kLsqLanes>(b1, mask); b2 = group_sum<kLsqLanes>(b2, mask);
+    if (lane != 0) continue;
+    // explicit symmetric inverse (cofactors / det), Appendix B
+    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    const double det = g00 * c00 + g01 * c01 + g02 * c02;
+    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
+    int st = 0;
+    Vec3 g = v3(0, 0, 0);
+    if (det > 1e-12 * tr * tr * tr) {
+      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+      const double id = 1.0 / det;
+      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+             (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    } else {
+      st = VOF_ST_SINGULAR_LSQ;
+      ++nsing;
+    }
+    W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
+    if (W.iface_stamp[c] == step) W.status[c] |= st;
+    else W.status[c] = st;
+  }
+  if (ncross) atomicAdd((unsigned long long*)&W.counters->n_crossing, (unsigned long long)ncross);
+  if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
+}
+
+// ---- per-side gradients and source (R5, R6) on interface cells ----------------------------------
+__global__ void k_source(MeshView M, StepArgs a, Workspace W) {
+  const int64_t n = W.counters->n_iface;
+  const int lane = threadIdx.x % kLsqLanes;
+  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
+  int nside = 0;
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + threadIdx.x / kLsqLanes; i < n; i += groups) {
+    const int32_t c = W.iface_idx[i];
+    double mdot = 0, Q = 0, ql = 0, qv = 0;
+    Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
+    const double Aint = W.A_int[c];
+    if (Aint > 0) {
+      const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+      const bool liq = a.alpha[c] > 0.5;
+      const double sigma = liq ? -1.0 : 1.0;  // the other side: vapour (-1) or liquid (+1)
+      Vec3 acc = v3(0, 0, 0);
+      double ws = 0;
+      for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+        const int32_t fe = M.cell_face[k];
+        const int32_t f = fe & 0x7fffffff;
+        const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
+        if (q < 0) continue;
+        if ((a.alpha[q] > 0.5) == liq) continue;
+        Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
+        if (fe < 0) Af = Af * -1.0;
+        const double w = fmax(0.0, sigma * dot(nn, Af));
+        acc = acc + v3(W.grad[3 * q], W.grad[3 * q + 1], W.grad[3 * q + 2]) * w;
+        ws += w;
+      }
+      acc = v3(group_sum<kLsqLanes>(acc.x, mask), group_sum<kLsqLanes>(acc.y, mask), group_sum<kLsqLanes>(acc.z, mask));
+      ws = group_sum<kLsqLanes>(ws, mask);
+      Vec3 go = v3(0, 0, 0);
+      if (ws > 0) go = acc * (1.0 / ws);
+      const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
+      gl = liq ? gown : go;
+      gv = liq ? go : gown;
+      ql = a.props.k_l * dot(gl, nn) * Aint;
+      qv = -a.props.k_v * dot(gv, nn) * Aint;
+      mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
+      Q = -mdot * a.props.h_lv;
+      if (lane == 0 && !(ws > 0)) {
+        W.status[c] |= VOF_ST_NO_SIDE;
+        ++nside;
+      }
+    }
+    if (lane != 0) continue;
+    a.mdot[c] = mdot;
+    a.Q[c] = Q;
+    W.q_l[c] = ql;
+    W.q_v[c] = qv;
+    W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
+    W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
+    W.mdotV[i] = mdot * M.cell_vol[c];
+    W.QV[i] = Q * M.cell_vol[c];
+  }
+  if (nside) atomicAdd((unsigned long long*)&W.counters->n_no_side, (unsigned long long)nside);
+}
+
+// ---- totals (R8): pairwise tree over the interface list padded with zeros to a power of two ------
+// One block reduces an aligned chunk of kReduceChunk leaves with the same pairing as the whole
+// tree, so chunk sums are tree nodes; the last block to finish folds the chunk sums the same way.
+// Padding with more zeros than the next power of two only adds exact "+ 0.0" nodes.
+__device__ void tree_block(const double* x, int64_t n, int64_t base, double* s, double* out) {
+  const int t = threadIdx.x;  // blockDim.x == kReduceChunk / 2
+  const int64_t i0 = base + 2 * t, i1 = i0 + 1;
+  s[t] = (i0 < n ? __ldcg(x + i0) : 0.0) + (i1 < n ? __ldcg(x + i1) : 0.0);
+  __syncthreads();
+  for (int w = kReduceChunk / 4; w > 0; w >>= 1) {
+    double v = 0;
+    if (t < w) v = s[2 * t] + s[2 * t + 1];
+    __syncthreads();
+    if (t < w) s[t] = v;
+    __syncthreads();
+  }
+  if (t == 0) *out = s[0];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kReduceChunk / 2) k_totals(Workspace W, double* totals) {
+  __shared__ double s[kReduceChunk / 2];
+  __shared__ bool last;
+  const int64_t n = W.counters->n_iface;
+  const int64_t nchunks = (n + kReduceChunk - 1) / kReduceChunk;
+  for (int64_t b = blockIdx.x; b < nchunks; b += gridDim.x) {
+    tree_block(W.mdotV, n, b * kReduceChunk, s, &W.partial[b]);
+    tree_block(W.QV, n, b * kReduceChunk, s, &W.partial[2 * kMaxPartials + b]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&W.counters->reduce_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int q = 0; q < 2; ++q) {
+    double* A = W.partial + 2 * q * kMaxPartials;
+    double* B = A + kMaxPartials;
+    int64_t m = nchunks;
+    while (m > 1) {
+      const int64_t mc = (m + kReduceChunk - 1) / kReduceChunk;
+      for (int64_t b = 0; b < mc; ++b) tree_block(A, m, b * kReduceChunk, s, &B[b]);
+      __threadfence_block();
+      double* t = A;
+      A = B;
+      B = t;
+      m = mc;
+    }
+    if (threadIdx.x == 0) totals[q] = m == 0 ? 0.0 : __ldcg(A);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) W.counters->reduce_done = 0;
+}
+
+// Lanes per cell: about four tetrahedra per lane, and the per-cell rows of a block within
+// ~110 KB of shared memory (two blocks per SM).
+int pick_group(const vof_mesh* m, const vof_options& o) {
+  if (o.group_size) return o.group_size;
+  int g = 1;
+  while (g < 32 && (g * 4 < m->mean_ct || (size_t)(kThreads / g) * m->max_ct * sizeof(TetRow) > 110 * 1024)) g *= 2;
+  return g;
+}
+
+template <int G>
+cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned) {
+  // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
+  int threads = kThreads;
+  while (threads > 32 && threads > G && (size_t)(threads / G) * m->max_ct * sizeof(TetRow) > 110 * 1024) threads /= 2;
+  const size_t smem = (size_t)(threads / G) * m->max_ct * sizeof(TetRow);
+  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_root<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_root<G>, threads, smem);
+  if (bps < 1) bps = 1;
+  const int64_t need = (m->n_cells + (threads / G) - 1) / (threads / G);
+  const int grid = (int)std::min<int64_t>(need, (int64_t)m->num_sms * bps);
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, m->max_ct, learned);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s);  // vof_mlp.cu
+
+vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s) {
+  const int learned = opt.root_mode == VOF_ROOT_LEARNED;
+  if (learned && !m->mlp) {
+    set_error("learned root search requested but no MLP weights are set");
+    return VOF_ESTATE;
+  }
+  Workspace& W = m->ws;
+  const MeshView& M = m->view;
+  Timing& tm = m->timing;
+  tm.start(KC_SELECT, s);
+  k_begin<<<1, 1, 0, s>>>(W.counters);
+  k_sel_count<<<m->n_sel_blocks, kThreads, 0, s>>>(M.n_cells, d_alpha, opt.alpha_eps, W.blk_count);
+  k_sel_scan<<<1, 1024, 0, s>>>(m->n_sel_blocks, W.blk_count, W.blk_off, W.counters);
+  k_sel_scatter<<<m->n_sel_blocks, kThreads, 0, s>>>(M, d_alpha, opt.alpha_eps, W);
+  k_mark<<<m->num_sms * 4, kThreads, 0, s>>>(M, W);
+  tm.stop(s);
+  const int vgrid = (int)std::min<int64_t>((M.n_verts + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
+  tm.start(KC_VERTEX, s);
+  k_bv_count<<<m->n_sel_blocks + m->n_vert_blocks, kThreads, 0, s>>>(M.n_cells, M.n_verts, m->n_sel_blocks, W);
+  k_bv_scan<<<1, 1024, 0, s>>>(m->n_sel_blocks, m->n_vert_blocks, W);
+  k_bv_scatter<<<m->n_sel_blocks + m->n_vert_blocks, kThreads, 0, s>>>(M.n_cells, M.n_verts, m->n_sel_blocks, W);
+  k_vertex<<<vgrid, kThreads, 0, s>>>(M, d_alpha, opt.vertex_mode, W);
+  tm.stop(s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "selection/vertex kernels");
+  if (learned) {
+    tm.start(KC_MLP, s);
+    e = launch_mlp_guess(m, s);
+    tm.stop(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
+  }
+  tm.start(KC_ROOT, s);
+  switch (pick_group(m, opt)) {
+    case 1: e = launch_root_g<1>(m, d_alpha, opt, s, learned); break;
+    case 2: e = launch_root_g<2>(m, d_alpha, opt, s, learned); break;
+    case 4: e = launch_root_g<4>(m, d_alpha, opt, s, learned); break;
+    case 8: e = launch_root_g<8>(m, d_alpha, opt, s, learned); break;
+    case 16: e = launch_root_g<16>(m, d_alpha, opt, s, learned); break;
+    default: e = launch_root_g<32>(m, d_alpha, opt, s, learned); break;
+  }
+  tm.stop(s);
+  if (e != cudaSuccess) return cuda_fail(e, "root kernel");
+  return VOF_OK;
+}
+
+vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s) {
+  const MeshView& M = m->view;
+  Workspace& W = m->ws;
+  cudaMemsetAsync(a.mdot, 0, M.n_cells * sizeof(double), s);
+  cudaMemsetAsync(a.Q, 0, M.n_cells * sizeof(double), s);
+  Timing& tm = m->timing;
+  const int cgrid = (int)std::min<int64_t>((M.n_cells + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
+  tm.start(KC_LSQ, s);
+  k_lsq<<<cgrid, kThreads, 0, s>>>(M, a, W);
+  tm.stop(s);
+  tm.start(KC_SOURCE, s);
+  k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+  tm.stop(s);
+  const int rgrid = (int)std::min<int64_t>((M.n_cells + kReduceChunk - 1) / kReduceChunk, 32);
+  tm.start(KC_TOTALS, s);
+  k_totals<<<std::max(rgrid, 1), kReduceChunk / 2, 0, s>>>(W, a.totals);
+  tm.stop(s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "source kernels");
+  return VOF_OK;
+}
+
+}  // namespace vof
