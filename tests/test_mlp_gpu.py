@@ -1,0 +1,141 @@
+"""GPU parity of the learned part: the BF16 MLP kernels against the FP64 oracle MLP, the GPU
+features against their NumPy definition, training, and the learned root search."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import case, gpu_step
+from oracle import iso_dataset, mlp as omlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2604_14938_gb300 as vof  # noqa: E402
+
+
+def _data(n=513, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1, 1, (n, 40)).astype(np.float32)
+    t = rng.uniform(0, 1, n).astype(np.float32)
+    return X, t
+
+
+def _bf16_params(p):
+    """The oracle parameters with the weights rounded as the kernels round them (biases FP32)."""
+    P = omlp.unflatten(np.asarray(p, np.float64))
+    for k in ("W1", "W2", "W3", "w4"):
+        P[k] = omlp.bf16_round(P[k])
+    for k in ("b1", "b2", "b3", "b4"):
+        P[k] = np.asarray(P[k], np.float32).astype(np.float64)
+    return omlp.flatten(P)
+
+
+def _oracle_forward_bf16(p, X):
+    """FP64 forward with the kernels' BF16 roundings: inputs and the first two hidden layers."""
+    P = omlp.unflatten(_bf16_params(p))
+    x = omlp.bf16_round(X)
+    h1 = omlp.bf16_round(omlp.gelu(x @ P["W1"].T + P["b1"]))
+    h2 = omlp.bf16_round(omlp.gelu(h1 @ P["W2"].T + P["b2"]))
+    h3 = omlp.gelu(h2 @ P["W3"].T + P["b3"])
+    return h3 @ P["w4"] + P["b4"][0]
+
+
+def test_forward_matches_oracle():
+    X, _ = _data()
+    p = omlp.init(4).astype(np.float32)
+    m = vof.Mlp(p)
+    y = m.forward(torch.as_tensor(X, device="cuda")).cpu().numpy()
+    ref = _oracle_forward_bf16(p, X.astype(np.float64))
+    assert np.max(np.abs(y - ref)) <= 2e-2 * (1 + np.abs(ref).max())
+    assert np.corrcoef(y, ref)[0, 1] > 0.9999
+    assert np.array_equal(m.params(), p)
+
+
+def test_gradient_matches_oracle():
+    X, t = _data(n=300, seed=1)
+    p = (omlp.init(2) + np.random.default_rng(2).normal(0, 0.05, omlp.N_PARAMS)).astype(np.float32)
+    m = vof.Mlp(p)
+    g, loss = m.grad(torch.as_tensor(X, device="cuda"), torch.as_tensor(t, device="cuda"))
+    g = g.cpu().numpy().astype(np.float64)
+    lo, go = omlp.loss_and_grad(_bf16_params(p), omlp.bf16_round(X.astype(np.float64)), t.astype(np.float64))
+    cos = g @ go / (np.linalg.norm(g) * np.linalg.norm(go))
+    assert cos > 0.999, cos
+    assert np.linalg.norm(g - go) <= 3e-2 * np.linalg.norm(go)
+    assert float(loss.item()) == pytest.approx(lo, rel=2e-2)
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (4096, 40)).astype(np.float32)
+    t = (0.5 + 0.3 * np.tanh(X[:, 0] - 0.5 * X[:, 3])).astype(np.float32)
+    m = vof.Mlp(omlp.init(5).astype(np.float32))
+    tX, tt = torch.as_tensor(X, device="cuda"), torch.as_tensor(t, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    first = None
+    for k in range(300):
+        m.train_step(tX, tt, 3e-3, loss)
+        if first is None:
+            first = float(loss.item())
+    m.train_step(tX, tt, 1e-9, loss)
+    assert float(loss.item()) < 0.05 * first
+
+
+def test_features_match_definition():
+    m, a, T, Tb = case("voronoi_film")
+    M, g = gpu_step(m, a, T, Tb)
+    F, ok = M.mlp_features()
+    F, ok = F.cpu().numpy(), ok.cpu().numpy()
+    O = oracle.Oracle(m)
+    I = g["iface_idx"]
+    ref = iso_dataset.features(m, I, g["phi_v"], a, O.geometry()["cell_vol"])
+    has = ~np.isnan(ref[:, 0])
+    assert np.array_equal(ok.astype(bool), has)
+    np.testing.assert_allclose(F[has], ref[has].astype(np.float32), rtol=1e-6, atol=1e-6)
+
+
+def _quick_mlp(seed=0, samples=40000, epochs=6):
+    X, t = iso_dataset.make(seed, samples)
+    m = vof.Mlp(omlp.init(seed).astype(np.float32))
+    tX, tt = torch.as_tensor(X, device="cuda"), torch.as_tensor(t, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for ep in range(epochs):
+        perm = torch.randperm(len(t), generator=g, device="cuda")
+        for b in range(0, len(t), 4096):
+            idx = perm[b:b + 4096]
+            m.train_step(tX[idx].contiguous(), tt[idx].contiguous(), 3e-3)
+    return m
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import os
+    if os.path.exists(vof.MLP_PATH):
+        return vof.Mlp(np.load(vof.MLP_PATH))
+    return _quick_mlp()
+
+
+@pytest.mark.parametrize("name", ["voronoi_film", "hex_sphere", "tet_sphere"])
+def test_learned_root_meets_the_bar_with_fewer_evaluations(trained, name):
+    """The learned path (guess + <= 2 FP64 secant steps + counted bisection fallback) reaches the
+    same |dalpha| <= 1e-10 bar as bisection and needs fewer FP64 cut-volume evaluations."""
+    m, a, T, Tb = case(name)
+    M, gb = gpu_step(m, a, T, Tb)
+    M.set_mlp(trained)
+    _, gl = gpu_step(m, a, T, Tb, dev_mesh=M, root_mode=vof.ROOT_LEARNED)
+    O = oracle.Oracle(m)
+    V = O.geometry()["cell_vol"]
+    I = gl["iface_idx"]
+    for c in I:
+        if gl["status"][c] & 1:
+            continue
+        assert abs(O.liquid_volume(c, gl["phi_v"], gl["iso"][c])["VL"] / V[c] - a[c]) <= 1e-10
+    assert gl["counts"]["n_not_converged"] == 0
+    assert gl["counts"]["evals_total"] < gb["counts"]["evals_total"]
+    r = O.run(a, T, Tb, synth.PROPS)
+    ref = r["pc"]["mdot"]
+    err = np.abs(gl["mdot"] - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    assert err.max() <= 1e-8
