@@ -150,7 +150,7 @@ def run_ours(args, rank, world, dev):
     for _ in range(args.steps):
         M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best)
     e2e_s = time.perf_counter() - t0
-    return m, desc, results, e2e_s, M
+    return m, (a, T, Tb), desc, results, e2e_s, M
 
 
 def cpu_baseline(m, a, T, Tb, budget_s=12.0):
@@ -225,7 +225,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    m, desc, res, e2e_s, M = run_ours(args, rank, world, dev)
+    m, fields, desc, res, e2e_s, M = run_ours(args, rank, world, dev)
     best = "learned" if "learned" in res else "bisect"
     r = res[best]
     n_iface = r["counts"]["n_iface"]
@@ -267,9 +267,7 @@ def main():
         "clocks": r["clocks"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import synth
-        wl = workload(args.workload)
-        cb, _, _ = cpu_baseline(wl[0], wl[1], wl[2], wl[3])
+        cb, _, _ = cpu_baseline(m, *fields)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))

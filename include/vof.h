@@ -59,7 +59,7 @@ typedef enum {
 /* Per-cell status bits (int32 arrays). */
 #define VOF_ST_DEGENERATE 1    /* phi_max - phi_min < 1e-14: c = phi_min, A_int = 0, mdot = 0 */
 #define VOF_ST_NOT_CONVERGED 2 /* |V_L(c)/V - alpha| > tol after the iteration cap */
-#define VOF_ST_FALLBACK 4      /* learned guess + secant missed tol; bisection finished it */
+#define VOF_ST_FALLBACK 4      /* learned guess + secant missed tol; bracketed bisection finished it */
 #define VOF_ST_SINGULAR_LSQ 8  /* det(G) <= 1e-12 (tr G / 3)^3: gradient set to 0 */
 #define VOF_ST_NO_SIDE 16      /* no face neighbour looks into the other phase: its gradient is 0 */
 #define VOF_ST_MLP_SKIPPED 32  /* more than 32 vertices: learned guess not used */
@@ -189,11 +189,48 @@ typedef struct {
    * interface cells of evaluations x tetrahedra), tetrahedra prepared, tetrahedra cut by the final
    * interface */
   int64_t tet_evals, tets_prepared, tets_sectioned;
+  int64_t evals32_total; /* FP32 evaluations of the learned path's refinement */
 } vof_counts;
 vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
 
 /* Mesh sizes and limits: n_cells, n_faces, n_verts, max vertices per cell, max tets per cell. */
 vof_status vof_mesh_info(const vof_mesh* mesh, int64_t* out5);
+
+/* ---- learned isovalue guess (the benchmark spec's learned part; the paper fixes no such model) ----
+ * A 40 -> 64 -> 64 -> 64 -> 1 GELU MLP predicting the normalised isovalue position
+ * t = (c - phi_min)/(phi_max - phi_min) of an interface cell. BF16 operands with FP32
+ * accumulation (forward on the tensor cores), FP32 master weights and Adam.
+ * Parameters (float32, row-major): W1[64][40], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
+ * w4[64], b4. Features (float32 [n][40]): alpha; faces/32; the vertex values normalised to [0,1]
+ * over the cell's range, sorted descending, padded to 32 with the smallest; bounding-box extents
+ * / V^(1/3) (3); (vertex mean - bounding-box centre) / V^(1/3) (3). Cells with more than 32
+ * vertices or a degenerate range have no features (VOF_ST_MLP_SKIPPED: plain bisection). */
+#define VOF_MLP_N_PARAMS 11009
+#define VOF_MLP_N_FEATURES 40
+#define VOF_MLP_MAX_BATCH 65536
+typedef struct vof_mlp vof_mlp; /* opaque, library-owned, device memory allocated at creation */
+
+/* Creates an MLP from host parameters (VOF_MLP_N_PARAMS floats); synchronises the device. */
+vof_status vof_mlp_create(const float* h_params, vof_mlp** out);
+vof_status vof_mlp_destroy(vof_mlp* mlp);
+/* Copies the FP32 master parameters to the host; synchronises. */
+vof_status vof_mlp_get_params(vof_mlp* mlp, float* h_params);
+/* d_y[i] = MLP(d_X[i]) for i < n (device float32, features [n][40]). */
+vof_status vof_mlp_forward(vof_mlp* mlp, const float* d_X, int64_t n, float* d_y, void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the mean squared error of a batch of
+ * n <= VOF_MLP_MAX_BATCH samples (d_t [n] targets); d_loss (device float [1], may be NULL) gets
+ * the batch loss before the step. Gradient partials are summed in a fixed order. */
+vof_status vof_mlp_train_step(vof_mlp* mlp, const float* d_X, const float* d_t, int64_t n, float lr, float* d_loss,
+                              void* stream);
+/* The gradient of the batch loss (device float [VOF_MLP_N_PARAMS]) without an update. */
+vof_status vof_mlp_grad(vof_mlp* mlp, const float* d_X, const float* d_t, int64_t n, float* d_grad, float* d_loss,
+                        void* stream);
+/* Attaches an MLP (or NULL) to a mesh for VOF_ROOT_LEARNED; allocates the mesh's feature buffers
+ * on first use. The MLP must outlive its use by the mesh. */
+vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp);
+/* Features of the interface cells of the last reconstruction, made with that reconstruction's
+ * d_alpha: d_X [n_iface][40], d_ok [n_iface] (1 where the cell has features). */
+vof_status vof_mlp_features(vof_mesh* mesh, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream);
 
 /* Per-kernel device time, measured with pairs of CUDA events recorded on the launch stream
  * around each kernel group (off by default; measurement support, not part of the method).

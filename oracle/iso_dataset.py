@@ -15,7 +15,7 @@ Features (40 per cell; the definition the GPU kernel restates):
 Cells with more than 32 vertices or a degenerate range are not samples.
 
 Run as a script to write an .npz with float32 features X [n, 40] and labels t [n]:
-  python -m oracle.iso_dataset --samples 2000000 --seeds 0-9 --out iso_train.npz
+  python -m oracle.iso_dataset --samples 2000000 --seeds 0-9 --jobs 10 --out iso_train.npz
 """
 from __future__ import annotations
 
@@ -129,21 +129,30 @@ def _verts(m, c):
     return vs
 
 
+def _one(args):
+    seed, per = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return make(seed, per)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=2_000_000)
     ap.add_argument("--seeds", default="0-9")
+    ap.add_argument("--jobs", type=int, default=1, help="worker processes (one seed each)")
     ap.add_argument("--out", required=True)
     args = ap.parse_args()
     a, b = (int(x) for x in args.seeds.split("-"))
     seeds = list(range(a, b + 1))
     per = args.samples // len(seeds)
-    Xs, Ts = [], []
-    for s in seeds:
-        X, T = make(s, per)
-        Xs.append(X)
-        Ts.append(T)
-    np.savez(args.out, X=np.concatenate(Xs), t=np.concatenate(Ts), seeds=np.array(seeds))
+    if args.jobs > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(args.jobs) as pool:
+            res = pool.map(_one, [(s, per) for s in seeds])
+    else:
+        res = [make(s, per) for s in seeds]
+    np.savez(args.out, X=np.concatenate([r[0] for r in res]), t=np.concatenate([r[1] for r in res]),
+             seeds=np.array(seeds))
 
 
 if __name__ == "__main__":

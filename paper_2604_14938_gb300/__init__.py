@@ -59,7 +59,7 @@ class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("step", "n_iface", "n_band", "n_crossing", "n_degenerate",
                                                "n_not_converged", "n_fallback", "n_singular", "n_no_side",
                                                "n_mlp_skipped", "evals_total", "tet_evals", "tets_prepared",
-                                               "tets_sectioned")]
+                                               "tets_sectioned", "evals32_total")]
 
 
 def lib():
@@ -217,3 +217,102 @@ class Mesh:
         c = Counts()
         _check(lib().vof_get_counts(self.h, ctypes.byref(c), _stream(stream)), "vof_get_counts")
         return {n: getattr(c, n) for n, _ in Counts._fields_}
+
+
+# ---------------------------------------------------------------------------------- learned guess
+N_MLP_PARAMS = 11009
+N_MLP_FEATURES = 40
+MLP_PATH = os.path.join(_HERE, "mlp_iso.npy")
+
+
+def _mlp_sig():
+    L = lib()
+    if getattr(L, "_mlp_sig", False):
+        return L
+    vp, st = ctypes.c_void_p, ctypes.c_int
+    for name, args in {"vof_mlp_create": [vp, vp], "vof_mlp_destroy": [vp], "vof_mlp_get_params": [vp, vp],
+                       "vof_mlp_forward": [vp, vp, ctypes.c_int64, vp, vp],
+                       "vof_mlp_train_step": [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp],
+                       "vof_mlp_grad": [vp, vp, vp, ctypes.c_int64, vp, vp, vp],
+                       "vof_mesh_set_mlp": [vp, vp], "vof_mlp_features": [vp, vp, vp, vp, vp]}.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L._mlp_sig = True
+    return L
+
+
+class Mlp:
+    """The isovalue-guess MLP on the device (vof_mlp_*). Parameters: float32 [N_MLP_PARAMS]."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        if p.shape != (N_MLP_PARAMS,):
+            raise ValueError(f"expected {N_MLP_PARAMS} parameters")
+        h = ctypes.c_void_p()
+        _check(_mlp_sig().vof_mlp_create(p.ctypes.data, ctypes.byref(h)), "vof_mlp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _mlp_sig().vof_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(N_MLP_PARAMS, np.float32)
+        _check(_mlp_sig().vof_mlp_get_params(self.h, out.ctypes.data), "vof_mlp_get_params")
+        return out
+
+    def forward(self, X, y=None, stream=None):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device) if y is None else y
+        _check(_mlp_sig().vof_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(y), _stream(stream)), "vof_mlp_forward")
+        return y
+
+    def train_step(self, X, t, lr: float, loss=None, stream=None):
+        _check(_mlp_sig().vof_mlp_train_step(self.h, _ptr(X), _ptr(t), X.shape[0], ctypes.c_float(lr), _ptr(loss),
+                                             _stream(stream)), "vof_mlp_train_step")
+
+    def grad(self, X, t, stream=None):
+        import torch
+        g = torch.empty(N_MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(_mlp_sig().vof_mlp_grad(self.h, _ptr(X), _ptr(t), X.shape[0], _ptr(g), _ptr(loss), _stream(stream)),
+               "vof_mlp_grad")
+        return g, loss
+
+
+def _mesh_set_mlp(self, mlp):
+    """Attaches an Mlp (kept alive by the mesh) for ROOT_LEARNED; None detaches."""
+    _check(_mlp_sig().vof_mesh_set_mlp(self.h, None if mlp is None else mlp.h), "vof_mesh_set_mlp")
+    self._mlp = mlp
+
+
+def _mesh_mlp_features(self, alpha, stream=None):
+    """(features [n_iface, 40] float32, ok [n_iface] int32) of the last reconstruction, which was
+    made with the CUDA float64 tensor `alpha`."""
+    import torch
+    n = self.counts()["n_iface"]
+    X = torch.empty((max(n, 1), N_MLP_FEATURES), dtype=torch.float32, device="cuda")
+    ok = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    _check(_mlp_sig().vof_mlp_features(self.h, _ptr(alpha), _ptr(X), _ptr(ok), _stream(stream)), "vof_mlp_features")
+    return X[:n], ok[:n]
+
+
+Mesh.set_mlp = _mesh_set_mlp
+Mesh.mlp_features = _mesh_mlp_features
+
+
+def load_default_mlp(mesh: Mesh) -> bool:
+    """Attaches the trained weights shipped with the package (mlp_iso.npy) to `mesh`; False if
+    there are none."""
+    if not os.path.exists(MLP_PATH):
+        return False
+    mesh.set_mlp(Mlp(np.load(MLP_PATH)))
+    return True

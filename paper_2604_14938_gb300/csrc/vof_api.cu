@@ -100,6 +100,7 @@ vof_status vof_get_counts(vof_mesh* m, vof_counts* out, void* stream) {
   out->tet_evals = c.tet_evals;
   out->tets_prepared = c.tets_prepared;
   out->tets_sectioned = c.tets_sectioned;
+  out->evals32_total = c.evals32_total;
   return VOF_OK;
 }
 

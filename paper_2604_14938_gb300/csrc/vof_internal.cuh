@@ -21,6 +21,7 @@ struct Counters {
   // algorithmic work of the root search: tetrahedron evaluations (sum of evals x tets per cell),
   // tetrahedra prepared, tetrahedra cut in the final geometry
   int64_t tet_evals, tets_prepared, tets_sectioned;
+  int64_t evals32_total;  // FP32 evaluations of the learned path's refinement
 };
 
 // Everything a step kernel reads or writes, by value (device pointers).
@@ -78,6 +79,10 @@ struct Workspace {
   double* QV;              // [n_cells]
   double* partial;         // [4][kMaxPartials]: two ping-pong buffers per total
   float* mlp_out;          // [n_cells] learned guesses (normalised position in the range)
+  const double* alpha_in;  // alpha of the current step
+  float* mlp_x;            // [n_cells][40] features of interface cells (allocated with an MLP)
+  int32_t* mlp_ok;         // [n_cells] 1 where the cell has features
+  float* mlp_y;            // [n_cells] raw MLP outputs
   // device staging for the host-buffer step
   double *io_alpha, *io_T, *io_Tb, *io_mdot, *io_Q, *io_totals;
 };
@@ -130,7 +135,7 @@ struct vof_mesh {
   vof::Workspace ws{};
   std::vector<void*> allocs;
   // learned isovalue guess (BF16 weights, device), see vof_mlp.cu
-  void* mlp = nullptr;
+  vof_mlp* mlp = nullptr;
   bool recon_done = false;
   vof::Timing timing;
 };

@@ -1,12 +1,566 @@
-// Learned isovalue guess: BF16 MLP inference/training kernels (filled in with the learned path).
+// Learned isovalue guess: a 40 -> 64 -> 64 -> 64 -> 1 GELU MLP that predicts the normalised
+// isovalue position t = (c - phi_min)/(phi_max - phi_min) of an interface cell from its volume
+// fraction, face count, sorted normalised vertex values and shape. BF16 operands, FP32
+// accumulation: the forward pass runs on the tensor cores (mma.sync m16n8k16 bf16), the backward
+// pass on the CUDA cores in FP32 over the BF16-rounded forward operands; FP32 master weights, Adam.
+//
+// Parameter vector (float32), row-major: W1 [64][40], b1 [64], W2 [64][64], b2 [64], W3 [64][64],
+// b3 [64], w4 [64], b4 [1]  (VOF_MLP_N_PARAMS = 11009).
+//
+// Features of an interface cell (40): alpha; faces / 32; the vertex values normalised to [0, 1]
+// over the cell's range, sorted descending, padded to 32 with the smallest; bounding-box extents
+// / V^(1/3) (3); (vertex mean - bounding-box centre) / V^(1/3) (3). Cells with more than 32
+// vertices or a degenerate range get no guess.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "vof_internal.cuh"
+
+namespace vof {
+namespace {
+
+constexpr int kIn = 40, kInPad = 48, kH = 64;
+constexpr int kNP = kH * kIn + kH + 2 * (kH * kH + kH) + kH + 1;
+constexpr int LDX = kInPad + 8;  // bf16 row strides in shared memory (bank-conflict free)
+constexpr int LDH = kH + 8;
+constexpr int kRows = 64;        // samples per CTA
+constexpr int kWarps = kRows / 16;
+constexpr int kMaxBatch = 1 << 16;
+constexpr int kMaxTiles = kMaxBatch / kRows;
+
+// offsets into the parameter vector
+constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+              ob3 = oW3 + kH * kH, ow4 = ob3 + kH, ob4 = ow4 + kH;
+static_assert(ob4 + 1 == kNP, "parameter layout");
+
+// BF16 copy of the weights in the layout the kernels load (W1 padded to 48 inputs).
+struct WeightsBF16 {
+  __nv_bfloat16 W1[kH][kInPad];
+  __nv_bfloat16 W2[kH][kH];
+  __nv_bfloat16 W3[kH][kH];
+  float b1[kH], b2[kH], b3[kH], w4[kH], b4;  // w4 holds bf16-rounded values
+};
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc[nt][.] = rows m0..m0+15 of X[.][0..K) times W[0..64)[0..K)^T (16 x 64 output per warp).
+// Fragment layouts of m16n8k16 (g = lane / 4, q = lane % 4): A a0a1 (row g, cols 2q, 2q+1),
+// a2a3 (row g+8), a4a5 (row g, cols +8), a6a7 (row g+8, cols +8); B b0b1 (k 2q, 2q+1; n g),
+// b2b3 (k +8); C c0c1 (row g, cols 2q, 2q+1), c2c3 (row g+8).
+template <int K, int LDA, int LDB>
+__device__ __forceinline__ void warp_gemm(const __nv_bfloat16* X, const __nv_bfloat16* W, int m0, float (&acc)[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 2 * q);
+    a[1] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 2 * q);
+    a[2] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 8 + 2 * q);
+    a[3] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 8 + 2 * q);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* w = W + (nt * 8 + g) * LDB + k0 + 2 * q;
+      mma16816(acc[nt], a, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+  }
+}
+
+struct Smem {
+  __nv_bfloat16 X[kRows * LDX];
+  __nv_bfloat16 W1[kH * LDX];
+  __nv_bfloat16 W2[kH * LDH];
+  __nv_bfloat16 W3[kH * LDH];
+  __nv_bfloat16 H1[kRows * LDH];
+  __nv_bfloat16 H2[kRows * LDH];
+  float b1[kH], b2[kH], b3[kH], w4[kH];
+  float b4;
+  float y[kRows];
+};
+
+// Stages weights (bf16) and biases into shared memory.
+__device__ void stage_weights(Smem& s, const WeightsBF16& w) {
+  for (int i = threadIdx.x; i < kH * kInPad; i += blockDim.x) s.W1[(i / kInPad) * LDX + i % kInPad] = w.W1[i / kInPad][i % kInPad];
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    s.W2[(i / kH) * LDH + i % kH] = w.W2[i / kH][i % kH];
+    s.W3[(i / kH) * LDH + i % kH] = w.W3[i / kH][i % kH];
+  }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    s.b1[i] = w.b1[i]; s.b2[i] = w.b2[i]; s.b3[i] = w.b3[i]; s.w4[i] = w.w4[i];
+  }
+  if (threadIdx.x == 0) s.b4 = w.b4;
+}
+
+// Forward pass of the warp's 16 rows. Z (optional, fp32 [kRows][kH] x 3) keeps pre-activations,
+// H3 (optional, fp32 [kRows][kH]) the last hidden layer; y gets the outputs.
+__device__ void warp_forward(Smem& s, int m0, float* Z1, float* Z2, float* Z3, float* H3) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  float acc[8][4];
+  warp_gemm<kInPad, LDX, LDX>(s.X, s.W1, m0, acc);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * q + (i & 1);
+      const float z = acc[nt][i] + s.b1[c];
+      if (Z1) Z1[r * kH + c] = z;
+      s.H1[r * LDH + c] = __float2bfloat16_rn(gelu(z));
+    }
+  __syncwarp();
+  warp_gemm<kH, LDH, LDH>(s.H1, s.W2, m0, acc);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * q + (i & 1);
+      const float z = acc[nt][i] + s.b2[c];
+      if (Z2) Z2[r * kH + c] = z;
+      s.H2[r * LDH + c] = __float2bfloat16_rn(gelu(z));
+    }
+  __syncwarp();
+  warp_gemm<kH, LDH, LDH>(s.H2, s.W3, m0, acc);
+  float part[2] = {0.f, 0.f};
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * q + (i & 1);
+      const float z = acc[nt][i] + s.b3[c];
+      const float h = gelu(z);
+      if (Z3) Z3[r * kH + c] = z;
+      if (H3) H3[r * kH + c] = h;
+      part[i >> 1] = fmaf(h, s.w4[c], part[i >> 1]);
+    }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 1);
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 2);
+  }
+  if (q == 0) {
+    s.y[m0 + g] = part[0] + s.b4;
+    s.y[m0 + g + 8] = part[1] + s.b4;
+  }
+  __syncwarp();
+}
+
+// Loads kRows feature rows (float32 [n][40], or zeros past n) into the bf16 X tile.
+__device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n) {
+  for (int i = threadIdx.x; i < kRows * kInPad; i += blockDim.x) {
+    const int r = i / kInPad, c = i % kInPad;
+    const int64_t gr = row0 + r;
+    const float v = (c < kIn && gr < n) ? X[gr * kIn + c] : 0.f;
+    s.X[r * LDX + c] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void __launch_bounds__(kRows * 2) k_mlp_forward(WeightsBF16* w, const float* X, int64_t n, float* y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  stage_weights(s, *w);
+  const int warp = threadIdx.x >> 5;
+  for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < n; row0 += (int64_t)gridDim.x * kRows) {
+    load_x(s, X, row0, n);
+    __syncthreads();
+    if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
+    __syncthreads();
+    for (int r = threadIdx.x; r < kRows; r += blockDim.x)
+      if (row0 + r < n) y[row0 + r] = s.y[r];
+    __syncthreads();
+  }
+}
+
+// ---- features of interface cells, written as float32 [n_iface][40]; flag[i] = 0 when skipped
+__global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, float* X, int32_t* ok) {
+  const int64_t n = W.counters->n_iface;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = W.iface_idx[i];
+    const int64_t v0 = M.cell_vert_off[c];
+    const int nv = (int)(M.cell_vert_off[c + 1] - v0);
+    float* x = X + i * kIn;
+    if (nv > 32) {
+      ok[i] = 0;
+      continue;
+    }
+    double p[32];
+    double lo = 1e300, hi = -1e300, bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
+    double mean[3] = {0, 0, 0};
+    for (int j = 0; j < nv; ++j) {
+      const int32_t v = M.cell_vert[v0 + j];
+      p[j] = W.phi_v[v];
+      lo = fmin(lo, p[j]);
+      hi = fmax(hi, p[j]);
+      const double xyz[3] = {M.vx[v], M.vy[v], M.vz[v]};
+      for (int k = 0; k < 3; ++k) {
+        bmin[k] = fmin(bmin[k], xyz[k]);
+        bmax[k] = fmax(bmax[k], xyz[k]);
+        mean[k] += xyz[k];
+      }
+    }
+    if (!(hi - lo >= 1e-14)) {
+      ok[i] = 0;
+      continue;
+    }
+    ok[i] = 1;
+    // insertion sort, descending
+    for (int j = 1; j < nv; ++j) {
+      const double t = p[j];
+      int k = j - 1;
+      while (k >= 0 && p[k] < t) {
+        p[k + 1] = p[k];
+        --k;
+      }
+      p[k + 1] = t;
+    }
+    const double inv = 1.0 / (hi - lo);
+    x[0] = (float)alpha[c];
+    x[1] = (float)((double)(M.cell_face_off[c + 1] - M.cell_face_off[c]) / 32.0);
+    for (int j = 0; j < 32; ++j) x[2 + j] = (float)((p[j < nv ? j : nv - 1] - lo) * inv);
+    const double s = cbrt(M.cell_vol[c]);
+    for (int k = 0; k < 3; ++k) {
+      x[34 + k] = (float)((bmax[k] - bmin[k]) / s);
+      x[37 + k] = (float)((mean[k] / nv - 0.5 * (bmin[k] + bmax[k])) / s);
+    }
+  }
+}
+
+// guess of interface cell i: t in [0, 1], or -1 without a guess
+__global__ void k_mlp_guess_out(const float* y, const int32_t* ok, Workspace W) {
+  const int64_t n = W.counters->n_iface;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    W.mlp_out[i] = ok[i] ? fminf(fmaxf(y[i], 0.f), 1.f) : -1.f;
+}
+
+// forward over the interface list (n read on the device)
+__global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, Workspace W, float* y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  const int64_t n = W.counters->n_iface;
+  if ((int64_t)blockIdx.x * kRows >= n) return;
+  stage_weights(s, *w);
+  const int warp = threadIdx.x >> 5;
+  for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < n; row0 += (int64_t)gridDim.x * kRows) {
+    load_x(s, X, row0, n);
+    __syncthreads();
+    if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
+    __syncthreads();
+    for (int r = threadIdx.x; r < kRows; r += blockDim.x)
+      if (row0 + r < n) y[row0 + r] = s.y[r];
+    __syncthreads();
+  }
+}
+
+// ---- training: forward (tensor cores) + backward (FP32) for one tile, gradient partials --------
+struct TrainSmem {
+  Smem f;
+  float Z1[kRows * kH], Z2[kRows * kH], Z3[kRows * kH], H3[kRows * kH];
+  float dA[kRows * kH], dB[kRows * kH];
+  float dy[kRows];
+};
+
+// partial gradient of tile `blockIdx.x` (scaled by 1/batch) into part[tile][kNP]
+__global__ void __launch_bounds__(256) k_mlp_train_tile(WeightsBF16* w, const float* X, const float* t, int64_t n,
+                                                       float inv_batch, float* part, float* loss_part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
+  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+  stage_weights(s.f, *w);
+  load_x(s.f, X, row0, n);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp < kWarps) warp_forward(s.f, warp * 16, s.Z1, s.Z2, s.Z3, s.H3);
+  __syncthreads();
+  float* P = part + (size_t)blockIdx.x * kNP;
+  // output layer
+  if (threadIdx.x < kRows) {
+    const int64_t gr = row0 + threadIdx.x;
+    const float r = gr < n ? s.f.y[threadIdx.x] - t[gr] : 0.f;
+    s.dy[threadIdx.x] = 2.f * r * inv_batch;
+    s.f.y[threadIdx.x] = r * r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float l = 0;
+    for (int r = 0; r < kRows; ++r) l += s.f.y[r];
+    loss_part[blockIdx.x] = l;
+  }
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
+    float gw = 0;
+    for (int r = 0; r < kRows; ++r) gw = fmaf(s.H3[r * kH + c], s.dy[r], gw);
+    P[ow4 + c] = gw;
+  }
+  if (threadIdx.x == 0) {
+    float gb = 0;
+    for (int r = 0; r < kRows; ++r) gb += s.dy[r];
+    P[ob4] = gb;
+  }
+  // dZ3 = dy w4 gelu'(Z3)  -> dA
+  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
+    const int r = i / kH, c = i % kH;
+    s.dA[i] = s.dy[r] * s.f.w4[c] * gelu_grad(s.Z3[i]);
+  }
+  __syncthreads();
+  // layer 3 weights: dW3[n][k] = sum_r dZ3[r][n] H2[r][k]; db3
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const int nn = i / kH, k = i % kH;
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.H2[r * LDH + k]), acc);
+    P[oW3 + i] = acc;
+  }
+  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc += s.dA[r * kH + nn];
+    P[ob3 + nn] = acc;
+  }
+  // dZ2 = (dZ3 W3) gelu'(Z2) -> dB
+  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
+    const int r = i / kH, k = i % kH;
+    float acc = 0;
+    for (int nn = 0; nn < kH; ++nn) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.W3[nn * LDH + k]), acc);
+    s.dB[i] = acc * gelu_grad(s.Z2[i]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const int nn = i / kH, k = i % kH;
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dB[r * kH + nn], __bfloat162float(s.f.H1[r * LDH + k]), acc);
+    P[oW2 + i] = acc;
+  }
+  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc += s.dB[r * kH + nn];
+    P[ob2 + nn] = acc;
+  }
+  __syncthreads();
+  // dZ1 = (dZ2 W2) gelu'(Z1) -> dA
+  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
+    const int r = i / kH, k = i % kH;
+    float acc = 0;
+    for (int nn = 0; nn < kH; ++nn) acc = fmaf(s.dB[r * kH + nn], __bfloat162float(s.f.W2[nn * LDH + k]), acc);
+    s.dA[i] = acc * gelu_grad(s.Z1[i]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
+    const int nn = i / kIn, k = i % kIn;
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.X[r * LDX + k]), acc);
+    P[oW1 + i] = acc;
+  }
+  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
+    float acc = 0;
+    for (int r = 0; r < kRows; ++r) acc += s.dA[r * kH + nn];
+    P[ob1 + nn] = acc;
+  }
+}
+
+// BF16 copy of parameter p (index into the vector) written into the kernel layout.
+__device__ void to_bf16(WeightsBF16* w, int p, float v) {
+  if (p < ob1) w->W1[p / kIn][p % kIn] = __float2bfloat16_rn(v);
+  else if (p < oW2) w->b1[p - ob1] = v;
+  else if (p < ob2) w->W2[(p - oW2) / kH][(p - oW2) % kH] = __float2bfloat16_rn(v);
+  else if (p < oW3) w->b2[p - ob2] = v;
+  else if (p < ob3) w->W3[(p - oW3) / kH][(p - oW3) % kH] = __float2bfloat16_rn(v);
+  else if (p < ow4) w->b3[p - ob3] = v;
+  else if (p < ob4) w->w4[p - ow4] = bf16r(v);
+  else w->b4 = v;
+}
+
+__global__ void k_mlp_set_bf16(const float* params, WeightsBF16* w) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kNP; p += gridDim.x * blockDim.x) to_bf16(w, p, params[p]);
+  // zero padding of W1 (inputs 40..47)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kH * (kInPad - kIn); i += gridDim.x * blockDim.x)
+    w->W1[i / (kInPad - kIn)][kIn + i % (kInPad - kIn)] = __float2bfloat16_rn(0.f);
+}
+
+// Sums the tile partials in tile order (deterministic); grad_out gets the gradient, and with
+// lr > 0 an Adam step updates the FP32 master parameters and their BF16 copy.
+__global__ void k_mlp_reduce_adam(const float* part, int ntiles, const float* loss_part, float* params, float* m1,
+                                  float* m2, WeightsBF16* w, float lr, float b1t, float b2t, int64_t n, float* grad_out,
+                                  float* loss_out) {
+  const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kNP; p += gridDim.x * blockDim.x) {
+    float g = 0;
+    for (int tl = 0; tl < ntiles; ++tl) g += part[(size_t)tl * kNP + p];
+    if (grad_out) grad_out[p] = g;
+    if (lr > 0) {
+      const float a = beta1 * m1[p] + (1 - beta1) * g;
+      const float b = beta2 * m2[p] + (1 - beta2) * g * g;
+      m1[p] = a;
+      m2[p] = b;
+      const float v = params[p] - lr * (a / (1 - b1t)) / (sqrtf(b / (1 - b2t)) + eps);
+      params[p] = v;
+      to_bf16(w, p, v);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && loss_out) {
+    float l = 0;
+    for (int tl = 0; tl < ntiles; ++tl) l += loss_part[tl];
+    *loss_out = l / (float)n;
+  }
+}
+
+}  // namespace
+
+}  // namespace vof
+
+struct vof_mlp {
+  float *params = nullptr, *m1 = nullptr, *m2 = nullptr, *part = nullptr, *loss_part = nullptr, *y = nullptr;
+  vof::WeightsBF16* w = nullptr;
+  int64_t adam_t = 0;
+  int64_t y_cap = 0;
+};
 
 namespace vof {
 
 cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
-  (void)m;
-  (void)s;
-  return cudaErrorNotSupported;
+  vof_mlp* mlp = (vof_mlp*)m->mlp;
+  const int grid = m->num_sms * 2;
+  float* X = m->ws.mlp_x;
+  int32_t* ok = m->ws.mlp_ok;
+  k_mlp_features<<<grid, 128, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
+    attr = true;
+  }
+  k_mlp_forward_iface<<<grid, kRows * 2, sizeof(Smem), s>>>(mlp->w, X, m->ws, m->ws.mlp_y);
+  k_mlp_guess_out<<<grid, 256, 0, s>>>(m->ws.mlp_y, ok, m->ws);
+  return cudaGetLastError();
 }
 
 }  // namespace vof
+
+using namespace vof;
+
+extern "C" {
+
+vof_status vof_mlp_create(const float* h_params, vof_mlp** out) {
+  if (!h_params || !out) { set_error("null argument"); return VOF_EINVAL; }
+  *out = nullptr;
+  for (int p = 0; p < kNP; ++p)
+    if (!std::isfinite(h_params[p])) { set_error("non-finite MLP parameter"); return VOF_EINVAL; }
+  vof_mlp* m = new (std::nothrow) vof_mlp;
+  if (!m) { set_error("host allocation failed"); return VOF_ENOMEM; }
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMalloc(&m->params, kNP * sizeof(float));
+  e = e ? e : cudaMalloc(&m->m1, kNP * sizeof(float));
+  e = e ? e : cudaMalloc(&m->m2, kNP * sizeof(float));
+  e = e ? e : cudaMalloc(&m->part, (size_t)kMaxTiles * kNP * sizeof(float));
+  e = e ? e : cudaMalloc(&m->loss_part, kMaxTiles * sizeof(float));
+  e = e ? e : cudaMalloc(&m->w, sizeof(WeightsBF16));
+  e = e ? e : cudaMemcpy(m->params, h_params, kNP * sizeof(float), cudaMemcpyHostToDevice);
+  e = e ? e : cudaMemset(m->m1, 0, kNP * sizeof(float));
+  e = e ? e : cudaMemset(m->m2, 0, kNP * sizeof(float));
+  if (e == cudaSuccess) {
+    k_mlp_set_bf16<<<(kNP + 255) / 256, 256>>>(m->params, m->w);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    cudaFree(m->params); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->part); cudaFree(m->loss_part); cudaFree(m->w);
+    delete m;
+    return cuda_fail(e, "vof_mlp_create");
+  }
+  *out = m;
+  return VOF_OK;
+}
+
+vof_status vof_mlp_destroy(vof_mlp* m) {
+  if (!m) return VOF_EINVAL;
+  cudaFree(m->params); cudaFree(m->m1); cudaFree(m->m2); cudaFree(m->part); cudaFree(m->loss_part); cudaFree(m->w);
+  delete m;
+  return VOF_OK;
+}
+
+vof_status vof_mlp_get_params(vof_mlp* m, float* h_params) {
+  if (!m || !h_params) { set_error("null argument"); return VOF_EINVAL; }
+  cudaError_t e = cudaMemcpy(h_params, m->params, kNP * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_get_params");
+  return VOF_OK;
+}
+
+vof_status vof_mlp_forward(vof_mlp* m, const float* d_X, int64_t n, float* d_y, void* stream) {
+  if (!m || (n > 0 && (!d_X || !d_y)) || n < 0) { set_error("bad argument"); return VOF_EINVAL; }
+  if (n == 0) return VOF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
+  const int grid = (int)std::min<int64_t>((n + kRows - 1) / kRows, 1024);
+  k_mlp_forward<<<grid, kRows * 2, sizeof(Smem), s>>>(m->w, d_X, n, d_y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_forward");
+  return VOF_OK;
+}
+
+static vof_status train_impl(vof_mlp* m, const float* d_X, const float* d_t, int64_t n, float lr, float* d_grad,
+                             float* d_loss, cudaStream_t s) {
+  if (!m || !d_X || !d_t || n < 1 || n > kMaxBatch || !(lr >= 0)) { set_error("bad argument"); return VOF_EINVAL; }
+  const int ntiles = (int)((n + kRows - 1) / kRows);
+  cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(TrainSmem));
+  k_mlp_train_tile<<<ntiles, 256, sizeof(TrainSmem), s>>>(m->w, d_X, d_t, n, 1.0f / (float)n, m->part, m->loss_part);
+  float b1t = 1, b2t = 1;
+  if (lr > 0) {
+    m->adam_t += 1;
+    b1t = (float)std::pow(0.9, (double)m->adam_t);
+    b2t = (float)std::pow(0.999, (double)m->adam_t);
+  }
+  k_mlp_reduce_adam<<<(kNP + 255) / 256, 256, 0, s>>>(m->part, ntiles, m->loss_part, m->params, m->m1, m->m2, m->w, lr,
+                                                      b1t, b2t, n, d_grad, d_loss);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "mlp training kernels");
+  return VOF_OK;
+}
+
+vof_status vof_mlp_train_step(vof_mlp* m, const float* d_X, const float* d_t, int64_t n, float lr, float* d_loss,
+                              void* stream) {
+  if (!(lr > 0)) { set_error("learning rate must be positive"); return VOF_EINVAL; }
+  return train_impl(m, d_X, d_t, n, lr, nullptr, d_loss, (cudaStream_t)stream);
+}
+
+vof_status vof_mlp_grad(vof_mlp* m, const float* d_X, const float* d_t, int64_t n, float* d_grad, float* d_loss,
+                        void* stream) {
+  if (!d_grad) { set_error("null gradient buffer"); return VOF_EINVAL; }
+  return train_impl(m, d_X, d_t, n, 0.0f, d_grad, d_loss, (cudaStream_t)stream);
+}
+
+vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp) {
+  if (!mesh) { set_error("null mesh"); return VOF_EINVAL; }
+  Workspace& W = mesh->ws;
+  if (mlp && !W.mlp_x) {
+    const size_t nc = (size_t)mesh->n_cells;
+    cudaError_t e = cudaMalloc(&W.mlp_x, nc * kIn * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&W.mlp_ok, nc * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&W.mlp_y, nc * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "vof_mesh_set_mlp");
+    mesh->allocs.push_back(W.mlp_x);
+    mesh->allocs.push_back(W.mlp_ok);
+    mesh->allocs.push_back(W.mlp_y);
+  }
+  mesh->mlp = mlp;
+  return VOF_OK;
+}
+
+vof_status vof_mlp_features(vof_mesh* m, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream) {
+  if (!m || !d_alpha || !d_X || !d_ok) { set_error("null argument"); return VOF_EINVAL; }
+  if (!m->recon_done) { set_error("vof_mlp_features needs a reconstruction"); return VOF_ESTATE; }
+  k_mlp_features<<<m->num_sms * 2, 128, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, d_X, d_ok);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_features");
+  return VOF_OK;
+}
+
+}  // extern "C"

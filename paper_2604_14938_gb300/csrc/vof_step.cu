@@ -123,7 +123,7 @@ __global__ void k_begin(Counters* cn) {
   cn->n_iface = cn->n_band = cn->n_crossing = cn->n_uvert = 0;
   cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
   cn->evals_total = 0;
-  cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = 0;
+  cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
 }
 
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
@@ -380,6 +380,74 @@ __device__ __forceinline__ double liquid_volume(const TetRow* rows, int nt, int 
   return group_sum<G>(part, mask);
 }
 
+// FP32 rows in normalised values (u = (phi - lo)/(hi - lo), volumes / V): the same cubics on
+// the FP32 pipe, used only to refine the learned guess before the FP64 phase.
+struct TetRow32 {
+  float s0, s1, s2, s3, a2, b2, c2, d2, d1, d3, v;
+};
+
+__device__ __forceinline__ uint32_t okey32(float x) {
+  uint32_t b = __float_as_uint(x);
+  b = b == 0x80000000u ? 0u : b;
+  return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ void cswap32(uint32_t& ka, float& va, uint32_t& kb, float& vb) {
+  const bool sw = ka < kb;
+  const uint32_t tk = sw ? kb : ka;
+  kb = sw ? ka : kb;
+  ka = tk;
+  const float tv = sw ? vb : va;
+  vb = sw ? va : vb;
+  va = tv;
+}
+
+__device__ __forceinline__ TetRow32 tet_prepare32(float p0, float p1, float p2, float p3, float vt) {
+  uint32_t k0 = okey32(p0), k1 = okey32(p1), k2 = okey32(p2), k3 = okey32(p3);
+  cswap32(k0, p0, k1, p1);
+  cswap32(k2, p2, k3, p3);
+  cswap32(k0, p0, k2, p2);
+  cswap32(k1, p1, k3, p3);
+  cswap32(k1, p1, k2, p2);
+  const float d01 = p0 - p1, d02 = p0 - p2, d03 = p0 - p3, d12 = p1 - p2, d13 = p1 - p3, d23 = p2 - p3;
+  TetRow32 r;
+  r.s0 = p0; r.s1 = p1; r.s2 = p2; r.s3 = p3;
+  r.v = vt;
+  const float P1 = d01 * (d02 * d03), P3 = d03 * (d13 * d23), K = d02 * d03, EF = d12 * d13;
+  r.d1 = P1 > 0.f ? vt / P1 : 0.f;
+  r.d3 = P3 > 0.f ? vt / P3 : 0.f;
+  if (K > 0.f && EF > 0.f) {
+    const float vk = vt / K;
+    r.a2 = vk * (d01 * d01);
+    r.b2 = 3.f * vk * d01;
+    r.c2 = 3.f * vk;
+    r.d2 = -(vk / EF) * (d01 + d12 + d13);
+  } else {
+    r.a2 = r.b2 = r.c2 = r.d2 = 0.f;
+  }
+  return r;
+}
+
+template <int G>
+__device__ __forceinline__ float liquid_volume32(const TetRow32* rows, int nt, int lane, unsigned mask, float u) {
+  const uint32_t kc = okey32(u);
+  float part = 0.f;
+  for (int t = lane; t < nt; t += G) {
+    const TetRow32& r = rows[t];
+    const int k = (okey32(r.s0) >= kc) + (okey32(r.s1) >= kc) + (okey32(r.s2) >= kc) + (okey32(r.s3) >= kc);
+    const float ref = k == 1 ? r.s0 : (k == 2 ? r.s1 : r.s3);
+    const float A = k == 2 ? r.a2 : (k >= 3 ? r.v : 0.f);
+    const float B = k == 2 ? r.b2 : 0.f;
+    const float C = k == 2 ? r.c2 : 0.f;
+    const float D = k == 1 ? r.d1 : (k == 2 ? r.d2 : (k == 3 ? r.d3 : 0.f));
+    const float x = ref - u;
+    part += fmaf(fmaf(fmaf(D, x, C), x, B), x, A);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(mask, part, o);
+  return part;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
                                                    int max_ct, int learned) {
@@ -391,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
   TetRow* rows = reinterpret_cast<TetRow*>(smem) + (size_t)gib * max_ct;
   const int64_t n_iface = W.counters->n_iface;
   const int64_t n_groups = (int64_t)gridDim.x * kGroups;
-  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, sect_acc = 0;
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, sect_acc = 0, ev32_acc = 0;
   // cells interleaved over blocks first, so that a short list still spreads over every SM
   for (int64_t i = (int64_t)gib * gridDim.x + blockIdx.x; i < n_iface; i += n_groups) {
     const int32_t cell = W.iface_idx[i];
@@ -418,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     const double a = alpha[cell];
     const double V = M.cell_vol[cell];
     const double invV = 1.0 / V;
-    int status = 0, evals = 0;
+    int status = 0, evals = 0, evals32 = 0;
     double c_best;
     if (hi - lo < 1e-14) {
       status = VOF_ST_DEGENERATE;
@@ -430,37 +498,81 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       double L = lo, H = hi;
       bool done = false;
       if (learned) {
-        // learned guess (normalised position in the range) + secant steps, then bracketed bisection
-        const float t = W.mlp_out[i];
-        if (t >= 0.0f) {
-          double c1 = lo + (double)t * (hi - lo);
-          c1 = fmin(fmax(c1, lo), hi);
+        // Learned path: MLP guess u0 of the normalised position u = (c - lo)/(hi - lo); FP32
+        // refinement of u (regula falsi with the Illinois modification, on FP32 tetrahedron rows
+        // in normalised values); then the FP64 phase: evaluations at the refined guess and at a
+        // second point next to it, at most max_secant secant steps, and bisection inside the
+        // bracket found so far as the counted fallback.
+        const float u0 = W.mlp_out[i];
+        if (u0 >= 0.0f) {
+          TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
+          const double range = hi - lo, irange = 1.0 / range;
+          for (int t = lane; t < nt; t += G) {
+            const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+            rows32[t] = tet_prepare32((float)((p_apex - lo) * irange), (float)((W.phi_v[cv[pk & 255]] - lo) * irange),
+                                      (float)((W.phi_v[cv[(pk >> 8) & 255]] - lo) * irange),
+                                      (float)((W.phi_v[cv[(pk >> 16) & 255]] - lo) * irange),
+                                      (float)(__ldg(M.tet_vol + t0 + t) * invV));
+          }
+          __syncwarp(mask);
+          const float af = (float)a;
+          float ua = 0.f, fa = 1.f - af, ub = 1.f, fb = -af;  // f(ua) > 0 > f(ub)
+          float uc = fminf(fmaxf(u0, 0.f), 1.f);
+          float fc = liquid_volume32<G>(rows32, nt, lane, mask, uc) - af;
+          ++evals32;
+          int side = 0;
+          for (int it = 0; it < 16; ++it) {
+            if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
+            if (fabsf(fc) < 2e-6f || ub - ua < 4e-6f) break;
+            // regula falsi step; Illinois: halve the retained end's value after two steps on one side
+            if (it == 0) {
+              const float step = 0.02f;  // probe next to the guess, towards the root
+              uc = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
+            } else {
+              uc = ua + (ub - ua) * (fa / (fa - fb));
+              if (!(uc > ua && uc < ub)) uc = 0.5f * (ua + ub);
+            }
+            fc = liquid_volume32<G>(rows32, nt, lane, mask, uc) - af;
+            ++evals32;
+            const int s2 = fc > 0.f ? 1 : -1;
+            if (s2 == side) {
+              if (s2 > 0) fb *= 0.5f; else fa *= 0.5f;
+            }
+            side = s2;
+          }
+          const float ubest = fabsf(fa) < fabsf(fb) ? ua : ub;
+          __syncwarp(mask);
+          for (int t = lane; t < nt; t += G) {
+            const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+            rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]], W.phi_v[cv[(pk >> 16) & 255]],
+                                  __ldg(M.tet_vol + t0 + t));
+          }
+          __syncwarp(mask);
+          // FP64 phase
+          double c1 = fmin(fmax(lo + (double)ubest * range, lo), hi);
           double f1 = liquid_volume<G>(rows, nt, lane, mask, c1) * invV - a;
           ++evals;
           if (fabs(f1) < f_best) { f_best = fabs(f1); c_best = c1; }
-          if (f1 > 0) L = c1; else H = c1;
+          if (f1 > 0) L = fmax(L, c1); else H = fmin(H, c1);
           if (fabs(f1) <= opt.tol_alpha) done = true;
-          // second point: a small step towards the root inside the bracket
-          double c0 = c1, f0 = f1;
           if (!done && opt.max_secant > 0) {
-            const double step = 1e-3 * (hi - lo);
-            double c2 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
-            double f2 = liquid_volume<G>(rows, nt, lane, mask, c2) * invV - a;
+            const double step = fmax(4e-6, (double)(ub - ua)) * range;
+            double c0 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+            double f0 = liquid_volume<G>(rows, nt, lane, mask, c0) * invV - a;
             ++evals;
-            if (fabs(f2) < f_best) { f_best = fabs(f2); c_best = c2; }
-            if (f2 > 0) L = fmax(L, c2); else H = fmin(H, c2);
-            if (fabs(f2) <= opt.tol_alpha) done = true;
-            c0 = c2; f0 = f2;
-            for (int s = 0; s < opt.max_secant && !done; ++s) {
+            if (fabs(f0) < f_best) { f_best = fabs(f0); c_best = c0; }
+            if (f0 > 0) L = fmax(L, c0); else H = fmin(H, c0);
+            if (fabs(f0) <= opt.tol_alpha) done = true;
+            for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
               if (f0 == f1) break;
-              double c3 = c0 - f0 * (c0 - c1) / (f0 - f1);
-              if (!(c3 > L && c3 < H)) c3 = 0.5 * (L + H);
-              const double f3 = liquid_volume<G>(rows, nt, lane, mask, c3) * invV - a;
+              double c2 = c0 - f0 * (c0 - c1) / (f0 - f1);
+              if (!(c2 > L && c2 < H)) c2 = 0.5 * (L + H);
+              const double f2 = liquid_volume<G>(rows, nt, lane, mask, c2) * invV - a;
               ++evals;
-              if (fabs(f3) < f_best) { f_best = fabs(f3); c_best = c3; }
-              if (f3 > 0) L = fmax(L, c3); else H = fmin(H, c3);
-              if (fabs(f3) <= opt.tol_alpha) done = true;
-              c1 = c0; f1 = f0; c0 = c3; f0 = f3;
+              if (fabs(f2) < f_best) { f_best = fabs(f2); c_best = c2; }
+              if (f2 > 0) L = fmax(L, c2); else H = fmin(H, c2);
+              if (fabs(f2) <= opt.tol_alpha) done = true;
+              c1 = c0; f1 = f0; c0 = c2; f0 = f2;
             }
           }
           if (!done) status |= VOF_ST_FALLBACK;
@@ -523,6 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       W.x_gamma[3 * cell + 1] = mom.y * ia;
       W.x_gamma[3 * cell + 2] = mom.z * ia;
       evals_acc += evals;
+      ev32_acc += evals32;
       tetev_acc += (int64_t)evals * nt;
       prep_acc += nt;
       if (status & VOF_ST_DEGENERATE) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
@@ -536,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     atomicAdd((unsigned long long*)&W.counters->evals_total, (unsigned long long)evals_acc);
     atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
     atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
+    if (ev32_acc) atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
   }
   if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
 }
@@ -817,6 +931,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   }
   Workspace& W = m->ws;
   const MeshView& M = m->view;
+  W.alpha_in = d_alpha;
   Timing& tm = m->timing;
   tm.start(KC_SELECT, s);
   k_begin<<<1, 1, 0, s>>>(W.counters);

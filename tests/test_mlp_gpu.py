@@ -86,7 +86,7 @@ def test_training_reduces_loss():
 def test_features_match_definition():
     m, a, T, Tb = case("voronoi_film")
     M, g = gpu_step(m, a, T, Tb)
-    F, ok = M.mlp_features()
+    F, ok = M.mlp_features(torch.as_tensor(a, dtype=torch.float64, device="cuda"))
     F, ok = F.cpu().numpy(), ok.cpu().numpy()
     O = oracle.Oracle(m)
     I = g["iface_idx"]
@@ -134,7 +134,8 @@ def test_learned_root_meets_the_bar_with_fewer_evaluations(trained, name):
             continue
         assert abs(O.liquid_volume(c, gl["phi_v"], gl["iso"][c])["VL"] / V[c] - a[c]) <= 1e-10
     assert gl["counts"]["n_not_converged"] == 0
-    assert gl["counts"]["evals_total"] < gb["counts"]["evals_total"]
+    # FP64 evaluations: the learned path needs far fewer than bisection
+    assert gl["counts"]["evals_total"] < 0.5 * gb["counts"]["evals_total"]
     r = O.run(a, T, Tb, synth.PROPS)
     ref = r["pc"]["mdot"]
     err = np.abs(gl["mdot"] - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
