@@ -232,6 +232,22 @@ vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp);
  * d_alpha: d_X [n_iface][40], d_ok [n_iface] (1 where the cell has features). */
 vof_status vof_mlp_features(vof_mesh* mesh, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream);
 
+/* ---- totals without allocation (no counterpart in the paper: a variant of the totals step) ----
+ * Some callers cannot allocate device memory where they need the totals: code that runs while
+ * its stream is being captured into a CUDA graph, real-time loops that must not enter an
+ * allocator, hosts that hand out all device memory from their own pool. vof_totals_static
+ * computes the same pairwise-tree sums as the d_totals of vof_phase_change_source,
+ * d_totals[0] = sum d_a[i], d_totals[1] = sum d_b[i] (i < n, zero-padded to a power of two, pairs
+ * summed level by level), over caller-supplied device arrays (e.g. mdot V and Q V of the interface
+ * cells in cell order). It allocates nothing: its chunk sums live in a 32 KB file-scope device
+ * array that every GPU loading the library holds until exit. The first call made with a device
+ * current looks up that array's address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. Every call shares the array and zeroes its block counter before launching, so
+ * calls that overlap on the GPU (two streams, or two host threads) race; order them on one stream.
+ * n > VOF_TOTALS_STATIC_MAX_N returns VOF_EINVAL. */
+#define VOF_TOTALS_STATIC_MAX_N 4194304
+vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, double* d_totals, void* stream);
+
 /* Per-kernel device time, measured with pairs of CUDA events recorded on the launch stream
  * around each kernel group (off by default; measurement support, not part of the method).
  * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
