@@ -37,62 +37,124 @@ L2_FLUSH_BYTES = 256 << 20
 KERNELS_PER_STEP = 12
 
 
+def _spheres(rng, k):
+    """k non-overlapping spheres with R ~ U[0.05, 0.2] inside the unit box."""
+    out = []
+    while len(out) < k:
+        R = rng.uniform(0.05, 0.2)
+        c = rng.uniform(R, 1 - R, 3)
+        if all(np.linalg.norm(c - np.array(o[:3])) > R + o[3] for o in out):
+            out.append((float(c[0]), float(c[1]), float(c[2]), float(R)))
+    return out
+
+
 def workload(name: str):
+    """(mesh or list of meshes, alpha, T, T_bnd, description, extra)."""
     import synth
     if name == "film250k":
         m = synth.voronoi_bcc(50, jitter=0.25, seed=1)
         reg = dict(type="film", z0=0.3, a=0.03)
         a = synth.alpha(m, reg, mode="subtet", level=3)
         T, Tb = synth.temperature(m, reg, dict(kind="film", dT=10.0))
-        desc = "jittered-BCC Voronoi 2x50^3=250k cells (seed 1, +-h/4), wavy film z<0.3+0.03sin(2pi x)sin(2pi y)"
-    elif name == "sphere32":
+        return m, a, T, Tb, ("jittered-BCC Voronoi 2x50^3=250k cells (seed 1, +-h/4), wavy film "
+                             "z<0.3+0.03sin(2pi x)sin(2pi y), T linear to T_sat+10 K at the wall"), {}
+    if name == "sphere32":
         m = synth.hex_box(32)
         reg = dict(type="spheres", spheres=[(0.5, 0.5, 0.5, 0.25)])
         a = synth.alpha(m, reg, mode="hexgrid", level=3)
         T, Tb = synth.temperature(m, reg, dict(kind="radial", dT=5.0))
-        desc = "hex 32^3 unit cube, vapour sphere R=0.25 at the centre, alpha from 8^3 samples"
-    else:
-        raise SystemExit(f"unknown workload {name}")
-    return m, a, T, Tb, desc
+        return m, a, T, Tb, "hex 32^3 unit cube, vapour sphere R=0.25 at the centre, alpha from 8^3 samples", {}
+    if name == "batch64":
+        rng = np.random.default_rng(3)
+        meshes, As, Ts, Tbs, kinds = [], [], [], [], []
+        for i in range(64):
+            size = float(np.exp(rng.uniform(np.log(8e3), np.log(5e5))))
+            kind = ["hex", "tet", "prism", "voronoi"][int(rng.integers(0, 4))]
+            if kind == "hex":
+                m = synth.hex_box(max(2, round(size ** (1 / 3))))
+            elif kind == "tet":
+                m = synth.tet_box(max(2, round((size / 6) ** (1 / 3))))
+            elif kind == "prism":
+                m = synth.prism_box(max(2, round((size / 2) ** (1 / 3))))
+            else:
+                m = synth.voronoi_bcc(max(2, round((size / 2) ** (1 / 3))), seed=int(rng.integers(0, 2 ** 31)))
+            reg = dict(type="spheres", spheres=_spheres(rng, int(rng.integers(1, 7))))
+            a = synth.alpha(m, reg, mode="hexgrid" if kind == "hex" else "subtet", level=3 if kind == "hex" else 2)
+            T, Tb = synth.temperature(m, reg, dict(kind="radial", dT=5.0))
+            meshes.append(m); As.append(a); Ts.append(T); Tbs.append(Tb); kinds.append(kind)
+        return (meshes, np.concatenate(As), np.concatenate(Ts), np.concatenate(Tbs),
+                f"64 meshes (seed 3), sizes log-uniform 8k-500k cells ({sum(m.n_cells for m in meshes)} cells), "
+                "kinds uniform over hex/Kuhn-tet/prism/jittered-BCC Voronoi, 1-6 spheres R~U[0.05,0.2], radial T",
+                {"kinds": {k: kinds.count(k) for k in set(kinds)}})
+    if name == "pipe8m":
+        m = synth.pipe(spacing=0.01537, layers=600, radius=1.0, length=6.0, seed=5)
+        reg = dict(type="pipe", r0=0.9, a=0.04, lam=0.5, t=0.0)
+        a = synth.alpha(m, reg, mode="subtet", level=2)
+        T, Tb = synth.temperature(m, reg, dict(kind="pipe", dT=8.0, radius=1.0))
+        return m, a, T, Tb, ("extruded jittered 2D Voronoi disk (radius 1, 600 layers over length 6, "
+                             f"{m.n_cells} cells), wall film r > 0.9 - 0.04 sin(2pi(z-t)/0.5) moving one layer "
+                             "(dz = 0.01 = phase velocity x dt) per step, T_sat+8 K at the wall"), {"layers": 600}
+    raise SystemExit(f"unknown workload {name}")
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 50 ms) kept only inside the marked timed window."""
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.index), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # the sampler is up before the timed window opens
         except OSError:
             self.proc = None
         return self
 
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
         self.out = ""
         if self.proc:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.out = self.proc.communicate(timeout=5)[0]
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    @staticmethod
+    def _ts(field):
+        try:
+            return time.mktime(time.strptime(field.split(".")[0], "%Y/%m/%d %H:%M:%S")) + \
+                float("0." + field.split(".")[1]) if "." in field else 0.0
+        except (ValueError, IndexError):
+            return None
+
     def summary(self):
         rows = [r.split(", ") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        t0, t1 = (self.t0 or 0.0) - 0.05, (self.t1 or 1e30) + 0.05
+        inside = [r for r in rows if (lambda t: t is not None and t0 <= t <= t1)(self._ts(r[0]))]
+        use = inside or rows
+        sm = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": float(rows[0][2]),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for r in use for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": float(use[0][2]),
+                "reasons": reasons, "samples": len(inside),
+                "window_s": round((self.t1 or 0) - (self.t0 or 0), 3)}
 
 
 def run_ours(args, rank, world, dev):
@@ -100,88 +162,139 @@ def run_ours(args, rank, world, dev):
     import paper_2604_14938_gb300 as vof
     import synth
 
-    m, a, T, Tb, desc = workload(args.workload)
-    M = vof.Mesh(m)
-    d = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
-    ta, tT, tTb = d(a), d(T), d(Tb)
-    mdot = torch.empty(m.n_cells, dtype=torch.float64, device=dev)
-    Q = torch.empty_like(mdot)
-    tot = torch.empty(2, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream()
-    learned_ok = False
-    if args.root in ("auto", "learned"):
-        learned_ok = hasattr(vof, "load_default_mlp") and vof.load_default_mlp(M)
-    modes = ["bisect"] + (["learned"] if learned_ok else [])
+    meshes, a, T, Tb, desc, extra = workload(args.workload)
+    batch = isinstance(meshes, list)
+    if batch:
+        B = vof.Batch(meshes)
+        M = B.mesh
+    else:
+        B, M = None, vof.Mesh(meshes)
+    nc = M.n_cells
+    pipe = args.workload == "pipe8m"
+    stream = torch.cuda.Stream(device=dev)
     results = {}
-    for mode in modes:
-        opt = vof.default_options(root_mode=vof.ROOT_LEARNED if mode == "learned" else vof.ROOT_BISECT)
+    with torch.cuda.stream(stream):
+        d = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
+        if pipe:
+            # 100 device-resident steps: the film translates one layer (n2d cells) per step
+            n2d = nc // extra["layers"]
+            ta_k = [d(np.roll(a, k * n2d)) for k in range(100)]
+            tT_k = [d(np.roll(T, k * n2d)) for k in range(100)]
+            tTb = None
+        else:
+            ta_k, tT_k, tTb = [d(a)], [d(T)], d(Tb)
+        mdot = torch.empty(nc, dtype=torch.float64, device=dev)
+        Q = torch.empty_like(mdot)
+        tot = torch.empty(2, dtype=torch.float64, device=dev)
+        btot = torch.empty((B.n, 2), dtype=torch.float64, device=dev) if batch else None
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        learned_ok = args.root in ("auto", "learned") and vof.load_default_mlp(M)
+        modes = (["bisect"] if args.root != "learned" else []) + (["learned"] if learned_ok else [])
+        tuned = {}
+        for mode in modes:
+            opt = vof.default_options(root_mode=vof.ROOT_LEARNED if mode == "learned" else vof.ROOT_BISECT)
+            tuned[mode] = M.autotune(ta_k[0], opt, reps=3)  # lanes per cell of each bin, for this mode
+
+            def one(k):
+                ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
+                if pipe:  # a different input pair every step: eager launches
+                    M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt, stream=stream)
+                else:
+                    M.step_graph(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt, stream=stream)
+                if batch:
+                    B.totals(btot, stream=stream)
+
+            for k in range(args.warmup):
+                one(k)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            iface = []
+            with Clocks(torch.cuda.current_device()) as clk:
+                clk.start()
+                for k, (s0, e0) in enumerate(ev):
+                    flush.fill_(k & 0xFF)  # write > L2 between steps (outside the events)
+                    s0.record(stream)
+                    one(k)
+                    e0.record(stream)
+                    if pipe:
+                        iface.append(M.counts(stream=stream)["n_iface"])  # after the step's events
+                stream.synchronize()
+                clk.stop()
+            if world > 1:
+                torch.distributed.barrier()
+            ms = sum(s0.elapsed_time(e0) for s0, e0 in ev)
+            cnt = M.counts(stream=stream)
+            units = sum(iface) if pipe else cnt["n_iface"] * args.steps
+            # one more pass, eager with per-kernel events, for the kernel times of the roofline
+            M.timing_enable(True)
+            for k in range(min(args.steps, 5)):
+                opt_e = opt
+                ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
+                M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt_e, stream=stream)
+            kt = M.timing_read(stream=stream)
+            M.timing_enable(False)
+            kcnt = M.counts(stream=stream)
+            results[mode] = dict(ms=ms, units=units, counts=cnt, kcounts=kcnt, ktime=kt, clocks=clk.summary())
+        # end to end: host buffers through vof_step_host, copies inside the timed region
+        opt_best = vof.default_options(root_mode=vof.ROOT_LEARNED if "learned" in results else vof.ROOT_BISECT)
+        pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
+        ha, hT = pin(a), pin(T)
+        hTb = None if pipe else pin(Tb)
+        hm = torch.empty(nc, dtype=torch.float64).pin_memory()
+        ht = torch.empty(2, dtype=torch.float64).pin_memory()
         for _ in range(args.warmup):
-            M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        M.timing_enable(True)
-        with Clocks(torch.cuda.current_device()) as clk:
-            for s, e in ev:
-                flush.fill_(s.__hash__() & 0xFF)  # write > L2 between steps (outside the events)
-                s.record(stream)
-                M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt)
-                e.record(stream)
-            torch.cuda.synchronize()
-        kt = M.timing_read()
-        M.timing_enable(False)
-        if world > 1:
-            torch.distributed.barrier()
-        ms = sum(s.elapsed_time(e) for s, e in ev)
-        cnt = M.counts()
-        results[mode] = dict(ms=ms, counts=cnt, ktime=kt, clocks=clk.summary())
-    # end to end: host buffers through the host-buffer ABI call, copies inside the timed region
-    opt_best = vof.default_options(root_mode=vof.ROOT_LEARNED if "learned" in results else vof.ROOT_BISECT)
-    pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
-    ha, hT, hTb = pin(a), pin(T), pin(Tb)
-    hm = torch.empty(m.n_cells, dtype=torch.float64).pin_memory()
-    ht = torch.empty(2, dtype=torch.float64).pin_memory()
-    for _ in range(args.warmup):
-        M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best)
-    e2e_s = time.perf_counter() - t0
-    return m, (a, T, Tb), desc, results, e2e_s, M
+            M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best, stream=stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best, stream=stream)
+        e2e_s = time.perf_counter() - t0
+        e2e_units = M.counts(stream=stream)["n_iface"] * args.steps
+    info = dict(n_cells=nc, batch=batch, pipe=pipe, tuned=tuned, extra=extra, e2e_units=e2e_units,
+                h2d=8 * (2 * nc + (0 if pipe else M.n_faces)), d2h=8 * (nc + 2))
+    return M, (meshes, a, T, Tb), desc, results, e2e_s, info
 
 
 def cpu_baseline(m, a, T, Tb, budget_s=12.0):
-    """The oracle as it stands on the host cores: vertex field + bisection reconstruction on a
-    prefix sample of the interface cells + the downstream steps, timed with perf_counter."""
+    """The oracle as it stands on the host cores: vertex field, bisection reconstruction of a prefix
+    sample of the interface cells (OpenMP over cells), the downstream steps over the whole mesh;
+    repeated to about budget_s seconds of work, timed with perf_counter."""
     import oracle
     import synth
 
     O = oracle.Oracle(m)
     O.geometry()  # mesh geometry is set-up work, as on the GPU
+
+    def once(cells):
+        phi = O.vertex_field(a)
+        rec = O.reconstruct(a, phi, cells=cells)
+        O.phase_change(a, rec, T, Tb, synth.PROPS)
+
     I = np.where((a > 1e-12) & (a < 1 - 1e-12))[0]
     n = min(len(I), 256)
     while True:
         t0 = time.perf_counter()
-        phi = O.vertex_field(a)
-        rec = O.reconstruct(a, phi, cells=I[:n])
-        O.phase_change(a, rec, T, Tb, synth.PROPS)
+        once(I[:n])
         dt = time.perf_counter() - t0
-        if n >= len(I) or dt > budget_s / 3:
+        if n >= len(I) or dt > budget_s / 4:
             break
-        n = min(len(I), int(n * max(2.0, budget_s / 3 / max(dt, 1e-3))))
+        n = min(len(I), int(n * max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        once(I[:n])
+    dt = (time.perf_counter() - t0) / reps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return dict(value=n / dt, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"{n} of {len(I)} interface cells (index-order prefix) reconstructed by FP64 bisection, "
-                       f"vertex field and downstream steps over the whole mesh; {dt:.2f} s"), n, dt
+                       f"vertex field and downstream steps over the whole mesh; {reps} repetitions, {dt:.2f} s each"), n, dt
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="film250k")
@@ -195,7 +308,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        m, a, T, Tb, desc = workload(args.workload)
+        m, a, T, Tb, desc, _ = workload(args.workload)
+        if isinstance(m, list):
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers single-mesh workloads"}))
+            return
         times, units = [], []
         base, n, dt = cpu_baseline(m, a, T, Tb, budget_s=6.0)
         import oracle
@@ -225,7 +341,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    m, fields, desc, res, e2e_s, M = run_ours(args, rank, world, dev)
+    M, fields, desc, res, e2e_s, info = run_ours(args, rank, world, dev)
     best = "learned" if "learned" in res else "bisect"
     r = res[best]
     n_iface = r["counts"]["n_iface"]
@@ -235,39 +351,49 @@ def main():
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_max = float(t.item())
-    value = world * n_iface * args.steps / (ms_max / 1e3)
-    # roofline of the dominant kernel (root search + geometry): algorithmic FP64 flops per launch
-    root_ms, root_n = r["ktime"]["root"]
-    c = r["counts"]
-    flops = M.root_flops(c)  # counters hold the last step, i.e. one launch of the root kernel
-    achieved = flops / (root_ms / root_n / 1e3) / 1e12 if root_n and flops else None
-    share = {k: round(v[0] / max(sum(x[0] for x in r["ktime"].values()), 1e-30), 4) for k, v in r["ktime"].items()}
+    value = world * r["units"] / (ms_max / 1e3)
+    # roofline of the dominant kernel (root search + geometry): algorithmic FP64 flops per launch,
+    # from the device counters of the same step whose kernel time the events measured
+    # per step: the eager timing pass records one selection group per step and one root-search
+    # launch per non-empty bin (bins run as parallel branches: their launch times are summed)
+    nst = max(r["ktime"]["select"][1], 1)
+    root_ms = r["ktime"]["root"][0] / nst
+    flops = M.root_flops(r["kcounts"])
+    achieved = flops / (root_ms / 1e3) / 1e12 if root_ms and flops else None
+    ksum = sum(v[0] for v in r["ktime"].values())
+    share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
+    nbins = sum(1 for c in M.bin_cells if c)  # root search and geometry launch once per non-empty bin
+    per_step = 13 + 2 * nbins + (3 if best == "learned" else 0) + (1 if info["batch"] else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n_cells": m.n_cells, "n_iface": n_iface,
-                   "root": best, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "paths": {k: {"value": world * v["counts"]["n_iface"] * args.steps / (v["ms"] / 1e3),
-                      "ms_per_step": v["ms"] / args.steps,
+        "config": {"workload": args.workload, "description": desc, "n_cells": info["n_cells"], "n_iface": n_iface,
+                   "root": best, "group_sizes_by_bin": info["tuned"][best],
+                   "step": "eager launches per step" if info["pipe"] else "CUDA graph replay",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single", **info["extra"]},
+        "paths": {k: {"value": world * v["units"] / (v["ms"] / 1e3), "ms_per_step": v["ms"] / args.steps,
                       "evals_per_cell": v["counts"]["evals_total"] / max(v["counts"]["n_iface"], 1),
-                      "fallbacks": v["counts"]["n_fallback"], "not_converged": v["counts"]["n_not_converged"]}
+                      "fp32_evals_per_cell": v["counts"]["evals32_total"] / max(v["counts"]["n_iface"], 1),
+                      "fallbacks": v["counts"]["n_fallback"], "not_converged": v["counts"]["n_not_converged"],
+                      "mlp_skipped": v["counts"]["n_mlp_skipped"], "group_sizes_by_bin": info["tuned"][k]}
                   for k, v in res.items()},
-        "kernel_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in r["ktime"].items() if v[1]},
+        "kernel_ms_per_step": {k: v[0] / nst for k, v in r["ktime"].items() if v[1]},
         "kernel_share": share,
-        "roofline": {"kernel": "k_root (isovalue root search + interface geometry)", "bound": "alu",
-                     "flops_per_launch": flops, "flops_per_iface_cell": flops / max(n_iface, 1),
+        "roofline": {"kernel": "k_root (isovalue root search; FP64 part)", "bound": "alu",
+                     "flops_per_launch": flops, "flops_per_iface_cell": flops / max(r["kcounts"]["n_iface"], 1),
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                     "peak_source": "FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (2 FMA), no FP64 figure in the measured peaks"},
-        "e2e": {"value": world * n_iface * args.steps / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": 8 * (2 * m.n_cells + m.n_faces), "d2h_bytes_per_step": 8 * (m.n_cells + 2)},
-        "gpu_launches": args.steps * (KERNELS_PER_STEP + (1 if best == "learned" else 0)),
+                     "peak_source": "FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (2 FMA); no FP64 figure in the "
+                                    "measured peaks (an FMA-chain probe measured 1.20 TFLOP/s)"},
+        "e2e": {"value": world * info["e2e_units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
+                "d2h_bytes_per_step": info["d2h"]},
+        "gpu_launches": args.steps * per_step,
         "clocks": r["clocks"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, _, _ = cpu_baseline(m, *fields)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not info["batch"]:
+        cb, _, _ = cpu_baseline(fields[0], fields[1], fields[2], None if info["pipe"] else fields[3])
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))

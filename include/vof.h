@@ -144,6 +144,39 @@ vof_status vof_step_host(vof_mesh* mesh, const double* h_alpha, const double* h_
                          const vof_props* props, const vof_options* opt, double* h_mdot, double* h_totals,
                          void* stream);
 
+/* vof_step replayed as a CUDA graph on a non-default stream: the first call, and any call whose
+ * pointers, properties, options or tuned group sizes differ from the captured ones, captures
+ * the whole step on the stream (relaxed capture mode) and instantiates it; other calls launch
+ * the graph. Same arguments and results as vof_step. Kernel timing is not recorded inside it. */
+vof_status vof_step_graph(vof_mesh* mesh, const double* d_alpha, const double* d_T, const double* d_T_bnd,
+                          const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q, double* d_totals,
+                          void* stream);
+
+/* Interface cells are binned by tetrahedron count ([1,4], [5,8], [9,24], [25,64], [65,192]); each
+ * bin's root search runs with its own lanes per cell G. vof_autotune reconstructs with d_alpha,
+ * then times the root search of every populated bin with G = 1, 2, 4, 8, 16, 32 (reps launches
+ * each, CUDA events) and keeps the fastest per bin; synchronises; h_G_out [5] (may be NULL) gets
+ * the choice (0 for empty bins). The choice applies when opt->group_size is 0.
+ * vof_set_group_sizes sets it directly (0 = the built-in default for that bin). */
+vof_status vof_autotune(vof_mesh* mesh, const double* d_alpha, const vof_options* opt, int reps, int* h_G_out,
+                        void* stream);
+vof_status vof_set_group_sizes(vof_mesh* mesh, const int* h_G);
+
+/* ---- batches of independent meshes (spec: many meshes of uneven size and cell type in one
+ * launch) ----
+ * A batch is the disjoint union of n meshes: cells, faces and vertices renumbered with the offsets
+ * vof_batch_offsets returns (host arrays of n + 1). vof_batch_mesh gives the union mesh, stepped
+ * like any mesh (vof_step, vof_step_graph; alpha, T, T_bnd, mdot, Q concatenated in mesh order).
+ * vof_batch_totals writes d_totals [n][2] = {sum mdot V, sum Q V} per mesh for the last step: the
+ * pairwise tree over each mesh's interface cells, as a single-mesh step computes it (at most 4.2 M
+ * interface cells per mesh). vof_batch_create synchronises. */
+typedef struct vof_batch vof_batch;
+vof_status vof_batch_create(const vof_mesh_desc* descs, int n_meshes, void* stream, vof_batch** out);
+vof_status vof_batch_destroy(vof_batch* batch);
+vof_status vof_batch_mesh(vof_batch* batch, vof_mesh** out);
+vof_status vof_batch_offsets(const vof_batch* batch, int64_t* h_cells, int64_t* h_faces, int64_t* h_verts);
+vof_status vof_batch_totals(vof_batch* batch, double* d_totals, void* stream);
+
 /* Workspace fields, copied with vof_copy_field into caller device memory (count = elements). */
 typedef enum {
   VOF_F_IFACE_IDX = 0, /* int32 [n_iface]: interface cells in increasing cell order */
@@ -195,6 +228,11 @@ vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
 
 /* Mesh sizes and limits: n_cells, n_faces, n_verts, max vertices per cell, max tets per cell. */
 vof_status vof_mesh_info(const vof_mesh* mesh, int64_t* out5);
+
+/* Cells of the mesh per tetrahedron-count bin (1-4, 5-8, 9-24, 25-64, 65-192 tetrahedra):
+ * a step launches the root search and the geometry once for every non-empty bin. Host array of 5.
+ * No counterpart in the paper (launch layout of this implementation). */
+vof_status vof_mesh_bins(const vof_mesh* mesh, int64_t* cells5);
 
 /* ---- learned isovalue guess (the benchmark spec's learned part; the paper fixes no such model) ----
  * A 40 -> 64 -> 64 -> 64 -> 1 GELU MLP predicting the normalised isovalue position
@@ -253,8 +291,8 @@ vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, do
  * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
  * vof_timing_read synchronises the stream and returns, per kernel class, the summed
  * milliseconds and the launch count since the last read (at most 8192 records are kept).
- * Classes: 0 selection, 1 vertex field, 2 root search + geometry, 3 least squares,
- * 4 per-side gradients + source, 5 totals, 6 learned guess. */
+ * Classes: 0 selection, 1 vertex field, 2 root search, 3 least squares, 4 per-side
+ * gradients + source, 5 totals, 6 learned guess, 7 interface geometry. */
 vof_status vof_timing_enable(vof_mesh* mesh, int on);
 vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
 

@@ -74,7 +74,7 @@ def lib():
             "vof_mesh_create": [vp, vp, vp], "vof_mesh_destroy": [vp], "vof_reconstruct": [vp, vp, vp, vp],
             "vof_phase_change_source": [vp] * 10, "vof_step": [vp] * 10, "vof_step_host": [vp] * 9,
             "vof_field_size": [vp, ctypes.c_int, vp, vp], "vof_copy_field": [vp, ctypes.c_int, vp, ctypes.c_int64, vp],
-            "vof_get_counts": [vp, vp, vp], "vof_mesh_info": [vp, vp],
+            "vof_get_counts": [vp, vp, vp], "vof_mesh_info": [vp, vp], "vof_mesh_bins": [vp, vp],
             "vof_timing_enable": [vp, ctypes.c_int], "vof_timing_read": [vp, vp, vp, ctypes.c_int, vp],
         }
         for name, args in sig.items():
@@ -136,11 +136,14 @@ class Mesh:
         info = (ctypes.c_int64 * 5)()
         _check(lib().vof_mesh_info(h, info), "vof_mesh_info")
         self.n_cells, self.n_faces, self.n_verts, self.max_cell_verts, self.max_cell_tets = list(info)
+        bins = (ctypes.c_int64 * 5)()
+        _check(lib().vof_mesh_bins(h, bins), "vof_mesh_bins")
+        self.bin_cells = list(bins)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not getattr(self, "_owned_by_batch", False):
             lib().vof_mesh_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -190,7 +193,7 @@ class Mesh:
         _check(lib().vof_copy_field(self.h, fid, _ptr(out), cnt.value, _stream(stream)), "vof_copy_field")
         return out.view(-1, width) if width > 1 else out
 
-    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp")
+    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp", "geom")
 
     def timing_enable(self, on: bool = True):
         _check(lib().vof_timing_enable(self.h, int(on)), "vof_timing_enable")
@@ -209,9 +212,14 @@ class Mesh:
     FLOPS_TET_EVAL, FLOPS_TET_PREP, FLOPS_TET_SECTION, FLOPS_EVAL = 8, 24, 60, 2
 
     def root_flops(self, counts: dict) -> int:
-        """Algorithmic FP64 flops of the root-search launches summed in `counts`."""
+        """Algorithmic FP64 flops of the root-search launches summed in `counts` (FP64 rows
+        prepared, tetrahedron evaluations, per-evaluation scaling)."""
         return (self.FLOPS_TET_EVAL * counts["tet_evals"] + self.FLOPS_TET_PREP * counts["tets_prepared"]
-                + self.FLOPS_TET_SECTION * counts["tets_sectioned"] + self.FLOPS_EVAL * counts["evals_total"])
+                + self.FLOPS_EVAL * counts["evals_total"])
+
+    def geom_flops(self, counts: dict) -> int:
+        """Algorithmic FP64 flops of the interface-geometry launches (cut tetrahedra)."""
+        return self.FLOPS_TET_SECTION * counts["tets_sectioned"]
 
     def counts(self, stream=None) -> dict:
         c = Counts()
@@ -316,3 +324,100 @@ def load_default_mlp(mesh: Mesh) -> bool:
         return False
     mesh.set_mlp(Mlp(np.load(MLP_PATH)))
     return True
+
+
+# ------------------------------------------------------------------- graphs, autotuning, batches
+def _ext_sig():
+    L = lib()
+    if getattr(L, "_ext_sig", False):
+        return L
+    vp, st = ctypes.c_void_p, ctypes.c_int
+    for name, args in {"vof_step_graph": [vp] * 10, "vof_autotune": [vp, vp, vp, ctypes.c_int, vp, vp],
+                       "vof_set_group_sizes": [vp, vp], "vof_batch_create": [vp, ctypes.c_int, vp, vp],
+                       "vof_batch_destroy": [vp], "vof_batch_mesh": [vp, vp], "vof_batch_offsets": [vp, vp, vp, vp],
+                       "vof_batch_totals": [vp, vp, vp]}.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L._ext_sig = True
+    return L
+
+
+def _mesh_step_graph(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: Options | None = None, stream=None):
+    """vof_step_graph: the step captured once into a CUDA graph and replayed (non-default stream)."""
+    o = opt or default_options()
+    p = props_of(props)
+    _check(_ext_sig().vof_step_graph(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p), ctypes.byref(o),
+                                     _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)), "vof_step_graph")
+
+
+def _mesh_autotune(self, alpha, opt: Options | None = None, reps: int = 5, stream=None) -> list:
+    """vof_autotune: lanes per cell of every tetrahedron-count bin, timed on `alpha`."""
+    o = opt or default_options()
+    G = (ctypes.c_int * 5)()
+    _check(_ext_sig().vof_autotune(self.h, _ptr(alpha), ctypes.byref(o), reps, G, _stream(stream)), "vof_autotune")
+    return list(G)
+
+
+def _mesh_set_group_sizes(self, G):
+    arr = (ctypes.c_int * 5)(*G)
+    _check(_ext_sig().vof_set_group_sizes(self.h, arr), "vof_set_group_sizes")
+
+
+Mesh.step_graph = _mesh_step_graph
+Mesh.autotune = _mesh_autotune
+Mesh.set_group_sizes = _mesh_set_group_sizes
+
+
+class Batch:
+    """Disjoint union of meshes stepped as one mesh (vof_batch_*); `mesh` is the union Mesh."""
+
+    def __init__(self, meshes, stream=None):
+        keeps, descs = [], (_Desc * len(meshes))()
+        for i, m in enumerate(meshes):
+            keep = [np.ascontiguousarray(a, dt) for a, dt in (
+                (m.cell_face_off, np.int64), (m.cell_face, np.int32), (m.face_vert_off, np.int64),
+                (m.face_vert, np.int32), (m.face_owner, np.int32), (m.face_neigh, np.int32),
+                (m.vx, np.float64), (m.vy, np.float64), (m.vz, np.float64))]
+            keeps.append(keep)
+            descs[i] = _Desc(len(keep[0]) - 1, len(keep[4]), len(keep[6]), *[a.ctypes.data for a in keep])
+        h = ctypes.c_void_p()
+        _check(_ext_sig().vof_batch_create(descs, len(meshes), _stream(stream), ctypes.byref(h)), "vof_batch_create")
+        self.h = h
+        self.n = len(meshes)
+        mh = ctypes.c_void_p()
+        _check(_ext_sig().vof_batch_mesh(h, ctypes.byref(mh)), "vof_batch_mesh")
+        self.mesh = Mesh.__new__(Mesh)
+        self.mesh.h = mh
+        self.mesh._owned_by_batch = True
+        info = (ctypes.c_int64 * 5)()
+        _check(lib().vof_mesh_info(mh, info), "vof_mesh_info")
+        (self.mesh.n_cells, self.mesh.n_faces, self.mesh.n_verts, self.mesh.max_cell_verts,
+         self.mesh.max_cell_tets) = list(info)
+        bins = (ctypes.c_int64 * 5)()
+        _check(lib().vof_mesh_bins(mh, bins), "vof_mesh_bins")
+        self.mesh.bin_cells = list(bins)
+        self.cell_off = np.zeros(self.n + 1, np.int64)
+        self.face_off = np.zeros(self.n + 1, np.int64)
+        self.vert_off = np.zeros(self.n + 1, np.int64)
+        _check(_ext_sig().vof_batch_offsets(h, self.cell_off.ctypes.data, self.face_off.ctypes.data,
+                                            self.vert_off.ctypes.data), "vof_batch_offsets")
+
+    def totals(self, out=None, stream=None):
+        """Per-mesh totals [n, 2] of the last step."""
+        import torch
+        out = torch.empty((self.n, 2), dtype=torch.float64, device="cuda") if out is None else out
+        _check(_ext_sig().vof_batch_totals(self.h, _ptr(out), _stream(stream)), "vof_batch_totals")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.mesh.h = None
+            _ext_sig().vof_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,6 +22,8 @@ struct Counters {
   // tetrahedra prepared, tetrahedra cut in the final geometry
   int64_t tet_evals, tets_prepared, tets_sectioned;
   int64_t evals32_total;  // FP32 evaluations of the learned path's refinement
+  int64_t bin_count[5];   // interface cells per tetrahedron-count bin
+  int64_t bin_next[5];    // next bin-list position to take (cells fetched dynamically by the root search)
 };
 
 // Everything a step kernel reads or writes, by value (device pointers).
@@ -79,6 +81,7 @@ struct Workspace {
   double* QV;              // [n_cells]
   double* partial;         // [4][kMaxPartials]: two ping-pong buffers per total
   float* mlp_out;          // [n_cells] learned guesses (normalised position in the range)
+  int32_t* bin_list;       // [kBins][n_cells] interface-list positions per bin
   const double* alpha_in;  // alpha of the current step
   float* mlp_x;            // [n_cells][40] features of interface cells (allocated with an MLP)
   int32_t* mlp_ok;         // [n_cells] 1 where the cell has features
@@ -88,6 +91,10 @@ struct Workspace {
 };
 
 constexpr int kSelTile = 2048;      // cells per selection block
+// Bins of interface cells by tetrahedron count; each bin's root search has its own lanes per cell.
+constexpr int kBins = 5;
+constexpr int kBinMaxTets[kBins] = {4, 8, 24, 64, 192};
+__host__ __device__ inline int bin_of(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 1 : (nt <= 24 ? 2 : (nt <= 64 ? 3 : 4))); }
 constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
 constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
 
@@ -106,7 +113,7 @@ struct StepArgs {
 
 namespace vof {
 // Optional per-kernel device timing: pairs of CUDA events recorded on the launch stream.
-enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_N };
+enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_GEOM, KC_N };
 struct Timing {
   bool on = false;
   int cap = 0, used = 0;
@@ -125,10 +132,22 @@ struct Timing {
 };
 }  // namespace vof
 
+namespace vof {
+// A captured step: the graph is valid while the arguments it bakes in (the key) are unchanged.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key;
+  int64_t captures = 0;
+};
+}  // namespace vof
+
 struct vof_mesh {
   int64_t n_cells = 0, n_faces = 0, n_verts = 0;
   int max_cv = 0, max_ct = 0;
   double mean_ct = 0;  // tetrahedra per cell, mean
+  int64_t bin_cells[vof::kBins] = {0, 0, 0, 0, 0};  // cells of the mesh per bin
+  int bin_max_ct[vof::kBins] = {0, 0, 0, 0, 0};     // largest tetrahedron count per bin
+  int bin_G[vof::kBins] = {0, 0, 0, 0, 0};          // lanes per cell (autotuned; 0 = default)
   int n_sel_blocks = 0, n_vert_blocks = 0;
   int num_sms = 0;
   vof::MeshView view{};
@@ -138,6 +157,12 @@ struct vof_mesh {
   vof_mlp* mlp = nullptr;
   bool recon_done = false;
   vof::Timing timing;
+  vof::GraphCache graph;
+  // the bins' root searches and geometries run as parallel branches (fork after binning, join
+  // before the least squares), so that one bin's slow cells overlap the other bins' work
+  cudaStream_t bin_stream[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace vof {
@@ -147,4 +172,6 @@ vof_status cuda_fail(cudaError_t e, const char* what);
 // step kernels (vof_step.cu)
 vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s);
 vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+                            int bin, int G);
 }  // namespace vof

@@ -234,9 +234,23 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   m->n_cells = nc; m->n_faces = nf; m->n_verts = nv;
   m->max_cv = max_cv; m->max_ct = max_ct;
   m->mean_ct = (double)cto[nc] / (double)nc;
+  for (int64_t c = 0; c < nc; ++c) {
+    const int nt = (int)(cto[c + 1] - cto[c]);
+    const int b = bin_of(nt);
+    m->bin_cells[b]++;
+    m->bin_max_ct[b] = std::max(m->bin_max_ct[b], nt);
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  {
+    cudaError_t es = cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming);
+    for (int b = 0; b < kBins && es == cudaSuccess; ++b) {
+      es = cudaStreamCreateWithFlags(&m->bin_stream[b], cudaStreamNonBlocking);
+      if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_join[b], cudaEventDisableTiming);
+    }
+    if (es != cudaSuccess) return cuda_fail(es, "bin streams");
+  }
   MeshView& V = m->view;
   V.n_cells = nc; V.n_faces = nf; V.n_verts = nv;
   int64_t *d_cfo, *d_fvo, *d_cvo, *d_cto, *d_vco;
@@ -324,6 +338,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.io_Q, nc));
   TRY(dev_alloc(m, &W.io_totals, 2));
   TRY(dev_alloc(m, &W.mlp_out, nc));
+  TRY(dev_alloc(m, &W.bin_list, (size_t)kBins * nc));
   cudaMemsetAsync(W.counters, 0, sizeof(Counters), s);
   cudaMemsetAsync(W.iface_stamp, 0, nc * sizeof(uint32_t), s);
   cudaMemsetAsync(W.band_stamp, 0, nc * sizeof(uint32_t), s);
@@ -337,10 +352,20 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
 }
 
 void destroy(vof_mesh* m) {
+  if (m->graph.exec) cudaGraphExecDestroy(m->graph.exec);
+  m->graph.exec = nullptr;
   for (cudaEvent_t e : m->timing.ev) cudaEventDestroy(e);
   m->timing.ev.clear();
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
+  for (int b = 0; b < kBins; ++b) {
+    if (m->bin_stream[b]) cudaStreamDestroy(m->bin_stream[b]);
+    if (m->ev_join[b]) cudaEventDestroy(m->ev_join[b]);
+    m->bin_stream[b] = nullptr;
+    m->ev_join[b] = nullptr;
+  }
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  m->ev_fork = nullptr;
 }
 
 }  // namespace
@@ -398,6 +423,12 @@ vof_status vof_mesh_destroy(vof_mesh* m) {
 vof_status vof_mesh_info(const vof_mesh* m, int64_t* out5) {
   if (!m || !out5) { set_error("null argument"); return VOF_EINVAL; }
   out5[0] = m->n_cells; out5[1] = m->n_faces; out5[2] = m->n_verts; out5[3] = m->max_cv; out5[4] = m->max_ct;
+  return VOF_OK;
+}
+
+vof_status vof_mesh_bins(const vof_mesh* m, int64_t* cells5) {
+  if (!m || !cells5) { set_error("null argument"); return VOF_EINVAL; }
+  for (int b = 0; b < vof::kBins; ++b) cells5[b] = m->bin_cells[b];
   return VOF_OK;
 }
 

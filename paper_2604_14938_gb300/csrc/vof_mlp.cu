@@ -186,56 +186,80 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward(WeightsBF16* w, const
   }
 }
 
-// ---- features of interface cells, written as float32 [n_iface][40]; flag[i] = 0 when skipped
+// ---- features of interface cells, written as float32 [n_iface][40]; flag[i] = 0 when skipped ---
+// One warp per cell: lane j holds vertex j (at most 32); the normalised values are sorted
+// descending by a bitonic network over the warp; differences are taken in FP64 (relative to the
+// cell's range and first vertex), everything after that in FP32.
 __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, float* X, int32_t* ok) {
   const int64_t n = W.counters->n_iface;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     const int32_t c = W.iface_idx[i];
     const int64_t v0 = M.cell_vert_off[c];
     const int nv = (int)(M.cell_vert_off[c + 1] - v0);
-    float* x = X + i * kIn;
     if (nv > 32) {
-      ok[i] = 0;
+      if (lane == 0) ok[i] = 0;
       continue;
     }
-    double p[32];
-    double lo = 1e300, hi = -1e300, bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
-    double mean[3] = {0, 0, 0};
-    for (int j = 0; j < nv; ++j) {
-      const int32_t v = M.cell_vert[v0 + j];
-      p[j] = W.phi_v[v];
-      lo = fmin(lo, p[j]);
-      hi = fmax(hi, p[j]);
-      const double xyz[3] = {M.vx[v], M.vy[v], M.vz[v]};
-      for (int k = 0; k < 3; ++k) {
-        bmin[k] = fmin(bmin[k], xyz[k]);
-        bmax[k] = fmax(bmax[k], xyz[k]);
-        mean[k] += xyz[k];
-      }
+    const bool has = lane < nv;
+    const int32_t v = has ? M.cell_vert[v0 + lane] : M.cell_vert[v0];
+    const double p = W.phi_v[v];
+    double lo = p, hi = p;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (!(hi - lo >= 1e-14)) {
-      ok[i] = 0;
+      if (lane == 0) ok[i] = 0;
       continue;
     }
-    ok[i] = 1;
-    // insertion sort, descending
-    for (int j = 1; j < nv; ++j) {
-      const double t = p[j];
-      int k = j - 1;
-      while (k >= 0 && p[k] < t) {
-        p[k + 1] = p[k];
-        --k;
+    // normalised value; missing lanes hold -1 so that they sort last
+    float u = has ? (float)((p - lo) / (hi - lo)) : -1.0f;
+    // bitonic sort, descending
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const float other = __shfl_xor_sync(0xffffffffu, u, j);
+        const bool up = ((lane & k) == 0);   // this block of the network sorts descending
+        const bool lower = ((lane & j) == 0);
+        const bool take_max = (up == lower);
+        u = take_max ? fmaxf(u, other) : fminf(u, other);
       }
-      p[k + 1] = t;
     }
-    const double inv = 1.0 / (hi - lo);
-    x[0] = (float)alpha[c];
-    x[1] = (float)((double)(M.cell_face_off[c + 1] - M.cell_face_off[c]) / 32.0);
-    for (int j = 0; j < 32; ++j) x[2 + j] = (float)((p[j < nv ? j : nv - 1] - lo) * inv);
-    const double s = cbrt(M.cell_vol[c]);
-    for (int k = 0; k < 3; ++k) {
-      x[34 + k] = (float)((bmax[k] - bmin[k]) / s);
-      x[37 + k] = (float)((mean[k] / nv - 0.5 * (bmin[k] + bmax[k])) / s);
+    const float smallest = __shfl_sync(0xffffffffu, u, nv - 1);
+    float* x = X + i * kIn;
+    x[2 + lane] = lane < nv ? u : smallest;
+    // shape: coordinates relative to the first vertex (FP64 difference, then FP32)
+    const int32_t vf = M.cell_vert[v0];
+    float rx = (float)(M.vx[v] - M.vx[vf]), ry = (float)(M.vy[v] - M.vy[vf]), rz = (float)(M.vz[v] - M.vz[vf]);
+    float mnx = rx, mny = ry, mnz = rz, mxx = rx, mxy = ry, mxz = rz;
+    float sx = has ? rx : 0.f, sy = has ? ry : 0.f, sz = has ? rz : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+      mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+      mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+      mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+      mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+      mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) {
+      const float is = 1.0f / cbrtf((float)M.cell_vol[c]);
+      x[0] = (float)alpha[c];
+      x[1] = (float)(M.cell_face_off[c + 1] - M.cell_face_off[c]) * (1.0f / 32.0f);
+      x[34] = (mxx - mnx) * is;
+      x[35] = (mxy - mny) * is;
+      x[36] = (mxz - mnz) * is;
+      x[37] = (sx / nv - 0.5f * (mnx + mxx)) * is;
+      x[38] = (sy / nv - 0.5f * (mny + mxy)) * is;
+      x[39] = (sz / nv - 0.5f * (mnz + mxz)) * is;
+      ok[i] = 1;
     }
   }
 }
@@ -433,7 +457,7 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   const int grid = m->num_sms * 2;
   float* X = m->ws.mlp_x;
   int32_t* ok = m->ws.mlp_ok;
-  k_mlp_features<<<grid, 128, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
+  k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
@@ -557,7 +581,7 @@ vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp) {
 vof_status vof_mlp_features(vof_mesh* m, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream) {
   if (!m || !d_alpha || !d_X || !d_ok) { set_error("null argument"); return VOF_EINVAL; }
   if (!m->recon_done) { set_error("vof_mlp_features needs a reconstruction"); return VOF_ESTATE; }
-  k_mlp_features<<<m->num_sms * 2, 128, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, d_X, d_ok);
+  k_mlp_features<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, d_X, d_ok);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_features");
   return VOF_OK;

@@ -66,55 +66,91 @@ __device__ __forceinline__ double norm(Vec3 a) { return sqrt(dot(a, a)); }
 __device__ __forceinline__ Vec3 pickv(int i, Vec3 a, Vec3 b, Vec3 c, Vec3 d) {
   return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
-// point where phi = c on the edge from corner i (value pi) to corner j (value pj)
-__device__ __forceinline__ Vec3 cutp(Vec3 Pi, double pi, Vec3 Pj, double pj, double c) {
-  return Pi + (Pj - Pi) * ((pi - c) / (pi - pj));
+__device__ __forceinline__ double flip_sign(double x, bool f) {
+  // integer sign flip: no FP64 instruction
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
 }
 
-// Section of one tetrahedron by phi = c: vector area (oriented from wet to dry), area, area moment.
+// Section of one tetrahedron by phi = c (m: bit i set when corner i is wet, phi_i >= c; 0 < m < 15):
+// vector area (oriented from wet to dry), area and area moment of the section polygon.
+// The polygon is a triangle (one lone corner) or a planar quadrilateral; both are handled as the
+// quadrilateral q0 q1 q2 q3 of cut points on (wet, dry) edges in cyclic order, a triangle
+// repeating its last point, so that every lane runs the same instructions. The four cut
+// parameters share one division; the two triangle areas of the quadrilateral are the
+// projections of their vector areas on the polygon's normal, so one reciprocal square root
+// serves the area, the normal and the centroid.
 __device__ void tet_section(Vec3 P0, Vec3 P1, Vec3 P2, Vec3 P3, double p0, double p1, double p2, double p3, unsigned m,
                             double c, Vec3& A, double& ar, Vec3& mom) {
   const int k = __popc(m);
-  A = v3(0, 0, 0);
-  ar = 0;
-  mom = v3(0, 0, 0);
-  if (k == 0 || k == 4) return;
-  if (k == 1 || k == 3) {
-    const int i = k == 1 ? __ffs(m) - 1 : __ffs(~m & 15u) - 1;  // the lone corner
-    const Vec3 X = pickv(i, P0, P1, P2, P3);
-    const double x = pick(i, p0, p1, p2, p3);
-    Vec3 q[3];
-    int n = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (j == i) continue;
-      q[n++] = cutp(X, x, pickv(j, P0, P1, P2, P3), pick(j, p0, p1, p2, p3), c);
+  const unsigned dm = ~m & 15u;
+  int wi[4], dj[4];
+  if (k == 2) {
+    const int a = __ffs(m) - 1, b = 31 - __clz(m), cc = __ffs(dm) - 1, d = 31 - __clz(dm);
+    wi[0] = a; dj[0] = cc;
+    wi[1] = a; dj[1] = d;
+    wi[2] = b; dj[2] = d;
+    wi[3] = b; dj[3] = cc;
+  } else {
+    // the lone corner and the other three in increasing order
+    const unsigned rest = k == 1 ? dm : m;
+    const int lone = k == 1 ? __ffs(m) - 1 : __ffs(dm) - 1;
+    const int j0 = __ffs(rest) - 1, j2 = 31 - __clz(rest);
+    const int j1 = __ffs(rest & ~(1u << j0) & ~(1u << j2)) - 1;
+    if (k == 1) {
+      wi[0] = lone; dj[0] = j0;
+      wi[1] = lone; dj[1] = j1;
+      wi[2] = lone; dj[2] = j2;
+      wi[3] = lone; dj[3] = j2;
+    } else {
+      wi[0] = j0; dj[0] = lone;
+      wi[1] = j1; dj[1] = lone;
+      wi[2] = j2; dj[2] = lone;
+      wi[3] = j2; dj[3] = lone;
     }
-    A = cross(q[1] - q[0], q[2] - q[0]) * 0.5;
-    const Vec3 g = (q[0] + q[1] + q[2]) * (1.0 / 3.0);
-    // wet -> dry: away from a lone wet corner, towards a lone dry corner
-    const double s = dot(A, g - X);
-    if ((k == 1 && s < 0) || (k == 3 && s > 0)) A = A * -1.0;
-    ar = norm(A);
-    mom = g * ar;
+  }
+  Vec3 Pw[4], Pd[4];
+  double D[4], W[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    Pw[e] = pickv(wi[e], P0, P1, P2, P3);
+    Pd[e] = pickv(dj[e], P0, P1, P2, P3);
+    const double pw = pick(wi[e], p0, p1, p2, p3), pd = pick(dj[e], p0, p1, p2, p3);
+    D[e] = pw - pd;  // > 0: pw >= c > pd
+    W[e] = pw - c;
+  }
+  double r[4];
+  const double D01 = D[0] * D[1], D23 = D[2] * D[3], prod = D01 * D23;
+  if (prod > 1e-280) {
+    const double ri = 1.0 / prod;
+    r[0] = ri * (D[1] * D23);
+    r[1] = ri * (D[0] * D23);
+    r[2] = ri * (D01 * D[3]);
+    r[3] = ri * (D01 * D[2]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r[e] = 1.0 / D[e];
+  }
+  Vec3 q[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) q[e] = Pw[e] + (Pd[e] - Pw[e]) * (W[e] * r[e]);
+  const Vec3 e1 = q[1] - q[0], e2 = q[2] - q[0], e3 = q[3] - q[0];
+  const Vec3 A1 = cross(e1, e2), A2 = cross(e2, e3);
+  const Vec3 S = A1 + A2;  // twice the vector area
+  const bool flip = dot(S, Pd[0] - Pw[0]) < 0;
+  const double nn = dot(S, S);
+  if (!(nn > 0)) {
+    A = v3(0, 0, 0);
+    ar = 0;
+    mom = v3(0, 0, 0);
     return;
   }
-  const unsigned dm = ~m & 15u;
-  const int ia = __ffs(m) - 1, ib = 31 - __clz(m), ic = __ffs(dm) - 1, id = 31 - __clz(dm);
-  const Vec3 Pa = pickv(ia, P0, P1, P2, P3), Pb = pickv(ib, P0, P1, P2, P3);
-  const Vec3 Pc = pickv(ic, P0, P1, P2, P3), Pd = pickv(id, P0, P1, P2, P3);
-  const double pa = pick(ia, p0, p1, p2, p3), pb = pick(ib, p0, p1, p2, p3);
-  const double pc = pick(ic, p0, p1, p2, p3), pd = pick(id, p0, p1, p2, p3);
-  const Vec3 q1 = cutp(Pa, pa, Pc, pc, c), q2 = cutp(Pa, pa, Pd, pd, c);
-  const Vec3 q3 = cutp(Pb, pb, Pd, pd, c), q4 = cutp(Pb, pb, Pc, pc, c);
-  A = cross(q3 - q1, q4 - q2) * 0.5;
-  if (dot(A, (Pc + Pd) - (Pa + Pb)) < 0) A = A * -1.0;
-  const double a1 = 0.5 * norm(cross(q2 - q1, q3 - q1)), a2 = 0.5 * norm(cross(q3 - q1, q4 - q1));
-  ar = norm(A);
-  if (a1 + a2 > 0) {
-    const Vec3 g = ((q1 + q2 + q3) * (a1 / 3.0) + (q1 + q3 + q4) * (a2 / 3.0)) * (1.0 / (a1 + a2));
-    mom = g * ar;
-  }
+  const double rs = rsqrt(nn);
+  ar = 0.5 * (nn * rs);
+  A = v3(flip_sign(0.5 * S.x, flip), flip_sign(0.5 * S.y, flip), flip_sign(0.5 * S.z, flip));
+  // moment = sum over the two triangles of area x centroid = (rs / 6) sum (A_i . S) (corner sum)
+  const double w1 = dot(A1, S) * rs * (1.0 / 6.0), w2 = dot(A2, S) * rs * (1.0 / 6.0);
+  const Vec3 g02 = q[0] + q[2];
+  mom = (g02 + q[1]) * w1 + (g02 + q[3]) * w2;
 }
 
 __global__ void k_begin(Counters* cn) {
@@ -124,6 +160,7 @@ __global__ void k_begin(Counters* cn) {
   cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
   cn->evals_total = 0;
   cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
+  for (int b = 0; b < kBins; ++b) cn->bin_count[b] = cn->bin_next[b] = 0;
 }
 
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
@@ -305,6 +342,29 @@ __global__ void k_vertex(MeshView M, const double* alpha, int mode, Workspace W)
   }
 }
 
+// ---- interface cells binned by tetrahedron count (warp-aggregated appends) ----------------------
+__global__ void k_bin(MeshView M, Workspace W) {
+  const int64_t n = W.counters->n_iface;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool act = i < n;
+    int b = -1;
+    if (act) {
+      const int32_t c = W.iface_idx[i];
+      b = bin_of((int)(M.cell_tet_off[c + 1] - M.cell_tet_off[c]));
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (act) {
+      const int leader = __ffs(peers) - 1;
+      unsigned long long pos = 0;
+      if (lane == leader) pos = atomicAdd((unsigned long long*)&W.counters->bin_count[b], (unsigned long long)__popc(peers));
+      pos = __shfl_sync(peers, pos, leader);
+      W.bin_list[(size_t)b * M.n_cells + pos + __popc(peers & ((1u << lane) - 1))] = (int32_t)i;
+    }
+  }
+}
+
 // ---- isovalue root search + interface geometry (R2, R3) ------------------------------------------
 // Once per cell and step every tetrahedron's corner values are sorted (s0 >= s1 >= s2 >= s3) and
 // its wet volume is written, for each number k of corners at or above c, as a cubic in a local
@@ -344,16 +404,35 @@ __device__ __forceinline__ TetRow tet_prepare(double p0, double p1, double p2, d
   TetRow r;
   r.s0 = p0; r.s1 = p1; r.s2 = p2; r.s3 = p3;
   r.v = vt;
-  // a zero denominator means the case cannot occur (its interval is empty)
-  const double P1 = d01 * (d02 * d03), P3 = d03 * (d13 * d23), K = d02 * d03, EF = d12 * d13;
-  r.d1 = P1 > 0 ? vt / P1 : 0.0;
-  r.d3 = P3 > 0 ? vt / P3 : 0.0;
-  if (K > 0 && EF > 0) {
-    const double vk = vt / K;
+  // One division per tetrahedron: R = vt / (product of the six differences, a zero difference
+  // entering as 1); each coefficient is R times the differences missing from its own
+  // denominator. A zero denominator means the case cannot occur (its interval is empty), so its
+  // coefficients are 0.
+  const bool n01 = d01 > 0, n02 = d02 > 0, n12 = d12 > 0, n23 = d23 > 0;
+  const double e01 = n01 ? d01 : 1.0, e02 = n02 ? d02 : 1.0, e03 = d03 > 0 ? d03 : 1.0;
+  const double e12 = n12 ? d12 : 1.0, e13 = d13 > 0 ? d13 : 1.0, e23 = n23 ? d23 : 1.0;
+  const double f1213 = e12 * e13, fA = f1213 * e23, fB = e01 * e02, fC = e01 * e23;
+  const double prod = fA * (fB * e03);
+  double d1, d3, vk, vke;
+  if (prod > 1e-280) {
+    const double R = vt / prod;
+    d1 = R * fA;             // vt / (d01 d02 d03)
+    d3 = R * (fB * e12);     // vt / (d03 d13 d23)
+    vk = R * (fC * f1213);   // vt / (d02 d03)
+    vke = R * fC;            // vt / (d02 d03 d12 d13)
+  } else {
+    d1 = vt / (e01 * (e02 * e03));
+    d3 = vt / (e03 * (e13 * e23));
+    vk = vt / (e02 * e03);
+    vke = vk / f1213;
+  }
+  r.d1 = n01 ? d1 : 0.0;
+  r.d3 = n23 ? d3 : 0.0;
+  if (n02 && n12) {
     r.a2 = vk * (d01 * d01);
     r.b2 = 3.0 * vk * d01;
     r.c2 = 3.0 * vk;
-    r.d2 = -(vk / EF) * (d01 + d12 + d13);
+    r.d2 = -vke * (d01 + d12 + d13);
   } else {
     r.a2 = r.b2 = r.c2 = r.d2 = 0.0;
   }
@@ -450,18 +529,23 @@ __device__ __forceinline__ float liquid_volume32(const TetRow32* rows, int nt, i
 
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
-                                                   int max_ct, int learned) {
+                                                   int max_ct, int learned, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int kGroups = blockDim.x / G;
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
   const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
   TetRow* rows = reinterpret_cast<TetRow*>(smem) + (size_t)gib * max_ct;
-  const int64_t n_iface = W.counters->n_iface;
-  const int64_t n_groups = (int64_t)gridDim.x * kGroups;
-  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, sect_acc = 0, ev32_acc = 0;
-  // cells interleaved over blocks first, so that a short list still spreads over every SM
-  for (int64_t i = (int64_t)gib * gridDim.x + blockIdx.x; i < n_iface; i += n_groups) {
+  const int64_t n_bin = W.counters->bin_count[bin];
+  const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
+  // each group takes the next cell of the bin when it is done with the last one: the learned
+  // path's fallback cells cost ten times a typical cell, so a static split leaves SMs idle
+  for (;;) {
+    int64_t j = 0;
+    if (lane == 0) j = (int64_t)atomicAdd((unsigned long long*)&W.counters->bin_next[bin], 1ull);
+    j = __shfl_sync(mask, j, 0, G);
+    if (j >= n_bin) break;
+    const int64_t i = list[j];  // position in the interface list
     const int32_t cell = W.iface_idx[i];
     const int64_t v0 = M.cell_vert_off[cell];
     const int nv = (int)(M.cell_vert_off[cell + 1] - v0);
@@ -477,12 +561,16 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     lo = group_min<G>(lo, mask);
     hi = group_max<G>(hi, mask);
     const double p_apex = W.phi_v[cv[0]];
-    for (int t = lane; t < nt; t += G) {
-      const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-      rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]], W.phi_v[cv[(pk >> 16) & 255]],
-                            __ldg(M.tet_vol + t0 + t));
-    }
-    __syncwarp(mask);
+    // FP64 rows of the cell's tetrahedra (after the FP32 phase on the learned path, whose rows
+    // share the same shared memory)
+    auto prepare64 = [&]() {
+      for (int t = lane; t < nt; t += G) {
+        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+        rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]],
+                              W.phi_v[cv[(pk >> 16) & 255]], __ldg(M.tet_vol + t0 + t));
+      }
+      __syncwarp(mask);
+    };
     const double a = alpha[cell];
     const double V = M.cell_vol[cell];
     const double invV = 1.0 / V;
@@ -496,15 +584,20 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       double f_best = fmin(1.0 - a, a);
       c_best = (1.0 - a) <= a ? lo : hi;
       double L = lo, H = hi;
-      bool done = false;
+      bool done = false, prepared = false;
       if (learned) {
-        // Learned path: MLP guess u0 of the normalised position u = (c - lo)/(hi - lo); FP32
-        // refinement of u (regula falsi with the Illinois modification, on FP32 tetrahedron rows
-        // in normalised values); then the FP64 phase: evaluations at the refined guess and at a
-        // second point next to it, at most max_secant secant steps, and bisection inside the
-        // bracket found so far as the counted fallback.
-        const float u0 = W.mlp_out[i];
-        if (u0 >= 0.0f) {
+        // Learned path: MLP guess u0 of the normalised position u = (c - lo)/(hi - lo) (a cell
+        // without features, more than 32 vertices, starts from 1 - alpha instead and is counted
+        // as skipped); FP32 refinement of u (regula falsi with the Illinois modification, on FP32
+        // tetrahedron rows in normalised values); then the FP64 phase: evaluations at the
+        // refined guess and at a second point next to it, at most max_secant secant steps, and
+        // bisection inside the bracket found so far as the counted fallback.
+        float u0 = W.mlp_out[i];
+        if (!(u0 >= 0.0f)) {
+          status |= VOF_ST_MLP_SKIPPED;
+          u0 = 1.0f - (float)a;
+        }
+        {
           TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
           const double range = hi - lo, irange = 1.0 / range;
           for (int t = lane; t < nt; t += G) {
@@ -520,18 +613,23 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
           float uc = fminf(fmaxf(u0, 0.f), 1.f);
           float fc = liquid_volume32<G>(rows32, nt, lane, mask, uc) - af;
           ++evals32;
+          float up = uc, fp = fc;  // previous raw evaluation (for the slope)
           int side = 0;
           for (int it = 0; it < 16; ++it) {
             if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
             if (fabsf(fc) < 2e-6f || ub - ua < 4e-6f) break;
             // regula falsi step; Illinois: halve the retained end's value after two steps on one side
+            float un;
             if (it == 0) {
               const float step = 0.02f;  // probe next to the guess, towards the root
-              uc = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
+              un = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
             } else {
-              uc = ua + (ub - ua) * (fa / (fa - fb));
-              if (!(uc > ua && uc < ub)) uc = 0.5f * (ua + ub);
+              un = ua + (ub - ua) * (fa / (fa - fb));
+              if (!(un > ua && un < ub)) un = 0.5f * (ua + ub);
             }
+            up = uc;
+            fp = fc;
+            uc = un;
             fc = liquid_volume32<G>(rows32, nt, lane, mask, uc) - af;
             ++evals32;
             const int s2 = fc > 0.f ? 1 : -1;
@@ -540,14 +638,13 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
             }
             side = s2;
           }
-          const float ubest = fabsf(fa) < fabsf(fb) ? ua : ub;
+          // slope df/du from the last two raw FP32 evaluations (else from the bracket)
+          float slope = (uc != up) ? (fc - fp) / (uc - up) : 0.f;
+          if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
+          const float ubest = uc;
           __syncwarp(mask);
-          for (int t = lane; t < nt; t += G) {
-            const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-            rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]], W.phi_v[cv[(pk >> 16) & 255]],
-                                  __ldg(M.tet_vol + t0 + t));
-          }
-          __syncwarp(mask);
+          prepare64();
+          prepared = true;
           // FP64 phase
           double c1 = fmin(fmax(lo + (double)ubest * range, lo), hi);
           double f1 = liquid_volume<G>(rows, nt, lane, mask, c1) * invV - a;
@@ -555,9 +652,15 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
           if (fabs(f1) < f_best) { f_best = fabs(f1); c_best = c1; }
           if (f1 > 0) L = fmax(L, c1); else H = fmin(H, c1);
           if (fabs(f1) <= opt.tol_alpha) done = true;
+          double spread = 1e-6 * range;  // distance between the first two FP64 points
           if (!done && opt.max_secant > 0) {
-            const double step = fmax(4e-6, (double)(ub - ua)) * range;
-            double c0 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+            // second point: one Newton step with the FP32 slope, kept inside the bracket
+            double c0 = c1 - f1 * range / (double)slope;
+            if (!(c0 > L && c0 < H) || c0 == c1) {
+              const double step = 4e-6 * range;
+              c0 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+            }
+            spread = fmax(spread, fabs(c0 - c1));
             double f0 = liquid_volume<G>(rows, nt, lane, mask, c0) * invV - a;
             ++evals;
             if (fabs(f0) < f_best) { f_best = fabs(f0); c_best = c0; }
@@ -575,11 +678,30 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
               c1 = c0; f1 = f0; c0 = c2; f0 = f2;
             }
           }
-          if (!done) status |= VOF_ST_FALLBACK;
-        } else {
-          status |= VOF_ST_MLP_SKIPPED;
+          if (!done) {
+            status |= VOF_ST_FALLBACK;
+            // When the FP64 points all lie on one side of the root, close the bracket next to
+            // them before bisecting: steps away from the nearest point towards the root,
+            // doubling (each an evaluation, counted).
+            const bool open_lo = !(L > lo), open_hi = !(H < hi);
+            if (open_lo != open_hi) {
+              double step = spread;
+              for (int k = 0; k < 40; ++k) {
+                const double cp = open_lo ? H - step : L + step;
+                if (!(cp > L && cp < H)) break;
+                const double fq = liquid_volume<G>(rows, nt, lane, mask, cp) * invV - a;
+                ++evals;
+                if (fabs(fq) < f_best) { f_best = fabs(fq); c_best = cp; }
+                if (fabs(fq) <= opt.tol_alpha) { done = true; break; }
+                if (fq > 0) L = cp; else H = cp;
+                if ((fq > 0) == open_lo) break;  // the open side is closed
+                step *= 2.0;
+              }
+            }
+          }
         }
       }
+      if (!prepared) prepare64();
       for (int it = 0; it < opt.max_bisect && !done; ++it) {
         const double mid = 0.5 * (L + H);
         const double f = liquid_volume<G>(rows, nt, lane, mask, mid) * invV - a;
@@ -592,48 +714,10 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       }
       if (f_best > opt.tol_alpha) status |= VOF_ST_NOT_CONVERGED;
     }
-    // interface geometry at c_best
-    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
-    double area = 0;
-    if (!(status & VOF_ST_DEGENERATE)) {
-      const uint64_t kc = okey(c_best);
-      const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
-      for (int t = lane; t < nt; t += G) {
-        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-        const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
-        const double q1 = W.phi_v[g1], q2 = W.phi_v[g2], q3 = W.phi_v[g3];
-        const unsigned m = (unsigned)(okey(p_apex) >= kc) | ((unsigned)(okey(q1) >= kc) << 1) |
-                           ((unsigned)(okey(q2) >= kc) << 2) | ((unsigned)(okey(q3) >= kc) << 3);
-        if (m == 0 || m == 15u) continue;
-        ++sect_acc;
-        const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
-        const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
-        const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
-        Vec3 tA, tm;
-        double ta;
-        tet_section(P0, P1, P2, P3, p_apex, q1, q2, q3, m, c_best, tA, ta, tm);
-        A = A + tA;
-        area += ta;
-        mom = mom + tm;
-      }
-      A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
-      area = group_sum<G>(area, mask);
-      mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
-    }
     if (lane == 0) {
       W.iso[cell] = c_best;
       W.status[cell] = status;
       W.evals[cell] = evals;
-      W.A_int[cell] = area;
-      const double an = norm(A);
-      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
-      W.n_int[3 * cell] = A.x * inv;
-      W.n_int[3 * cell + 1] = A.y * inv;
-      W.n_int[3 * cell + 2] = A.z * inv;
-      const double ia = area > 0 ? 1.0 / area : 0.0;
-      W.x_gamma[3 * cell] = mom.x * ia;
-      W.x_gamma[3 * cell + 1] = mom.y * ia;
-      W.x_gamma[3 * cell + 2] = mom.z * ia;
       evals_acc += evals;
       ev32_acc += evals32;
       tetev_acc += (int64_t)evals * nt;
@@ -651,7 +735,117 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
     if (ev32_acc) atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
   }
+}
+
+// Interface geometry at the isovalue found by k_root (paper Sec. 2.1): area, unit normal (vapour
+// -> liquid) and centroid of the reconstructed surface, summed over the cell's cut tetrahedra.
+// G lanes per cell. A first pass classifies the tetrahedra (integer work only) and appends the
+// cut ones to the group's list in shared memory, in tetrahedron order; the FP64 sections then
+// run over that list with every lane busy. The work is proportional to the tetrahedron count,
+// so cells are split statically.
+template <int G>
+__global__ void __launch_bounds__(kThreads, 2) k_geom(MeshView M, Workspace W, int bin, int max_ct) {
+  extern __shared__ uint16_t cut_list[];
+  const int kGroups = blockDim.x / G;
+  const int gib = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
+  const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const unsigned mask = gbits << base;
+  uint16_t* lst = cut_list + (size_t)gib * max_ct;
+  const int64_t n_bin = W.counters->bin_count[bin];
+  const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
+  const int64_t n_groups = (int64_t)gridDim.x * kGroups;
+  // warps filled with 32 / G consecutive cells, consecutive warps spread over the blocks first
+  const int64_t j0 = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * (32 / G) + (threadIdx.x & 31) / G;
+  int64_t sect_acc = 0;
+  for (int64_t j = j0; j < n_bin; j += n_groups) {
+    const int32_t cell = W.iface_idx[list[j]];
+    const int status = W.status[cell];
+    const double c = W.iso[cell];
+    const int64_t v0 = M.cell_vert_off[cell];
+    const int64_t t0 = M.cell_tet_off[cell];
+    const int nt = (int)(M.cell_tet_off[cell + 1] - t0);
+    const int32_t* cv = M.cell_vert + v0;
+    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
+    double area = 0;
+    if (!(status & VOF_ST_DEGENERATE)) {
+      const uint64_t kc = okey(c);
+      const double p_apex = W.phi_v[cv[0]];
+      const unsigned m0 = (unsigned)(okey(p_apex) >= kc);
+      int n_cut = 0;
+      for (int r0 = 0; r0 < nt; r0 += G) {
+        const int t = r0 + lane;
+        unsigned m = 0;
+        if (t < nt) {
+          const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+          m = m0 | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
+              ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
+              ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
+        }
+        const bool cut = t < nt && m != 0 && m != 15u;
+        const unsigned bal = (__ballot_sync(mask, cut) >> base) & gbits;
+        if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((t << 4) | m);
+        n_cut += __popc(bal);
+      }
+      __syncwarp(mask);
+      const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
+      for (int jj = lane; jj < n_cut; jj += G) {
+        const unsigned e = lst[jj];
+        const int t = (int)(e >> 4);
+        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+        const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
+        const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
+        const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
+        const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
+        Vec3 tA, tm;
+        double ta;
+        tet_section(P0, P1, P2, P3, p_apex, W.phi_v[g1], W.phi_v[g2], W.phi_v[g3], e & 15u, c, tA, ta, tm);
+        A = A + tA;
+        area += ta;
+        mom = mom + tm;
+      }
+      sect_acc += lane == 0 ? n_cut : 0;
+      A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
+      area = group_sum<G>(area, mask);
+      mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
+    }
+    if (lane == 0) {
+      W.A_int[cell] = area;
+      const double an = norm(A);
+      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
+      W.n_int[3 * cell] = A.x * inv;
+      W.n_int[3 * cell + 1] = A.y * inv;
+      W.n_int[3 * cell + 2] = A.z * inv;
+      const double ia = area > 0 ? 1.0 / area : 0.0;
+      W.x_gamma[3 * cell] = mom.x * ia;
+      W.x_gamma[3 * cell + 1] = mom.y * ia;
+      W.x_gamma[3 * cell + 2] = mom.z * ia;
+    }
+    __syncwarp(mask);  // the list is reused by the group's next cell
+  }
   if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
+}
+
+// Geometry lanes per cell of a bin: about three cut tetrahedra per lane (two thirds of a cell's
+// tetrahedra are cut on these meshes).
+template <int G>
+void launch_geom_g(vof_mesh* m, cudaStream_t s, int bin) {
+  const int max_ct = std::max(1, m->bin_max_ct[bin]);
+  const size_t smem = (size_t)(kThreads / G) * max_ct * sizeof(uint16_t);
+  const int64_t need = (m->bin_cells[bin] + (kThreads / G) - 1) / (kThreads / G);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * 2));  // resident
+  k_geom<G><<<grid, kThreads, smem, s>>>(m->view, m->ws, bin, max_ct);
+}
+
+void launch_geom_bin(vof_mesh* m, cudaStream_t s, int bin) {
+  switch (bin) {
+    case 0: launch_geom_g<1>(m, s, bin); break;
+    case 1: launch_geom_g<2>(m, s, bin); break;
+    case 2: launch_geom_g<4>(m, s, bin); break;
+    case 3: launch_geom_g<8>(m, s, bin); break;
+    default: launch_geom_g<16>(m, s, bin); break;
+  }
 }
 
 // ---- crossing point (R4) -----------------------------------------------------------------------
@@ -840,18 +1034,29 @@ __global__ void k_source(MeshView M, StepArgs a, Workspace W) {
 // tree, so chunk sums are tree nodes; the last block to finish folds the chunk sums the same way.
 // Padding with more zeros than the next power of two only adds exact "+ 0.0" nodes.
 __device__ void tree_block(const double* x, int64_t n, int64_t base, double* s, double* out) {
-  const int t = threadIdx.x;  // blockDim.x == kReduceChunk / 2
+  // Thread t pairs leaves 2t and 2t+1; the next five levels pair neighbouring lanes inside the
+  // warp (lane t + 2^k joins lane t), which is the same pairing as the level-by-level tree; the
+  // 32 warp sums then go through the last five levels in warp 0.
+  const int t = threadIdx.x;  // blockDim.x == kReduceChunk / 2 == 1024
+  const int lane = t & 31;
   const int64_t i0 = base + 2 * t, i1 = i0 + 1;
-  s[t] = (i0 < n ? __ldcg(x + i0) : 0.0) + (i1 < n ? __ldcg(x + i1) : 0.0);
-  __syncthreads();
-  for (int w = kReduceChunk / 4; w > 0; w >>= 1) {
-    double v = 0;
-    if (t < w) v = s[2 * t] + s[2 * t + 1];
-    __syncthreads();
-    if (t < w) s[t] = v;
-    __syncthreads();
+  double v = (i0 < n ? __ldcg(x + i0) : 0.0) + (i1 < n ? __ldcg(x + i1) : 0.0);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double w = __shfl_down_sync(0xffffffffu, v, o);
+    if ((lane & (2 * o - 1)) == 0) v += w;
   }
-  if (t == 0) *out = s[0];
+  if (lane == 0) s[t >> 5] = v;
+  __syncthreads();
+  if (t < 32) {
+    v = s[t];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      if ((lane & (2 * o - 1)) == 0) v += w;
+    }
+    if (t == 0) *out = v;
+  }
   __syncthreads();
 }
 
@@ -889,21 +1094,26 @@ __global__ void __launch_bounds__(kReduceChunk / 2) k_totals(Workspace W, double
   if (threadIdx.x == 0) W.counters->reduce_done = 0;
 }
 
-// Lanes per cell: about four tetrahedra per lane, and the per-cell rows of a block within
-// ~110 KB of shared memory (two blocks per SM).
-int pick_group(const vof_mesh* m, const vof_options& o) {
+
+// Lanes per cell of a bin: the autotuned choice, else about four tetrahedra per lane with the
+// bin's rows within ~110 KB of shared memory per block.
+int pick_group(const vof_mesh* m, const vof_options& o, int bin) {
   if (o.group_size) return o.group_size;
+  if (m->bin_G[bin]) return m->bin_G[bin];
+  const double mean = bin == 0 ? 2.0 : (bin == 1 ? 6.0 : (bin == 2 ? 16.0 : (bin == 3 ? 36.0 : 100.0)));
   int g = 1;
-  while (g < 32 && (g * 4 < m->mean_ct || (size_t)(kThreads / g) * m->max_ct * sizeof(TetRow) > 110 * 1024)) g *= 2;
+  while (g < 32 && (g * 4 < mean || (size_t)(kThreads / g) * m->bin_max_ct[bin] * 88 > 110 * 1024)) g *= 2;
   return g;
 }
 
 template <int G>
-cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned) {
+cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+                          int bin) {
+  const int max_ct = m->bin_max_ct[bin];
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
-  while (threads > 32 && threads > G && (size_t)(threads / G) * m->max_ct * sizeof(TetRow) > 110 * 1024) threads /= 2;
-  const size_t smem = (size_t)(threads / G) * m->max_ct * sizeof(TetRow);
+  while (threads > 32 && threads > G && (size_t)(threads / G) * max_ct * sizeof(TetRow) > 110 * 1024) threads /= 2;
+  const size_t smem = (size_t)(threads / G) * max_ct * sizeof(TetRow);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
@@ -913,15 +1123,17 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   int bps = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_root<G>, threads, smem);
   if (bps < 1) bps = 1;
-  const int64_t need = (m->n_cells + (threads / G) - 1) / (threads / G);
-  const int grid = (int)std::min<int64_t>(need, (int64_t)m->num_sms * bps);
-  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, m->max_ct, learned);
+  const int64_t need = (m->bin_cells[bin] + (threads / G) - 1) / (threads / G);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, learned, bin);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s);  // vof_mlp.cu
+cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+                            int bin, int G);
 
 vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s) {
   const int learned = opt.root_mode == VOF_ROOT_LEARNED;
@@ -955,18 +1167,39 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     tm.stop(s);
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
-  tm.start(KC_ROOT, s);
-  switch (pick_group(m, opt)) {
-    case 1: e = launch_root_g<1>(m, d_alpha, opt, s, learned); break;
-    case 2: e = launch_root_g<2>(m, d_alpha, opt, s, learned); break;
-    case 4: e = launch_root_g<4>(m, d_alpha, opt, s, learned); break;
-    case 8: e = launch_root_g<8>(m, d_alpha, opt, s, learned); break;
-    case 16: e = launch_root_g<16>(m, d_alpha, opt, s, learned); break;
-    default: e = launch_root_g<32>(m, d_alpha, opt, s, learned); break;
+  k_bin<<<m->num_sms * 2, kThreads, 0, s>>>(M, W);
+  // one branch per non-empty bin: root search, then geometry; the branches join on s
+  e = cudaEventRecord(m->ev_fork, s);
+  for (int b = 0; b < kBins && e == cudaSuccess; ++b) {
+    if (!m->bin_cells[b]) continue;
+    cudaStream_t sb = m->bin_stream[b];
+    e = cudaStreamWaitEvent(sb, m->ev_fork, 0);
+    if (e != cudaSuccess) break;
+    tm.start(KC_ROOT, sb);
+    e = launch_root_bin(m, d_alpha, opt, sb, learned, b, pick_group(m, opt, b));
+    tm.stop(sb);
+    if (e != cudaSuccess) break;
+    tm.start(KC_GEOM, sb);
+    launch_geom_bin(m, sb, b);
+    tm.stop(sb);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev_join[b], sb);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_join[b], 0);
   }
-  tm.stop(s);
-  if (e != cudaSuccess) return cuda_fail(e, "root kernel");
+  if (e != cudaSuccess) return cuda_fail(e, "root search / geometry kernels");
   return VOF_OK;
+}
+
+cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+                            int bin, int G) {
+  switch (G) {
+    case 1: return launch_root_g<1>(m, alpha, opt, s, learned, bin);
+    case 2: return launch_root_g<2>(m, alpha, opt, s, learned, bin);
+    case 4: return launch_root_g<4>(m, alpha, opt, s, learned, bin);
+    case 8: return launch_root_g<8>(m, alpha, opt, s, learned, bin);
+    case 16: return launch_root_g<16>(m, alpha, opt, s, learned, bin);
+    default: return launch_root_g<32>(m, alpha, opt, s, learned, bin);
+  }
 }
 
 vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s) {

@@ -58,16 +58,18 @@ def case(name):
     return m, a, T, Tb
 
 
-def gpu_step(m, a, T, Tb, props=None, dev_mesh=None, **opt):
-    """Runs one step through the C ABI; returns (device mesh, dict of numpy outputs)."""
+def gpu_step(m, a, T, Tb, props=None, dev_mesh=None, n_cells=None, **opt):
+    """Runs one step through the C ABI; returns (device mesh, dict of numpy outputs). `m` may be
+    None when `dev_mesh` and `n_cells` are given."""
     import torch
     import paper_2604_14938_gb300 as vof
     props = props or synth.PROPS
     M = dev_mesh or vof.Mesh(m)
+    nc = m.n_cells if m is not None else n_cells
     d = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     ta, tT = d(a), d(T)
     tTb = None if Tb is None else d(Tb)
-    mdot = torch.empty(m.n_cells, dtype=torch.float64, device="cuda")
+    mdot = torch.empty(nc, dtype=torch.float64, device="cuda")
     Q = torch.empty_like(mdot)
     tot = torch.empty(2, dtype=torch.float64, device="cuda")
     M.step(ta, tT, tTb, props, mdot, Q, tot, vof.default_options(**opt))

@@ -195,3 +195,28 @@ def test_host_buffer_step_matches_device_step():
     M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, vof.default_options())
     assert np.array_equal(hm.numpy(), g["mdot"])
     assert np.array_equal(ht.numpy(), g["totals"])
+
+
+def test_iteration_cap_sets_status_not_a_fault():
+    """A forced bisection cap leaves NOT_CONVERGED bits and counts; the step completes."""
+    m, a, T, Tb = case("voronoi_spheres")
+    M, g = gpu_step(m, a, T, Tb, max_bisect=3)
+    I = g["iface_idx"]
+    nc = g["counts"]["n_not_converged"]
+    assert nc > 0
+    assert nc == int(np.sum((g["status"][I] & 2) != 0))
+    assert np.all(g["evals"][I] <= 3)
+    assert np.all(np.isfinite(g["mdot"]))
+
+
+def test_non_finite_and_out_of_range_alpha():
+    """NaN and alpha outside [0, 1] never select a cell; the rest of the step is unchanged."""
+    m, a, T, Tb = case("voronoi_film")
+    M, g0 = gpu_step(m, a, T, Tb)
+    a2 = a.copy()
+    bulk = np.where((a == 0) | (a == 1))[0][:50]
+    a2[bulk[:25]] = np.nan
+    a2[bulk[25:]] = np.where(a[bulk[25:]] == 0, -0.5, 1.5)
+    _, g1 = gpu_step(m, a2, T, Tb, dev_mesh=M)
+    assert g1["counts"]["n_iface"] == g0["counts"]["n_iface"]
+    assert np.array_equal(g1["iface_idx"], g0["iface_idx"])
