@@ -363,7 +363,7 @@ def main():
     ksum = sum(v[0] for v in r["ktime"].values())
     share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
     nbins = sum(1 for c in M.bin_cells if c)  # root search and geometry launch once per non-empty bin
-    per_step = 13 + 2 * nbins + (3 if best == "learned" else 0) + (1 if info["batch"] else 0)
+    per_step = 10 + 2 * nbins + (2 if best == "learned" else 0) + (1 if info["batch"] else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

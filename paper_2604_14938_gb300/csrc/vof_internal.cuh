@@ -10,6 +10,18 @@
 
 namespace vof {
 
+// Order-preserving map of a double onto uint64 (-0.0 folded onto +0.0) and its inverse: integer
+// operations only, so that comparisons, minima and maxima of FP64 values stay off the FP64 pipe.
+__device__ __forceinline__ uint64_t okey(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  b = b == 0x8000000000000000ull ? 0ull : b;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_inv(uint64_t k) {
+  const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
 // Device counters of one step; reset by the step's first kernel.
 struct Counters {
   uint32_t step;        // incremented on the device every step (membership stamps)
@@ -39,6 +51,7 @@ struct MeshView {
   const int64_t* cell_tet_off;
   const uint32_t* cell_tet;  // three local vertex indices (8 bits each) of the base triangle
   const double* tet_vol;     // positive volumes, apex = local vertex 0
+  const float* tet_vfrac;    // tet_vol / cell volume, FP32
   const int64_t* vert_cell_off;
   const int32_t* vert_cell;
   const double* vert_w;      // inverse-distance weights, normalised per vertex
@@ -57,10 +70,8 @@ struct Workspace {
   uint32_t* face_stamp;    // [n_faces]
   int64_t* blk_count;      // [n_sel_blocks]
   int64_t* blk_off;        // [n_sel_blocks]
-  int64_t* blk_count2;     // [n_sel_blocks + n_vert_blocks] band cells, then vertices
-  int64_t* blk_off2;
-  int32_t* band_idx;       // [n_cells] band cells in increasing order
-  int32_t* vert_idx;       // [n_verts] vertices of interface cells in increasing order
+  int32_t* band_idx;       // [n_cells] band cells (unordered)
+  int32_t* vert_idx;       // [n_verts] vertices of interface cells (unordered)
   double* phi_v;           // [n_verts]
   double* iso;             // [n_cells]
   double* A_int;           // [n_cells]
@@ -77,9 +88,11 @@ struct Workspace {
   double* d_own;           // [n_faces]
   double* d_neigh;         // [n_faces]
   double* A_int_f;         // [n_faces]
+  int32_t* xface_list;     // [n_faces] crossing faces next to the band (n_crossing of them this step)
   double* mdotV;           // [n_cells] in interface-list order
   double* QV;              // [n_cells]
   double* partial;         // [4][kMaxPartials]: two ping-pong buffers per total
+  double* tile_part;       // [2][ceil(n_cells / kSrcTile)]: totals of aligned tiles of the interface list
   float* mlp_out;          // [n_cells] learned guesses (normalised position in the range)
   int32_t* bin_list;       // [kBins][n_cells] interface-list positions per bin
   const double* alpha_in;  // alpha of the current step
@@ -96,6 +109,7 @@ constexpr int kBins = 5;
 constexpr int kBinMaxTets[kBins] = {4, 8, 24, 64, 192};
 __host__ __device__ inline int bin_of(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 1 : (nt <= 24 ? 2 : (nt <= 64 ? 3 : 4))); }
 constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
+constexpr int kSrcTile = 64;        // interface cells per source tile (an aligned subtree of the totals)
 constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
 
 struct StepArgs {
@@ -148,7 +162,7 @@ struct vof_mesh {
   int64_t bin_cells[vof::kBins] = {0, 0, 0, 0, 0};  // cells of the mesh per bin
   int bin_max_ct[vof::kBins] = {0, 0, 0, 0, 0};     // largest tetrahedron count per bin
   int bin_G[vof::kBins] = {0, 0, 0, 0, 0};          // lanes per cell (autotuned; 0 = default)
-  int n_sel_blocks = 0, n_vert_blocks = 0;
+  int n_sel_blocks = 0;
   int num_sms = 0;
   vof::MeshView view{};
   vof::Workspace ws{};

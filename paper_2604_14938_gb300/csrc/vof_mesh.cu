@@ -54,8 +54,8 @@ __global__ void k_face_geom(int64_t nf, const int64_t* fvo, const int32_t* fv, c
 
 // Tetrahedron volumes (apex = local vertex 0), cell volume = their sum, centroid.
 __global__ void k_cell_geom(int64_t nc, const int64_t* cvo, const int32_t* cv, const int64_t* cto, const uint32_t* ct,
-                            const double* vx, const double* vy, const double* vz, double* tvol, double* vol,
-                            double* cen, int32_t* bad) {
+                            const double* vx, const double* vy, const double* vz, double* tvol, float* tvf,
+                            double* vol, double* cen, int32_t* bad) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int32_t* V = cv + cvo[c];
@@ -79,6 +79,8 @@ __global__ void k_cell_geom(int64_t nc, const int64_t* cvo, const int32_t* cv, c
   }
   vol[c] = sv;
   cen[3 * c] = sx / sv; cen[3 * c + 1] = sy / sv; cen[3 * c + 2] = sz / sv;
+  // volume fractions (FP32) for the FP32 refinement of the learned root search
+  for (int64_t t = cto[c]; t < cto[c + 1]; ++t) tvf[t] = (float)(tvol[t] / sv);
 }
 
 // Inverse-distance weights of the cells around each vertex, normalised to sum 1.
@@ -273,8 +275,10 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(upload(m, &d_vco, vco.data(), nv + 1, s));
   TRY(upload(m, &d_vc, vc.data(), vc.size(), s));
   double *d_tvol, *d_vol, *d_cen, *d_fa, *d_fc, *d_w;
+  float* d_tvf;
   int32_t* d_bad;
   TRY(dev_alloc(m, &d_tvol, ct.size()));
+  TRY(dev_alloc(m, &d_tvf, ct.size()));
   TRY(dev_alloc(m, &d_vol, nc));
   TRY(dev_alloc(m, &d_cen, 3 * nc));
   TRY(dev_alloc(m, &d_fa, 3 * nf));
@@ -284,7 +288,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
   k_face_geom<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_fvo, d_fv, d_vx, d_vy, d_vz, d_fa, d_fc);
   k_cell_geom<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_cto, d_ct, d_vx, d_vy, d_vz, d_tvol,
-                                                            d_vol, d_cen, d_bad);
+                                                            d_tvf, d_vol, d_cen, d_bad);
   k_idw<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, d_vco, d_vc, d_vx, d_vy, d_vz, d_cen, d_w);
   int32_t h_bad = 0;
   cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -294,6 +298,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   V.cell_face_off = d_cfo; V.cell_face = d_cf; V.face_owner = d_own; V.face_neigh = d_nei;
   V.vx = d_vx; V.vy = d_vy; V.vz = d_vz;
   V.cell_vert_off = d_cvo; V.cell_vert = d_cv; V.cell_tet_off = d_cto; V.cell_tet = d_ct; V.tet_vol = d_tvol;
+  V.tet_vfrac = d_tvf;
   V.vert_cell_off = d_vco; V.vert_cell = d_vc; V.vert_w = d_w;
   V.cell_vol = d_vol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
   // ---- workspace
@@ -307,9 +312,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.face_stamp, nf));
   TRY(dev_alloc(m, &W.blk_count, m->n_sel_blocks));
   TRY(dev_alloc(m, &W.blk_off, m->n_sel_blocks));
-  m->n_vert_blocks = (int)((nv + kSelTile - 1) / kSelTile);
-  TRY(dev_alloc(m, &W.blk_count2, m->n_sel_blocks + m->n_vert_blocks));
-  TRY(dev_alloc(m, &W.blk_off2, m->n_sel_blocks + m->n_vert_blocks));
+  TRY(dev_alloc(m, &W.tile_part, 2 * (size_t)((nc + kSrcTile - 1) / kSrcTile)));
   TRY(dev_alloc(m, &W.band_idx, nc));
   TRY(dev_alloc(m, &W.vert_idx, nv));
   TRY(dev_alloc(m, &W.phi_v, nv));
@@ -328,6 +331,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.d_own, nf));
   TRY(dev_alloc(m, &W.d_neigh, nf));
   TRY(dev_alloc(m, &W.A_int_f, nf));
+  TRY(dev_alloc(m, &W.xface_list, nf));
   TRY(dev_alloc(m, &W.mdotV, nc));
   TRY(dev_alloc(m, &W.QV, nc));
   TRY(dev_alloc(m, &W.partial, 4 * kMaxPartials));

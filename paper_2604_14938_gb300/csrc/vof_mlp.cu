@@ -97,10 +97,13 @@ struct Smem {
 
 // Stages weights (bf16) and biases into shared memory.
 __device__ void stage_weights(Smem& s, const WeightsBF16& w) {
-  for (int i = threadIdx.x; i < kH * kInPad; i += blockDim.x) s.W1[(i / kInPad) * LDX + i % kInPad] = w.W1[i / kInPad][i % kInPad];
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    s.W2[(i / kH) * LDH + i % kH] = w.W2[i / kH][i % kH];
-    s.W3[(i / kH) * LDH + i % kH] = w.W3[i / kH][i % kH];
+  // 16-byte chunks: 6 per W1 row (48 bf16), 8 per W2 / W3 row (64 bf16); row strides of 56 and
+  // 72 bf16 keep every chunk 16-byte aligned
+  for (int i = threadIdx.x; i < kH * 6; i += blockDim.x)
+    reinterpret_cast<uint4*>(s.W1 + (i / 6) * LDX)[i % 6] = reinterpret_cast<const uint4*>(&w.W1[i / 6][0])[i % 6];
+  for (int i = threadIdx.x; i < kH * 8; i += blockDim.x) {
+    reinterpret_cast<uint4*>(s.W2 + (i / 8) * LDH)[i % 8] = reinterpret_cast<const uint4*>(&w.W2[i / 8][0])[i % 8];
+    reinterpret_cast<uint4*>(s.W3 + (i / 8) * LDH)[i % 8] = reinterpret_cast<const uint4*>(&w.W3[i / 8][0])[i % 8];
   }
   for (int i = threadIdx.x; i < kH; i += blockDim.x) {
     s.b1[i] = w.b1[i]; s.b2[i] = w.b2[i]; s.b3[i] = w.b3[i]; s.w4[i] = w.w4[i];
@@ -205,18 +208,21 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
     const bool has = lane < nv;
     const int32_t v = has ? M.cell_vert[v0 + lane] : M.cell_vert[v0];
     const double p = W.phi_v[v];
-    double lo = p, hi = p;
+    // range by integer min/max of the order keys (no FP64 compares)
+    uint64_t klo = okey(p), khi = klo;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      klo = min(klo, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)klo, o));
+      khi = max(khi, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)khi, o));
     }
-    if (!(hi - lo >= 1e-14)) {
+    const double lo = okey_inv(klo), range = okey_inv(khi) - lo;
+    if (!(range >= 1e-14)) {
       if (lane == 0) ok[i] = 0;
       continue;
     }
-    // normalised value; missing lanes hold -1 so that they sort last
-    float u = has ? (float)((p - lo) / (hi - lo)) : -1.0f;
+    // normalised value (FP64 difference, FP32 scaling); missing lanes hold -1 so that they sort last
+    const float irange = 1.0f / (float)range;
+    float u = has ? (float)(p - lo) * irange : -1.0f;
     // bitonic sort, descending
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
@@ -264,15 +270,10 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
   }
 }
 
-// guess of interface cell i: t in [0, 1], or -1 without a guess
-__global__ void k_mlp_guess_out(const float* y, const int32_t* ok, Workspace W) {
-  const int64_t n = W.counters->n_iface;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    W.mlp_out[i] = ok[i] ? fminf(fmaxf(y[i], 0.f), 1.f) : -1.f;
-}
-
-// forward over the interface list (n read on the device)
-__global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, Workspace W, float* y) {
+// forward over the interface list (n read on the device); writes the guess of interface cell i,
+// clamped to [0, 1], or -1 where the cell has no features
+__global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
+                                                                 Workspace W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int64_t n = W.counters->n_iface;
@@ -284,8 +285,10 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w,
     __syncthreads();
     if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
     __syncthreads();
-    for (int r = threadIdx.x; r < kRows; r += blockDim.x)
-      if (row0 + r < n) y[row0 + r] = s.y[r];
+    for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+      const int64_t i = row0 + r;
+      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(s.y[r], 0.f), 1.f) : -1.f;
+    }
     __syncthreads();
   }
 }
@@ -463,8 +466,7 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
     attr = true;
   }
-  k_mlp_forward_iface<<<grid, kRows * 2, sizeof(Smem), s>>>(mlp->w, X, m->ws, m->ws.mlp_y);
-  k_mlp_guess_out<<<grid, 256, 0, s>>>(m->ws.mlp_y, ok, m->ws);
+  k_mlp_forward_iface<<<grid, kRows * 2, sizeof(Smem), s>>>(mlp->w, X, ok, m->ws);
   return cudaGetLastError();
 }
 

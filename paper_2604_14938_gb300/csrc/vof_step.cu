@@ -11,6 +11,7 @@
 //                       / [(p_a - p_c)(p_a - p_d)(p_b - p_c)(p_b - p_d)]
 // with w = p - c on wet corners and u = c - p on dry corners: every denominator is a product of
 // (wet - dry) differences, so no term is singular and nothing cancels.
+#include <cooperative_groups.h>
 #include <cstring>
 
 #include "vof_internal.cuh"
@@ -18,14 +19,34 @@
 namespace vof {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ uint64_t okey(double x) {
-  // order-preserving map of a double onto uint64 (-0.0 folded onto +0.0), integer operations
-  // only, so that the wet test phi >= c stays off the FP64 pipe
-  uint64_t b = (uint64_t)__double_as_longlong(x);
-  b = b == 0x8000000000000000ull ? 0ull : b;
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+// |x| as an order-preserving integer key, so that magnitude tests stay off the FP64 pipe (an
+// FP64 compare costs a warp instruction on the 1/64-rate pipe, like an FMA)
+__device__ __forceinline__ uint64_t mag(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }  // x > 0
+__device__ __forceinline__ bool inside(double x, double L, double H) {  // L < x < H
+  const uint64_t k = okey(x);
+  return k > okey(L) && k < okey(H);
+}
+__device__ __forceinline__ double dmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+__device__ __forceinline__ double dmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+
+template <int G>
+__device__ __forceinline__ uint64_t group_umin(uint64_t v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = min(v, (uint64_t)__shfl_xor_sync(mask, (unsigned long long)v, o));
+  return v;
+}
+template <int G>
+__device__ __forceinline__ uint64_t group_umax(uint64_t v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(mask, (unsigned long long)v, o));
+  return v;
 }
 
 template <int G>
@@ -153,7 +174,8 @@ __device__ void tet_section(Vec3 P0, Vec3 P1, Vec3 P2, Vec3 P3, double p0, doubl
   mom = (g02 + q[1]) * w1 + (g02 + q[3]) * w2;
 }
 
-__global__ void k_begin(Counters* cn) {
+// First work of a step: step stamp, counters reset (run by one thread of the first kernel).
+__device__ __forceinline__ void begin_step(Counters* cn) {
   cn->step += 1;
   cn->reduce_done = 0;
   cn->n_iface = cn->n_band = cn->n_crossing = cn->n_uvert = 0;
@@ -166,7 +188,8 @@ __global__ void k_begin(Counters* cn) {
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
 
 // ---- selection: per-tile counts, scan, order-preserving scatter -------------------------------
-__global__ void k_sel_count(int64_t nc, const double* alpha, double eps, int64_t* blk_count) {
+__global__ void k_sel_count(int64_t nc, const double* alpha, double eps, int64_t* blk_count, Counters* cn) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(cn);  // no other block reads the counters
   const int64_t base = (int64_t)blockIdx.x * kSelTile;
   int cnt = 0;
   for (int64_t c = base + threadIdx.x; c < min(nc, base + kSelTile); c += blockDim.x) cnt += is_iface(alpha[c], eps);
@@ -230,7 +253,20 @@ __global__ void k_sel_scatter(MeshView M, const double* alpha, double eps, Works
   }
 }
 
-// Band and vertex stamps of the interface cells: 8 lanes per cell over its faces and vertices.
+// Appends value to list at the next free slot of *counter: one atomic per group of lanes that
+// arrive together (warp-aggregated); the order of the list is not defined.
+__device__ __forceinline__ void append(int64_t* counter, int32_t* list, int32_t value) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd((unsigned long long*)counter, (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  list[base + g.thread_rank()] = value;
+}
+
+// Band cells (interface cells and their face neighbours) and the vertices of interface cells:
+// stamped with the step, and listed by whichever lane stamps them first. 8 lanes per interface
+// cell over its faces and vertices. The lists are unordered: every later use is per cell or per
+// vertex.
 __global__ void k_mark(MeshView M, Workspace W) {
   const uint32_t step = W.counters->step;
   const int64_t n = W.counters->n_iface;
@@ -238,90 +274,16 @@ __global__ void k_mark(MeshView M, Workspace W) {
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / 8);
   for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 8) + threadIdx.x / 8; i < n; i += groups) {
     const int32_t c = W.iface_idx[i];
-    if (lane == 0) atomicMax(&W.band_stamp[c], step);
+    if (lane == 0 && atomicExch(&W.band_stamp[c], step) != step) append(&W.counters->n_band, W.band_idx, c);
     for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += 8) {
       const int32_t fc = M.cell_face[k] & 0x7fffffff;
       const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
-      if (q >= 0) atomicMax(&W.band_stamp[q], step);
+      if (q >= 0 && atomicExch(&W.band_stamp[q], step) != step) append(&W.counters->n_band, W.band_idx, q);
     }
-    for (int64_t k = M.cell_vert_off[c] + lane; k < M.cell_vert_off[c + 1]; k += 8)
-      atomicMax(&W.vert_stamp[M.cell_vert[k]], step);
-  }
-}
-
-// ---- band cells and interface vertices: the same count / scan / scatter over the stamps -------
-// Blocks [0, nbc) cover cells (band stamp), blocks [nbc, nbc + nbv) cover vertices.
-__global__ void k_bv_count(int64_t nc, int64_t nv, int nbc, Workspace W) {
-  const uint32_t step = W.counters->step;
-  const bool cells = blockIdx.x < (unsigned)nbc;
-  const int64_t base = (int64_t)(cells ? blockIdx.x : blockIdx.x - nbc) * kSelTile;
-  const int64_t n = cells ? nc : nv;
-  const uint32_t* st = cells ? W.band_stamp : W.vert_stamp;
-  int cnt = 0;
-  for (int64_t i = base + threadIdx.x; i < min(n, base + kSelTile); i += blockDim.x) cnt += st[i] == step;
-  __shared__ int s[kThreads / 32];
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < kThreads / 32; ++w) t += s[w];
-    W.blk_count2[blockIdx.x] = t;
-  }
-}
-
-__global__ void k_bv_scan(int nbc, int nbv, Workspace W) {
-  __shared__ int64_t s[1024];
-  for (int seg = 0; seg < 2; ++seg) {
-    const int off = seg ? nbc : 0, nb = seg ? nbv : nbc;
-    int64_t carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-      const int i = base + threadIdx.x;
-      const int64_t v = i < nb ? W.blk_count2[off + i] : 0;
-      s[threadIdx.x] = v;
-      __syncthreads();
-      for (int o = 1; o < 1024; o <<= 1) {
-        const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
-        __syncthreads();
-        s[threadIdx.x] += t;
-        __syncthreads();
-      }
-      if (i < nb) W.blk_off2[off + i] = carry + s[threadIdx.x] - v;
-      carry += s[1023];
-      __syncthreads();
+    for (int64_t k = M.cell_vert_off[c] + lane; k < M.cell_vert_off[c + 1]; k += 8) {
+      const int32_t v = M.cell_vert[k];
+      if (atomicExch(&W.vert_stamp[v], step) != step) append(&W.counters->n_uvert, W.vert_idx, v);
     }
-    if (threadIdx.x == 0) {
-      if (seg) W.counters->n_uvert = carry;
-      else W.counters->n_band = carry;
-    }
-  }
-}
-
-__global__ void k_bv_scatter(int64_t nc, int64_t nv, int nbc, Workspace W) {
-  const uint32_t step = W.counters->step;
-  const bool cells = blockIdx.x < (unsigned)nbc;
-  const int64_t base = (int64_t)(cells ? blockIdx.x : blockIdx.x - nbc) * kSelTile;
-  const int64_t n = cells ? nc : nv;
-  const int64_t end = min(n, base + kSelTile);
-  const uint32_t* st = cells ? W.band_stamp : W.vert_stamp;
-  int32_t* out = cells ? W.band_idx : W.vert_idx;
-  int64_t pos = W.blk_off2[blockIdx.x];
-  __shared__ int wsum[kThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t r = base; r < end; r += blockDim.x) {
-    const int64_t i = r + threadIdx.x;
-    const bool f = i < end && st[i] == step;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wsum[wid] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      before += w < wid ? wsum[w] : 0;
-      total += wsum[w];
-    }
-    if (f) out[pos + before + __popc(bal & ((1u << lane) - 1))] = (int32_t)i;
-    pos += total;
-    __syncthreads();
   }
 }
 
@@ -408,13 +370,14 @@ __device__ __forceinline__ TetRow tet_prepare(double p0, double p1, double p2, d
   // entering as 1); each coefficient is R times the differences missing from its own
   // denominator. A zero denominator means the case cannot occur (its interval is empty), so its
   // coefficients are 0.
-  const bool n01 = d01 > 0, n02 = d02 > 0, n12 = d12 > 0, n23 = d23 > 0;
-  const double e01 = n01 ? d01 : 1.0, e02 = n02 ? d02 : 1.0, e03 = d03 > 0 ? d03 : 1.0;
-  const double e12 = n12 ? d12 : 1.0, e13 = d13 > 0 ? d13 : 1.0, e23 = n23 ? d23 : 1.0;
+  // corner values differ exactly when their keys do (keys sorted descending)
+  const bool n01 = k0 > k1, n02 = k0 > k2, n12 = k1 > k2, n23 = k2 > k3;
+  const double e01 = n01 ? d01 : 1.0, e02 = n02 ? d02 : 1.0, e03 = k0 > k3 ? d03 : 1.0;
+  const double e12 = n12 ? d12 : 1.0, e13 = k1 > k3 ? d13 : 1.0, e23 = n23 ? d23 : 1.0;
   const double f1213 = e12 * e13, fA = f1213 * e23, fB = e01 * e02, fC = e01 * e23;
-  const double prod = fA * (fB * e03);
+  const double prod = fA * (fB * e03);  // >= 0
   double d1, d3, vk, vke;
-  if (prod > 1e-280) {
+  if (__double_as_longlong(prod) > __double_as_longlong(1e-280)) {
     const double R = vt / prod;
     d1 = R * fA;             // vt / (d01 d02 d03)
     d3 = R * (fB * e12);     // vt / (d03 d13 d23)
@@ -529,12 +492,15 @@ __device__ __forceinline__ float liquid_volume32(const TetRow32* rows, int nt, i
 
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
-                                                   int max_ct, int learned, int bin) {
+                                                   int max_ct, int max_cv, int learned, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
   const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  TetRow* rows = reinterpret_cast<TetRow*>(smem) + (size_t)gib * max_ct;
+  // per group: the rows, then the cell's normalised vertex values (FP32) for the learned path
+  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float);
+  TetRow* rows = reinterpret_cast<TetRow*>(smem + (size_t)gib * grp_bytes);
+  float* uvert = reinterpret_cast<float*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow));
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
   int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
@@ -552,14 +518,14 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     const int64_t t0 = M.cell_tet_off[cell];
     const int nt = (int)(M.cell_tet_off[cell + 1] - t0);
     const int32_t* cv = M.cell_vert + v0;
-    double lo = 1e300, hi = -1e300;
+    // range of the vertex values, by integer min/max of the order keys
+    uint64_t klo = ~0ull, khi = 0ull;
     for (int j = lane; j < nv; j += G) {
-      const double p = W.phi_v[cv[j]];
-      lo = fmin(lo, p);
-      hi = fmax(hi, p);
+      const uint64_t k = okey(W.phi_v[cv[j]]);
+      klo = min(klo, k);
+      khi = max(khi, k);
     }
-    lo = group_min<G>(lo, mask);
-    hi = group_max<G>(hi, mask);
+    const double lo = okey_inv(group_umin<G>(klo, mask)), hi = okey_inv(group_umax<G>(khi, mask));
     const double p_apex = W.phi_v[cv[0]];
     // FP64 rows of the cell's tetrahedra (after the FP32 phase on the learned path, whose rows
     // share the same shared memory)
@@ -574,17 +540,29 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     const double a = alpha[cell];
     const double V = M.cell_vol[cell];
     const double invV = 1.0 / V;
+    const uint64_t ktol = mag(opt.tol_alpha);
     int status = 0, evals = 0, evals32 = 0;
     double c_best;
+    uint64_t kbest = 0;  // |f| at c_best, as a magnitude key
     if (hi - lo < 1e-14) {
       status = VOF_ST_DEGENERATE;
       c_best = lo;
     } else {
       // f(lo) = 1 - alpha (everything wet), f(hi) = -alpha
-      double f_best = fmin(1.0 - a, a);
+      kbest = mag(fmin(1.0 - a, a));
       c_best = (1.0 - a) <= a ? lo : hi;
       double L = lo, H = hi;
       bool done = false, prepared = false;
+      // one FP64 evaluation: residual, best point and bracket updated, convergence test
+      auto eval64 = [&](double c) -> double {
+        const double f = liquid_volume<G>(rows, nt, lane, mask, c) * invV - a;
+        ++evals;
+        const uint64_t kf = mag(f);
+        if (kf < kbest) { kbest = kf; c_best = c; }
+        if (positive(f)) L = dmax(L, c); else H = dmin(H, c);
+        if (kf <= ktol) done = true;
+        return f;
+      };
       if (learned) {
         // Learned path: MLP guess u0 of the normalised position u = (c - lo)/(hi - lo) (a cell
         // without features, more than 32 vertices, starts from 1 - alpha instead and is counted
@@ -597,15 +575,16 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
           status |= VOF_ST_MLP_SKIPPED;
           u0 = 1.0f - (float)a;
         }
+        const double range = hi - lo;
         {
           TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
-          const double range = hi - lo, irange = 1.0 / range;
+          const double irange = 1.0 / range;
+          for (int j = lane; j < nv; j += G) uvert[j] = (float)((W.phi_v[cv[j]] - lo) * irange);
+          __syncwarp(mask);
           for (int t = lane; t < nt; t += G) {
             const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-            rows32[t] = tet_prepare32((float)((p_apex - lo) * irange), (float)((W.phi_v[cv[pk & 255]] - lo) * irange),
-                                      (float)((W.phi_v[cv[(pk >> 8) & 255]] - lo) * irange),
-                                      (float)((W.phi_v[cv[(pk >> 16) & 255]] - lo) * irange),
-                                      (float)(__ldg(M.tet_vol + t0 + t) * invV));
+            rows32[t] = tet_prepare32(uvert[0], uvert[pk & 255], uvert[(pk >> 8) & 255], uvert[(pk >> 16) & 255],
+                                      __ldg(M.tet_vfrac + t0 + t));
           }
           __syncwarp(mask);
           const float af = (float)a;
@@ -646,35 +625,27 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
           prepare64();
           prepared = true;
           // FP64 phase
-          double c1 = fmin(fmax(lo + (double)ubest * range, lo), hi);
-          double f1 = liquid_volume<G>(rows, nt, lane, mask, c1) * invV - a;
-          ++evals;
-          if (fabs(f1) < f_best) { f_best = fabs(f1); c_best = c1; }
-          if (f1 > 0) L = fmax(L, c1); else H = fmin(H, c1);
-          if (fabs(f1) <= opt.tol_alpha) done = true;
+          double c1 = dmin(dmax(lo + (double)ubest * range, lo), hi);
+          double f1 = eval64(c1);
           double spread = 1e-6 * range;  // distance between the first two FP64 points
           if (!done && opt.max_secant > 0) {
             // second point: one Newton step with the FP32 slope, kept inside the bracket
-            double c0 = c1 - f1 * range / (double)slope;
-            if (!(c0 > L && c0 < H) || c0 == c1) {
+            double c0 = fma(-f1, range * (double)(1.0f / slope), c1);
+            if (!inside(c0, L, H) || c0 == c1) {
               const double step = 4e-6 * range;
-              c0 = f1 > 0 ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+              c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
             }
-            spread = fmax(spread, fabs(c0 - c1));
-            double f0 = liquid_volume<G>(rows, nt, lane, mask, c0) * invV - a;
-            ++evals;
-            if (fabs(f0) < f_best) { f_best = fabs(f0); c_best = c0; }
-            if (f0 > 0) L = fmax(L, c0); else H = fmin(H, c0);
-            if (fabs(f0) <= opt.tol_alpha) done = true;
+            spread = dmax(spread, fabs(c0 - c1));
+            double f0 = eval64(c0);
             for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
-              if (f0 == f1) break;
-              double c2 = c0 - f0 * (c0 - c1) / (f0 - f1);
-              if (!(c2 > L && c2 < H)) c2 = 0.5 * (L + H);
-              const double f2 = liquid_volume<G>(rows, nt, lane, mask, c2) * invV - a;
-              ++evals;
-              if (fabs(f2) < f_best) { f_best = fabs(f2); c_best = c2; }
-              if (f2 > 0) L = fmax(L, c2); else H = fmin(H, c2);
-              if (fabs(f2) <= opt.tol_alpha) done = true;
+              if (__double_as_longlong(f0) == __double_as_longlong(f1)) break;
+              // secant point; the reciprocal of f0 - f1 from an FP32 seed and one FP64 Newton step
+              const double d = f0 - f1;
+              double r = (double)(1.0f / (float)d);
+              r = fma(r, fma(-d, r, 1.0), r);
+              double c2 = fma(-f0, (c0 - c1) * r, c0);
+              if (!inside(c2, L, H)) c2 = 0.5 * (L + H);
+              const double f2 = eval64(c2);
               c1 = c0; f1 = f0; c0 = c2; f0 = f2;
             }
           }
@@ -683,18 +654,14 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
             // When the FP64 points all lie on one side of the root, close the bracket next to
             // them before bisecting: steps away from the nearest point towards the root,
             // doubling (each an evaluation, counted).
-            const bool open_lo = !(L > lo), open_hi = !(H < hi);
+            const bool open_lo = !(okey(L) > okey(lo)), open_hi = !(okey(H) < okey(hi));
             if (open_lo != open_hi) {
               double step = spread;
-              for (int k = 0; k < 40; ++k) {
+              for (int k = 0; k < 40 && !done; ++k) {
                 const double cp = open_lo ? H - step : L + step;
-                if (!(cp > L && cp < H)) break;
-                const double fq = liquid_volume<G>(rows, nt, lane, mask, cp) * invV - a;
-                ++evals;
-                if (fabs(fq) < f_best) { f_best = fabs(fq); c_best = cp; }
-                if (fabs(fq) <= opt.tol_alpha) { done = true; break; }
-                if (fq > 0) L = cp; else H = cp;
-                if ((fq > 0) == open_lo) break;  // the open side is closed
+                if (!inside(cp, L, H)) break;
+                const double fq = eval64(cp);
+                if (positive(fq) == open_lo) break;  // the open side is closed
                 step *= 2.0;
               }
             }
@@ -703,16 +670,11 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       }
       if (!prepared) prepare64();
       for (int it = 0; it < opt.max_bisect && !done; ++it) {
-        const double mid = 0.5 * (L + H);
-        const double f = liquid_volume<G>(rows, nt, lane, mask, mid) * invV - a;
-        ++evals;
-        if (fabs(f) < f_best) { f_best = fabs(f); c_best = mid; }
-        if (fabs(f) <= opt.tol_alpha) break;
-        if (f > 0) L = mid; else H = mid;
-        const double scale = fmax(fabs(L), fabs(H));
-        if (H - L <= 4.0 * (nextafter(scale, 2.0 * scale + 1.0) - scale)) break;
+        eval64(0.5 * (L + H));
+        // stop when the bracket is down to a few representable values
+        if (okey(H) - okey(L) <= 4) break;
       }
-      if (f_best > opt.tol_alpha) status |= VOF_ST_NOT_CONVERGED;
+      if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
     }
     if (lane == 0) {
       W.iso[cell] = c_best;
@@ -881,71 +843,95 @@ __device__ double crossing_t(const MeshView& M, const Workspace& W, const double
   return *src >= 0 ? best_t : t_lin;
 }
 
-// ---- interface-modified least squares (R7) on band cells, crossing-face outputs -----------------
-// 8 lanes per band cell over its faces; the nine sums of G and b are reduced across the lanes.
+// ---- crossing faces next to the band (R4): list, then one thread per face ------------------------
+// A face is listed once: by its owner when the owner is a band cell, else by its neighbour.
 constexpr int kLsqLanes = 8;
+constexpr int kLsqCellLanes = 4;  // lanes per band cell in the least squares
 
-__global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
+__global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
   const int lane = threadIdx.x % kLsqLanes;
-  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
-  int ncross = 0, nsing = 0;
   for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + threadIdx.x / kLsqLanes; j < nb; j += groups) {
+    const int32_t c = W.band_idx[j];
+    const double aP = alpha[c];
+    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+      if (nbr < 0) continue;
+      const int32_t q = o == c ? nbr : o;
+      if (!((aP - 0.5) * (alpha[q] - 0.5) < 0)) continue;
+      if (o == c || W.band_stamp[o] != step) {
+        const unsigned long long slot = atomicAdd((unsigned long long*)&W.counters->n_crossing, 1ull);
+        W.xface_list[slot] = f;
+      }
+    }
+  }
+}
+
+// Crossing point, distances and projected interface area of each listed face.
+__global__ void k_xface(MeshView M, const double* alpha, int xf_mode, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t n = W.counters->n_crossing;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f = W.xface_list[j];
+    const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+    int32_t src;
+    const double t = crossing_t(M, W, alpha, f, xf_mode, step, &src);
+    const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
+    const Vec3 xn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]);
+    const Vec3 xf = xo + (xn - xo) * t;
+    W.x_f[3 * f] = xf.x; W.x_f[3 * f + 1] = xf.y; W.x_f[3 * f + 2] = xf.z;
+    W.d_own[f] = norm(xf - xo);
+    W.d_neigh[f] = norm(xf - xn);
+    const int32_t sc = src >= 0 ? src : (has_plane(W, o, step) ? o : (has_plane(W, nbr, step) ? nbr : -1));
+    double af = 0;
+    if (sc >= 0) {
+      const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
+      const Vec3 nn = v3(W.n_int[3 * sc], W.n_int[3 * sc + 1], W.n_int[3 * sc + 2]);
+      af = fabs(W.A_int[sc] * dot(nn, Af) / norm(Af));
+    }
+    W.A_int_f[f] = af;
+    W.face_stamp[f] = step;
+  }
+}
+
+// ---- interface-modified least squares (R7) on band cells -----------------------------------------
+// L lanes per band cell over its faces; the nine sums of G and b are reduced across the lanes. A
+// crossing face contributes its crossing point x_f (k_xface) with T_sat; every face runs the same
+// instructions (the point and the value are selected, not branched on).
+template <int L>
+__global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t nb = W.counters->n_band;
+  const int lane = threadIdx.x % L;
+  const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / L);
+  int nsing = 0;
+  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / L) + threadIdx.x / L; j < nb; j += groups) {
     const int32_t c = W.band_idx[j];
     const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
     const double TP = a.T[c], aP = a.alpha[c];
     double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
-    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
       const int32_t f = M.cell_face[k] & 0x7fffffff;
       const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
       const int32_t q = o == c ? nbr : o;
-      Vec3 r;
-      double dT;
-      if (q >= 0) {
-        const double aQ = a.alpha[q];
-        if ((aP - 0.5) * (aQ - 0.5) < 0) {
-          int32_t src;
-          const double t = crossing_t(M, W, a.alpha, f, a.opt.xf_mode, step, &src);
-          const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
-          const Vec3 xn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]);
-          const Vec3 xf = xo + (xn - xo) * t;
-          r = xf - xP;
-          dT = a.props.T_sat - TP;
-          // crossing-face outputs, written once: by the owner if it is in the band
-          if (o == c || W.band_stamp[o] != step) {
-            W.x_f[3 * f] = xf.x; W.x_f[3 * f + 1] = xf.y; W.x_f[3 * f + 2] = xf.z;
-            W.d_own[f] = norm(xf - xo);
-            W.d_neigh[f] = norm(xf - xn);
-            const int32_t sc = src >= 0 ? src : (has_plane(W, o, step) ? o : (has_plane(W, nbr, step) ? nbr : -1));
-            double af = 0;
-            if (sc >= 0) {
-              const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
-              const Vec3 nn = v3(W.n_int[3 * sc], W.n_int[3 * sc + 1], W.n_int[3 * sc + 2]);
-              af = fabs(W.A_int[sc] * dot(nn, Af) / norm(Af));
-            }
-            W.A_int_f[f] = af;
-            W.face_stamp[f] = step;
-            ++ncross;
-          }
-        } else {
-          r = v3(M.cell_cen[3 * q], M.cell_cen[3 * q + 1], M.cell_cen[3 * q + 2]) - xP;
-          dT = a.T[q] - TP;
-        }
-      } else {
-        if (!a.T_bnd) continue;
-        r = v3(M.face_cen[3 * f], M.face_cen[3 * f + 1], M.face_cen[3 * f + 2]) - xP;
-        dT = a.T_bnd[f] - TP;
-      }
+      if (q < 0 && !a.T_bnd) continue;
+      const bool cross = q >= 0 && (aP - 0.5) * (a.alpha[q] - 0.5) < 0;
+      const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
+      const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
+      const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
+      const double dT = Tq - TP;
       g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
       g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
       b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
     }
-    g00 = group_sum<kLsqLanes>(g00, mask); g01 = group_sum<kLsqLanes>(g01, mask);
-    g02 = group_sum<kLsqLanes>(g02, mask); g11 = group_sum<kLsqLanes>(g11, mask);
-    g12 = group_sum<kLsqLanes>(g12, mask); g22 = group_sum<kLsqLanes>(g22, mask);
-    b0 = group_sum<kLsqLanes>(b0, mask); b1 = group_sum<kLsqLanes>(b1, mask); b2 = group_sum<kLsqLanes>(b2, mask);
+    g00 = group_sum<L>(g00, mask); g01 = group_sum<L>(g01, mask);
+    g02 = group_sum<L>(g02, mask); g11 = group_sum<L>(g11, mask);
+    g12 = group_sum<L>(g12, mask); g22 = group_sum<L>(g22, mask);
+    b0 = group_sum<L>(b0, mask); b1 = group_sum<L>(b1, mask); b2 = group_sum<L>(b2, mask);
     if (lane != 0) continue;
     // explicit symmetric inverse (cofactors / det), Appendix B
     const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
@@ -966,109 +952,146 @@ __global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
     if (W.iface_stamp[c] == step) W.status[c] |= st;
     else W.status[c] = st;
   }
-  if (ncross) atomicAdd((unsigned long long*)&W.counters->n_crossing, (unsigned long long)ncross);
   if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
 }
 
-// ---- per-side gradients and source (R5, R6) on interface cells ----------------------------------
-__global__ void k_source(MeshView M, StepArgs a, Workspace W) {
-  const int64_t n = W.counters->n_iface;
-  const int lane = threadIdx.x % kLsqLanes;
-  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
-  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
-  int nside = 0;
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + threadIdx.x / kLsqLanes; i < n; i += groups) {
-    const int32_t c = W.iface_idx[i];
-    double mdot = 0, Q = 0, ql = 0, qv = 0;
-    Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
-    const double Aint = W.A_int[c];
-    if (Aint > 0) {
-      const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
-      const bool liq = a.alpha[c] > 0.5;
-      const double sigma = liq ? -1.0 : 1.0;  // the other side: vapour (-1) or liquid (+1)
-      Vec3 acc = v3(0, 0, 0);
-      double ws = 0;
-      for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
-        const int32_t fe = M.cell_face[k];
-        const int32_t f = fe & 0x7fffffff;
-        const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
-        if (q < 0) continue;
-        if ((a.alpha[q] > 0.5) == liq) continue;
-        Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
-        if (fe < 0) Af = Af * -1.0;
-        const double w = fmax(0.0, sigma * dot(nn, Af));
-        acc = acc + v3(W.grad[3 * q], W.grad[3 * q + 1], W.grad[3 * q + 2]) * w;
-        ws += w;
-      }
-      acc = v3(group_sum<kLsqLanes>(acc.x, mask), group_sum<kLsqLanes>(acc.y, mask), group_sum<kLsqLanes>(acc.z, mask));
-      ws = group_sum<kLsqLanes>(ws, mask);
-      Vec3 go = v3(0, 0, 0);
-      if (ws > 0) go = acc * (1.0 / ws);
-      const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
-      gl = liq ? gown : go;
-      gv = liq ? go : gown;
-      ql = a.props.k_l * dot(gl, nn) * Aint;
-      qv = -a.props.k_v * dot(gv, nn) * Aint;
-      mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
-      Q = -mdot * a.props.h_lv;
-      if (lane == 0 && !(ws > 0)) {
-        W.status[c] |= VOF_ST_NO_SIDE;
-        ++nside;
-      }
-    }
-    if (lane != 0) continue;
-    a.mdot[c] = mdot;
-    a.Q[c] = Q;
-    W.q_l[c] = ql;
-    W.q_v[c] = qv;
-    W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
-    W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
-    W.mdotV[i] = mdot * M.cell_vol[c];
-    W.QV[i] = Q * M.cell_vol[c];
-  }
-  if (nside) atomicAdd((unsigned long long*)&W.counters->n_no_side, (unsigned long long)nside);
-}
+// ---- per-side gradients and source (R5, R6) on interface cells, totals (R8) -----------------------
+// The totals are the pairwise tree over the interface list (cell order) padded with zeros to a
+// power of two. Each block takes aligned tiles of kSrcTile interface cells: it computes their
+// sources (8 lanes per cell over its faces), then the tile's subtree from shared memory; the last
+// block to finish folds the tile sums in 512-leaf subtrees, level by level, so the pairing is the
+// whole tree's. Cells outside the interface get mdot = Q = 0.
 
-// ---- totals (R8): pairwise tree over the interface list padded with zeros to a power of two ------
-// One block reduces an aligned chunk of kReduceChunk leaves with the same pairing as the whole
-// tree, so chunk sums are tree nodes; the last block to finish folds the chunk sums the same way.
-// Padding with more zeros than the next power of two only adds exact "+ 0.0" nodes.
-__device__ void tree_block(const double* x, int64_t n, int64_t base, double* s, double* out) {
-  // Thread t pairs leaves 2t and 2t+1; the next five levels pair neighbouring lanes inside the
-  // warp (lane t + 2^k joins lane t), which is the same pairing as the level-by-level tree; the
-  // 32 warp sums then go through the last five levels in warp 0.
-  const int t = threadIdx.x;  // blockDim.x == kReduceChunk / 2 == 1024
-  const int lane = t & 31;
-  const int64_t i0 = base + 2 * t, i1 = i0 + 1;
-  double v = (i0 < n ? __ldcg(x + i0) : 0.0) + (i1 < n ? __ldcg(x + i1) : 0.0);
+// Pairwise tree of x[base, base + 512) (zeros past n) in a 256-thread block; the result is valid in
+// thread 0. Thread t pairs leaves 2t and 2t+1, lanes then pair their neighbours (lane t + 2^k
+// joins lane t), and warp 0 pairs the eight warp sums.
+__device__ double block_tree512(const double* x, int64_t n, int64_t base, double* s8) {
+  const int t = threadIdx.x, lane = t & 31;
+  const int64_t i0 = base + 2 * t;
+  double v = (i0 < n ? __ldcg(x + i0) : 0.0) + (i0 + 1 < n ? __ldcg(x + i0 + 1) : 0.0);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double w = __shfl_down_sync(0xffffffffu, v, o);
     if ((lane & (2 * o - 1)) == 0) v += w;
   }
-  if (lane == 0) s[t >> 5] = v;
+  if (lane == 0) s8[t >> 5] = v;
   __syncthreads();
+  double r = 0;
   if (t < 32) {
-    v = s[t];
+    v = t < 8 ? s8[t] : 0.0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < 8; o <<= 1) {
       const double w = __shfl_down_sync(0xffffffffu, v, o);
       if ((lane & (2 * o - 1)) == 0) v += w;
     }
-    if (t == 0) *out = v;
+    r = v;
   }
   __syncthreads();
+  return r;
 }
 
-__global__ void __launch_bounds__(kReduceChunk / 2) k_totals(Workspace W, double* totals) {
-  __shared__ double s[kReduceChunk / 2];
+__global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Workspace W) {
+  __shared__ double tm[kSrcTile], tq[kSrcTile], s8[8];
   __shared__ bool last;
+  const uint32_t step = W.counters->step;
   const int64_t n = W.counters->n_iface;
-  const int64_t nchunks = (n + kReduceChunk - 1) / kReduceChunk;
-  for (int64_t b = blockIdx.x; b < nchunks; b += gridDim.x) {
-    tree_block(W.mdotV, n, b * kReduceChunk, s, &W.partial[b]);
-    tree_block(W.QV, n, b * kReduceChunk, s, &W.partial[2 * kMaxPartials + b]);
+  const int64_t ntiles = (n + kSrcTile - 1) / kSrcTile;
+  const int64_t tcap = (M.n_cells + kSrcTile - 1) / kSrcTile;
+  const int lane = threadIdx.x % kLsqLanes;
+  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
+  constexpr int kPerPass = kThreads / kLsqLanes;  // cells per pass of the block
+  int nside = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int pass = 0; pass < kSrcTile / kPerPass; ++pass) {
+      const int slot = pass * kPerPass + threadIdx.x / kLsqLanes;
+      const int64_t i = tile * kSrcTile + slot;
+      double mV = 0, qV = 0;
+      if (i < n) {
+        const int32_t c = W.iface_idx[i];
+        double mdot = 0, Q = 0, ql = 0, qv = 0;
+        Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
+        const double Aint = W.A_int[c];
+        if (Aint > 0) {
+          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+          const bool liq = a.alpha[c] > 0.5;
+          const double sigma = liq ? -1.0 : 1.0;  // the other side: vapour (-1) or liquid (+1)
+          Vec3 acc = v3(0, 0, 0);
+          double ws = 0;
+          for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+            const int32_t fe = M.cell_face[k];
+            const int32_t f = fe & 0x7fffffff;
+            const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
+            if (q < 0) continue;
+            if ((a.alpha[q] > 0.5) == liq) continue;
+            Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
+            if (fe < 0) Af = Af * -1.0;
+            const double w = fmax(0.0, sigma * dot(nn, Af));
+            acc = acc + v3(W.grad[3 * q], W.grad[3 * q + 1], W.grad[3 * q + 2]) * w;
+            ws += w;
+          }
+          acc = v3(group_sum<kLsqLanes>(acc.x, mask), group_sum<kLsqLanes>(acc.y, mask),
+                   group_sum<kLsqLanes>(acc.z, mask));
+          ws = group_sum<kLsqLanes>(ws, mask);
+          Vec3 go = v3(0, 0, 0);
+          if (ws > 0) go = acc * (1.0 / ws);
+          const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
+          gl = liq ? gown : go;
+          gv = liq ? go : gown;
+          ql = a.props.k_l * dot(gl, nn) * Aint;
+          qv = -a.props.k_v * dot(gv, nn) * Aint;
+          mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
+          Q = -mdot * a.props.h_lv;
+          if (lane == 0 && !(ws > 0)) {
+            W.status[c] |= VOF_ST_NO_SIDE;
+            ++nside;
+          }
+        }
+        mV = mdot * M.cell_vol[c];
+        qV = Q * M.cell_vol[c];
+        if (lane == 0) {
+          a.mdot[c] = mdot;
+          a.Q[c] = Q;
+          W.q_l[c] = ql;
+          W.q_v[c] = qv;
+          W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
+          W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
+          W.mdotV[i] = mV;
+          W.QV[i] = qV;
+        }
+      }
+      if (lane == 0) {
+        tm[slot] = mV;
+        tq[slot] = qV;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // the tile's subtree: lane t pairs leaves 2t and 2t+1, then five levels across the lanes
+      const int t = threadIdx.x;
+      double vm = tm[2 * t] + tm[2 * t + 1], vq = tq[2 * t] + tq[2 * t + 1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double wm = __shfl_down_sync(0xffffffffu, vm, o), wq = __shfl_down_sync(0xffffffffu, vq, o);
+        if ((t & (2 * o - 1)) == 0) {
+          vm += wm;
+          vq += wq;
+        }
+      }
+      if (t == 0) {
+        W.tile_part[tile] = vm;
+        W.tile_part[tcap + tile] = vq;
+      }
+    }
+    __syncthreads();
   }
+  if (nside) atomicAdd((unsigned long long*)&W.counters->n_no_side, (unsigned long long)nside);
+  // every other cell: no source
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.n_cells; c += (int64_t)gridDim.x * blockDim.x)
+    if (W.iface_stamp[c] != step) {
+      a.mdot[c] = 0.0;
+      a.Q[c] = 0.0;
+    }
+  // the last block folds the tile sums
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&W.counters->reduce_done, 1u) == gridDim.x - 1;
@@ -1076,24 +1099,27 @@ __global__ void __launch_bounds__(kReduceChunk / 2) k_totals(Workspace W, double
   if (!last) return;
   __threadfence();
   for (int q = 0; q < 2; ++q) {
-    double* A = W.partial + 2 * q * kMaxPartials;
-    double* B = A + kMaxPartials;
-    int64_t m = nchunks;
+    const double* src = W.tile_part + q * tcap;
+    double* bufs[2] = {W.partial + 2 * q * kMaxPartials, W.partial + (2 * q + 1) * kMaxPartials};
+    int64_t m = ntiles;
+    int pp = 0;
     while (m > 1) {
-      const int64_t mc = (m + kReduceChunk - 1) / kReduceChunk;
-      for (int64_t b = 0; b < mc; ++b) tree_block(A, m, b * kReduceChunk, s, &B[b]);
-      __threadfence_block();
-      double* t = A;
-      A = B;
-      B = t;
+      const int64_t mc = (m + 511) / 512;
+      double* dst = bufs[pp];
+      for (int64_t b = 0; b < mc; ++b) {
+        const double r = block_tree512(src, m, b * 512, s8);
+        if (threadIdx.x == 0) dst[b] = r;
+      }
+      __syncthreads();
+      src = dst;
+      pp ^= 1;
       m = mc;
     }
-    if (threadIdx.x == 0) totals[q] = m == 0 ? 0.0 : __ldcg(A);
+    if (threadIdx.x == 0) a.totals[q] = m == 0 ? 0.0 : __ldcg(src);
     __syncthreads();
   }
   if (threadIdx.x == 0) W.counters->reduce_done = 0;
 }
-
 
 // Lanes per cell of a bin: the autotuned choice, else about four tetrahedra per lane with the
 // bin's rows within ~110 KB of shared memory per block.
@@ -1112,8 +1138,10 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   const int max_ct = m->bin_max_ct[bin];
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
-  while (threads > 32 && threads > G && (size_t)(threads / G) * max_ct * sizeof(TetRow) > 110 * 1024) threads /= 2;
-  const size_t smem = (size_t)(threads / G) * max_ct * sizeof(TetRow);
+  const int max_cv = m->max_cv;
+  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float);
+  while (threads > 32 && threads > G && (size_t)(threads / G) * grp_bytes > 110 * 1024) threads /= 2;
+  const size_t smem = (size_t)(threads / G) * grp_bytes;
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
@@ -1125,7 +1153,7 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   if (bps < 1) bps = 1;
   const int64_t need = (m->bin_cells[bin] + (threads / G) - 1) / (threads / G);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
-  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, learned, bin);
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, learned, bin);
   return cudaGetLastError();
 }
 
@@ -1146,17 +1174,13 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   W.alpha_in = d_alpha;
   Timing& tm = m->timing;
   tm.start(KC_SELECT, s);
-  k_begin<<<1, 1, 0, s>>>(W.counters);
-  k_sel_count<<<m->n_sel_blocks, kThreads, 0, s>>>(M.n_cells, d_alpha, opt.alpha_eps, W.blk_count);
+  k_sel_count<<<m->n_sel_blocks, kThreads, 0, s>>>(M.n_cells, d_alpha, opt.alpha_eps, W.blk_count, W.counters);
   k_sel_scan<<<1, 1024, 0, s>>>(m->n_sel_blocks, W.blk_count, W.blk_off, W.counters);
   k_sel_scatter<<<m->n_sel_blocks, kThreads, 0, s>>>(M, d_alpha, opt.alpha_eps, W);
   k_mark<<<m->num_sms * 4, kThreads, 0, s>>>(M, W);
   tm.stop(s);
   const int vgrid = (int)std::min<int64_t>((M.n_verts + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
   tm.start(KC_VERTEX, s);
-  k_bv_count<<<m->n_sel_blocks + m->n_vert_blocks, kThreads, 0, s>>>(M.n_cells, M.n_verts, m->n_sel_blocks, W);
-  k_bv_scan<<<1, 1024, 0, s>>>(m->n_sel_blocks, m->n_vert_blocks, W);
-  k_bv_scatter<<<m->n_sel_blocks + m->n_vert_blocks, kThreads, 0, s>>>(M.n_cells, M.n_verts, m->n_sel_blocks, W);
   k_vertex<<<vgrid, kThreads, 0, s>>>(M, d_alpha, opt.vertex_mode, W);
   tm.stop(s);
   cudaError_t e = cudaGetLastError();
@@ -1205,19 +1229,15 @@ cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options&
 vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s) {
   const MeshView& M = m->view;
   Workspace& W = m->ws;
-  cudaMemsetAsync(a.mdot, 0, M.n_cells * sizeof(double), s);
-  cudaMemsetAsync(a.Q, 0, M.n_cells * sizeof(double), s);
   Timing& tm = m->timing;
   const int cgrid = (int)std::min<int64_t>((M.n_cells + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
   tm.start(KC_LSQ, s);
-  k_lsq<<<cgrid, kThreads, 0, s>>>(M, a, W);
+  k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
+  k_xface<<<m->num_sms * 8, 64, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
+  k_lsq<kLsqCellLanes><<<cgrid, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   tm.start(KC_SOURCE, s);
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
-  tm.stop(s);
-  const int rgrid = (int)std::min<int64_t>((M.n_cells + kReduceChunk - 1) / kReduceChunk, 32);
-  tm.start(KC_TOTALS, s);
-  k_totals<<<std::max(rgrid, 1), kReduceChunk / 2, 0, s>>>(W, a.totals);
   tm.stop(s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "source kernels");
