@@ -212,14 +212,10 @@ class Mesh:
     FLOPS_TET_EVAL, FLOPS_TET_PREP, FLOPS_TET_SECTION, FLOPS_EVAL = 8, 24, 60, 2
 
     def root_flops(self, counts: dict) -> int:
-        """Algorithmic FP64 flops of the root-search launches summed in `counts` (FP64 rows
-        prepared, tetrahedron evaluations, per-evaluation scaling)."""
+        """Algorithmic FP64 flops of the root-search launches summed in `counts`: rows prepared,
+        tetrahedron evaluations, per-evaluation scaling, and the sections of the cut tetrahedra."""
         return (self.FLOPS_TET_EVAL * counts["tet_evals"] + self.FLOPS_TET_PREP * counts["tets_prepared"]
-                + self.FLOPS_EVAL * counts["evals_total"])
-
-    def geom_flops(self, counts: dict) -> int:
-        """Algorithmic FP64 flops of the interface-geometry launches (cut tetrahedra)."""
-        return self.FLOPS_TET_SECTION * counts["tets_sectioned"]
+                + self.FLOPS_TET_SECTION * counts["tets_sectioned"] + self.FLOPS_EVAL * counts["evals_total"])
 
     def counts(self, stream=None) -> dict:
         c = Counts()

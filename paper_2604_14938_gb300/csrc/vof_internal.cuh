@@ -177,6 +177,9 @@ struct vof_mesh {
   cudaStream_t bin_stream[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // side branch of a whole step: crossing-face list, from the band to the least squares
+  cudaStream_t xm_stream = nullptr;
+  cudaEvent_t ev_xfork = nullptr, ev_xjoin = nullptr;
 };
 
 namespace vof {
@@ -184,8 +187,12 @@ void set_error(const std::string& msg);
 vof_status cuda_fail(cudaError_t e, const char* what);
 
 // step kernels (vof_step.cu)
-vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s);
-vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s);
+// early_xmark: the step's source stage will use the same alpha, so the crossing faces are listed
+// on a side branch as soon as the band is known, and launch_source(..., xmark_done = true) only
+// joins that branch.
+vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s,
+                              bool early_xmark = false);
+vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xmark_done = false);
 cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
                             int bin, int G);
 }  // namespace vof

@@ -247,6 +247,9 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
   {
     cudaError_t es = cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaStreamCreateWithFlags(&m->xm_stream, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xfork, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xjoin, cudaEventDisableTiming);
     for (int b = 0; b < kBins && es == cudaSuccess; ++b) {
       es = cudaStreamCreateWithFlags(&m->bin_stream[b], cudaStreamNonBlocking);
       if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_join[b], cudaEventDisableTiming);
@@ -370,6 +373,11 @@ void destroy(vof_mesh* m) {
   }
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
   m->ev_fork = nullptr;
+  if (m->xm_stream) cudaStreamDestroy(m->xm_stream);
+  if (m->ev_xfork) cudaEventDestroy(m->ev_xfork);
+  if (m->ev_xjoin) cudaEventDestroy(m->ev_xjoin);
+  m->xm_stream = nullptr;
+  m->ev_xfork = m->ev_xjoin = nullptr;
 }
 
 }  // namespace
@@ -457,16 +465,23 @@ vof_status vof_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options
   return st;
 }
 
-vof_status vof_phase_change_source(vof_mesh* m, const double* d_alpha, const double* d_T, const double* d_T_bnd,
-                                   const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q,
-                                   double* d_totals, void* stream) {
+static vof_status check_source_args(const vof_mesh* m, const double* d_alpha, const double* d_T, const vof_props* props,
+                                    const vof_options* opt, const double* d_mdot, const double* d_Q,
+                                    const double* d_totals) {
   if (!m || !d_alpha || !d_T || !props || !d_mdot || !d_Q || !d_totals) { set_error("null argument"); return VOF_EINVAL; }
   if (vof_status st = check_opt(opt)) return st;
-  if (!m->recon_done) { set_error("vof_phase_change_source called before vof_reconstruct"); return VOF_ESTATE; }
   if (!(props->h_lv > 0) || !(props->k_l >= 0) || !(props->k_v >= 0) || !std::isfinite(props->T_sat)) {
     set_error("bad properties");
     return VOF_EINVAL;
   }
+  return VOF_OK;
+}
+
+vof_status vof_phase_change_source(vof_mesh* m, const double* d_alpha, const double* d_T, const double* d_T_bnd,
+                                   const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q,
+                                   double* d_totals, void* stream) {
+  if (vof_status st = check_source_args(m, d_alpha, d_T, props, opt, d_mdot, d_Q, d_totals)) return st;
+  if (!m->recon_done) { set_error("vof_phase_change_source called before vof_reconstruct"); return VOF_ESTATE; }
   StepArgs a{d_alpha, d_T, d_T_bnd, d_mdot, d_Q, d_totals, *props, *opt};
   return launch_source(m, a, (cudaStream_t)stream);
 }
@@ -474,9 +489,13 @@ vof_status vof_phase_change_source(vof_mesh* m, const double* d_alpha, const dou
 vof_status vof_step(vof_mesh* m, const double* d_alpha, const double* d_T, const double* d_T_bnd,
                     const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q, double* d_totals,
                     void* stream) {
-  vof_status st = vof_reconstruct(m, d_alpha, opt, stream);
+  // both stages see the same alpha, so the crossing-face list runs on a side branch
+  if (vof_status st = check_source_args(m, d_alpha, d_T, props, opt, d_mdot, d_Q, d_totals)) return st;
+  vof_status st = launch_reconstruct(m, d_alpha, *opt, (cudaStream_t)stream, true);
   if (st) return st;
-  return vof_phase_change_source(m, d_alpha, d_T, d_T_bnd, props, opt, d_mdot, d_Q, d_totals, stream);
+  m->recon_done = true;
+  StepArgs a{d_alpha, d_T, d_T_bnd, d_mdot, d_Q, d_totals, *props, *opt};
+  return launch_source(m, a, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

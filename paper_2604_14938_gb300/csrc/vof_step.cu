@@ -490,8 +490,63 @@ __device__ __forceinline__ float liquid_volume32(const TetRow32* rows, int nt, i
   return part;
 }
 
+// Interface geometry of one cell at the isovalue c (paper Sec. 2.1): vector area (wet -> dry),
+// area and area moment of the cut polygons, summed over the cell's tetrahedra by G lanes. A first
+// pass classifies the tetrahedra (integer work only) and appends the cut ones to the group's list
+// lst in shared memory, in tetrahedron order; the FP64 sections then run over that list with
+// every lane busy. Returns the number of cut tetrahedra.
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
+__device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace& W, const int32_t* cv, int64_t t0,
+                                             int nt, double c, int lane, unsigned mask, uint16_t* lst, Vec3& A,
+                                             double& area, Vec3& mom) {
+  const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
+  const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const uint64_t kc = okey(c);
+  const double p_apex = W.phi_v[cv[0]];
+  const unsigned m0 = (unsigned)(okey(p_apex) >= kc);
+  int n_cut = 0;
+  for (int r0 = 0; r0 < nt; r0 += G) {
+    const int t = r0 + lane;
+    unsigned m = 0;
+    if (t < nt) {
+      const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+      m = m0 | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
+          ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
+          ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
+    }
+    const bool cut = t < nt && m != 0 && m != 15u;
+    const unsigned bal = (__ballot_sync(mask, cut) >> base) & gbits;
+    if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((t << 4) | m);
+    n_cut += __popc(bal);
+  }
+  __syncwarp(mask);
+  A = v3(0, 0, 0);
+  mom = v3(0, 0, 0);
+  area = 0;
+  const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
+  for (int jj = lane; jj < n_cut; jj += G) {
+    const unsigned e = lst[jj];
+    const int t = (int)(e >> 4);
+    const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+    const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
+    const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
+    const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
+    const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
+    Vec3 tA, tm;
+    double ta;
+    tet_section(P0, P1, P2, P3, p_apex, W.phi_v[g1], W.phi_v[g2], W.phi_v[g3], e & 15u, c, tA, ta, tm);
+    A = A + tA;
+    area += ta;
+    mom = mom + tm;
+  }
+  A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
+  area = group_sum<G>(area, mask);
+  mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
+  return n_cut;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
                                                    int max_ct, int max_cv, int learned, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gib = threadIdx.x / G;  // group in block
@@ -503,7 +558,7 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
   float* uvert = reinterpret_cast<float*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow));
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
-  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0, sect_acc = 0;
   // each group takes the next cell of the bin when it is done with the last one: the learned
   // path's fallback cells cost ten times a typical cell, so a static split leaves SMs idle
   for (;;) {
@@ -576,10 +631,19 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
           u0 = 1.0f - (float)a;
         }
         const double range = hi - lo;
+        // Local FP32 coordinate u in [-1, 0] with the minority phase next to u = 0: for
+        // alpha <= 1/2, u = (phi - phi_max)/range and the wet volume is matched to t = alpha; for
+        // alpha > 1/2, u = (phi_min - phi)/range (the field reflected) and the wet volume of the
+        // reflected field, the original dry volume, is matched to t = 1 - alpha. A small volume
+        // fraction and a root next to an extreme vertex value then keep their relative precision.
+        const bool refl = a > 0.5;
+        const double org = refl ? lo : hi, dir = refl ? -1.0 : 1.0;
+        const float af = (float)(refl ? 1.0 - a : a);
+        float ubest, slope;
         {
           TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
-          const double irange = 1.0 / range;
-          for (int j = lane; j < nv; j += G) uvert[j] = (float)((W.phi_v[cv[j]] - lo) * irange);
+          const double srange = dir / range;
+          for (int j = lane; j < nv; j += G) uvert[j] = (float)((W.phi_v[cv[j]] - org) * srange);
           __syncwarp(mask);
           for (int t = lane; t < nt; t += G) {
             const uint32_t pk = __ldg(M.cell_tet + t0 + t);
@@ -587,16 +651,16 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
                                       __ldg(M.tet_vfrac + t0 + t));
           }
           __syncwarp(mask);
-          const float af = (float)a;
-          float ua = 0.f, fa = 1.f - af, ub = 1.f, fb = -af;  // f(ua) > 0 > f(ub)
-          float uc = fminf(fmaxf(u0, 0.f), 1.f);
+          float ua = -1.f, fa = 1.f - af, ub = 0.f, fb = -af;  // f(ua) > 0 > f(ub)
+          float uc = fminf(fmaxf(refl ? -u0 : u0 - 1.f, -1.f), 0.f);
           float fc = liquid_volume32<G>(rows32, nt, lane, mask, uc) - af;
           ++evals32;
           float up = uc, fp = fc;  // previous raw evaluation (for the slope)
           int side = 0;
           for (int it = 0; it < 16; ++it) {
             if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
-            if (fabsf(fc) < 2e-6f || ub - ua < 4e-6f) break;
+            // relative tests: |f| against the target, the bracket against its distance from 0
+            if (fabsf(fc) <= 1e-6f * af || ub - ua <= 1e-6f * fmaxf(fabsf(ua), fabsf(ub))) break;
             // regula falsi step; Illinois: halve the retained end's value after two steps on one side
             float un;
             if (it == 0) {
@@ -617,15 +681,18 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
             }
             side = s2;
           }
-          // slope df/du from the last two raw FP32 evaluations (else from the bracket)
-          float slope = (uc != up) ? (fc - fp) / (uc - up) : 0.f;
+          // slope df/du from the last two raw FP32 evaluations (else from the bracket); with
+          // c = org + dir u range and f = dir (V/V_cell - alpha), df/dc is slope / range either way
+          slope = (uc != up) ? (fc - fp) / (uc - up) : 0.f;
           if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
-          const float ubest = uc;
+          ubest = uc;
+        }
+        {
           __syncwarp(mask);
           prepare64();
           prepared = true;
           // FP64 phase
-          double c1 = dmin(dmax(lo + (double)ubest * range, lo), hi);
+          double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
           double f1 = eval64(c1);
           double spread = 1e-6 * range;  // distance between the first two FP64 points
           if (!done && opt.max_secant > 0) {
@@ -676,10 +743,28 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
       }
       if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
     }
+    // interface geometry at c_best; the rows' shared memory now holds the cut list
+    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
+    double area = 0;
+    if (!(status & VOF_ST_DEGENERATE)) {
+      __syncwarp(mask);
+      sect_acc += cell_geometry<G>(M, W, cv, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows), A,
+                                   area, mom);
+    }
     if (lane == 0) {
       W.iso[cell] = c_best;
       W.status[cell] = status;
       W.evals[cell] = evals;
+      W.A_int[cell] = area;
+      const double an = norm(A);
+      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
+      W.n_int[3 * cell] = A.x * inv;
+      W.n_int[3 * cell + 1] = A.y * inv;
+      W.n_int[3 * cell + 2] = A.z * inv;
+      const double ia = area > 0 ? 1.0 / area : 0.0;
+      W.x_gamma[3 * cell] = mom.x * ia;
+      W.x_gamma[3 * cell + 1] = mom.y * ia;
+      W.x_gamma[3 * cell + 2] = mom.z * ia;
       evals_acc += evals;
       ev32_acc += evals32;
       tetev_acc += (int64_t)evals * nt;
@@ -696,119 +781,10 @@ __global__ void __launch_bounds__(kThreads) k_root(MeshView M, const double* alp
     atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
     atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
     if (ev32_acc) atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
+    if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
   }
 }
 
-// Interface geometry at the isovalue found by k_root (paper Sec. 2.1): area, unit normal (vapour
-// -> liquid) and centroid of the reconstructed surface, summed over the cell's cut tetrahedra.
-// G lanes per cell. A first pass classifies the tetrahedra (integer work only) and appends the
-// cut ones to the group's list in shared memory, in tetrahedron order; the FP64 sections then
-// run over that list with every lane busy. The work is proportional to the tetrahedron count,
-// so cells are split statically.
-template <int G>
-__global__ void __launch_bounds__(kThreads, 2) k_geom(MeshView M, Workspace W, int bin, int max_ct) {
-  extern __shared__ uint16_t cut_list[];
-  const int kGroups = blockDim.x / G;
-  const int gib = threadIdx.x / G;
-  const int lane = threadIdx.x % G;
-  const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
-  const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-  const unsigned mask = gbits << base;
-  uint16_t* lst = cut_list + (size_t)gib * max_ct;
-  const int64_t n_bin = W.counters->bin_count[bin];
-  const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
-  const int64_t n_groups = (int64_t)gridDim.x * kGroups;
-  // warps filled with 32 / G consecutive cells, consecutive warps spread over the blocks first
-  const int64_t j0 = ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * (32 / G) + (threadIdx.x & 31) / G;
-  int64_t sect_acc = 0;
-  for (int64_t j = j0; j < n_bin; j += n_groups) {
-    const int32_t cell = W.iface_idx[list[j]];
-    const int status = W.status[cell];
-    const double c = W.iso[cell];
-    const int64_t v0 = M.cell_vert_off[cell];
-    const int64_t t0 = M.cell_tet_off[cell];
-    const int nt = (int)(M.cell_tet_off[cell + 1] - t0);
-    const int32_t* cv = M.cell_vert + v0;
-    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
-    double area = 0;
-    if (!(status & VOF_ST_DEGENERATE)) {
-      const uint64_t kc = okey(c);
-      const double p_apex = W.phi_v[cv[0]];
-      const unsigned m0 = (unsigned)(okey(p_apex) >= kc);
-      int n_cut = 0;
-      for (int r0 = 0; r0 < nt; r0 += G) {
-        const int t = r0 + lane;
-        unsigned m = 0;
-        if (t < nt) {
-          const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-          m = m0 | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
-              ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
-              ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
-        }
-        const bool cut = t < nt && m != 0 && m != 15u;
-        const unsigned bal = (__ballot_sync(mask, cut) >> base) & gbits;
-        if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((t << 4) | m);
-        n_cut += __popc(bal);
-      }
-      __syncwarp(mask);
-      const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
-      for (int jj = lane; jj < n_cut; jj += G) {
-        const unsigned e = lst[jj];
-        const int t = (int)(e >> 4);
-        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-        const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
-        const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
-        const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
-        const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
-        Vec3 tA, tm;
-        double ta;
-        tet_section(P0, P1, P2, P3, p_apex, W.phi_v[g1], W.phi_v[g2], W.phi_v[g3], e & 15u, c, tA, ta, tm);
-        A = A + tA;
-        area += ta;
-        mom = mom + tm;
-      }
-      sect_acc += lane == 0 ? n_cut : 0;
-      A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
-      area = group_sum<G>(area, mask);
-      mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
-    }
-    if (lane == 0) {
-      W.A_int[cell] = area;
-      const double an = norm(A);
-      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
-      W.n_int[3 * cell] = A.x * inv;
-      W.n_int[3 * cell + 1] = A.y * inv;
-      W.n_int[3 * cell + 2] = A.z * inv;
-      const double ia = area > 0 ? 1.0 / area : 0.0;
-      W.x_gamma[3 * cell] = mom.x * ia;
-      W.x_gamma[3 * cell + 1] = mom.y * ia;
-      W.x_gamma[3 * cell + 2] = mom.z * ia;
-    }
-    __syncwarp(mask);  // the list is reused by the group's next cell
-  }
-  if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
-}
-
-// Geometry lanes per cell of a bin: about three cut tetrahedra per lane (two thirds of a cell's
-// tetrahedra are cut on these meshes).
-template <int G>
-void launch_geom_g(vof_mesh* m, cudaStream_t s, int bin) {
-  const int max_ct = std::max(1, m->bin_max_ct[bin]);
-  const size_t smem = (size_t)(kThreads / G) * max_ct * sizeof(uint16_t);
-  const int64_t need = (m->bin_cells[bin] + (kThreads / G) - 1) / (kThreads / G);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * 2));  // resident
-  k_geom<G><<<grid, kThreads, smem, s>>>(m->view, m->ws, bin, max_ct);
-}
-
-void launch_geom_bin(vof_mesh* m, cudaStream_t s, int bin) {
-  switch (bin) {
-    case 0: launch_geom_g<1>(m, s, bin); break;
-    case 1: launch_geom_g<2>(m, s, bin); break;
-    case 2: launch_geom_g<4>(m, s, bin); break;
-    case 3: launch_geom_g<8>(m, s, bin); break;
-    default: launch_geom_g<16>(m, s, bin); break;
-  }
-}
 
 // ---- crossing point (R4) -----------------------------------------------------------------------
 __device__ __forceinline__ bool has_plane(const Workspace& W, int32_t c, uint32_t step) {
@@ -1163,7 +1139,8 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s);  // vof_mlp.cu
 cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
                             int bin, int G);
 
-vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s) {
+vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s,
+                              bool early_xmark) {
   const int learned = opt.root_mode == VOF_ROOT_LEARNED;
   if (learned && !m->mlp) {
     set_error("learned root search requested but no MLP weights are set");
@@ -1179,6 +1156,15 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   k_sel_scatter<<<m->n_sel_blocks, kThreads, 0, s>>>(M, d_alpha, opt.alpha_eps, W);
   k_mark<<<m->num_sms * 4, kThreads, 0, s>>>(M, W);
   tm.stop(s);
+  if (early_xmark) {
+    // crossing faces next to the band: needed only by the least squares
+    cudaEventRecord(m->ev_xfork, s);
+    cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
+    tm.start(KC_LSQ, m->xm_stream);
+    k_xmark<<<m->num_sms * 4, kThreads, 0, m->xm_stream>>>(M, d_alpha, W);
+    tm.stop(m->xm_stream);
+    cudaEventRecord(m->ev_xjoin, m->xm_stream);
+  }
   const int vgrid = (int)std::min<int64_t>((M.n_verts + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
   tm.start(KC_VERTEX, s);
   k_vertex<<<vgrid, kThreads, 0, s>>>(M, d_alpha, opt.vertex_mode, W);
@@ -1192,7 +1178,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
   k_bin<<<m->num_sms * 2, kThreads, 0, s>>>(M, W);
-  // one branch per non-empty bin: root search, then geometry; the branches join on s
+  // one branch per non-empty bin (root search and geometry); the branches join on s
   e = cudaEventRecord(m->ev_fork, s);
   for (int b = 0; b < kBins && e == cudaSuccess; ++b) {
     if (!m->bin_cells[b]) continue;
@@ -1203,10 +1189,6 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     e = launch_root_bin(m, d_alpha, opt, sb, learned, b, pick_group(m, opt, b));
     tm.stop(sb);
     if (e != cudaSuccess) break;
-    tm.start(KC_GEOM, sb);
-    launch_geom_bin(m, sb, b);
-    tm.stop(sb);
-    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(m->ev_join[b], sb);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_join[b], 0);
   }
@@ -1226,13 +1208,14 @@ cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options&
   }
 }
 
-vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s) {
+vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xmark_done) {
   const MeshView& M = m->view;
   Workspace& W = m->ws;
   Timing& tm = m->timing;
   const int cgrid = (int)std::min<int64_t>((M.n_cells + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
+  if (xmark_done) cudaStreamWaitEvent(s, m->ev_xjoin, 0);
   tm.start(KC_LSQ, s);
-  k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
+  if (!xmark_done) k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
   k_xface<<<m->num_sms * 8, 64, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
   k_lsq<kLsqCellLanes><<<cgrid, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
