@@ -193,7 +193,7 @@ def run_ours(args, rank, world, dev):
         tuned = {}
         for mode in modes:
             opt = vof.default_options(root_mode=vof.ROOT_LEARNED if mode == "learned" else vof.ROOT_BISECT)
-            tuned[mode] = M.autotune(ta_k[0], opt, reps=3)  # lanes per cell of each bin, for this mode
+            tuned[mode] = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
 
             def one(k):
                 ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
@@ -363,7 +363,7 @@ def main():
     ksum = sum(v[0] for v in r["ktime"].values())
     share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
     nbins = sum(1 for c in M.bin_cells if c)  # the root search (with the geometry) launches once per non-empty bin
-    per_step = 10 + nbins + (2 if best == "learned" else 0) + (1 if info["batch"] else 0)
+    per_step = 5 + nbins + (2 if best == "learned" else 0) + (1 if info["batch"] else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -27,7 +27,7 @@ struct Counters {
   uint32_t step;        // incremented on the device every step (membership stamps)
   uint32_t reduce_done; // blocks finished in the totals reduction
   int64_t n_iface, n_band, n_crossing;
-  int64_t n_uvert;  // distinct vertices of interface cells
+  int64_t n_uvert;  // distinct vertices of interface cells (vertex field values computed)
   int64_t n_degenerate, n_not_converged, n_fallback, n_singular, n_no_side, n_mlp_skipped;
   int64_t evals_total;
   // algorithmic work of the root search: tetrahedron evaluations (sum of evals x tets per cell),
@@ -52,6 +52,7 @@ struct MeshView {
   const uint32_t* cell_tet;  // three local vertex indices (8 bits each) of the base triangle
   const double* tet_vol;     // positive volumes, apex = local vertex 0
   const float* tet_vfrac;    // tet_vol / cell volume, FP32
+  const float2* rel_pos;     // [cell-vertex entry][3]: vertex - apex of the cell, as (hi, lo) float pairs
   const int64_t* vert_cell_off;
   const int32_t* vert_cell;
   const double* vert_w;      // inverse-distance weights, normalised per vertex
@@ -71,8 +72,8 @@ struct Workspace {
   int64_t* blk_count;      // [n_sel_blocks]
   int64_t* blk_off;        // [n_sel_blocks]
   int32_t* band_idx;       // [n_cells] band cells (unordered)
-  int32_t* vert_idx;       // [n_verts] vertices of interface cells (unordered)
   double* phi_v;           // [n_verts]
+  float2* phi_ff;          // [n_verts] phi_v as a (hi, lo) float pair
   double* iso;             // [n_cells]
   double* A_int;           // [n_cells]
   double* n_int;           // [n_cells][3]
@@ -157,13 +158,14 @@ struct GraphCache {
 
 struct vof_mesh {
   int64_t n_cells = 0, n_faces = 0, n_verts = 0;
-  int max_cv = 0, max_ct = 0;
+  int max_cv = 0, max_ct = 0, max_cf = 0;  // vertices, tetrahedra, faces of the largest cell
   double mean_ct = 0;  // tetrahedra per cell, mean
   int64_t bin_cells[vof::kBins] = {0, 0, 0, 0, 0};  // cells of the mesh per bin
   int bin_max_ct[vof::kBins] = {0, 0, 0, 0, 0};     // largest tetrahedron count per bin
   int bin_G[vof::kBins] = {0, 0, 0, 0, 0};          // lanes per cell (autotuned; 0 = default)
   int n_sel_blocks = 0;
   int num_sms = 0;
+  int sel_grid = 0;  // blocks of the cooperative selection launch (all resident)
   vof::MeshView view{};
   vof::Workspace ws{};
   std::vector<void*> allocs;

@@ -83,6 +83,24 @@ __global__ void k_cell_geom(int64_t nc, const int64_t* cvo, const int32_t* cv, c
   for (int64_t t = cto[c]; t < cto[c + 1]; ++t) tvf[t] = (float)(tvol[t] / sv);
 }
 
+// Vertex positions relative to the cell's apex (local vertex 0), split into (hi, lo) float pairs
+// (hi = x rounded to FP32, lo = the rest rounded to FP32): the interface geometry of a step runs
+// on the FP32 pipe in pair arithmetic.
+__global__ void k_rel_pos(int64_t nc, const int64_t* cvo, const int32_t* cv, const double* vx, const double* vy,
+                          const double* vz, float2* rel) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int32_t a = cv[cvo[c]];
+  for (int64_t k = cvo[c]; k < cvo[c + 1]; ++k) {
+    const int32_t v = cv[k];
+    const double d[3] = {vx[v] - vx[a], vy[v] - vy[a], vz[v] - vz[a]};
+    for (int q = 0; q < 3; ++q) {
+      const float h = __double2float_rn(d[q]);
+      rel[3 * k + q] = make_float2(h, __double2float_rn(d[q] - (double)h));
+    }
+  }
+}
+
 // Inverse-distance weights of the cells around each vertex, normalised to sum 1.
 __global__ void k_idw(int64_t nv, const int64_t* vco, const int32_t* vc, const double* vx, const double* vy,
                       const double* vz, const double* cen, double* w) {
@@ -235,6 +253,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
 
   m->n_cells = nc; m->n_faces = nf; m->n_verts = nv;
   m->max_cv = max_cv; m->max_ct = max_ct;
+  for (int64_t c = 0; c < nc; ++c) m->max_cf = std::max(m->max_cf, (int)(d->cell_face_off[c + 1] - d->cell_face_off[c]));
   m->mean_ct = (double)cto[nc] / (double)nc;
   for (int64_t c = 0; c < nc; ++c) {
     const int nt = (int)(cto[c + 1] - cto[c]);
@@ -279,6 +298,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(upload(m, &d_vc, vc.data(), vc.size(), s));
   double *d_tvol, *d_vol, *d_cen, *d_fa, *d_fc, *d_w;
   float* d_tvf;
+  float2* d_rel;
+  TRY(dev_alloc(m, &d_rel, 3 * cv.size()));
   int32_t* d_bad;
   TRY(dev_alloc(m, &d_tvol, ct.size()));
   TRY(dev_alloc(m, &d_tvf, ct.size()));
@@ -292,6 +313,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   k_face_geom<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_fvo, d_fv, d_vx, d_vy, d_vz, d_fa, d_fc);
   k_cell_geom<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_cto, d_ct, d_vx, d_vy, d_vz, d_tvol,
                                                             d_tvf, d_vol, d_cen, d_bad);
+  k_rel_pos<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_vx, d_vy, d_vz, d_rel);
   k_idw<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, d_vco, d_vc, d_vx, d_vy, d_vz, d_cen, d_w);
   int32_t h_bad = 0;
   cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -302,6 +324,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   V.vx = d_vx; V.vy = d_vy; V.vz = d_vz;
   V.cell_vert_off = d_cvo; V.cell_vert = d_cv; V.cell_tet_off = d_cto; V.cell_tet = d_ct; V.tet_vol = d_tvol;
   V.tet_vfrac = d_tvf;
+  V.rel_pos = d_rel;
   V.vert_cell_off = d_vco; V.vert_cell = d_vc; V.vert_w = d_w;
   V.cell_vol = d_vol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
   // ---- workspace
@@ -317,8 +340,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.blk_off, m->n_sel_blocks));
   TRY(dev_alloc(m, &W.tile_part, 2 * (size_t)((nc + kSrcTile - 1) / kSrcTile)));
   TRY(dev_alloc(m, &W.band_idx, nc));
-  TRY(dev_alloc(m, &W.vert_idx, nv));
   TRY(dev_alloc(m, &W.phi_v, nv));
+  TRY(dev_alloc(m, &W.phi_ff, nv));
   TRY(dev_alloc(m, &W.iso, nc));
   TRY(dev_alloc(m, &W.A_int, nc));
   TRY(dev_alloc(m, &W.n_int, 3 * nc));

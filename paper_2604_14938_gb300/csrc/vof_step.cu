@@ -68,10 +68,6 @@ __device__ __forceinline__ double group_max(double v, unsigned mask) {
   return v;
 }
 
-__device__ __forceinline__ double pick(int i, double a, double b, double c, double d) {
-  return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
-}
-
 struct Vec3 {
   double x, y, z;
 };
@@ -80,99 +76,7 @@ __device__ __forceinline__ Vec3 operator-(Vec3 a, Vec3 b) { return {a.x - b.x, a
 __device__ __forceinline__ Vec3 operator+(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ Vec3 operator*(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
 __device__ __forceinline__ double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ Vec3 cross(Vec3 a, Vec3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
 __device__ __forceinline__ double norm(Vec3 a) { return sqrt(dot(a, a)); }
-__device__ __forceinline__ Vec3 pickv(int i, Vec3 a, Vec3 b, Vec3 c, Vec3 d) {
-  return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
-}
-__device__ __forceinline__ double flip_sign(double x, bool f) {
-  // integer sign flip: no FP64 instruction
-  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
-}
-
-// Section of one tetrahedron by phi = c (m: bit i set when corner i is wet, phi_i >= c; 0 < m < 15):
-// vector area (oriented from wet to dry), area and area moment of the section polygon.
-// The polygon is a triangle (one lone corner) or a planar quadrilateral; both are handled as the
-// quadrilateral q0 q1 q2 q3 of cut points on (wet, dry) edges in cyclic order, a triangle
-// repeating its last point, so that every lane runs the same instructions. The four cut
-// parameters share one division; the two triangle areas of the quadrilateral are the
-// projections of their vector areas on the polygon's normal, so one reciprocal square root
-// serves the area, the normal and the centroid.
-__device__ void tet_section(Vec3 P0, Vec3 P1, Vec3 P2, Vec3 P3, double p0, double p1, double p2, double p3, unsigned m,
-                            double c, Vec3& A, double& ar, Vec3& mom) {
-  const int k = __popc(m);
-  const unsigned dm = ~m & 15u;
-  int wi[4], dj[4];
-  if (k == 2) {
-    const int a = __ffs(m) - 1, b = 31 - __clz(m), cc = __ffs(dm) - 1, d = 31 - __clz(dm);
-    wi[0] = a; dj[0] = cc;
-    wi[1] = a; dj[1] = d;
-    wi[2] = b; dj[2] = d;
-    wi[3] = b; dj[3] = cc;
-  } else {
-    // the lone corner and the other three in increasing order
-    const unsigned rest = k == 1 ? dm : m;
-    const int lone = k == 1 ? __ffs(m) - 1 : __ffs(dm) - 1;
-    const int j0 = __ffs(rest) - 1, j2 = 31 - __clz(rest);
-    const int j1 = __ffs(rest & ~(1u << j0) & ~(1u << j2)) - 1;
-    if (k == 1) {
-      wi[0] = lone; dj[0] = j0;
-      wi[1] = lone; dj[1] = j1;
-      wi[2] = lone; dj[2] = j2;
-      wi[3] = lone; dj[3] = j2;
-    } else {
-      wi[0] = j0; dj[0] = lone;
-      wi[1] = j1; dj[1] = lone;
-      wi[2] = j2; dj[2] = lone;
-      wi[3] = j2; dj[3] = lone;
-    }
-  }
-  Vec3 Pw[4], Pd[4];
-  double D[4], W[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    Pw[e] = pickv(wi[e], P0, P1, P2, P3);
-    Pd[e] = pickv(dj[e], P0, P1, P2, P3);
-    const double pw = pick(wi[e], p0, p1, p2, p3), pd = pick(dj[e], p0, p1, p2, p3);
-    D[e] = pw - pd;  // > 0: pw >= c > pd
-    W[e] = pw - c;
-  }
-  double r[4];
-  const double D01 = D[0] * D[1], D23 = D[2] * D[3], prod = D01 * D23;
-  if (prod > 1e-280) {
-    const double ri = 1.0 / prod;
-    r[0] = ri * (D[1] * D23);
-    r[1] = ri * (D[0] * D23);
-    r[2] = ri * (D01 * D[3]);
-    r[3] = ri * (D01 * D[2]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) r[e] = 1.0 / D[e];
-  }
-  Vec3 q[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) q[e] = Pw[e] + (Pd[e] - Pw[e]) * (W[e] * r[e]);
-  const Vec3 e1 = q[1] - q[0], e2 = q[2] - q[0], e3 = q[3] - q[0];
-  const Vec3 A1 = cross(e1, e2), A2 = cross(e2, e3);
-  const Vec3 S = A1 + A2;  // twice the vector area
-  const bool flip = dot(S, Pd[0] - Pw[0]) < 0;
-  const double nn = dot(S, S);
-  if (!(nn > 0)) {
-    A = v3(0, 0, 0);
-    ar = 0;
-    mom = v3(0, 0, 0);
-    return;
-  }
-  const double rs = rsqrt(nn);
-  ar = 0.5 * (nn * rs);
-  A = v3(flip_sign(0.5 * S.x, flip), flip_sign(0.5 * S.y, flip), flip_sign(0.5 * S.z, flip));
-  // moment = sum over the two triangles of area x centroid = (rs / 6) sum (A_i . S) (corner sum)
-  const double w1 = dot(A1, S) * rs * (1.0 / 6.0), w2 = dot(A2, S) * rs * (1.0 / 6.0);
-  const Vec3 g02 = q[0] + q[2];
-  mom = (g02 + q[1]) * w1 + (g02 + q[3]) * w2;
-}
 
 // First work of a step: step stamp, counters reset (run by one thread of the first kernel).
 __device__ __forceinline__ void begin_step(Counters* cn) {
@@ -187,142 +91,156 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
 
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
 
-// ---- selection: per-tile counts, scan, order-preserving scatter -------------------------------
-__global__ void k_sel_count(int64_t nc, const double* alpha, double eps, int64_t* blk_count, Counters* cn) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(cn);  // no other block reads the counters
-  const int64_t base = (int64_t)blockIdx.x * kSelTile;
-  int cnt = 0;
-  for (int64_t c = base + threadIdx.x; c < min(nc, base + kSelTile); c += blockDim.x) cnt += is_iface(alpha[c], eps);
-  __shared__ int s[kThreads / 32];
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+// ---- the step's selection as one cooperative kernel ----------------------------------------------
+// Three phases separated by grid-wide barriers (the launch is cooperative, so every block is
+// resident): (1) step stamp and counters, interface cells per tile of kSelTile cells (each thread
+// takes 8 consecutive cells); (2) each tile's offset from the counts of the tiles before it, the
+// order-preserving scatter of the interface list, the tetrahedron-count bins (block-aggregated
+// appends); (3) band and vertex stamps, the band list, and the vertex field of each vertex of an
+// interface cell, computed by the lane that stamps the vertex first.
+__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* s8) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < kThreads / 32; ++w) t += s[w];
-    blk_count[blockIdx.x] = t;
-  }
+  if ((threadIdx.x & 31) == 0) s8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int64_t t = 0;
+  for (int w = 0; w < kThreads / 32; ++w) t += s8[w];
+  return t;
 }
 
-__global__ void k_sel_scan(int nb, const int64_t* cnt, int64_t* off, Counters* cn) {
-  __shared__ int64_t s[1024];
-  int64_t carry = 0;
-  for (int base = 0; base < nb; base += 1024) {
-    const int i = base + threadIdx.x;
-    const int64_t v = i < nb ? cnt[i] : 0;
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
-      __syncthreads();
-      s[threadIdx.x] += t;
-      __syncthreads();
-    }
-    if (i < nb) off[i] = carry + s[threadIdx.x] - v;
-    carry += s[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) cn->n_iface = carry;
-}
-
-__global__ void k_sel_scatter(MeshView M, const double* alpha, double eps, Workspace W) {
-  const uint32_t step = W.counters->step;
-  const int64_t base = (int64_t)blockIdx.x * kSelTile;
-  const int64_t end = min(M.n_cells, base + kSelTile);
-  int64_t pos = W.blk_off[blockIdx.x];
-  __shared__ int wsum[kThreads / 32];
+__global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* alpha, double eps, int vertex_mode,
+                                                     Workspace W) {
+  cg::grid_group grid = cg::this_grid();
+  constexpr int kPer = kSelTile / kThreads;  // consecutive cells per thread in a tile
+  static_assert(kPer == 8, "tile layout");
+  extern __shared__ int32_t band_buf[];  // (kThreads / 32) * (1 + max faces per cell)
+  __shared__ int64_t s8[kThreads / 32];
+  __shared__ int wpre[kThreads / 32 + 1];
+  __shared__ int s_bin[kBins], s_nb;
+  __shared__ unsigned long long s_binbase[kBins], s_gb;
+  const int64_t nc = M.n_cells;
+  const int64_t ntiles = (nc + kSelTile - 1) / kSelTile;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t r = base; r < end; r += blockDim.x) {
-    const int64_t c = r + threadIdx.x;
-    const bool f = c < end && is_iface(alpha[c], eps);
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wsum[wid] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      before += w < wid ? wsum[w] : 0;
-      total += wsum[w];
-    }
-    if (f) {
-      const int64_t p = pos + before + __popc(bal & ((1u << lane) - 1));
-      W.iface_idx[p] = (int32_t)c;
-      W.iface_stamp[c] = step;
-    }
-    pos += total;
-    __syncthreads();
+  // interface flags of this thread's kPer cells of tile t
+  auto flags = [&](int64_t t) {
+    unsigned f = 0;
+    const int64_t c0 = t * kSelTile + (int64_t)threadIdx.x * kPer;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (c0 + k < nc && is_iface(alpha[c0 + k], eps)) f |= 1u << k;
+    return f;
+  };
+  // (1)
+  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(W.counters);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t cnt = block_sum(__popc(flags(t)), s8);
+    if (threadIdx.x == 0) W.blk_count[t] = cnt;
   }
-}
-
-// Appends value to list at the next free slot of *counter: one atomic per group of lanes that
-// arrive together (warp-aggregated); the order of the list is not defined.
-__device__ __forceinline__ void append(int64_t* counter, int32_t* list, int32_t value) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned long long base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd((unsigned long long*)counter, (unsigned long long)g.size());
-  base = g.shfl(base, 0);
-  list[base + g.thread_rank()] = value;
-}
-
-// Band cells (interface cells and their face neighbours) and the vertices of interface cells:
-// stamped with the step, and listed by whichever lane stamps them first. 8 lanes per interface
-// cell over its faces and vertices. The lists are unordered: every later use is per cell or per
-// vertex.
-__global__ void k_mark(MeshView M, Workspace W) {
+  grid.sync();
+  // (2)
   const uint32_t step = W.counters->step;
-  const int64_t n = W.counters->n_iface;
-  const int lane = threadIdx.x & 7;
-  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / 8);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 8) + threadIdx.x / 8; i < n; i += groups) {
-    const int32_t c = W.iface_idx[i];
-    if (lane == 0 && atomicExch(&W.band_stamp[c], step) != step) append(&W.counters->n_band, W.band_idx, c);
-    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += 8) {
-      const int32_t fc = M.cell_face[k] & 0x7fffffff;
-      const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
-      if (q >= 0 && atomicExch(&W.band_stamp[q], step) != step) append(&W.counters->n_band, W.band_idx, q);
-    }
-    for (int64_t k = M.cell_vert_off[c] + lane; k < M.cell_vert_off[c + 1]; k += 8) {
-      const int32_t v = M.cell_vert[k];
-      if (atomicExch(&W.vert_stamp[v], step) != step) append(&W.counters->n_uvert, W.vert_idx, v);
-    }
+  if (blockIdx.x == 0) {
+    int64_t tot = 0;
+    for (int64_t u = threadIdx.x; u < ntiles; u += blockDim.x) tot += W.blk_count[u];
+    tot = block_sum(tot, s8);
+    if (threadIdx.x == 0) W.counters->n_iface = tot;
   }
-}
-
-// ---- vertex field (R1) --------------------------------------------------------------------------
-__global__ void k_vertex(MeshView M, const double* alpha, int mode, Workspace W) {
-  const int64_t n = W.counters->n_uvert;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = W.vert_idx[j];
-    const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
-    double s = 0;
-    if (mode == 0) {
-      for (int64_t k = k0; k < k1; ++k) s = fma(M.vert_w[k], alpha[M.vert_cell[k]], s);
-    } else {
-      for (int64_t k = k0; k < k1; ++k) s += alpha[M.vert_cell[k]];
-      s /= (double)(k1 - k0);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t before = 0;
+    for (int64_t u = threadIdx.x; u < t; u += blockDim.x) before += W.blk_count[u];
+    const int64_t tile_pos = block_sum(before, s8);
+    // exclusive scan of the per-thread counts: within the warp, then over the warps
+    const unsigned f = flags(t);
+    const int cnt = __popc(f);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
-    W.phi_v[v] = s;
+    if (lane == 31) wpre[wid + 1] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      wpre[0] = 0;
+      for (int w = 1; w <= kThreads / 32; ++w) wpre[w] += wpre[w - 1];
+    }
+    __syncthreads();
+    int64_t p = tile_pos + wpre[wid] + incl - cnt;
+    // bins: slots within the block from shared counters, one global atomic per bin and tile
+    if (threadIdx.x < kBins) s_bin[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t c0 = t * kSelTile + (int64_t)threadIdx.x * kPer;
+    int bslot[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      bslot[k] = -1;
+      if ((f >> k) & 1u) {
+        const int64_t c = c0 + k;
+        W.iface_idx[p + __popc(f & ((1u << k) - 1u))] = (int32_t)c;
+        W.iface_stamp[c] = step;
+        const int b = bin_of((int)(M.cell_tet_off[c + 1] - M.cell_tet_off[c]));
+        bslot[k] = (b << 24) | atomicAdd(&s_bin[b], 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kBins)
+      s_binbase[threadIdx.x] =
+          s_bin[threadIdx.x] ? atomicAdd((unsigned long long*)&W.counters->bin_count[threadIdx.x],
+                                         (unsigned long long)s_bin[threadIdx.x]) : 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (bslot[k] >= 0) {
+        const int b = bslot[k] >> 24;
+        W.bin_list[(size_t)b * nc + s_binbase[b] + (bslot[k] & 0xffffff)] = (int32_t)(p + __popc(f & ((1u << k) - 1u)));
+      }
+    __syncthreads();
   }
-}
-
-// ---- interface cells binned by tetrahedron count (warp-aggregated appends) ----------------------
-__global__ void k_bin(MeshView M, Workspace W) {
-  const int64_t n = W.counters->n_iface;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const bool act = i < n;
-    int b = -1;
-    if (act) {
-      const int32_t c = W.iface_idx[i];
-      b = bin_of((int)(M.cell_tet_off[c + 1] - M.cell_tet_off[c]));
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    if (act) {
-      const int leader = __ffs(peers) - 1;
-      unsigned long long pos = 0;
-      if (lane == leader) pos = atomicAdd((unsigned long long*)&W.counters->bin_count[b], (unsigned long long)__popc(peers));
-      pos = __shfl_sync(peers, pos, leader);
-      W.bin_list[(size_t)b * M.n_cells + pos + __popc(peers & ((1u << lane) - 1))] = (int32_t)i;
+  grid.sync();
+  // (3) a warp per interface cell, eight cells per block pass: lane j takes face j and vertex j
+  // (and j + 32, ...). New band cells go to a shared buffer that one atomic per pass appends to
+  // the band list; a vertex gets its field value from the lane that stamps it first.
+  {
+    const int64_t n = W.counters->n_iface;
+    for (int64_t base = (int64_t)blockIdx.x * (kThreads / 32); base < n; base += (int64_t)gridDim.x * (kThreads / 32)) {
+      if (threadIdx.x == 0) s_nb = 0;
+      __syncthreads();
+      const int64_t i = base + wid;
+      if (i < n) {
+        const int32_t c = W.iface_idx[i];
+        if (lane == 0 && atomicExch(&W.band_stamp[c], step) != step) band_buf[atomicAdd(&s_nb, 1)] = c;
+        const int64_t f0 = M.cell_face_off[c], f1 = M.cell_face_off[c + 1];
+        const int64_t v0 = M.cell_vert_off[c], v1 = M.cell_vert_off[c + 1];
+        for (int64_t j = lane; j < max(f1 - f0, v1 - v0); j += 32) {
+          if (f0 + j < f1) {
+            const int32_t fc = M.cell_face[f0 + j] & 0x7fffffff;
+            const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
+            if (q >= 0 && atomicExch(&W.band_stamp[q], step) != step) band_buf[atomicAdd(&s_nb, 1)] = q;
+          }
+          if (v0 + j < v1) {
+            const int32_t v = M.cell_vert[v0 + j];
+            if (atomicExch(&W.vert_stamp[v], step) != step) {
+              // vertex field (R1): inverse-distance weights, or the plain mean
+              const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
+              double sum = 0;
+              if (vertex_mode == 0) {
+                for (int64_t k = k0; k < k1; ++k) sum = fma(M.vert_w[k], alpha[M.vert_cell[k]], sum);
+              } else {
+                for (int64_t k = k0; k < k1; ++k) sum += alpha[M.vert_cell[k]];
+                sum /= (double)(k1 - k0);
+              }
+              W.phi_v[v] = sum;
+              const float h = __double2float_rn(sum);
+              W.phi_ff[v] = make_float2(h, __double2float_rn(sum - (double)h));
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_gb = s_nb ? atomicAdd((unsigned long long*)&W.counters->n_band, (unsigned long long)s_nb) : 0ull;
+      __syncthreads();
+      for (int k = threadIdx.x; k < s_nb; k += blockDim.x) W.band_idx[s_gb + k] = band_buf[k];
+      __syncthreads();
     }
   }
 }
@@ -490,20 +408,162 @@ __device__ __forceinline__ float liquid_volume32(const TetRow32* rows, int nt, i
   return part;
 }
 
+// ---- pair ("double-float") arithmetic on the FP32 pipe ---------------------------------------------
+// A value is hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits. The sums use Knuth's
+// error-free two-sum, the products the FMA-based exact product (Dekker); every step is written
+// with the round-to-nearest intrinsics so that nothing is contracted or reordered. On GB300 an
+// FP64 instruction costs 64 FP32 issue slots, so the interface geometry (about 130 FP64
+// operations per cut tetrahedron) runs several times faster in pairs, at a precision (1e-14
+// relative) far inside the tolerances of its outputs.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_make(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_norm(float s, float e) {  // |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_scale(ff a, float b) {  // b exact in FP32
+  const float p = __fmul_rn(a.hi, b);
+  return ff_norm(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+// 1 / a: FP32 reciprocal and one Newton step on the pair residual
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  const float y = __frcp_rn(a.hi);
+  const float r = __fmaf_rn(-a.lo, y, __fmaf_rn(-a.hi, y, 1.0f));  // 1 - a y
+  return ff_norm(y, __fmul_rn(y, r));
+}
+// 1 / sqrt(a), a > 0: FP32 estimate and one Newton step on the pair residual
+__device__ __forceinline__ ff ff_rsqrt(ff a) {
+  const float y = rsqrtf(a.hi);
+  const ff ay2 = ff_scale(ff_scale(a, y), y);
+  const float r = __fadd_rn(__fsub_rn(1.0f, ay2.hi), -ay2.lo);  // 1 - a y^2
+  return ff_norm(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+}
+struct ff3 {
+  ff x, y, z;
+};
+__device__ __forceinline__ ff3 ff3_load(const float2* p) { return {ff_make(p[0]), ff_make(p[1]), ff_make(p[2])}; }
+__device__ __forceinline__ ff3 ff3_add(ff3 a, ff3 b) { return {ff_add(a.x, b.x), ff_add(a.y, b.y), ff_add(a.z, b.z)}; }
+__device__ __forceinline__ ff3 ff3_sub(ff3 a, ff3 b) { return {ff_sub(a.x, b.x), ff_sub(a.y, b.y), ff_sub(a.z, b.z)}; }
+__device__ __forceinline__ ff3 ff3_mul(ff3 a, ff s) { return {ff_mul(a.x, s), ff_mul(a.y, s), ff_mul(a.z, s)}; }
+__device__ __forceinline__ ff ff3_dot(ff3 a, ff3 b) {
+  return ff_add(ff_add(ff_mul(a.x, b.x), ff_mul(a.y, b.y)), ff_mul(a.z, b.z));
+}
+__device__ __forceinline__ ff3 ff3_cross(ff3 a, ff3 b) {
+  return {ff_sub(ff_mul(a.y, b.z), ff_mul(a.z, b.y)), ff_sub(ff_mul(a.z, b.x), ff_mul(a.x, b.z)),
+          ff_sub(ff_mul(a.x, b.y), ff_mul(a.y, b.x))};
+}
+__device__ __forceinline__ ff3 ff3_pick(int i, ff3 a, ff3 b, ff3 c, ff3 d) {
+  return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
+}
+__device__ __forceinline__ ff ff_pick(int i, ff a, ff b, ff c, ff d) { return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d)); }
+
+// The section of tet_section in pair arithmetic, with positions relative to the cell's apex (P0 is
+// the origin) and w_i = phi_i - c: the same quadrilateral of cut points, vector area (wet -> dry),
+// area and area moment (about the apex).
+__device__ void tet_section_ff(ff3 P1, ff3 P2, ff3 P3, ff w0, ff w1, ff w2, ff w3, unsigned m, ff3& A, ff& ar,
+                               ff3& mom) {
+  const ff3 P0 = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  const int k = __popc(m);
+  const unsigned dm = ~m & 15u;
+  int wi[4], dj[4];
+  if (k == 2) {
+    const int a = __ffs(m) - 1, b = 31 - __clz(m), cc = __ffs(dm) - 1, d = 31 - __clz(dm);
+    wi[0] = a; dj[0] = cc;
+    wi[1] = a; dj[1] = d;
+    wi[2] = b; dj[2] = d;
+    wi[3] = b; dj[3] = cc;
+  } else {
+    const unsigned rest = k == 1 ? dm : m;
+    const int lone = k == 1 ? __ffs(m) - 1 : __ffs(dm) - 1;
+    const int j0 = __ffs(rest) - 1, j2 = 31 - __clz(rest);
+    const int j1 = __ffs(rest & ~(1u << j0) & ~(1u << j2)) - 1;
+    if (k == 1) {
+      wi[0] = lone; dj[0] = j0;
+      wi[1] = lone; dj[1] = j1;
+      wi[2] = lone; dj[2] = j2;
+      wi[3] = lone; dj[3] = j2;
+    } else {
+      wi[0] = j0; dj[0] = lone;
+      wi[1] = j1; dj[1] = lone;
+      wi[2] = j2; dj[2] = lone;
+      wi[3] = j2; dj[3] = lone;
+    }
+  }
+  ff3 q[4];
+  ff3 Pw0, Pd0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const ff3 Pw = ff3_pick(wi[e], P0, P1, P2, P3), Pd = ff3_pick(dj[e], P0, P1, P2, P3);
+    const ff ww = ff_pick(wi[e], w0, w1, w2, w3), wd = ff_pick(dj[e], w0, w1, w2, w3);
+    // t = (phi_w - c) / (phi_w - phi_d), in [0, 1)
+    const ff t = ff_mul(ww, ff_rcp(ff_sub(ww, wd)));
+    q[e] = ff3_add(Pw, ff3_mul(ff3_sub(Pd, Pw), t));
+    if (e == 0) {
+      Pw0 = Pw;
+      Pd0 = Pd;
+    }
+  }
+  const ff3 e1 = ff3_sub(q[1], q[0]), e2 = ff3_sub(q[2], q[0]), e3 = ff3_sub(q[3], q[0]);
+  const ff3 A1 = ff3_cross(e1, e2), A2 = ff3_cross(e2, e3);
+  const ff3 S = ff3_add(A1, A2);  // twice the vector area
+  // orientation from the leading parts: the wet and the dry corner lie strictly apart
+  const float o = S.x.hi * (Pd0.x.hi - Pw0.x.hi) + S.y.hi * (Pd0.y.hi - Pw0.y.hi) + S.z.hi * (Pd0.z.hi - Pw0.z.hi);
+  const ff nn = ff3_dot(S, S);
+  if (!(nn.hi > 0.f)) {
+    const ff z = {0.f, 0.f};
+    A = {z, z, z};
+    ar = z;
+    mom = {z, z, z};
+    return;
+  }
+  const ff rs = ff_rsqrt(nn);
+  ar = ff_scale(ff_mul(nn, rs), 0.5f);
+  const ff half = o < 0.f ? ff{-0.5f, 0.f} : ff{0.5f, 0.f};
+  A = {ff_mul(S.x, half), ff_mul(S.y, half), ff_mul(S.z, half)};
+  // moment = (rs / 6) sum_i (A_i . S) (corner sum of triangle i)
+  const ff sixth = {0.1666666716337204f, -4.967053879312289e-09f};  // 1/6 as a pair
+  const ff r6 = ff_mul(rs, sixth);
+  const ff wa = ff_mul(ff3_dot(A1, S), r6), wb = ff_mul(ff3_dot(A2, S), r6);
+  const ff3 g02 = ff3_add(q[0], q[2]);
+  mom = ff3_add(ff3_mul(ff3_add(g02, q[1]), wa), ff3_mul(ff3_add(g02, q[3]), wb));
+}
+
 // Interface geometry of one cell at the isovalue c (paper Sec. 2.1): vector area (wet -> dry),
 // area and area moment of the cut polygons, summed over the cell's tetrahedra by G lanes. A first
 // pass classifies the tetrahedra (integer work only) and appends the cut ones to the group's list
 // lst in shared memory, in tetrahedron order; the FP64 sections then run over that list with
 // every lane busy. Returns the number of cut tetrahedra.
 template <int G>
-__device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace& W, const int32_t* cv, int64_t t0,
-                                             int nt, double c, int lane, unsigned mask, uint16_t* lst, Vec3& A,
-                                             double& area, Vec3& mom) {
+__device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace& W, const int32_t* cv, int64_t v0,
+                                             int64_t t0, int nt, double c, int lane, unsigned mask, uint16_t* lst,
+                                             Vec3& A, double& area, Vec3& mom) {
   const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
   const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   const uint64_t kc = okey(c);
-  const double p_apex = W.phi_v[cv[0]];
-  const unsigned m0 = (unsigned)(okey(p_apex) >= kc);
+  const unsigned m0 = (unsigned)(okey(W.phi_v[cv[0]]) >= kc);
   int n_cut = 0;
   for (int r0 = 0; r0 < nt; r0 += G) {
     const int t = r0 + lane;
@@ -520,28 +580,40 @@ __device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace&
     n_cut += __popc(bal);
   }
   __syncwarp(mask);
-  A = v3(0, 0, 0);
-  mom = v3(0, 0, 0);
-  area = 0;
-  const Vec3 P0 = v3(M.vx[cv[0]], M.vy[cv[0]], M.vz[cv[0]]);
+  // sections in pair arithmetic, positions relative to the apex
+  const ff cf = ff_of(c);
+  const ff w0 = ff_sub(ff_make(W.phi_ff[cv[0]]), cf);
+  const ff z = {0.f, 0.f};
+  ff3 sA = {z, z, z}, sm = {z, z, z};
+  ff sa = z;
+  const float2* rp = M.rel_pos + 3 * v0;
   for (int jj = lane; jj < n_cut; jj += G) {
     const unsigned e = lst[jj];
     const int t = (int)(e >> 4);
     const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-    const int32_t g1 = cv[pk & 255], g2 = cv[(pk >> 8) & 255], g3 = cv[(pk >> 16) & 255];
-    const Vec3 P1 = v3(M.vx[g1], M.vy[g1], M.vz[g1]);
-    const Vec3 P2 = v3(M.vx[g2], M.vy[g2], M.vz[g2]);
-    const Vec3 P3 = v3(M.vx[g3], M.vy[g3], M.vz[g3]);
-    Vec3 tA, tm;
-    double ta;
-    tet_section(P0, P1, P2, P3, p_apex, W.phi_v[g1], W.phi_v[g2], W.phi_v[g3], e & 15u, c, tA, ta, tm);
-    A = A + tA;
-    area += ta;
-    mom = mom + tm;
+    const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
+    ff3 tA, tm;
+    ff ta;
+    tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), w0,
+                   ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
+                   ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
+    sA = ff3_add(sA, tA);
+    sa = ff_add(sa, ta);
+    sm = ff3_add(sm, tm);
   }
-  A = v3(group_sum<G>(A.x, mask), group_sum<G>(A.y, mask), group_sum<G>(A.z, mask));
-  area = group_sum<G>(area, mask);
-  mom = v3(group_sum<G>(mom.x, mask), group_sum<G>(mom.y, mask), group_sum<G>(mom.z, mask));
+  // group sums in pairs, then FP64
+  ff v[7] = {sA.x, sA.y, sA.z, sa, sm.x, sm.y, sm.z};
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+      v[q] = ff_add(v[q], ff{__shfl_xor_sync(mask, v[q].hi, o), __shfl_xor_sync(mask, v[q].lo, o)});
+  const int32_t a = cv[0];
+  A = v3(ff_to_double(v[0]), ff_to_double(v[1]), ff_to_double(v[2]));
+  area = ff_to_double(v[3]);
+  // the moment about the apex, moved to the origin: + area x apex
+  mom = v3(fma(area, M.vx[a], ff_to_double(v[4])), fma(area, M.vy[a], ff_to_double(v[5])),
+           fma(area, M.vz[a], ff_to_double(v[6])));
   return n_cut;
 }
 
@@ -748,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
     double area = 0;
     if (!(status & VOF_ST_DEGENERATE)) {
       __syncwarp(mask);
-      sect_acc += cell_geometry<G>(M, W, cv, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows), A,
+      sect_acc += cell_geometry<G>(M, W, cv, v0, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows), A,
                                    area, mom);
     }
     if (lane == 0) {
@@ -1150,12 +1222,24 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   const MeshView& M = m->view;
   W.alpha_in = d_alpha;
   Timing& tm = m->timing;
-  tm.start(KC_SELECT, s);
-  k_sel_count<<<m->n_sel_blocks, kThreads, 0, s>>>(M.n_cells, d_alpha, opt.alpha_eps, W.blk_count, W.counters);
-  k_sel_scan<<<1, 1024, 0, s>>>(m->n_sel_blocks, W.blk_count, W.blk_off, W.counters);
-  k_sel_scatter<<<m->n_sel_blocks, kThreads, 0, s>>>(M, d_alpha, opt.alpha_eps, W);
-  k_mark<<<m->num_sms * 4, kThreads, 0, s>>>(M, W);
-  tm.stop(s);
+  // selection, band, vertex field and bins: one cooperative launch, as many blocks as are resident
+  const size_t sel_smem = (size_t)(kThreads / 32) * (1 + m->max_cf) * sizeof(int32_t);
+  if (!m->sel_grid) {
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_select, kThreads, sel_smem);
+    m->sel_grid = m->num_sms * std::max(1, std::min(bps, 4));
+  }
+  {
+    const double eps = opt.alpha_eps;
+    int vmode = opt.vertex_mode;
+    MeshView Mv = M;
+    void* args[] = {&Mv, (void*)&d_alpha, (void*)&eps, &vmode, &W};
+    tm.start(KC_SELECT, s);
+    cudaError_t el = cudaLaunchCooperativeKernel((const void*)k_select, dim3(m->sel_grid), dim3(kThreads),
+                                                 args, sel_smem, s);
+    tm.stop(s);
+    if (el != cudaSuccess) return cuda_fail(el, "selection kernel (cooperative launch)");
+  }
   if (early_xmark) {
     // crossing faces next to the band: needed only by the least squares
     cudaEventRecord(m->ev_xfork, s);
@@ -1165,19 +1249,14 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     tm.stop(m->xm_stream);
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
   }
-  const int vgrid = (int)std::min<int64_t>((M.n_verts + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
-  tm.start(KC_VERTEX, s);
-  k_vertex<<<vgrid, kThreads, 0, s>>>(M, d_alpha, opt.vertex_mode, W);
-  tm.stop(s);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "selection/vertex kernels");
+  if (e != cudaSuccess) return cuda_fail(e, "selection kernels");
   if (learned) {
     tm.start(KC_MLP, s);
     e = launch_mlp_guess(m, s);
     tm.stop(s);
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
-  k_bin<<<m->num_sms * 2, kThreads, 0, s>>>(M, W);
   // one branch per non-empty bin (root search and geometry); the branches join on s
   e = cudaEventRecord(m->ev_fork, s);
   for (int b = 0; b < kBins && e == cudaSuccess; ++b) {
