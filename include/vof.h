@@ -292,9 +292,9 @@ vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, do
  * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
  * vof_timing_read synchronises the stream and returns, per kernel class, the summed
  * milliseconds and the launch count since the last read (at most 8192 records are kept).
- * Classes: 0 selection and band, 1 vertex field, 2 root search and interface geometry,
- * 3 crossing faces and least squares, 4 per-side gradients, source and totals, 5 and 7 (unused),
- * 6 learned guess. */
+ * Classes: 0 selection, band and vertex field, 2 root search and interface geometry, 3 list of
+ * the crossing faces, 4 crossing faces, least squares, per-side gradients, source and totals,
+ * 6 learned guess; 1, 5 and 7 are unused. */
 vof_status vof_timing_enable(vof_mesh* mesh, int on);
 vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
 

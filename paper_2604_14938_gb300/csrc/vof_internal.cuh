@@ -104,13 +104,13 @@ struct Workspace {
   double *io_alpha, *io_T, *io_Tb, *io_mdot, *io_Q, *io_totals;
 };
 
-constexpr int kSelTile = 2048;      // cells per selection block
+constexpr int kSelTile = 512;       // cells per selection tile (2 consecutive cells per thread)
 // Bins of interface cells by tetrahedron count; each bin's root search has its own lanes per cell.
 constexpr int kBins = 5;
 constexpr int kBinMaxTets[kBins] = {4, 8, 24, 64, 192};
 __host__ __device__ inline int bin_of(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 1 : (nt <= 24 ? 2 : (nt <= 64 ? 3 : 4))); }
 constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
-constexpr int kSrcTile = 64;        // interface cells per source tile (an aligned subtree of the totals)
+constexpr int kSrcTile = 16;        // interface cells per source tile (an aligned subtree of the totals)
 constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
 
 struct StepArgs {

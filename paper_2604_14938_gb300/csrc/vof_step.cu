@@ -94,7 +94,7 @@ __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps 
 // ---- the step's selection as one cooperative kernel ----------------------------------------------
 // Three phases separated by grid-wide barriers (the launch is cooperative, so every block is
 // resident): (1) step stamp and counters, interface cells per tile of kSelTile cells (each thread
-// takes 8 consecutive cells); (2) each tile's offset from the counts of the tiles before it, the
+// takes kSelTile / kThreads consecutive cells); (2) each tile's offset from the counts of the tiles before it, the
 // order-preserving scatter of the interface list, the tetrahedron-count bins (block-aggregated
 // appends); (3) band and vertex stamps, the band list, and the vertex field of each vertex of an
 // interface cell, computed by the lane that stamps the vertex first.
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
                                                      Workspace W) {
   cg::grid_group grid = cg::this_grid();
   constexpr int kPer = kSelTile / kThreads;  // consecutive cells per thread in a tile
-  static_assert(kPer == 8, "tile layout");
+  static_assert(kPer >= 1 && kPer <= 32 && kSelTile % kThreads == 0, "tile layout");
   extern __shared__ int32_t band_buf[];  // (kThreads / 32) * (1 + max faces per cell)
   __shared__ int64_t s8[kThreads / 32];
   __shared__ int wpre[kThreads / 32 + 1];
@@ -625,9 +625,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
   const int lane = threadIdx.x % G;
   const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
   // per group: the rows, then the cell's normalised vertex values (FP32) for the learned path
-  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float);
+  const size_t uv_bytes = (size_t)((max_cv + 1) & ~1) * sizeof(float);
+  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + uv_bytes + (size_t)((2 * max_ct + 7) & ~7);
   TetRow* rows = reinterpret_cast<TetRow*>(smem + (size_t)gib * grp_bytes);
   float* uvert = reinterpret_cast<float*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow));
+  uint16_t* actl = reinterpret_cast<uint16_t*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow) + uv_bytes);
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
   int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0, sect_acc = 0;
@@ -656,6 +658,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
     const double p_apex = W.phi_v[cv[0]];
     // FP64 rows of the cell's tetrahedra (after the FP32 phase on the learned path, whose rows
     // share the same shared memory)
+    int n_rows = nt, n_prep = 0;  // rows evaluated; rows prepared for this cell
+    double wet_sum = 0;          // volume of the tetrahedra wet over the whole window (windowed rows)
     auto prepare64 = [&]() {
       for (int t = lane; t < nt; t += G) {
         const uint32_t pk = __ldg(M.cell_tet + t0 + t);
@@ -663,12 +667,52 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
                               W.phi_v[cv[(pk >> 16) & 255]], __ldg(M.tet_vol + t0 + t));
       }
       __syncwarp(mask);
+      n_rows = nt;
+      n_prep += nt;
+      wet_sum = 0;
+    };
+    // Rows valid for c in [wlo, whi) only: a tetrahedron whose corners all lie at or above whi is
+    // wet there (its volume goes to wet_sum), one whose corners all lie below wlo is dry; only
+    // the others (listed in actl) are prepared and evaluated.
+    auto prepare_window = [&](double wlo, double whi) {
+      const uint64_t kwl = okey(wlo), kwh = okey(whi), ka = okey(p_apex);
+      const int base = (threadIdx.x & 31) / G * G;
+      const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+      double ws = 0;
+      int n = 0;
+      for (int r0 = 0; r0 < nt; r0 += G) {
+        const int t = r0 + lane;
+        bool act = false;
+        if (t < nt) {
+          const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+          const uint64_t k1 = okey(W.phi_v[cv[pk & 255]]), k2 = okey(W.phi_v[cv[(pk >> 8) & 255]]),
+                         k3 = okey(W.phi_v[cv[(pk >> 16) & 255]]);
+          const uint64_t kmin = min(min(ka, k1), min(k2, k3)), kmax = max(max(ka, k1), max(k2, k3));
+          if (kmin >= kwh) ws += __ldg(M.tet_vol + t0 + t);
+          else act = kmax >= kwl;
+        }
+        const unsigned bal = (__ballot_sync(mask, act) >> base) & gbits;
+        if (act) actl[n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+        n += __popc(bal);
+      }
+      wet_sum = group_sum<G>(ws, mask);
+      __syncwarp(mask);
+      for (int k = lane; k < n; k += G) {
+        const int t = actl[k];
+        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+        rows[k] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]],
+                              W.phi_v[cv[(pk >> 16) & 255]], __ldg(M.tet_vol + t0 + t));
+      }
+      __syncwarp(mask);
+      n_rows = n;
+      n_prep += n;
     };
     const double a = alpha[cell];
     const double V = M.cell_vol[cell];
     const double invV = 1.0 / V;
     const uint64_t ktol = mag(opt.tol_alpha);
     int status = 0, evals = 0, evals32 = 0;
+    int64_t tev = 0;  // tetrahedron evaluations
     double c_best;
     uint64_t kbest = 0;  // |f| at c_best, as a magnitude key
     if (hi - lo < 1e-14) {
@@ -682,8 +726,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       bool done = false, prepared = false;
       // one FP64 evaluation: residual, best point and bracket updated, convergence test
       auto eval64 = [&](double c) -> double {
-        const double f = liquid_volume<G>(rows, nt, lane, mask, c) * invV - a;
+        const double f = (liquid_volume<G>(rows, n_rows, lane, mask, c) + wet_sum) * invV - a;
         ++evals;
+        tev += n_rows;
         const uint64_t kf = mag(f);
         if (kf < kbest) { kbest = kf; c_best = c; }
         if (positive(f)) L = dmax(L, c); else H = dmin(H, c);
@@ -761,18 +806,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         }
         {
           __syncwarp(mask);
-          prepare64();
-          prepared = true;
-          // FP64 phase
+          // FP64 phase on the rows of a window of 2e-3 of the range around the refined point
+          // (a thousand times the FP32 refinement's accuracy); every FP64 point stays inside it
           double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
+          const double wlo = dmax(c1 - 1e-3 * range, lo), whi = dmin(c1 + 1e-3 * range, hi);
+          prepare_window(wlo, whi);
+          prepared = true;
           double f1 = eval64(c1);
           double spread = 1e-6 * range;  // distance between the first two FP64 points
           if (!done && opt.max_secant > 0) {
             // second point: one Newton step with the FP32 slope, kept inside the bracket
             double c0 = fma(-f1, range * (double)(1.0f / slope), c1);
-            if (!inside(c0, L, H) || c0 == c1) {
+            if (!inside(c0, dmax(L, wlo), dmin(H, whi)) || c0 == c1) {
               const double step = 4e-6 * range;
-              c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+              c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + dmin(H, whi))) : fmax(c1 - step, 0.5 * (c1 + dmax(L, wlo)));
             }
             spread = dmax(spread, fabs(c0 - c1));
             double f0 = eval64(c0);
@@ -783,13 +830,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
               double r = (double)(1.0f / (float)d);
               r = fma(r, fma(-d, r, 1.0), r);
               double c2 = fma(-f0, (c0 - c1) * r, c0);
-              if (!inside(c2, L, H)) c2 = 0.5 * (L + H);
+              const double Lw = dmax(L, wlo), Hw = dmin(H, whi);
+              if (!inside(c2, Lw, Hw)) c2 = 0.5 * (Lw + Hw);
               const double f2 = eval64(c2);
               c1 = c0; f1 = f0; c0 = c2; f0 = f2;
             }
           }
           if (!done) {
             status |= VOF_ST_FALLBACK;
+            prepare64();  // the fallback may leave the window: every row
             // When the FP64 points all lie on one side of the root, close the bracket next to
             // them before bisecting: steps away from the nearest point towards the root,
             // doubling (each an evaluation, counted).
@@ -839,8 +888,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       W.x_gamma[3 * cell + 2] = mom.z * ia;
       evals_acc += evals;
       ev32_acc += evals32;
-      tetev_acc += (int64_t)evals * nt;
-      prep_acc += nt;
+      tetev_acc += tev;
+      prep_acc += n_prep;
       if (status & VOF_ST_DEGENERATE) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
       if (status & VOF_ST_NOT_CONVERGED) atomicAdd((unsigned long long*)&W.counters->n_not_converged, 1ull);
       if (status & VOF_ST_FALLBACK) atomicAdd((unsigned long long*)&W.counters->n_fallback, 1ull);
@@ -919,10 +968,11 @@ __global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
 }
 
 // Crossing point, distances and projected interface area of each listed face.
-__global__ void k_xface(MeshView M, const double* alpha, int xf_mode, Workspace W) {
+__device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode, Workspace& W) {
   const uint32_t step = W.counters->step;
   const int64_t n = W.counters->n_crossing;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+  // faces interleaved over the blocks
+  for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t f = W.xface_list[j];
     const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
     int32_t src;
@@ -947,17 +997,18 @@ __global__ void k_xface(MeshView M, const double* alpha, int xf_mode, Workspace 
 
 // ---- interface-modified least squares (R7) on band cells -----------------------------------------
 // L lanes per band cell over its faces; the nine sums of G and b are reduced across the lanes. A
-// crossing face contributes its crossing point x_f (k_xface) with T_sat; every face runs the same
+// crossing face contributes its crossing point x_f (computed first) with T_sat; every face runs the same
 // instructions (the point and the value are selected, not branched on).
 template <int L>
-__global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
+__device__ void lsq_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
   const int lane = threadIdx.x % L;
   const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / L);
   int nsing = 0;
-  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / L) + threadIdx.x / L; j < nb; j += groups) {
+  // groups interleaved over the blocks, so that a short band still spreads over every SM
+  for (int64_t j = (int64_t)(threadIdx.x / L) * gridDim.x + blockIdx.x; j < nb; j += groups) {
     const int32_t c = W.band_idx[j];
     const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
     const double TP = a.T[c], aP = a.alpha[c];
@@ -1004,16 +1055,18 @@ __global__ void k_lsq(MeshView M, StepArgs a, Workspace W) {
 }
 
 // ---- per-side gradients and source (R5, R6) on interface cells, totals (R8) -----------------------
+constexpr int kSrcLanes = 16;  // lanes per interface cell over its faces
 // The totals are the pairwise tree over the interface list (cell order) padded with zeros to a
 // power of two. Each block takes aligned tiles of kSrcTile interface cells: it computes their
-// sources (8 lanes per cell over its faces), then the tile's subtree from shared memory; the last
-// block to finish folds the tile sums in 512-leaf subtrees, level by level, so the pairing is the
-// whole tree's. Cells outside the interface get mdot = Q = 0.
+// sources (kSrcLanes lanes per cell over its faces), then the tile's subtree from shared memory;
+// after a grid barrier block 0 folds the tile sums in subtrees of 2 kThreads leaves, level by
+// level, so the pairing is the whole tree's. Cells outside the interface get mdot = Q = 0.
 
-// Pairwise tree of x[base, base + 512) (zeros past n) in a 256-thread block; the result is valid in
-// thread 0. Thread t pairs leaves 2t and 2t+1, lanes then pair their neighbours (lane t + 2^k
-// joins lane t), and warp 0 pairs the eight warp sums.
-__device__ double block_tree512(const double* x, int64_t n, int64_t base, double* s8) {
+// Pairwise tree of x[base, base + 2 T) (zeros past n) in a block of T threads (T a multiple of 32,
+// at most 1024); the result is valid in thread 0. Thread t pairs leaves 2t and 2t+1, lanes then
+// pair their neighbours (lane t + 2^k joins lane t), and warp 0 pairs the warp sums.
+template <int T>
+__device__ double block_tree(const double* x, int64_t n, int64_t base, double* sw) {
   const int t = threadIdx.x, lane = t & 31;
   const int64_t i0 = base + 2 * t;
   double v = (i0 < n ? __ldcg(x + i0) : 0.0) + (i0 + 1 < n ? __ldcg(x + i0 + 1) : 0.0);
@@ -1022,13 +1075,13 @@ __device__ double block_tree512(const double* x, int64_t n, int64_t base, double
     const double w = __shfl_down_sync(0xffffffffu, v, o);
     if ((lane & (2 * o - 1)) == 0) v += w;
   }
-  if (lane == 0) s8[t >> 5] = v;
+  if (lane == 0) sw[t >> 5] = v;
   __syncthreads();
   double r = 0;
   if (t < 32) {
-    v = t < 8 ? s8[t] : 0.0;
+    v = t < T / 32 ? sw[t] : 0.0;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < T / 32; o <<= 1) {
       const double w = __shfl_down_sync(0xffffffffu, v, o);
       if ((lane & (2 * o - 1)) == 0) v += w;
     }
@@ -1038,21 +1091,60 @@ __device__ double block_tree512(const double* x, int64_t n, int64_t base, double
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Workspace W) {
-  __shared__ double tm[kSrcTile], tq[kSrcTile], s8[8];
-  __shared__ bool last;
+constexpr int kSrcThreads = kThreads;  // threads of a source pass: kSrcTile cells x kSrcLanes lanes
+
+__device__ __forceinline__ double flip_if(double x, bool f) {  // -x when f, by the sign bit
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
+}
+
+__device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
+  constexpr int L = kSrcLanes;
+  static_assert(kSrcTile * L == kSrcThreads, "one tile per block pass");
+  __shared__ double part[kSrcTile][L][4];  // per lane: other-side gradient sum (3), weight sum
+  __shared__ double tm[kSrcTile], tq[kSrcTile];
   const uint32_t step = W.counters->step;
   const int64_t n = W.counters->n_iface;
   const int64_t ntiles = (n + kSrcTile - 1) / kSrcTile;
   const int64_t tcap = (M.n_cells + kSrcTile - 1) / kSrcTile;
-  const int lane = threadIdx.x % kLsqLanes;
-  const unsigned mask = 0xffu << ((threadIdx.x & 31) / kLsqLanes * kLsqLanes);
-  constexpr int kPerPass = kThreads / kLsqLanes;  // cells per pass of the block
+  const int lane = threadIdx.x % L, slot = threadIdx.x / L;
   int nside = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    for (int pass = 0; pass < kSrcTile / kPerPass; ++pass) {
-      const int slot = pass * kPerPass + threadIdx.x / kLsqLanes;
+    // (1) L lanes per cell over its faces: weights max(0, n . A_f) towards the other phase and the
+    // weighted gradients of the neighbours there
+    {
       const int64_t i = tile * kSrcTile + slot;
+      double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+      if (i < n) {
+        const int32_t c = W.iface_idx[i];
+        if (W.A_int[c] > 0) {
+          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+          const bool liq = a.alpha[c] > 0.5;  // the other side is vapour (weights of -n) or liquid (+n)
+          for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
+            const int32_t fe = M.cell_face[k];
+            const int32_t f = fe & 0x7fffffff;
+            const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
+            if (q < 0) continue;
+            if ((a.alpha[q] > 0.5) == liq) continue;
+            const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
+            double w = flip_if(dot(nn, Af), (fe < 0) != liq);  // outward area of c, towards the other side
+            w = positive(w) ? w : 0.0;
+            p0 = fma(W.grad[3 * q], w, p0);
+            p1 = fma(W.grad[3 * q + 1], w, p1);
+            p2 = fma(W.grad[3 * q + 2], w, p2);
+            p3 += w;
+          }
+        }
+      }
+      part[slot][lane][0] = p0;
+      part[slot][lane][1] = p1;
+      part[slot][lane][2] = p2;
+      part[slot][lane][3] = p3;
+    }
+    __syncthreads();
+    // (2) one thread per cell: the lane sums in lane order, then the cell's source
+    if (threadIdx.x < kSrcTile) {
+      const int sl = threadIdx.x;
+      const int64_t i = tile * kSrcTile + sl;
       double mV = 0, qV = 0;
       if (i < n) {
         const int32_t c = W.iface_idx[i];
@@ -1060,26 +1152,15 @@ __global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Wor
         Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
         const double Aint = W.A_int[c];
         if (Aint > 0) {
-          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
-          const bool liq = a.alpha[c] > 0.5;
-          const double sigma = liq ? -1.0 : 1.0;  // the other side: vapour (-1) or liquid (+1)
           Vec3 acc = v3(0, 0, 0);
           double ws = 0;
-          for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
-            const int32_t fe = M.cell_face[k];
-            const int32_t f = fe & 0x7fffffff;
-            const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
-            if (q < 0) continue;
-            if ((a.alpha[q] > 0.5) == liq) continue;
-            Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
-            if (fe < 0) Af = Af * -1.0;
-            const double w = fmax(0.0, sigma * dot(nn, Af));
-            acc = acc + v3(W.grad[3 * q], W.grad[3 * q + 1], W.grad[3 * q + 2]) * w;
-            ws += w;
+#pragma unroll 2
+          for (int l = 0; l < L; ++l) {
+            acc = acc + v3(part[sl][l][0], part[sl][l][1], part[sl][l][2]);
+            ws += part[sl][l][3];
           }
-          acc = v3(group_sum<kLsqLanes>(acc.x, mask), group_sum<kLsqLanes>(acc.y, mask),
-                   group_sum<kLsqLanes>(acc.z, mask));
-          ws = group_sum<kLsqLanes>(ws, mask);
+          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+          const bool liq = a.alpha[c] > 0.5;
           Vec3 go = v3(0, 0, 0);
           if (ws > 0) go = acc * (1.0 / ws);
           const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
@@ -1089,36 +1170,33 @@ __global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Wor
           qv = -a.props.k_v * dot(gv, nn) * Aint;
           mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
           Q = -mdot * a.props.h_lv;
-          if (lane == 0 && !(ws > 0)) {
+          if (!(ws > 0)) {
             W.status[c] |= VOF_ST_NO_SIDE;
             ++nside;
           }
         }
         mV = mdot * M.cell_vol[c];
         qV = Q * M.cell_vol[c];
-        if (lane == 0) {
-          a.mdot[c] = mdot;
-          a.Q[c] = Q;
-          W.q_l[c] = ql;
-          W.q_v[c] = qv;
-          W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
-          W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
-          W.mdotV[i] = mV;
-          W.QV[i] = qV;
-        }
+        a.mdot[c] = mdot;
+        a.Q[c] = Q;
+        W.q_l[c] = ql;
+        W.q_v[c] = qv;
+        W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
+        W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
+        W.mdotV[i] = mV;
+        W.QV[i] = qV;
       }
-      if (lane == 0) {
-        tm[slot] = mV;
-        tq[slot] = qV;
-      }
+      tm[sl] = mV;
+      tq[sl] = qV;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-      // the tile's subtree: lane t pairs leaves 2t and 2t+1, then five levels across the lanes
+      // the tile's subtree: lane t pairs leaves 2t and 2t+1, then the levels across the lanes
       const int t = threadIdx.x;
-      double vm = tm[2 * t] + tm[2 * t + 1], vq = tq[2 * t] + tq[2 * t + 1];
+      double vm = t < kSrcTile / 2 ? tm[2 * t] + tm[2 * t + 1] : 0.0;
+      double vq = t < kSrcTile / 2 ? tq[2 * t] + tq[2 * t + 1] : 0.0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
+      for (int o = 1; o < kSrcTile / 2; o <<= 1) {
         const double wm = __shfl_down_sync(0xffffffffu, vm, o), wq = __shfl_down_sync(0xffffffffu, vq, o);
         if ((t & (2 * o - 1)) == 0) {
           vm += wm;
@@ -1139,23 +1217,24 @@ __global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Wor
       a.mdot[c] = 0.0;
       a.Q[c] = 0.0;
     }
-  // the last block folds the tile sums
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&W.counters->reduce_done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
+}
+
+// Block 0 folds the tile sums into the two totals.
+__device__ __noinline__ void fold_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
+  __shared__ double sw[kThreads / 32];
+  const int64_t n = W.counters->n_iface;
+  const int64_t ntiles = (n + kSrcTile - 1) / kSrcTile;
+  const int64_t tcap = (M.n_cells + kSrcTile - 1) / kSrcTile;
   for (int q = 0; q < 2; ++q) {
     const double* src = W.tile_part + q * tcap;
     double* bufs[2] = {W.partial + 2 * q * kMaxPartials, W.partial + (2 * q + 1) * kMaxPartials};
     int64_t m = ntiles;
     int pp = 0;
     while (m > 1) {
-      const int64_t mc = (m + 511) / 512;
+      const int64_t mc = (m + 2 * kThreads - 1) / (2 * kThreads);
       double* dst = bufs[pp];
       for (int64_t b = 0; b < mc; ++b) {
-        const double r = block_tree512(src, m, b * 512, s8);
+        const double r = block_tree<kThreads>(src, m, b * 2 * kThreads, sw);
         if (threadIdx.x == 0) dst[b] = r;
       }
       __syncthreads();
@@ -1166,6 +1245,26 @@ __global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Wor
     if (threadIdx.x == 0) a.totals[q] = m == 0 ? 0.0 : __ldcg(src);
     __syncthreads();
   }
+}
+
+__global__ void k_xface(MeshView M, const double* alpha, int xf_mode, Workspace W) { xface_phase(M, alpha, xf_mode, W); }
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) k_lsq(MeshView M, StepArgs a, Workspace W) { lsq_phase<L>(M, a, W); }
+
+// Sources and tile sums; the last block to finish folds the totals.
+__global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Workspace W) {
+  __shared__ bool last;
+  source_phase(M, a, W);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's tile sums before its arrival
+    last = atomicAdd(&W.counters->reduce_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  fold_phase(M, a, W);
   if (threadIdx.x == 0) W.counters->reduce_done = 0;
 }
 
@@ -1187,7 +1286,8 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
   const int max_cv = m->max_cv;
-  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float);
+  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float) +
+                           (size_t)((2 * max_ct + 7) & ~7);
   while (threads > 32 && threads > G && (size_t)(threads / G) * grp_bytes > 110 * 1024) threads /= 2;
   const size_t smem = (size_t)(threads / G) * grp_bytes;
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
@@ -1291,14 +1391,13 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
   const MeshView& M = m->view;
   Workspace& W = m->ws;
   Timing& tm = m->timing;
-  const int cgrid = (int)std::min<int64_t>((M.n_cells + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4);
   if (xmark_done) cudaStreamWaitEvent(s, m->ev_xjoin, 0);
   tm.start(KC_LSQ, s);
   if (!xmark_done) k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
-  k_xface<<<m->num_sms * 8, 64, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
-  k_lsq<kLsqCellLanes><<<cgrid, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   tm.start(KC_SOURCE, s);
+  k_xface<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
+  k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   cudaError_t e = cudaGetLastError();
