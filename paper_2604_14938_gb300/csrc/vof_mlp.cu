@@ -164,8 +164,8 @@ __device__ void warp_forward(Smem& s, int m0, float* Z1, float* Z2, float* Z3, f
 }
 
 // Loads kRows feature rows (float32 [n][40], or zeros past n) into the bf16 X tile.
-__device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n) {
-  for (int i = threadIdx.x; i < kRows * kInPad; i += blockDim.x) {
+__device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n, int rows = kRows) {
+  for (int i = threadIdx.x; i < rows * kInPad; i += blockDim.x) {
     const int r = i / kInPad, c = i % kInPad;
     const int64_t gr = row0 + r;
     const float v = (c < kIn && gr < n) ? X[gr * kIn + c] : 0.f;
@@ -220,9 +220,13 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
       if (lane == 0) ok[i] = 0;
       continue;
     }
-    // normalised value (FP64 difference, FP32 scaling); missing lanes hold -1 so that they sort last
+    // normalised value from the (hi, lo) float pairs of the vertex values (no FP64 instruction:
+    // each costs 64 FP32 issue slots on this part); missing lanes hold -1 so that they sort last
+    const float2 pf = W.phi_ff[v];
+    const int src = __ffs(__ballot_sync(0xffffffffu, okey(p) == klo)) - 1;
+    const float lox = __shfl_sync(0xffffffffu, pf.x, src), loy = __shfl_sync(0xffffffffu, pf.y, src);
     const float irange = 1.0f / (float)range;
-    float u = has ? (float)(p - lo) * irange : -1.0f;
+    float u = has ? ((pf.x - lox) + (pf.y - loy)) * irange : -1.0f;
     // bitonic sort, descending
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
@@ -238,9 +242,10 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
     const float smallest = __shfl_sync(0xffffffffu, u, nv - 1);
     float* x = X + i * kIn;
     x[2 + lane] = lane < nv ? u : smallest;
-    // shape: coordinates relative to the first vertex (FP64 difference, then FP32)
-    const int32_t vf = M.cell_vert[v0];
-    float rx = (float)(M.vx[v] - M.vx[vf]), ry = (float)(M.vy[v] - M.vy[vf]), rz = (float)(M.vz[v] - M.vz[vf]);
+    // shape: coordinates relative to the first vertex (the leading FP32 parts of the mesh's
+    // relative positions, that is the FP64 differences rounded to FP32)
+    const float2* rp = M.rel_pos + 3 * (v0 + (has ? lane : 0));
+    float rx = rp[0].x, ry = rp[1].x, rz = rp[2].x;
     float mnx = rx, mny = ry, mnz = rz, mxx = rx, mxy = ry, mxz = rz;
     float sx = has ? rx : 0.f, sy = has ? ry : 0.f, sz = has ? rz : 0.f;
 #pragma unroll
@@ -271,21 +276,23 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
 }
 
 // forward over the interface list (n read on the device); writes the guess of interface cell i,
-// clamped to [0, 1], or -1 where the cell has no features
-__global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
-                                                                 Workspace W) {
+// clamped to [0, 1], or -1 where the cell has no features. Blocks of kFwdRows rows (two warps),
+// so that a few thousand interface cells still spread over most SMs.
+constexpr int kFwdRows = 32;
+__global__ void __launch_bounds__(kFwdRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
+                                                                    Workspace W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const int64_t n = W.counters->n_iface;
-  if ((int64_t)blockIdx.x * kRows >= n) return;
+  if ((int64_t)blockIdx.x * kFwdRows >= n) return;
   stage_weights(s, *w);
   const int warp = threadIdx.x >> 5;
-  for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < n; row0 += (int64_t)gridDim.x * kRows) {
-    load_x(s, X, row0, n);
+  for (int64_t row0 = (int64_t)blockIdx.x * kFwdRows; row0 < n; row0 += (int64_t)gridDim.x * kFwdRows) {
+    load_x(s, X, row0, n, kFwdRows);
     __syncthreads();
-    if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
+    warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
     __syncthreads();
-    for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+    for (int r = threadIdx.x; r < kFwdRows; r += blockDim.x) {
       const int64_t i = row0 + r;
       if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(s.y[r], 0.f), 1.f) : -1.f;
     }
@@ -457,7 +464,6 @@ namespace vof {
 
 cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   vof_mlp* mlp = (vof_mlp*)m->mlp;
-  const int grid = m->num_sms * 2;
   float* X = m->ws.mlp_x;
   int32_t* ok = m->ws.mlp_ok;
   k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
@@ -466,7 +472,7 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
     attr = true;
   }
-  k_mlp_forward_iface<<<grid, kRows * 2, sizeof(Smem), s>>>(mlp->w, X, ok, m->ws);
+  k_mlp_forward_iface<<<m->num_sms * 3, kFwdRows * 2, sizeof(Smem), s>>>(mlp->w, X, ok, m->ws);
   return cudaGetLastError();
 }
 
