@@ -57,6 +57,7 @@ struct MeshView {
   const int32_t* vert_cell;
   const double* vert_w;      // inverse-distance weights, normalised per vertex
   const double* cell_vol;
+  const double* cell_ivol;   // 1 / cell_vol
   const double* cell_cen;    // [n][3]
   const double* face_area;   // [n][3] outward from owner
   const double* face_cen;    // [n][3]

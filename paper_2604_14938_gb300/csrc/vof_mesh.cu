@@ -55,7 +55,7 @@ __global__ void k_face_geom(int64_t nf, const int64_t* fvo, const int32_t* fv, c
 // Tetrahedron volumes (apex = local vertex 0), cell volume = their sum, centroid.
 __global__ void k_cell_geom(int64_t nc, const int64_t* cvo, const int32_t* cv, const int64_t* cto, const uint32_t* ct,
                             const double* vx, const double* vy, const double* vz, double* tvol, float* tvf,
-                            double* vol, double* cen, int32_t* bad) {
+                            double* vol, double* ivol, double* cen, int32_t* bad) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int32_t* V = cv + cvo[c];
@@ -78,6 +78,7 @@ __global__ void k_cell_geom(int64_t nc, const int64_t* cvo, const int32_t* cv, c
     sz += v * (az + vz[i0] + vz[i1] + vz[i2]) * 0.25;
   }
   vol[c] = sv;
+  ivol[c] = 1.0 / sv;
   cen[3 * c] = sx / sv; cen[3 * c + 1] = sy / sv; cen[3 * c + 2] = sz / sv;
   // volume fractions (FP32) for the FP32 refinement of the learned root search
   for (int64_t t = cto[c]; t < cto[c + 1]; ++t) tvf[t] = (float)(tvol[t] / sv);
@@ -299,6 +300,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   double *d_tvol, *d_vol, *d_cen, *d_fa, *d_fc, *d_w;
   float* d_tvf;
   float2* d_rel;
+  double* d_ivol;
+  TRY(dev_alloc(m, &d_ivol, nc));
   TRY(dev_alloc(m, &d_rel, 3 * cv.size()));
   int32_t* d_bad;
   TRY(dev_alloc(m, &d_tvol, ct.size()));
@@ -312,7 +315,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
   k_face_geom<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_fvo, d_fv, d_vx, d_vy, d_vz, d_fa, d_fc);
   k_cell_geom<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_cto, d_ct, d_vx, d_vy, d_vz, d_tvol,
-                                                            d_tvf, d_vol, d_cen, d_bad);
+                                                            d_tvf, d_vol, d_ivol, d_cen, d_bad);
   k_rel_pos<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_vx, d_vy, d_vz, d_rel);
   k_idw<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, d_vco, d_vc, d_vx, d_vy, d_vz, d_cen, d_w);
   int32_t h_bad = 0;
@@ -326,7 +329,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   V.tet_vfrac = d_tvf;
   V.rel_pos = d_rel;
   V.vert_cell_off = d_vco; V.vert_cell = d_vc; V.vert_w = d_w;
-  V.cell_vol = d_vol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
+  V.cell_vol = d_vol; V.cell_ivol = d_ivol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
   // ---- workspace
   Workspace& W = m->ws;
   m->n_sel_blocks = (int)((nc + kSelTile - 1) / kSelTile);

@@ -423,7 +423,20 @@ __device__ __forceinline__ ff ff_of(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+// FP32 -> FP64 by the bits (exact; zero, normal and infinite/NaN values), so that the widening
+// stays off the FP64 unit; subnormals take the conversion instruction
+__device__ __forceinline__ double fl2d(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu, mant = b & 0x7fffffu;
+  const uint64_t sgn = (uint64_t)(b & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (mant == 0u) return __longlong_as_double((long long)sgn);
+    return (double)f;
+  }
+  const uint64_t de = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);  // 1023 - 127
+  return __longlong_as_double((long long)(sgn | (de << 52) | ((uint64_t)mant << 29)));
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return fl2d(a.hi) + fl2d(a.lo); }
 __device__ __forceinline__ ff ff_norm(float s, float e) {  // |s| >= |e|
   const float h = __fadd_rn(s, e);
   return {h, __fsub_rn(e, __fsub_rn(h, s))};
@@ -551,15 +564,15 @@ __device__ void tet_section_ff(ff3 P1, ff3 P2, ff3 P3, ff w0, ff w1, ff w2, ff w
   mom = ff3_add(ff3_mul(ff3_add(g02, q[1]), wa), ff3_mul(ff3_add(g02, q[3]), wb));
 }
 
-// Interface geometry of one cell at the isovalue c (paper Sec. 2.1): vector area (wet -> dry),
-// area and area moment of the cut polygons, summed over the cell's tetrahedra by G lanes. A first
+// Interface geometry of one cell at the isovalue c (paper Sec. 2.1): area, unit normal (vapour ->
+// liquid) and centroid of the cut polygons, summed over the cell's tetrahedra by G lanes. A first
 // pass classifies the tetrahedra (integer work only) and appends the cut ones to the group's list
-// lst in shared memory, in tetrahedron order; the FP64 sections then run over that list with
-// every lane busy. Returns the number of cut tetrahedra.
+// lst in shared memory, in tetrahedron order; the sections (FP32 pairs) then run over that list
+// with every lane busy. Returns the number of cut tetrahedra.
 template <int G>
 __device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace& W, const int32_t* cv, int64_t v0,
                                              int64_t t0, int nt, double c, int lane, unsigned mask, uint16_t* lst,
-                                             Vec3& A, double& area, Vec3& mom) {
+                                             double& area, Vec3& nrm, Vec3& xg) {
   const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
   const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   const uint64_t kc = okey(c);
@@ -608,12 +621,25 @@ __device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace&
 #pragma unroll
     for (int q = 0; q < 7; ++q)
       v[q] = ff_add(v[q], ff{__shfl_xor_sync(mask, v[q].hi, o), __shfl_xor_sync(mask, v[q].lo, o)});
+  // unit normal (vapour -> liquid: against the wet -> dry vector area) and centroid, still in pairs;
+  // one FP64 addition per output
   const int32_t a = cv[0];
-  A = v3(ff_to_double(v[0]), ff_to_double(v[1]), ff_to_double(v[2]));
   area = ff_to_double(v[3]);
-  // the moment about the apex, moved to the origin: + area x apex
-  mom = v3(fma(area, M.vx[a], ff_to_double(v[4])), fma(area, M.vy[a], ff_to_double(v[5])),
-           fma(area, M.vz[a], ff_to_double(v[6])));
+  const ff3 Av = {v[0], v[1], v[2]};
+  const ff nn = ff3_dot(Av, Av);
+  if (nn.hi > 0.f) {
+    const ff rs = ff_neg(ff_rsqrt(nn));
+    nrm = v3(ff_to_double(ff_mul(v[0], rs)), ff_to_double(ff_mul(v[1], rs)), ff_to_double(ff_mul(v[2], rs)));
+  } else {
+    nrm = v3(0, 0, 0);
+  }
+  if (v[3].hi > 0.f) {
+    const ff ia = ff_rcp(v[3]);
+    xg = v3(M.vx[a] + ff_to_double(ff_mul(v[4], ia)), M.vy[a] + ff_to_double(ff_mul(v[5], ia)),
+            M.vz[a] + ff_to_double(ff_mul(v[6], ia)));
+  } else {
+    xg = v3(0, 0, 0);
+  }
   return n_cut;
 }
 
@@ -708,8 +734,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       n_prep += n;
     };
     const double a = alpha[cell];
-    const double V = M.cell_vol[cell];
-    const double invV = 1.0 / V;
+    const double invV = M.cell_ivol[cell];
     const uint64_t ktol = mag(opt.tol_alpha);
     int status = 0, evals = 0, evals32 = 0;
     int64_t tev = 0;  // tetrahedron evaluations
@@ -759,8 +784,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         float ubest, slope;
         {
           TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
-          const double srange = dir / range;
-          for (int j = lane; j < nv; j += G) uvert[j] = (float)((W.phi_v[cv[j]] - org) * srange);
+          // u from the vertex values' float pairs (FP32 work only): (phi - org) * dir / range
+          const float r32 = __frcp_rn((float)range);
+          const float su = refl ? -r32 : r32;
+          const ff of = ff_of(org);
+          for (int j = lane; j < nv; j += G) {
+            const float2 pv = W.phi_ff[cv[j]];
+            uvert[j] = __fmul_rn(__fadd_rn(__fsub_rn(pv.x, of.hi), __fsub_rn(pv.y, of.lo)), su);
+          }
           __syncwarp(mask);
           for (int t = lane; t < nt; t += G) {
             const uint32_t pk = __ldg(M.cell_tet + t0 + t);
@@ -865,27 +896,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
     }
     // interface geometry at c_best; the rows' shared memory now holds the cut list
-    Vec3 A = v3(0, 0, 0), mom = v3(0, 0, 0);
+    Vec3 nrm = v3(0, 0, 0), xg = v3(0, 0, 0);
     double area = 0;
     if (!(status & VOF_ST_DEGENERATE)) {
       __syncwarp(mask);
-      sect_acc += cell_geometry<G>(M, W, cv, v0, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows), A,
-                                   area, mom);
+      sect_acc += cell_geometry<G>(M, W, cv, v0, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows),
+                                   area, nrm, xg);
     }
     if (lane == 0) {
       W.iso[cell] = c_best;
       W.status[cell] = status;
       W.evals[cell] = evals;
       W.A_int[cell] = area;
-      const double an = norm(A);
-      const double inv = an > 0 ? -1.0 / an : 0.0;  // vapour -> liquid
-      W.n_int[3 * cell] = A.x * inv;
-      W.n_int[3 * cell + 1] = A.y * inv;
-      W.n_int[3 * cell + 2] = A.z * inv;
-      const double ia = area > 0 ? 1.0 / area : 0.0;
-      W.x_gamma[3 * cell] = mom.x * ia;
-      W.x_gamma[3 * cell + 1] = mom.y * ia;
-      W.x_gamma[3 * cell + 2] = mom.z * ia;
+      W.n_int[3 * cell] = nrm.x;
+      W.n_int[3 * cell + 1] = nrm.y;
+      W.n_int[3 * cell + 2] = nrm.z;
+      W.x_gamma[3 * cell] = xg.x;
+      W.x_gamma[3 * cell + 1] = xg.y;
+      W.x_gamma[3 * cell + 2] = xg.z;
       evals_acc += evals;
       ev32_acc += evals32;
       tetev_acc += tev;
