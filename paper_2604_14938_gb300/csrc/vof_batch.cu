@@ -173,26 +173,32 @@ vof_status vof_autotune(vof_mesh* m, const double* d_alpha, const vof_options* o
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int learned = opt->root_mode == VOF_ROOT_LEARNED && m->mlp;
-  for (int b = 0; b < kBins; ++b) {
-    if (!m->bin_cells[b] || !cn.bin_count[b]) continue;
+  // Coordinate descent over the populated bins, largest first: each candidate G of a bin is timed
+  // as reps whole reconstructions (selection, learned guess, every bin's root search as parallel
+  // branches), the other bins at their current choice, so that the choice accounts for the bins
+  // sharing the GPU.
+  vof_options o = *opt;
+  o.group_size = 0;
+  int order[kBins], nb = 0;
+  for (int b = 0; b < kBins; ++b)
+    if (m->bin_cells[b] && cn.bin_count[b]) order[nb++] = b;
+  for (int i = 1; i < nb; ++i)
+    for (int j = i; j > 0 && cn.bin_count[order[j]] > cn.bin_count[order[j - 1]]; --j) std::swap(order[j], order[j - 1]);
+  for (int b = 0; b < kBins; ++b)
+    if (!m->bin_cells[b] || !cn.bin_count[b]) m->bin_G[b] = 0;
+  for (int i = 0; i < nb; ++i) {
+    const int b = order[i];
     float best = 1e30f;
-    int best_G = 0;
-    // the root search takes its cells from a per-bin cursor that a step resets once; every
-    // launch here resets it first
-    int64_t* cursor = &m->ws.counters->bin_next[b];
+    int best_G = m->bin_G[b];
     for (int G = 1; G <= 32; G *= 2) {
-      // warm-up launch (also rejects infeasible shapes)
-      cudaMemsetAsync(cursor, 0, sizeof(int64_t), s);
-      if (launch_root_bin(m, d_alpha, *opt, s, learned, b, G) != cudaSuccess) {
+      m->bin_G[b] = G;
+      // warm-up reconstruction (also rejects infeasible shapes)
+      if (launch_reconstruct(m, d_alpha, o, s) != VOF_OK) {
         cudaGetLastError();
         continue;
       }
       cudaEventRecord(e0, s);
-      for (int r = 0; r < reps; ++r) {
-        cudaMemsetAsync(cursor, 0, sizeof(int64_t), s);
-        launch_root_bin(m, d_alpha, *opt, s, learned, b, G);
-      }
+      for (int r = 0; r < reps; ++r) launch_reconstruct(m, d_alpha, o, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) break;
       float ms = 0;
