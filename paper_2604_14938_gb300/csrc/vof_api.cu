@@ -146,13 +146,25 @@ vof_status vof_step_host(vof_mesh* m, const double* h_alpha, const double* h_T, 
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& W = m->ws;
   const size_t nc = (size_t)m->n_cells, nf = (size_t)m->n_faces;
-  cudaError_t e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && h_T_bnd) e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, s);
+  // alpha on the caller's stream; T and T_bnd, needed only by the source stage, on the mesh's copy
+  // stream, overlapping the reconstruction (the source stage waits for them)
+  cudaError_t e = cudaEventRecord(m->ev_io_start, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_stream, m->ev_io_start, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, m->io_stream);
+  if (e == cudaSuccess && h_T_bnd) e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, m->io_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(m->ev_io_done, m->io_stream);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  m->io_pending = true;
   vof_status st = vof_step(m, W.io_alpha, W.io_T, h_T_bnd ? W.io_Tb : nullptr, props, opt, W.io_mdot, W.io_Q,
                            W.io_totals, stream);
-  if (st) return st;
+  if (st) {
+    if (m->io_pending) {  // the step stopped before its source stage: let the copies finish
+      cudaStreamSynchronize(m->io_stream);
+      m->io_pending = false;
+    }
+    return st;
+  }
   e = cudaMemcpyAsync(h_mdot, W.io_mdot, nc * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_totals, W.io_totals, 2 * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

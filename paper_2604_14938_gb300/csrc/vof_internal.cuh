@@ -183,6 +183,11 @@ struct vof_mesh {
   // side branch of a whole step: crossing-face list, from the band to the least squares
   cudaStream_t xm_stream = nullptr;
   cudaEvent_t ev_xfork = nullptr, ev_xjoin = nullptr;
+  // host-buffer step: T and T_bnd are copied on their own stream while the reconstruction runs;
+  // the source stage waits for ev_io_done when io_pending is set
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t ev_io_start = nullptr, ev_io_done = nullptr;
+  bool io_pending = false;
 };
 
 namespace vof {

@@ -270,6 +270,9 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
     if (es == cudaSuccess) es = cudaStreamCreateWithFlags(&m->xm_stream, cudaStreamNonBlocking);
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xfork, cudaEventDisableTiming);
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xjoin, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_io_start, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_io_done, cudaEventDisableTiming);
     for (int b = 0; b < kBins && es == cudaSuccess; ++b) {
       es = cudaStreamCreateWithFlags(&m->bin_stream[b], cudaStreamNonBlocking);
       if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_join[b], cudaEventDisableTiming);
@@ -404,6 +407,11 @@ void destroy(vof_mesh* m) {
   if (m->ev_xjoin) cudaEventDestroy(m->ev_xjoin);
   m->xm_stream = nullptr;
   m->ev_xfork = m->ev_xjoin = nullptr;
+  if (m->io_stream) cudaStreamDestroy(m->io_stream);
+  if (m->ev_io_start) cudaEventDestroy(m->ev_io_start);
+  if (m->ev_io_done) cudaEventDestroy(m->ev_io_done);
+  m->io_stream = nullptr;
+  m->ev_io_start = m->ev_io_done = nullptr;
 }
 
 }  // namespace

@@ -1420,6 +1420,10 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
   Workspace& W = m->ws;
   Timing& tm = m->timing;
   if (xmark_done) cudaStreamWaitEvent(s, m->ev_xjoin, 0);
+  if (m->io_pending) {  // T and T_bnd of a host-buffer step, copied on the side
+    cudaStreamWaitEvent(s, m->ev_io_done, 0);
+    m->io_pending = false;
+  }
   tm.start(KC_LSQ, s);
   if (!xmark_done) k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
   tm.stop(s);
