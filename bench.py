@@ -32,9 +32,6 @@ METRIC = "interface cells/s (recon+LSQ∇T+mdot), learned vs bisection, at |Δα
 UNIT = "interface cells/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
-# library kernels per step: begin, 3 interface selection, 3 band/vertex lists, vertex field,
-# root search, least squares, source, totals
-KERNELS_PER_STEP = 12
 
 
 def _spheres(rng, k):
@@ -193,7 +190,11 @@ def run_ours(args, rank, world, dev):
         tuned = {}
         for mode in modes:
             opt = vof.default_options(root_mode=vof.ROOT_LEARNED if mode == "learned" else vof.ROOT_BISECT)
-            tuned[mode] = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
+            if args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
+                tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
+                M.set_group_sizes(tuned[mode])
+            else:
+                tuned[mode] = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
 
             def one(k):
                 ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
@@ -300,6 +301,8 @@ def main():
     ap.add_argument("--workload", default="film250k")
     ap.add_argument("--root", default="auto", choices=["auto", "bisect", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--group-sizes", default="",
+                    help="lanes per cell of the five tetrahedron-count bins, comma-separated (skips the autotuner)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
