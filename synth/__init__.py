@@ -204,15 +204,44 @@ def points(mesh: Mesh) -> tuple[np.ndarray, np.ndarray]:
     return c, f
 
 
+_CHUNK = 1 << 16
+
+
+def _nearest_sphere(s: np.ndarray, x: np.ndarray):
+    """(j, r_j, g) per point: the sphere j minimising |x - c_j| - R_j, the distance to its centre,
+    and that minimum. Few spheres: brute force. Many: the 8 nearest centres from a k-d tree, which
+    settle the minimum wherever the 8th centre is at least R_max beyond it; the other points fall
+    back to brute force."""
+    def brute(xs):
+        r = np.linalg.norm(xs[:, None, :] - s[None, :, :3], axis=2)
+        j = np.argmin(r - s[None, :, 3], axis=1)
+        rr = r[np.arange(len(xs)), j]
+        return j, rr, rr - s[j, 3]
+    k = 8
+    if len(s) <= 4 * k:
+        return brute(x)
+    from scipy.spatial import cKDTree
+    d, idx = cKDTree(s[:, :3]).query(x, k=k, workers=-1)
+    r = np.linalg.norm(x[:, None, :] - s[idx, :3], axis=2)
+    gk = r - s[idx, 3]
+    a = np.argmin(gk, axis=1)
+    rows = np.arange(len(x))
+    j, rr, g = idx[rows, a], r[rows, a], gk[rows, a]
+    bad = np.nonzero(d[:, -1] - s[:, 3].max() < g)[0]
+    if len(bad):
+        j[bad], rr[bad], g[bad] = brute(x[bad])
+    return j, rr, g
+
+
 def region_g(region: dict, x: np.ndarray) -> np.ndarray:
     """Signed liquid indicator g(x) (> 0 in the liquid) of a region, vectorised."""
+    if len(x) > _CHUNK:
+        return np.concatenate([region_g(region, x[i:i + _CHUNK]) for i in range(0, len(x), _CHUNK)])
     t = region["type"]
     if t == "plane":
         return region["d"] - x @ np.asarray(region["n"], float)
     if t == "spheres":
-        s = np.asarray(region["spheres"], float)
-        r = np.linalg.norm(x[:, None, :] - s[None, :, :3], axis=2) - s[None, :, 3]
-        return r.min(axis=1)
+        return _nearest_sphere(np.asarray(region["spheres"], float), x)[2]
     if t == "film":
         return (region["z0"] + region["a"] * np.sin(2 * np.pi * x[:, 0] / region.get("lx", 1.0))
                 * np.sin(2 * np.pi * x[:, 1] / region.get("ly", 1.0)) - x[:, 2])
@@ -233,6 +262,8 @@ def temperature_at(region: dict, profile: dict, x: np.ndarray) -> np.ndarray:
       'stefan'  vapour x < x_g: T_sat + dT (1 - x/x_g); liquid T_sat
       'quadratic' T = T0 + g.x + 0.5 x^T H x
     """
+    if len(x) > _CHUNK:  # bounded temporaries (sphere regions broadcast points x spheres)
+        return np.concatenate([temperature_at(region, profile, x[i:i + _CHUNK]) for i in range(0, len(x), _CHUNK)])
     k = profile["kind"]
     Ts = profile.get("T_sat", T_SAT)
     if k == "linear":
@@ -246,9 +277,7 @@ def temperature_at(region: dict, profile: dict, x: np.ndarray) -> np.ndarray:
     liquid = region_g(region, x) > 0
     if k == "radial":
         s = np.asarray(region["spheres"], float)
-        r = np.linalg.norm(x[:, None, :] - s[None, :, :3], axis=2)
-        j = np.argmin(r - s[None, :, 3], axis=1)
-        rr = r[np.arange(len(x)), j]
+        j, rr, _ = _nearest_sphere(s, x)
         RR = s[j, 3]
         T = Ts + profile["dT"] * (1 - RR / np.maximum(rr, 1e-300))
     elif k == "film":

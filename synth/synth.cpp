@@ -511,58 +511,114 @@ Mesh* voronoi_from_sites(const std::vector<double>& S, const double* lo, const d
     }
     cells[s] = std::move(p);
   }
-  // global vertices from canonical keys
-  std::unordered_map<std::array<int32_t, 4>, int32_t, KeyHash> vmap;
-  std::vector<std::vector<int32_t>> gid(ns);
-  for (int64_t s = 0; s < ns; ++s) {
-    gid[s].resize(cells[s].verts.size());
+  // Global vertices from canonical keys. Entry q = (cell s, local vertex i), numbered in cell
+  // order; a vertex takes its id in the order of its first entry. The entries are hashed into
+  // buckets (a stable counting sort), each bucket finds the first entry of every key on its own,
+  // and one pass in entry order hands out the ids.
+  std::vector<int64_t> voff(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) voff[s + 1] = voff[s] + (int64_t)cells[s].verts.size();
+  const int64_t nq = voff[ns];
+  constexpr int kBuckets = 4096;
+  std::vector<std::array<int32_t, 4>> key(nq);
+  std::vector<uint32_t> kb(nq);
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < ns; ++s)
     for (size_t i = 0; i < cells[s].verts.size(); ++i) {
       const auto& pl = cells[s].verts[i].planes;
-      std::array<int32_t, 4> key = {pl[0], pl[1], pl[2], (int32_t)s};
-      std::sort(key.begin(), key.end());
-      auto it = vmap.find(key);
-      if (it == vmap.end()) {
-        const int32_t id = (int32_t)m->vx.size();
-        double y[3];
-        key_point(key, S, lo, hi, y);
-        m->vx.push_back(y[0]); m->vy.push_back(y[1]); m->vz.push_back(y[2]);
-        vmap.emplace(key, id);
-        gid[s][i] = id;
-      } else {
-        gid[s][i] = it->second;
-      }
+      std::array<int32_t, 4> k = {pl[0], pl[1], pl[2], (int32_t)s};
+      std::sort(k.begin(), k.end());
+      key[voff[s] + i] = k;
+      kb[voff[s] + i] = (uint32_t)(KeyHash()(k) % kBuckets);
+    }
+  std::vector<int64_t> bstart(kBuckets + 1, 0), order(nq);
+  for (int64_t q = 0; q < nq; ++q) bstart[kb[q] + 1]++;
+  for (int b = 0; b < kBuckets; ++b) bstart[b + 1] += bstart[b];
+  {
+    std::vector<int64_t> pos(bstart.begin(), bstart.end() - 1);
+    for (int64_t q = 0; q < nq; ++q) order[pos[kb[q]]++] = q;
+  }
+  std::vector<int64_t> rep(nq);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < kBuckets; ++b) {
+    std::unordered_map<std::array<int32_t, 4>, int64_t, KeyHash> first;
+    first.reserve((size_t)(bstart[b + 1] - bstart[b]));
+    for (int64_t t = bstart[b]; t < bstart[b + 1]; ++t) {
+      const int64_t q = order[t];  // increasing within the bucket
+      rep[q] = first.emplace(key[q], q).first->second;
     }
   }
-  // faces: owner = lower site id for interior faces
-  std::unordered_map<uint64_t, int64_t> fmap;
+  std::vector<int32_t> vid(nq);
+  int32_t nv = 0;
+  for (int64_t q = 0; q < nq; ++q) vid[q] = rep[q] == q ? nv++ : vid[rep[q]];
+  m->vx.resize(nv);
+  m->vy.resize(nv);
+  m->vz.resize(nv);
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < nq; ++q)
+    if (rep[q] == q) {
+      double y[3];
+      key_point(key[q], S, lo, hi, y);
+      m->vx[vid[q]] = y[0];
+      m->vy[vid[q]] = y[1];
+      m->vz[vid[q]] = y[2];
+    }
+  // Faces, in cell order: cell s emits its box faces and its faces toward higher sites (owner =
+  // lower site id); a face toward a lower site p must match the loop p emitted, reversed.
+  std::vector<int64_t> fcount(ns + 1, 0), fvcount(ns + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < ns; ++s)
+    for (const CFace& f : cells[s].faces)
+      if (f.plane < 0 || f.plane > s) { fcount[s + 1]++; fvcount[s + 1] += (int64_t)f.v.size(); }
+  for (int64_t s = 0; s < ns; ++s) { fcount[s + 1] += fcount[s]; fvcount[s + 1] += fvcount[s]; }
+  const int64_t nf = fcount[ns];
+  m->face_vert_off.assign(nf + 1, 0);
+  m->face_vert.resize(fvcount[ns]);
+  m->face_owner.resize(nf);
+  m->face_neigh.resize(nf);
+  std::vector<uint8_t> matched(nf, 0);
+  int64_t errors = 0;
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t fi = fcount[s], vo = fvcount[s];
+    for (const CFace& f : cells[s].faces) {
+      if (!(f.plane < 0 || f.plane > s)) continue;
+      for (int v : f.v) m->face_vert[vo++] = vid[voff[s] + v];
+      m->face_vert_off[fi + 1] = vo;
+      m->face_owner[fi] = (int32_t)s;
+      m->face_neigh[fi] = f.plane < 0 ? -1 : f.plane;
+      fi++;
+    }
+  }
+#pragma omp parallel for schedule(static) reduction(+ : errors)
   for (int64_t s = 0; s < ns; ++s) {
     for (const CFace& f : cells[s].faces) {
-      std::vector<int32_t> loop;
-      for (int v : f.v) loop.push_back(gid[s][v]);
-      if (f.plane < 0) {
-        add_face(*m, loop.data(), (int)loop.size(), (int32_t)s, -1);
-      } else if (f.plane > s) {
-        fmap[((uint64_t)s << 32) | (uint32_t)f.plane] = (int64_t)m->face_owner.size();
-        add_face(*m, loop.data(), (int)loop.size(), (int32_t)s, f.plane);
-      } else {
-        auto it = fmap.find(((uint64_t)f.plane << 32) | (uint32_t)s);
-        if (it == fmap.end()) { m->conform_errors++; continue; }
-        const int64_t fi = it->second;
-        const int64_t o = m->face_vert_off[fi];
-        const int n = (int)(m->face_vert_off[fi + 1] - o);
-        bool ok = n == (int)loop.size();
-        int st = -1;
-        for (int i = 0; ok && i < n; ++i)
-          if (m->face_vert[o + i] == loop[0]) st = i;
-        ok = ok && st >= 0;
-        for (int i = 0; ok && i < n; ++i) ok = m->face_vert[o + ((st - i) % n + n) % n] == loop[i];
-        if (!ok) m->conform_errors++;
-        fmap.erase(it);
+      if (f.plane < 0 || f.plane > s) continue;
+      // the face that the lower site p = f.plane emitted toward s
+      const int64_t p = f.plane;
+      int64_t fi = fcount[p];
+      bool found = false;
+      for (const CFace& g : cells[p].faces) {
+        if (!(g.plane < 0 || g.plane > p)) continue;
+        if (g.plane == s) { found = true; break; }
+        fi++;
       }
+      if (!found) { errors++; continue; }
+      matched[fi] = 1;
+      const int64_t o = m->face_vert_off[fi];
+      const int n = (int)(m->face_vert_off[fi + 1] - o);
+      bool ok = n == (int)f.v.size();
+      int st = -1;
+      for (int i = 0; ok && i < n; ++i)
+        if (m->face_vert[o + i] == vid[voff[s] + f.v[0]]) st = i;
+      ok = ok && st >= 0;
+      for (int i = 0; ok && i < n; ++i) ok = m->face_vert[o + ((st - i) % n + n) % n] == vid[voff[s] + f.v[i]];
+      if (!ok) errors++;
     }
   }
-  m->conform_errors += (int64_t)fmap.size();  // faces never matched by the other cell
-  for (auto& kv : fmap) m->face_neigh[kv.second] = -1;
+  // faces never matched by the other cell
+  for (int64_t fi = 0; fi < nf; ++fi)
+    if (m->face_neigh[fi] >= 0 && !matched[fi]) { errors++; m->face_neigh[fi] = -1; }
+  m->conform_errors += errors;
   m->n_cells = ns;
   build_cell_faces(*m);
   return m;
@@ -951,11 +1007,30 @@ void synth_alpha(int64_t nc, const double* vx, const double* vy, const double* v
 #pragma omp parallel
   {
     CellTets ct;
+    std::vector<double> near;
 #pragma omp for schedule(dynamic, 512)
     for (int64_t c = 0; c < nc; ++c) {
       cell_tets(m, c, ct);
       const double g0 = R.g(ct.apex);
       if (std::fabs(g0) > L * ct.rad * 1.0001 + 1e-12) { alpha[c] = g0 > 0 ? 1.0 : 0.0; continue; }
+      Region Rc = R;
+      if (R.type == 1 && R.np > 32) {
+        // Every sample lies within Rb of the apex (2 rad covers the bounding box too), where sphere
+        // s contributes a term in [d_s - R_s - Rb, d_s - R_s + Rb]. A sphere whose lowest term is
+        // above the smallest highest term can never be the minimum, so g is unchanged without it.
+        const double Rb = 2 * ct.rad * 1.0001 + 1e-12;
+        auto dist = [&](const double* q) {
+          return std::sqrt((ct.apex[0] - q[0]) * (ct.apex[0] - q[0]) + (ct.apex[1] - q[1]) * (ct.apex[1] - q[1]) +
+                           (ct.apex[2] - q[2]) * (ct.apex[2] - q[2]));
+        };
+        double mu = 1e300;
+        for (int k = 0; k + 4 <= R.np; k += 4) mu = std::min(mu, dist(R.p + k) - R.p[k + 3] + Rb);
+        const double tol = 1e-9 * (1 + std::fabs(mu));
+        near.clear();
+        for (int k = 0; k + 4 <= R.np; k += 4)
+          if (dist(R.p + k) - R.p[k + 3] - Rb <= mu + tol) near.insert(near.end(), R.p + k, R.p + k + 4);
+        Rc = Region{1, near.data(), (int)near.size()};
+      }
       if (mode == 1) {
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
         for (auto& t : ct.tets)
@@ -968,7 +1043,7 @@ void synth_alpha(int64_t nc, const double* vx, const double* vy, const double* v
             for (int i = 0; i < n; ++i) {
               const double x[3] = {lo[0] + (hi[0] - lo[0]) * (i + 0.5) / n, lo[1] + (hi[1] - lo[1]) * (j + 0.5) / n,
                                    lo[2] + (hi[2] - lo[2]) * (k + 0.5) / n};
-              in += R.g(x) > 0;
+              in += Rc.g(x) > 0;
             }
         alpha[c] = (double)in / ((double)n * n * n);
       } else {
@@ -978,7 +1053,7 @@ void synth_alpha(int64_t nc, const double* vx, const double* vy, const double* v
           const double vx2 = t[6] - t[0], vy2 = t[7] - t[1], vz2 = t[8] - t[2];
           const double wx = t[9] - t[0], wy = t[10] - t[1], wz = t[11] - t[2];
           const double vol = std::fabs(ux * (vy2 * wz - vz2 * wy) - uy * (vx2 * wz - vz2 * wx) + uz * (vx2 * wy - vy2 * wx)) / 6.0;
-          s += vol * tet_fraction(t.data(), level, R);
+          s += vol * tet_fraction(t.data(), level, Rc);
           vt += vol;
         }
         alpha[c] = std::min(1.0, std::max(0.0, s / vt));

@@ -77,3 +77,48 @@ def gpu_step(m, a, T, Tb, props=None, dev_mesh=None, n_cells=None, **opt):
     out = {k: M.field(k).cpu().numpy() for k in vof.FIELDS}
     out.update(mdot=mdot.cpu().numpy(), Q=Q.cpu().numpy(), totals=tot.cpu().numpy(), counts=M.counts())
     return M, out
+
+
+def rel_err(x, y):
+    """Per-element (per-row for vectors: Euclidean norm) error of x against y, relative to
+    max(|y|, 1e-3 max|y|)."""
+    x, y = np.asarray(x, float), np.asarray(y, float)
+    if y.ndim == 2:
+        dn, yn = np.linalg.norm(x - y, axis=1), np.linalg.norm(y, axis=1)
+    else:
+        dn, yn = np.abs(x - y), np.abs(y)
+    if yn.size == 0:
+        return dn
+    scale = np.maximum(yn, 1e-3 * yn.max())
+    return dn / np.where(scale == 0, 1.0, scale)
+
+
+def ulp_spread(O, a, rec, T, Tb, props, keys, draws=2, seed=0):
+    """The oracle's own conditioning, cell by cell: the largest rel_err of its downstream outputs
+    when every cell centroid is moved by at most one ulp (random sign). Returns (unperturbed
+    outputs, {key: spread per row})."""
+    g = O.geometry()
+    cen0 = g["cell_cen"].copy()
+    pc0 = O.phase_change(a, rec, T, Tb, props)
+    rng = np.random.default_rng(seed)
+    spread = {k: np.zeros(len(pc0[k])) for k in keys}
+    try:
+        for _ in range(draws):
+            s = rng.integers(-1, 2, cen0.shape)
+            g["cell_cen"][:] = np.where(s > 0, np.nextafter(cen0, np.inf), np.where(s < 0, np.nextafter(cen0, -np.inf), cen0))
+            pc = O.phase_change(a, rec, T, Tb, props)
+            for k in keys:
+                spread[k] = np.maximum(spread[k], rel_err(pc[k], pc0[k]))
+    finally:
+        g["cell_cen"][:] = cen0
+    return pc0, spread
+
+
+def within(gpu, orc, spread, rel=1e-8, factor=100.0):
+    """(ok, worst ratio): rel_err(gpu, orc) <= max(rel, factor * spread) row by row. Where the
+    oracle's own answer moves by more than rel/factor under one-ulp input rounding (an
+    ill-conditioned least-squares stencil), the allowance grows with it."""
+    e = rel_err(gpu, orc)
+    allow = np.maximum(rel, factor * np.asarray(spread))
+    r = e / allow
+    return bool(np.all(r <= 1.0)), float(r.max()) if r.size else 0.0
