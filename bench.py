@@ -307,7 +307,7 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_max = float(t.item())
     value = world * r["units"] / (ms_max / 1e3)
-    # roofline of the dominant kernel (root search + geometry): algorithmic FP64 flops per launch,
+    # roofline of the dominant kernel (the root search): algorithmic FP64 flops per launch,
     # from the device counters of the same step whose kernel time the events measured
     # per step: the eager timing pass records one selection group per step and one root-search
     # launch per non-empty bin (bins run as parallel branches: their launch times are summed)
@@ -317,8 +317,9 @@ def main():
     achieved = flops / (root_ms / 1e3) / 1e12 if root_ms and flops else None
     ksum = sum(v[0] for v in r["ktime"].values())
     share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
-    nbins = sum(1 for c in M.bin_cells if c)  # the root search (with the geometry) launches once per non-empty bin
-    per_step = 5 + nbins + (2 if best == "learned" else 0) + (1 if info["batch"] else 0)
+    nbins = sum(1 for c in M.bin_cells if c)  # the root search launches once per non-empty bin
+    # selection, crossing list, crossing faces, least squares, source, geometry; guess (2); batch totals
+    per_step = 6 + nbins + (2 if best == "learned" else 0) + (1 if info["batch"] else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -336,7 +337,7 @@ def main():
                   for k, v in res.items()},
         "kernel_ms_per_step": {k: v[0] / nst for k, v in r["ktime"].items() if v[1]},
         "kernel_share": share,
-        "roofline": {"kernel": "k_root (isovalue root search + interface geometry)", "bound": "alu",
+        "roofline": {"kernel": "k_root (isovalue root search)", "bound": "alu",
                      "flops_per_launch": flops, "flops_per_iface_cell": flops / max(r["kcounts"]["n_iface"], 1),
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,

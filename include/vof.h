@@ -231,7 +231,8 @@ vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
 vof_status vof_mesh_info(const vof_mesh* mesh, int64_t* out5);
 
 /* Cells of the mesh per tetrahedron-count bin (1-4, 5-8, 9-24, 25-64, 65-192 tetrahedra):
- * a step launches the root search (with the interface geometry) once for every non-empty bin.
+ * a step launches the root search once for every non-empty bin (then the interface geometry
+ * once over all interface cells).
  * Host array of 5.
  * No counterpart in the paper (launch layout of this implementation). */
 vof_status vof_mesh_bins(const vof_mesh* mesh, int64_t* cells5);
@@ -293,9 +294,9 @@ vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, do
  * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
  * vof_timing_read synchronises the stream and returns, per kernel class, the summed
  * milliseconds and the launch count since the last read (at most 8192 records are kept).
- * Classes: 0 selection, band and vertex field, 2 root search and interface geometry, 3 list of
- * the crossing faces, 4 crossing faces, least squares, per-side gradients, source and totals,
- * 6 learned guess; 1, 5 and 7 are unused. */
+ * Classes: 0 selection, band and vertex field, 2 root search, 3 list of the crossing faces,
+ * 4 crossing faces, least squares, per-side gradients, source and totals, 6 learned guess,
+ * 7 interface geometry; 1 and 5 are unused. */
 vof_status vof_timing_enable(vof_mesh* mesh, int on);
 vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
 

@@ -213,9 +213,14 @@ class Mesh:
 
     def root_flops(self, counts: dict) -> int:
         """Algorithmic FP64 flops of the root-search launches summed in `counts`: rows prepared,
-        tetrahedron evaluations, per-evaluation scaling, and the sections of the cut tetrahedra."""
+        tetrahedron evaluations and per-evaluation scaling."""
         return (self.FLOPS_TET_EVAL * counts["tet_evals"] + self.FLOPS_TET_PREP * counts["tets_prepared"]
-                + self.FLOPS_TET_SECTION * counts["tets_sectioned"] + self.FLOPS_EVAL * counts["evals_total"])
+                + self.FLOPS_EVAL * counts["evals_total"])
+
+    def geom_flops(self, counts: dict) -> int:
+        """Algorithmic flops of the interface-geometry launches in `counts` (the sections of the cut
+        tetrahedra; the kernel runs them in FP32 pair arithmetic)."""
+        return self.FLOPS_TET_SECTION * counts["tets_sectioned"]
 
     def counts(self, stream=None) -> dict:
         c = Counts()

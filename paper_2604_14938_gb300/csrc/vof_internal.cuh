@@ -166,7 +166,8 @@ struct vof_mesh {
   int bin_G[vof::kBins] = {0, 0, 0, 0, 0};          // lanes per cell (autotuned; 0 = default)
   int n_sel_blocks = 0;
   int num_sms = 0;
-  int sel_grid = 0;  // blocks of the cooperative selection launch (all resident)
+  int sel_grid = 0;   // blocks of the cooperative selection launch (all resident)
+  int geom_grid = 0;  // blocks of the interface-geometry launch
   vof::MeshView view{};
   vof::Workspace ws{};
   std::vector<void*> allocs;

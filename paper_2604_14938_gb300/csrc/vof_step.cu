@@ -564,66 +564,11 @@ __device__ void tet_section_ff(ff3 P1, ff3 P2, ff3 P3, ff w0, ff w1, ff w2, ff w
   mom = ff3_add(ff3_mul(ff3_add(g02, q[1]), wa), ff3_mul(ff3_add(g02, q[3]), wb));
 }
 
-// Interface geometry of one cell at the isovalue c (paper Sec. 2.1): area, unit normal (vapour ->
-// liquid) and centroid of the cut polygons, summed over the cell's tetrahedra by G lanes. A first
-// pass classifies the tetrahedra (integer work only) and appends the cut ones to the group's list
-// lst in shared memory, in tetrahedron order; the sections (FP32 pairs) then run over that list
-// with every lane busy. Returns the number of cut tetrahedra.
-template <int G>
-__device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace& W, const int32_t* cv, int64_t v0,
-                                             int64_t t0, int nt, double c, int lane, unsigned mask, uint16_t* lst,
-                                             double& area, Vec3& nrm, Vec3& xg) {
-  const int base = (threadIdx.x & 31) / G * G;  // the group's first lane in the warp
-  const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-  const uint64_t kc = okey(c);
-  const unsigned m0 = (unsigned)(okey(W.phi_v[cv[0]]) >= kc);
-  int n_cut = 0;
-  for (int r0 = 0; r0 < nt; r0 += G) {
-    const int t = r0 + lane;
-    unsigned m = 0;
-    if (t < nt) {
-      const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-      m = m0 | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
-          ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
-          ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
-    }
-    const bool cut = t < nt && m != 0 && m != 15u;
-    const unsigned bal = (__ballot_sync(mask, cut) >> base) & gbits;
-    if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((t << 4) | m);
-    n_cut += __popc(bal);
-  }
-  __syncwarp(mask);
-  // sections in pair arithmetic, positions relative to the apex
-  const ff cf = ff_of(c);
-  const ff w0 = ff_sub(ff_make(W.phi_ff[cv[0]]), cf);
-  const ff z = {0.f, 0.f};
-  ff3 sA = {z, z, z}, sm = {z, z, z};
-  ff sa = z;
-  const float2* rp = M.rel_pos + 3 * v0;
-  for (int jj = lane; jj < n_cut; jj += G) {
-    const unsigned e = lst[jj];
-    const int t = (int)(e >> 4);
-    const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-    const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
-    ff3 tA, tm;
-    ff ta;
-    tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), w0,
-                   ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
-                   ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
-    sA = ff3_add(sA, tA);
-    sa = ff_add(sa, ta);
-    sm = ff3_add(sm, tm);
-  }
-  // group sums in pairs, then FP64
-  ff v[7] = {sA.x, sA.y, sA.z, sa, sm.x, sm.y, sm.z};
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < 7; ++q)
-      v[q] = ff_add(v[q], ff{__shfl_xor_sync(mask, v[q].hi, o), __shfl_xor_sync(mask, v[q].lo, o)});
-  // unit normal (vapour -> liquid: against the wet -> dry vector area) and centroid, still in pairs;
-  // one FP64 addition per output
-  const int32_t a = cv[0];
+// Unit normal (vapour -> liquid: against the wet -> dry vector area), area and centroid of a cell's
+// interface from its summed pairs v = (vector area, area, area moment about the apex at a);
+// still in pairs, then one FP64 addition per output.
+__device__ __forceinline__ void geometry_outputs(const ff* v, double ax, double ay, double az, double& area,
+                                                 Vec3& nrm, Vec3& xg) {
   area = ff_to_double(v[3]);
   const ff3 Av = {v[0], v[1], v[2]};
   const ff nn = ff3_dot(Av, Av);
@@ -635,12 +580,11 @@ __device__ __forceinline__ int cell_geometry(const MeshView& M, const Workspace&
   }
   if (v[3].hi > 0.f) {
     const ff ia = ff_rcp(v[3]);
-    xg = v3(M.vx[a] + ff_to_double(ff_mul(v[4], ia)), M.vy[a] + ff_to_double(ff_mul(v[5], ia)),
-            M.vz[a] + ff_to_double(ff_mul(v[6], ia)));
+    xg = v3(ax + ff_to_double(ff_mul(v[4], ia)), ay + ff_to_double(ff_mul(v[5], ia)),
+            az + ff_to_double(ff_mul(v[6], ia)));
   } else {
     xg = v3(0, 0, 0);
   }
-  return n_cut;
 }
 
 template <int G>
@@ -658,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
   uint16_t* actl = reinterpret_cast<uint16_t*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow) + uv_bytes);
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
-  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0, sect_acc = 0;
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
   // each group takes the next cell of the bin when it is done with the last one: the learned
   // path's fallback cells cost ten times a typical cell, so a static split leaves SMs idle
   for (;;) {
@@ -895,25 +839,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       }
       if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
     }
-    // interface geometry at c_best; the rows' shared memory now holds the cut list
-    Vec3 nrm = v3(0, 0, 0), xg = v3(0, 0, 0);
-    double area = 0;
-    if (!(status & VOF_ST_DEGENERATE)) {
-      __syncwarp(mask);
-      sect_acc += cell_geometry<G>(M, W, cv, v0, t0, nt, c_best, lane, mask, reinterpret_cast<uint16_t*>(rows),
-                                   area, nrm, xg);
-    }
+    // the interface geometry at c_best follows in k_geom
     if (lane == 0) {
       W.iso[cell] = c_best;
       W.status[cell] = status;
       W.evals[cell] = evals;
-      W.A_int[cell] = area;
-      W.n_int[3 * cell] = nrm.x;
-      W.n_int[3 * cell + 1] = nrm.y;
-      W.n_int[3 * cell + 2] = nrm.z;
-      W.x_gamma[3 * cell] = xg.x;
-      W.x_gamma[3 * cell + 1] = xg.y;
-      W.x_gamma[3 * cell + 2] = xg.z;
       evals_acc += evals;
       ev32_acc += evals32;
       tetev_acc += tev;
@@ -930,8 +860,162 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
     atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
     atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
     if (ev32_acc) atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
-    if (sect_acc) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect_acc);
   }
+}
+
+// Interface geometry (paper Sec. 2.1: area, unit normal and centroid of the cut polygons) at the
+// isovalues of the root search: a warp per interface cell, in interface-list order, each lane
+// sectioning its share of the cell's cut tetrahedra in FP32 pair arithmetic. Kept apart from the
+// root search, whose per-cell chain is FP64 latency: here every cell is in flight at once and the
+// chain is one or two sections and the pair sums.
+// Interface geometry (paper Sec. 2.1: area, unit normal and centroid of the cut polygons) at the
+// isovalues of the root search, kept apart from it: the root search's per-cell chain is FP64
+// latency, while here every cell is in flight at once. A warp takes kGeomCells consecutive
+// interface cells and lists their cut tetrahedra together (tetrahedron order within a cell), so
+// that the sections (FP32 pair arithmetic) keep most lanes busy; each lane adds its sections into
+// its own partial sums per cell in shared memory, and kGeomRed lanes per cell then add the 32
+// partials in a fixed order: the result does not depend on timing.
+constexpr int kGeomCells = 2;  // at most 4 (two bits of a list entry)
+constexpr int kGeomRed = 32 / kGeomCells;
+constexpr int kGeomWarps = kThreads / 32;
+
+struct GeomSlot {
+  int64_t v0, t0;  // first vertex / tetrahedron entry of the cell
+  double c;        // isovalue
+  float2 cf, w0;   // isovalue and apex value minus it, as pairs
+  int32_t cell;    // -1: no cell
+  int32_t nt;      // tetrahedra (0 for a degenerate cell)
+};
+
+size_t geom_smem_bytes(int max_ct) {
+  return (size_t)kGeomWarps * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomCells * sizeof(GeomSlot) +
+                               (size_t)kGeomCells * max_ct * sizeof(uint32_t));
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_geom(MeshView M, Workspace W, int max_ct) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  float2* part = reinterpret_cast<float2*>(smem) + (size_t)warp * kGeomCells * 7 * 32;  // [cell][k][lane]
+  GeomSlot* slot = reinterpret_cast<GeomSlot*>(reinterpret_cast<float2*>(smem) + (size_t)kGeomWarps * kGeomCells * 7 * 32) +
+                   warp * kGeomCells;
+  uint32_t* lst = reinterpret_cast<uint32_t*>(reinterpret_cast<GeomSlot*>(reinterpret_cast<float2*>(smem) +
+                                                                          (size_t)kGeomWarps * kGeomCells * 7 * 32) +
+                                              kGeomWarps * kGeomCells) +
+                  (size_t)warp * kGeomCells * max_ct;
+  const int64_t n = W.counters->n_iface;
+  int64_t sect = 0;
+  for (int64_t i0 = ((int64_t)blockIdx.x * kGeomWarps + warp) * kGeomCells; i0 < n;
+       i0 += (int64_t)gridDim.x * kGeomWarps * kGeomCells) {
+    if (lane < kGeomCells) {
+      GeomSlot g = {0, 0, 0.0, make_float2(0.f, 0.f), make_float2(0.f, 0.f), -1, 0};
+      if (i0 + lane < n) {
+        g.cell = W.iface_idx[i0 + lane];
+        g.v0 = M.cell_vert_off[g.cell];
+        if (!(W.status[g.cell] & VOF_ST_DEGENERATE)) {
+          g.t0 = M.cell_tet_off[g.cell];
+          g.nt = (int32_t)(M.cell_tet_off[g.cell + 1] - g.t0);
+          g.c = W.iso[g.cell];
+          const ff cf = ff_of(g.c);
+          const ff w0 = ff_sub(ff_make(W.phi_ff[M.cell_vert[g.v0]]), cf);
+          g.cf = make_float2(cf.hi, cf.lo);
+          g.w0 = make_float2(w0.hi, w0.lo);
+        }
+      }
+      slot[lane] = g;
+    }
+#pragma unroll
+    for (int k = 0; k < kGeomCells * 7; ++k) part[k * 32 + lane] = make_float2(0.f, 0.f);
+    __syncwarp();
+    int off[kGeomCells + 1];
+    off[0] = 0;
+#pragma unroll
+    for (int q = 0; q < kGeomCells; ++q) off[q + 1] = off[q] + slot[q].nt;
+    // the cut tetrahedra of the warp's cells, by integer order keys
+    int n_cut = 0;
+    for (int r0 = 0; r0 < off[kGeomCells]; r0 += 32) {
+      const int q = r0 + lane;
+      bool cut = false;
+      uint32_t ent = 0;
+      if (q < off[kGeomCells]) {
+        int sl = 0, base = 0;
+#pragma unroll
+        for (int k = 1; k < kGeomCells; ++k)
+          if (q >= off[k]) { sl = k; base = off[k]; }
+        const GeomSlot& g = slot[sl];
+        const int t = q - base;
+        const uint64_t kc = okey(g.c);
+        const int32_t* cv = M.cell_vert + g.v0;
+        const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
+        const unsigned m = (unsigned)(okey(W.phi_v[cv[0]]) >= kc) | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
+                           ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
+                           ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
+        cut = m != 0u && m != 15u;
+        ent = ((uint32_t)t << 6) | ((uint32_t)sl << 4) | m;
+      }
+      const unsigned bal = __ballot_sync(full, cut);
+      if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = ent;
+      n_cut += __popc(bal);
+    }
+    __syncwarp();
+    // sections, each added to this lane's partials of its cell
+    for (int jj = lane; jj < n_cut; jj += 32) {
+      const uint32_t e = lst[jj];
+      const int sl = (int)((e >> 4) & 3u), t = (int)(e >> 6);
+      const GeomSlot& g = slot[sl];
+      const int32_t* cv = M.cell_vert + g.v0;
+      const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
+      const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
+      const float2* rp = M.rel_pos + 3 * g.v0;
+      const ff cf = ff_make(g.cf);
+      ff3 tA, tm;
+      ff ta;
+      tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), ff_make(g.w0),
+                     ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
+                     ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
+      const ff add[7] = {tA.x, tA.y, tA.z, ta, tm.x, tm.y, tm.z};
+      float2* pc = part + (size_t)sl * 7 * 32 + lane;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const ff r = ff_add(ff_make(pc[k * 32]), add[k]);
+        pc[k * 32] = make_float2(r.hi, r.lo);
+      }
+    }
+    sect += n_cut;
+    __syncwarp();
+    // per cell: kGeomRed lanes add the 32 partials (lane l takes l, l + kGeomRed, ...), then a tree
+    const int sl = lane / kGeomRed, l = lane % kGeomRed;
+    ff v[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const float2* pc = part + ((size_t)sl * 7 + k) * 32;
+      ff acc = ff_make(pc[l]);
+#pragma unroll
+      for (int j = 1; j < 32 / kGeomRed; ++j) acc = ff_add(acc, ff_make(pc[l + j * kGeomRed]));
+      v[k] = acc;
+    }
+#pragma unroll
+    for (int o = kGeomRed / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = ff_add(v[k], ff{__shfl_xor_sync(full, v[k].hi, o), __shfl_xor_sync(full, v[k].lo, o)});
+    const GeomSlot& g = slot[sl];
+    if (l == 0 && g.cell >= 0) {
+      const int32_t a = M.cell_vert[g.v0];
+      double area;
+      Vec3 nrm, xg;
+      geometry_outputs(v, M.vx[a], M.vy[a], M.vz[a], area, nrm, xg);
+      const int32_t cell = g.cell;
+      W.A_int[cell] = area;
+      W.n_int[3 * cell] = nrm.x;
+      W.n_int[3 * cell + 1] = nrm.y;
+      W.n_int[3 * cell + 2] = nrm.z;
+      W.x_gamma[3 * cell] = xg.x;
+      W.x_gamma[3 * cell + 1] = xg.y;
+      W.x_gamma[3 * cell + 2] = xg.z;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && sect) atomicAdd((unsigned long long*)&W.counters->tets_sectioned, (unsigned long long)sect);
 }
 
 
@@ -1357,6 +1441,12 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_select, kThreads, sel_smem);
     m->sel_grid = m->num_sms * std::max(1, std::min(bps, 4));
   }
+  if (!m->geom_grid) {  // the geometry grid: every resident warp of the device
+    int bps = 0;
+    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem_bytes(m->max_ct));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_geom, kThreads, geom_smem_bytes(m->max_ct));
+    m->geom_grid = m->num_sms * std::max(1, bps);
+  }
   {
     const double eps = opt.alpha_eps;
     int vmode = opt.vertex_mode;
@@ -1385,7 +1475,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     tm.stop(s);
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
-  // one branch per non-empty bin (root search and geometry); the branches join on s
+  // one branch per non-empty bin (root search); the branches join on s, then the geometry
   e = cudaEventRecord(m->ev_fork, s);
   for (int b = 0; b < kBins && e == cudaSuccess; ++b) {
     if (!m->bin_cells[b]) continue;
@@ -1399,7 +1489,12 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     if (e == cudaSuccess) e = cudaEventRecord(m->ev_join[b], sb);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_join[b], 0);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "root search / geometry kernels");
+  if (e != cudaSuccess) return cuda_fail(e, "root search kernels");
+  tm.start(KC_GEOM, s);
+  k_geom<<<m->geom_grid, kThreads, geom_smem_bytes(m->max_ct), s>>>(M, W, m->max_ct);
+  tm.stop(s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "interface geometry kernel");
   return VOF_OK;
 }
 
