@@ -95,19 +95,26 @@ struct Smem {
   float y[kRows];
 };
 
-// Stages weights (bf16) and biases into shared memory.
+// 16-byte asynchronous copy global -> shared (no register round trip; completes at cp_async_wait)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Starts the copy of the weights (bf16) and biases into shared memory; they are there after
+// cp_async_wait() and a barrier. 16-byte chunks: 6 per W1 row (48 bf16), 8 per W2 / W3 row
+// (64 bf16); row strides of 56 and 72 bf16 keep every chunk 16-byte aligned, and b1, b2, b3, w4
+// are contiguous in both layouts.
 __device__ void stage_weights(Smem& s, const WeightsBF16& w) {
-  // 16-byte chunks: 6 per W1 row (48 bf16), 8 per W2 / W3 row (64 bf16); row strides of 56 and
-  // 72 bf16 keep every chunk 16-byte aligned
-  for (int i = threadIdx.x; i < kH * 6; i += blockDim.x)
-    reinterpret_cast<uint4*>(s.W1 + (i / 6) * LDX)[i % 6] = reinterpret_cast<const uint4*>(&w.W1[i / 6][0])[i % 6];
+  for (int i = threadIdx.x; i < kH * 6; i += blockDim.x) cp_async16(s.W1 + (i / 6) * LDX + (i % 6) * 8, &w.W1[i / 6][(i % 6) * 8]);
   for (int i = threadIdx.x; i < kH * 8; i += blockDim.x) {
-    reinterpret_cast<uint4*>(s.W2 + (i / 8) * LDH)[i % 8] = reinterpret_cast<const uint4*>(&w.W2[i / 8][0])[i % 8];
-    reinterpret_cast<uint4*>(s.W3 + (i / 8) * LDH)[i % 8] = reinterpret_cast<const uint4*>(&w.W3[i / 8][0])[i % 8];
+    cp_async16(s.W2 + (i / 8) * LDH + (i % 8) * 8, &w.W2[i / 8][(i % 8) * 8]);
+    cp_async16(s.W3 + (i / 8) * LDH + (i % 8) * 8, &w.W3[i / 8][(i % 8) * 8]);
   }
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-    s.b1[i] = w.b1[i]; s.b2[i] = w.b2[i]; s.b3[i] = w.b3[i]; s.w4[i] = w.w4[i];
-  }
+  static_assert(offsetof(Smem, w4) == offsetof(Smem, b1) + 3 * kH * sizeof(float), "biases contiguous");
+  static_assert(offsetof(WeightsBF16, w4) == offsetof(WeightsBF16, b1) + 3 * kH * sizeof(float), "biases contiguous");
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) cp_async16(s.b1 + 4 * i, w.b1 + 4 * i);
   if (threadIdx.x == 0) s.b4 = w.b4;
 }
 
@@ -163,8 +170,32 @@ __device__ void warp_forward(Smem& s, int m0, float* Z1, float* Z2, float* Z3, f
   __syncwarp();
 }
 
-// Loads kRows feature rows (float32 [n][40], or zeros past n) into the bf16 X tile.
+// Loads kRows feature rows (float32 [n][40], or zeros past n) into the bf16 X tile: four values
+// per load when X is 16-byte aligned (rows are 160 bytes), all of a thread's loads issued before
+// its stores.
 __device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n, int rows = kRows) {
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+    constexpr int C4 = kInPad / 4, U = 8;
+    for (int i0 = threadIdx.x; i0 < rows * C4; i0 += U * blockDim.x) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * blockDim.x, r = i / C4, c4 = i % C4;
+        const int64_t gr = row0 + r;
+        v[u] = (i < rows * C4 && c4 < kIn / 4 && gr < n) ? __ldg(reinterpret_cast<const float4*>(X + gr * kIn) + c4)
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= rows * C4) break;
+        __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(s.X + (i / C4) * LDX + (i % C4) * 4);
+        d[0] = __floats2bfloat162_rn(v[u].x, v[u].y);
+        d[1] = __floats2bfloat162_rn(v[u].z, v[u].w);
+      }
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < rows * kInPad; i += blockDim.x) {
     const int r = i / kInPad, c = i % kInPad;
     const int64_t gr = row0 + r;
@@ -180,6 +211,7 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward(WeightsBF16* w, const
   const int warp = threadIdx.x >> 5;
   for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < n; row0 += (int64_t)gridDim.x * kRows) {
     load_x(s, X, row0, n);
+    cp_async_wait();
     __syncthreads();
     if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
     __syncthreads();
@@ -279,22 +311,95 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
 // clamped to [0, 1], or -1 where the cell has no features. Blocks of kFwdRows rows (two warps),
 // so that a few thousand interface cells still spread over most SMs.
 constexpr int kFwdRows = 32;
-__global__ void __launch_bounds__(kFwdRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
-                                                                    Workspace W) {
+constexpr int kFwdColGroups = 4;  // warps per 16-row tile, each computing 16 of the 64 columns
+constexpr int kFwdThreads = (kFwdRows / 16) * kFwdColGroups * 32;
+
+// Columns [16 cg, 16 cg + 16) of rows m0..m0+15 of X[.][0..K) times W^T (two n-tiles of 8).
+template <int K, int LDA, int LDB>
+__device__ __forceinline__ void warp_gemm_cols(const __nv_bfloat16* X, const __nv_bfloat16* W, int m0, int cg,
+                                               float (&acc)[2][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 2 * q);
+    a[1] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 2 * q);
+    a[2] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 8 + 2 * q);
+    a[3] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 8 + 2 * q);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const __nv_bfloat16* w = W + ((2 * cg + j) * 8 + g) * LDB + k0 + 2 * q;
+      mma16816(acc[j], a, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+  }
+}
+
+// hidden layer: bias + GELU of this warp's 16 columns into H (bf16)
+__device__ __forceinline__ void hidden_cols(const float (&acc)[2][4], const float* b, __nv_bfloat16* H, int m0, int cg) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = (2 * cg + j) * 8 + 2 * q + (i & 1);
+      H[r * LDH + c] = __float2bfloat16_rn(gelu(acc[j][i] + b[c]));
+    }
+}
+
+// forward over the interface list (n read on the device); writes the guess of interface cell i,
+// clamped to [0, 1], or -1 where the cell has no features. A block takes kFwdRows rows at a time;
+// each 16-row tile is shared by kFwdColGroups warps that split the 64 hidden columns (block
+// barriers between the layers), so that the GELUs, the bulk of the work, spread over four times
+// as many warps. The output sums the column groups' partial dot products in a fixed order.
+__global__ void __launch_bounds__(kFwdThreads) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
+                                                                  Workspace W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  float* yp = reinterpret_cast<float*>(smem_raw + sizeof(Smem));  // [kFwdColGroups][kFwdRows]
   const int64_t n = W.counters->n_iface;
   if ((int64_t)blockIdx.x * kFwdRows >= n) return;
   stage_weights(s, *w);
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int m0 = (warp / kFwdColGroups) * 16, cg = warp % kFwdColGroups;
   for (int64_t row0 = (int64_t)blockIdx.x * kFwdRows; row0 < n; row0 += (int64_t)gridDim.x * kFwdRows) {
     load_x(s, X, row0, n, kFwdRows);
+    cp_async_wait();
     __syncthreads();
-    warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
+    float acc[2][4];
+    warp_gemm_cols<kInPad, LDX, LDX>(s.X, s.W1, m0, cg, acc);
+    hidden_cols(acc, s.b1, s.H1, m0, cg);
+    __syncthreads();
+    warp_gemm_cols<kH, LDH, LDH>(s.H1, s.W2, m0, cg, acc);
+    hidden_cols(acc, s.b2, s.H2, m0, cg);
+    __syncthreads();
+    warp_gemm_cols<kH, LDH, LDH>(s.H2, s.W3, m0, cg, acc);
+    float part[2] = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = (2 * cg + j) * 8 + 2 * q + (i & 1);
+        part[i >> 1] = fmaf(gelu(acc[j][i] + s.b3[c]), s.w4[c], part[i >> 1]);
+      }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 1);
+      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 2);
+    }
+    if (q == 0) {
+      yp[cg * kFwdRows + m0 + g] = part[0];
+      yp[cg * kFwdRows + m0 + g + 8] = part[1];
+    }
     __syncthreads();
     for (int r = threadIdx.x; r < kFwdRows; r += blockDim.x) {
       const int64_t i = row0 + r;
-      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(s.y[r], 0.f), 1.f) : -1.f;
+      float y = yp[r];
+#pragma unroll
+      for (int k = 1; k < kFwdColGroups; ++k) y += yp[k * kFwdRows + r];
+      y += s.b4;
+      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(y, 0.f), 1.f) : -1.f;
     }
     __syncthreads();
   }
@@ -316,6 +421,7 @@ __global__ void __launch_bounds__(256) k_mlp_train_tile(WeightsBF16* w, const fl
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
   stage_weights(s.f, *w);
   load_x(s.f, X, row0, n);
+  cp_async_wait();
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   if (warp < kWarps) warp_forward(s.f, warp * 16, s.Z1, s.Z2, s.Z3, s.H3);
@@ -469,10 +575,12 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
+    cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float)));
     attr = true;
   }
-  k_mlp_forward_iface<<<m->num_sms * 3, kFwdRows * 2, sizeof(Smem), s>>>(mlp->w, X, ok, m->ws);
+  k_mlp_forward_iface<<<m->num_sms * 2, kFwdThreads, sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float), s>>>(
+      mlp->w, X, ok, m->ws);
   return cudaGetLastError();
 }
 

@@ -224,7 +224,19 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
               const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
               double sum = 0;
               if (vertex_mode == 0) {
-                for (int64_t k = k0; k < k1; ++k) sum = fma(M.vert_w[k], alpha[M.vert_cell[k]], sum);
+                // four cells' loads in flight at a time; the sum keeps the cell order
+                int64_t k = k0;
+                for (; k + 4 <= k1; k += 4) {
+                  const int32_t ca = M.vert_cell[k], cb = M.vert_cell[k + 1], cc = M.vert_cell[k + 2],
+                                cd = M.vert_cell[k + 3];
+                  const double wa = M.vert_w[k], wb = M.vert_w[k + 1], wc = M.vert_w[k + 2], wd = M.vert_w[k + 3];
+                  const double aa = alpha[ca], ab = alpha[cb], ac = alpha[cc], ad = alpha[cd];
+                  sum = fma(wa, aa, sum);
+                  sum = fma(wb, ab, sum);
+                  sum = fma(wc, ac, sum);
+                  sum = fma(wd, ad, sum);
+                }
+                for (; k < k1; ++k) sum = fma(M.vert_w[k], alpha[M.vert_cell[k]], sum);
               } else {
                 for (int64_t k = k0; k < k1; ++k) sum += alpha[M.vert_cell[k]];
                 sum /= (double)(k1 - k0);
