@@ -59,6 +59,8 @@ def _lib():
                                            ctypes.c_void_p, ctypes.c_void_p]
         _LIB.orc_reconstruct.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 7)
+        _LIB.orc_reconstruct_m.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 7)
         _LIB.orc_phase_change.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 6
                                           + [ctypes.c_int] + [ctypes.c_void_p] * 15)
         _LIB.orc_vertex_field.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
@@ -113,17 +115,19 @@ class Oracle:
         _lib().orc_liquid_volume(self.ref, int(cell), _p(phi), float(c), _p(x), _p(out))
         return dict(VL=out[0], area=out[1], vec_area=out[2:5].copy(), centroid=out[5:8].copy(), nloops=int(out[8]))
 
-    def reconstruct(self, alpha, phi, eps=1e-12, tol=1e-12, max_iter=100, cells=None) -> dict:
-        """R0 + R3 (+ geometry at the root). Arrays over all cells; untouched cells hold nan/0."""
+    def reconstruct(self, alpha, phi, eps=1e-12, tol=1e-12, max_iter=100, cells=None, method="bisect") -> dict:
+        """R0 + R3 (+ geometry at the root). Arrays over all cells; untouched cells hold nan/0.
+        method "bisect": bisection on V_L(c)/V - alpha; "cubic": bisection over the sorted vertex
+        values, then the interval's cubic (interpolated from four evaluations) solved on its own."""
         nc = self.c.n_cells
         a = np.ascontiguousarray(alpha, np.float64)
         r = dict(iso=np.full(nc, np.nan), status=np.zeros(nc, np.int32), evals=np.zeros(nc, np.int32),
                  A_int=np.zeros(nc), n_int=np.zeros((nc, 3)), x_gamma=np.zeros((nc, 3)),
                  nloops=np.zeros(nc, np.int32))
         cl = None if cells is None else np.ascontiguousarray(cells, np.int64)
-        _lib().orc_reconstruct(self.ref, _p(a), _p(phi), _p(self.geometry()["cell_vol"]), eps, tol, max_iter,
-                               _p(cl), 0 if cl is None else len(cl),
-                               *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
+        _lib().orc_reconstruct_m(self.ref, _p(a), _p(phi), _p(self.geometry()["cell_vol"]), eps, tol, max_iter,
+                                 _p(cl), 0 if cl is None else len(cl), {"bisect": 0, "cubic": 1}[method],
+                                 *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
         return r
 
     def phase_change(self, alpha, recon: dict, T, T_bnd, props: dict, eps=1e-12, xf_mode=XF_RECON) -> dict:

@@ -13,7 +13,8 @@
 //       (faces fanned from their lowest-id vertex, the cell fanned from its lowest-id vertex),
 //       phi linear on each; the wet part of each tetrahedron by clipping with the plane phi = c
 //       through the cuts of Eq. edge_intersection
-//   R3  isovalue by bisection on V_L(c)/V - alpha
+//   R3  isovalue by bisection on V_L(c)/V - alpha; or by the interval cubic (bisection over the
+//       sorted vertex values, then the cubic V_L has between two of them, solved on its own)
 //   R4  crossing point x_f on faces with (alpha_P - 1/2)(alpha_Q - 1/2) < 0
 //   R5  per-side gradients: own phase from the modified LSQ gradient, other phase from one upwind
 //       sweep over the neighbours on that side
@@ -187,10 +188,13 @@ void clip_tet(const VPt* T, double c, const V3& x0, IsoGeom& g, V3& moment) {
     int v[3] = {F[f][0], F[f][1], F[f][2]};
     if (s < 0) std::swap(v[1], v[2]);
     std::vector<V3> W;
+    // wet corners are those strictly above c: {phi > c} has the volume of {phi >= c}, and a corner
+    // at exactly c then enters the wet polygons and the section as the cut of its edges to wet
+    // corners (lambda = 1), so the wet surface stays closed when c equals a vertex value
     for (int k = 0; k < 3; ++k) {
       const int i = v[k], j = v[(k + 1) % 3];
-      if (T[i].phi >= c) W.push_back(T[i].x);
-      if ((T[i].phi - c) * (T[j].phi - c) < 0) {
+      if (T[i].phi > c) W.push_back(T[i].x);
+      if ((T[i].phi > c) != (T[j].phi > c)) {
         W.push_back(cut(i, j));
         const std::pair<int, int> e = {std::min(i, j), std::max(i, j)};
         if (std::find(sec_edge.begin(), sec_edge.end(), e) == sec_edge.end()) {
@@ -292,6 +296,54 @@ RootResult bisect(const OrcMesh& m, int64_t cell, const double* phi, double alph
   return r;
 }
 
+// R3, interval cubic (the NEXT row N1 of the hot-path scope): between two consecutive distinct
+// vertex values of the cell no tetrahedron changes its number of wet corners, so V_L(c) is one
+// cubic polynomial there (R2 is exact for a linear field on each tetrahedron). Steps: sort the
+// cell's distinct vertex values u_0 < ... < u_m; bisect over that list (one evaluation per probe)
+// for the pair u_k < u_k+1 with f(u_k) > 0 >= f(u_k+1), where f = V_L/V - alpha, f(u_0) = 1 - alpha
+// and f(u_m) = -alpha; interpolate the cubic through f at u_k, u_k + h/3, u_k + 2h/3 and u_k+1
+// (h = u_k+1 - u_k, Newton's divided differences on those four points); solve it on the interval
+// by bisection on the polynomial, without further cut-volume evaluations; one last evaluation at
+// the root checks |f| <= tol.
+RootResult interval_cubic(const OrcMesh& m, int64_t cell, const double* phi, double alpha, double V, double tol,
+                          int max_iter) {
+  const std::vector<int32_t> vs = cell_vertices(m, cell);
+  std::vector<double> u;
+  for (int32_t v : vs) u.push_back(phi[v]);
+  std::sort(u.begin(), u.end());
+  u.erase(std::unique(u.begin(), u.end()), u.end());
+  RootResult r;
+  if (u.back() - u.front() < 1e-14) { r.c = u.front(); r.status = ST_DEGENERATE; return r; }
+  const V3 x0 = mean_point(m, vs);
+  auto f = [&](double c) {
+    r.evals++;
+    return liquid_volume(m, cell, phi, c, &x0).VL / V - alpha;
+  };
+  size_t lo = 0, hi = u.size() - 1;
+  double f_lo = 1 - alpha, f_hi = -alpha;
+  while (hi - lo > 1) {
+    const size_t mid = (lo + hi) / 2;
+    const double fm = f(u[mid]);
+    if (fm == 0) { r.c = u[mid]; return r; }
+    if (fm > 0) { lo = mid; f_lo = fm; } else { hi = mid; f_hi = fm; }
+  }
+  const double x[4] = {u[lo], u[lo] + (u[hi] - u[lo]) / 3, u[lo] + 2 * (u[hi] - u[lo]) / 3, u[hi]};
+  double d[4] = {f_lo, f(x[1]), f(x[2]), f_hi};
+  for (int j = 1; j < 4; ++j)  // divided differences, in place
+    for (int i = 3; i >= j; --i) d[i] = (d[i] - d[i - 1]) / (x[i] - x[i - j]);
+  auto p = [&](double c) { return d[0] + (c - x[0]) * (d[1] + (c - x[1]) * (d[2] + (c - x[2]) * d[3])); };
+  double a = x[0], b = x[3];  // p(a) > 0 >= p(b)
+  for (int it = 0; it < max_iter; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    if (p(mid) > 0) a = mid; else b = mid;
+  }
+  const double fa = std::fabs(p(a)), fb = std::fabs(p(b));
+  r.c = fa <= fb ? a : b;
+  if (std::fabs(f(r.c)) > tol) r.status = ST_NOT_CONVERGED;
+  return r;
+}
+
 double pairwise_sum(std::vector<double> a) {
   if (a.empty()) return 0.0;
   size_t n = 1;
@@ -344,9 +396,10 @@ void orc_liquid_volume(const OrcMesh* m, int64_t cell, const double* phi, double
 // R0 + R3 + geometry at the root for every cell with eps < alpha < 1 - eps (other cells get
 // iso = nan, status 0, evals 0, zero geometry). Arrays are [n_cells] or [3 n_cells].
 // `cells`, when non-null, restricts the work to the listed cells (n_list of them).
-void orc_reconstruct(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
-                     double tol, int max_iter, const int64_t* cells, int64_t n_list, double* iso, int32_t* status,
-                     int32_t* evals, double* A_int, double* n_int, double* x_gamma, int32_t* nloops) {
+// method 0: bisection (R3); method 1: interval cubic (R3, NEXT row N1).
+void orc_reconstruct_m(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
+                       double tol, int max_iter, const int64_t* cells, int64_t n_list, int method, double* iso,
+                       int32_t* status, int32_t* evals, double* A_int, double* n_int, double* x_gamma, int32_t* nloops) {
   const OrcMesh& m = *mp;
   std::vector<int64_t> todo;
   if (cells) {
@@ -358,7 +411,8 @@ void orc_reconstruct(const OrcMesh* mp, const double* alpha, const double* phi, 
 #pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < (int64_t)todo.size(); ++t) {
     const int64_t c = todo[t];
-    const RootResult r = bisect(m, c, phi, alpha[c], cell_vol[c], tol, max_iter);
+    const RootResult r = method == 1 ? interval_cubic(m, c, phi, alpha[c], cell_vol[c], tol, max_iter)
+                                     : bisect(m, c, phi, alpha[c], cell_vol[c], tol, max_iter);
     iso[c] = r.c;
     status[c] = r.status;
     evals[c] = r.evals;
@@ -372,6 +426,13 @@ void orc_reconstruct(const OrcMesh* mp, const double* alpha, const double* phi, 
     }
     nloops[c] = 0;
   }
+}
+
+void orc_reconstruct(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
+                     double tol, int max_iter, const int64_t* cells, int64_t n_list, double* iso, int32_t* status,
+                     int32_t* evals, double* A_int, double* n_int, double* x_gamma, int32_t* nloops) {
+  orc_reconstruct_m(mp, alpha, phi, cell_vol, eps, tol, max_iter, cells, n_list, 0, iso, status, evals, A_int, n_int,
+                    x_gamma, nloops);
 }
 
 // R4: crossing point of face f (owner o, neighbour n); returns t along x_o -> x_n, and the cell

@@ -206,6 +206,73 @@ def test_P4_bisection_matches_closed_form_root():
         assert abs(r["iso"][c] - _tet_root(f, a[c])) <= 1e-10 * (f.max() - f.min())
 
 
+def test_P3_exact_at_vertex_values():
+    """P3: at c equal to a vertex value the cut volume of a tetrahedron equals the closed form
+    sum_i (f_i - c)_+^3 / prod_j (f_i - f_j) (no jump there), and on a Voronoi cell it equals the
+    mean of its values just below and just above."""
+    m = synth.tet_box(2)
+    O = oracle.Oracle(m)
+    phi = np.random.default_rng(21).uniform(-1, 1, m.n_verts)
+    V = O.geometry()["cell_vol"]
+    for c in range(m.n_cells):
+        f = phi[cell_vertex_ids(m, c)]
+        den = [np.prod([f[i] - f[j] for j in range(4) if j != i]) for i in range(4)]
+        for x in f:
+            exact = sum(max(f[i] - x, 0.0) ** 3 / den[i] for i in range(4))
+            assert O.liquid_volume(c, phi, x)["VL"] / V[c] == pytest.approx(exact, abs=1e-13)
+    m = synth.voronoi_bcc(5, seed=11)
+    reg = dict(type="spheres", spheres=[(0.5, 0.5, 0.5, 0.3)])
+    O, a, phi, cells = _idw_cells(m, reg, n=10, seed=2)
+    V = O.geometry()["cell_vol"]
+    for c in cells:
+        f = np.unique(phi[cell_vertex_ids(m, c)])
+        e = 1e-9 * (f[-1] - f[0])
+        for x in f[1:-1]:
+            mid = 0.5 * (O.liquid_volume(c, phi, x - e)["VL"] + O.liquid_volume(c, phi, x + e)["VL"])
+            assert abs(O.liquid_volume(c, phi, x)["VL"] - mid) <= 1e-8 * V[c]
+
+
+def test_P11_interval_cubic_matches_closed_form_root():
+    """P11 (NEXT row N1, interval cubic): on tetrahedra with a linear field the interval-cubic root
+    equals the closed-form root of the tetrahedron's cut-volume cubic, with |V_L(c)/V - alpha| <=
+    1e-12, after at most one bisection step over the four vertex values and two interior samples
+    (plus the final check)."""
+    m = synth.tet_box(2)
+    O = oracle.Oracle(m)
+    rng = np.random.default_rng(18)
+    phi = rng.uniform(-1, 1, m.n_verts)
+    a = rng.uniform(0.01, 0.99, m.n_cells)
+    r = O.reconstruct(a, phi, method="cubic")
+    V = O.geometry()["cell_vol"]
+    for c in range(m.n_cells):
+        f = phi[cell_vertex_ids(m, c)]
+        assert r["status"][c] == 0
+        assert abs(O.liquid_volume(c, phi, r["iso"][c])["VL"] / V[c] - a[c]) <= 1e-12
+        assert abs(r["iso"][c] - _tet_root(f, a[c])) <= 1e-10 * (f.max() - f.min())
+        assert r["evals"][c] <= 2 + 2 + 1
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "hex", "tet"])
+def test_P11_interval_cubic_residual_and_evaluations(kind):
+    """P11: on every interface cell of a curved interface the interval-cubic root meets
+    |V_L(c)/V - alpha| <= 1e-12, agrees with the bisection root (the root is unique where the
+    interface has area), and takes ceil(log2(distinct vertex values - 1)) + 3 evaluations at most."""
+    m = MESHES[kind]()
+    reg = dict(type="spheres", spheres=[(0.47, 0.52, 0.5, 0.33)])
+    O, a, phi, cells = _idw_cells(m, reg, n=60, seed=3)
+    V = O.geometry()["cell_vol"]
+    rc = O.reconstruct(a, phi, cells=cells, method="cubic")
+    rb = O.reconstruct(a, phi, cells=cells)
+    for c in cells:
+        u = np.unique(phi[cell_vertex_ids(m, c)])
+        assert rc["status"][c] == 0
+        assert abs(O.liquid_volume(c, phi, rc["iso"][c])["VL"] / V[c] - a[c]) <= 1e-12
+        assert rc["evals"][c] <= int(np.ceil(np.log2(max(len(u) - 1, 1)))) + 3
+        if rc["A_int"][c] > 1e-6 * V[c] ** (2 / 3):
+            assert abs(rc["iso"][c] - rb["iso"][c]) <= 1e-8 * (u[-1] - u[0])
+        assert rc["evals"][c] < rb["evals"][c]
+
+
 def test_P4_residual_voronoi():
     """P4: every converged Voronoi cell meets |V_L(c)/V - alpha| <= 1e-12 in a few tens of
     evaluations."""
