@@ -128,10 +128,12 @@ def run_ours(args, rank, world, dev):
         btot = torch.empty((B.n, 2), dtype=torch.float64, device=dev) if batch else None
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
         learned_ok = args.root in ("auto", "learned") and vof.load_default_mlp(M)
-        modes = (["bisect"] if args.root != "learned" else []) + (["learned"] if learned_ok else [])
+        modes = ((["bisect"] if args.root in ("auto", "bisect") else []) + (["learned"] if learned_ok else [])
+                 + (["cubic"] if args.root in ("auto", "cubic") else []))
         tuned = {}
         for mode in modes:
-            opt = vof.default_options(root_mode=vof.ROOT_LEARNED if mode == "learned" else vof.ROOT_BISECT)
+            opt = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
+                                                 "cubic": vof.ROOT_CUBIC}[mode])
             if args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
                 tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
                 M.set_group_sizes(tuned[mode])
@@ -252,7 +254,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="film250k", choices=list(WORKLOADS))
-    ap.add_argument("--root", default="auto", choices=["auto", "bisect", "learned"])
+    ap.add_argument("--root", default="auto", choices=["auto", "bisect", "learned", "cubic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--group-sizes", default="",
                     help="lanes per cell of the five tetrahedron-count bins, comma-separated (skips the autotuner)")
@@ -297,7 +299,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     M, fields, desc, res, e2e_s, info = run_ours(args, rank, world, dev)
-    best = "learned" if "learned" in res else "bisect"
+    best = "learned" if "learned" in res else ("bisect" if "bisect" in res else "cubic")
     r = res[best]
     n_iface = r["counts"]["n_iface"]
     ms = r["ms"]

@@ -72,6 +72,12 @@ typedef enum {
 /* Root-search modes. */
 #define VOF_ROOT_BISECT 0  /* plain FP64 bisection on [phi_min, phi_max] */
 #define VOF_ROOT_LEARNED 1 /* BF16 MLP guess, <= max_secant FP64 secant steps, bracketed bisection fallback */
+/* Interval cubic: V_L(c) is one cubic between consecutive vertex values of a cell (Sec. 2.1 with
+ * the cell split into tetrahedra of its own vertices); an FP32 refinement picks the interval, one
+ * FP64 pass sums the straddling tetrahedra's pieces into that cubic, and its root follows from
+ * the polynomial alone (bisection fallback, counted). The paper has no such mode: it is the
+ * scope's next step for the root search. */
+#define VOF_ROOT_CUBIC 2
 
 typedef struct vof_mesh vof_mesh; /* opaque, library-owned */
 
@@ -99,7 +105,7 @@ typedef struct {
   double alpha_eps;  /* interface cells: alpha_eps < alpha < 1 - alpha_eps (default 1e-12) */
   double tol_alpha;  /* root accepted when |V_L(c)/V - alpha| <= tol_alpha (default 1e-12) */
   int max_bisect;    /* bisection iteration cap (default 100) */
-  int root_mode;     /* VOF_ROOT_BISECT or VOF_ROOT_LEARNED */
+  int root_mode;     /* VOF_ROOT_BISECT, VOF_ROOT_LEARNED or VOF_ROOT_CUBIC */
   int max_secant;    /* secant steps after the learned guess (default 2) */
   int xf_mode;       /* VOF_XF_* (default VOF_XF_RECON) */
   int vertex_mode;   /* 0 inverse distance to cell centroids (default), 1 plain average */

@@ -18,7 +18,7 @@ _LIB = None
 VOF_ST_DEGENERATE, VOF_ST_NOT_CONVERGED, VOF_ST_FALLBACK = 1, 2, 4
 VOF_ST_SINGULAR_LSQ, VOF_ST_NO_SIDE, VOF_ST_MLP_SKIPPED = 8, 16, 32
 XF_RECON, XF_LINEAR, XF_AS_PRINTED = 0, 1, 2
-ROOT_BISECT, ROOT_LEARNED = 0, 1
+ROOT_BISECT, ROOT_LEARNED, ROOT_CUBIC = 0, 1, 2
 
 FIELDS = {
     "iface_idx": (0, np.int32, 1), "phi_v": (1, np.float64, 1), "iso": (2, np.float64, 1),

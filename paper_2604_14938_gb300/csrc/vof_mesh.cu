@@ -481,7 +481,7 @@ vof_status vof_mesh_bins(const vof_mesh* m, int64_t* cells5) {
 static vof_status check_opt(const vof_options* o) {
   if (!o) { set_error("null options"); return VOF_EINVAL; }
   if (!(o->alpha_eps >= 0 && o->alpha_eps < 0.5) || !(o->tol_alpha > 0) || o->max_bisect < 1 || o->max_bisect > 1000 ||
-      (o->root_mode != VOF_ROOT_BISECT && o->root_mode != VOF_ROOT_LEARNED) || o->max_secant < 0 || o->max_secant > 8 ||
+      (o->root_mode != VOF_ROOT_BISECT && o->root_mode != VOF_ROOT_LEARNED && o->root_mode != VOF_ROOT_CUBIC) || o->max_secant < 0 || o->max_secant > 8 ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {

@@ -601,7 +601,7 @@ __device__ __forceinline__ void geometry_outputs(const ff* v, double ax, double 
 
 template <int G>
 __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
-                                                   int max_ct, int max_cv, int learned, int bin) {
+                                                   int max_ct, int max_cv, int mode, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
@@ -716,14 +716,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         if (kf <= ktol) done = true;
         return f;
       };
-      if (learned) {
+      if (mode != VOF_ROOT_BISECT) {
         // Learned path: MLP guess u0 of the normalised position u = (c - lo)/(hi - lo) (a cell
         // without features, more than 32 vertices, starts from 1 - alpha instead and is counted
         // as skipped); FP32 refinement of u (regula falsi with the Illinois modification, on FP32
         // tetrahedron rows in normalised values); then the FP64 phase: evaluations at the
         // refined guess and at a second point next to it, at most max_secant secant steps, and
-        // bisection inside the bracket found so far as the counted fallback.
-        float u0 = W.mlp_out[i];
+        // bisection inside the bracket found so far as the counted fallback. The interval-cubic
+        // mode starts the same FP32 refinement from 1 - alpha and replaces the FP64 phase.
+        float u0 = mode == VOF_ROOT_LEARNED ? W.mlp_out[i] : 1.0f - (float)a;
         if (!(u0 >= 0.0f)) {
           status |= VOF_ST_MLP_SKIPPED;
           u0 = 1.0f - (float)a;
@@ -791,7 +792,98 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
           if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
           ubest = uc;
         }
-        {
+        if (mode == VOF_ROOT_CUBIC) {
+          // Interval cubic (the next row N1 of the scope): between two consecutive vertex values
+          // of the cell no tetrahedron changes its number of wet corners, so V_L is one cubic
+          // there. The FP32-refined point picks the interval [va, vb]; one FP64 pass over the rows
+          // straddling it sums their pieces as a cubic in y = c - cm (cm the midpoint); when the
+          // target lies outside the cubic's values at the ends, the neighbouring interval is
+          // taken instead; then safeguarded Newton steps on the polynomial alone give the root.
+          __syncwarp(mask);
+          double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
+          if (!(okey(c1) < okey(hi))) c1 = okey_inv(okey(hi) - 1);  // an interval above c1 exists
+          // largest vertex value <= c and smallest above it, by integer keys
+          auto vertex_interval = [&](double c, double& va, double& vb) {
+            const uint64_t kc = okey(c);
+            uint64_t ka = 0ull, kb = ~0ull;
+            for (int j = lane; j < nv; j += G) {
+              const uint64_t k = okey(W.phi_v[cv[j]]);
+              if (k <= kc) ka = max(ka, k); else kb = min(kb, k);
+            }
+            va = okey_inv(group_umax<G>(ka, mask));
+            vb = okey_inv(group_umin<G>(kb, mask));
+          };
+          double va, vb, cm = 0, P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+          vertex_interval(c1, va, vb);
+          const double tgt = a * M.cell_vol[cell];
+          bool bracketed = false;
+          for (int mv = 0; mv < 8; ++mv) {
+            prepare_window(va, vb);  // rows straddling [va, vb]; wet_sum: tetrahedra wet over it
+            prepared = true;
+            cm = 0.5 * (va + vb);
+            const uint64_t kb = okey(vb);
+            double q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+            for (int k = lane; k < n_rows; k += G) {
+              const TetRow& r = rows[k];
+              // the piece on (va, vb]: its wet corners are those at or above vb
+              const int nk = (okey(r.s0) >= kb) + (okey(r.s1) >= kb) + (okey(r.s2) >= kb) + (okey(r.s3) >= kb);
+              const double ref = nk == 1 ? r.s0 : (nk == 2 ? r.s1 : r.s3);
+              const double A = nk == 2 ? r.a2 : (nk >= 3 ? r.v : 0.0);
+              const double B = nk == 2 ? r.b2 : 0.0;
+              const double C = nk == 2 ? r.c2 : 0.0;
+              const double D = nk == 1 ? r.d1 : (nk == 2 ? r.d2 : (nk == 3 ? r.d3 : 0.0));
+              // A + B x + C x^2 + D x^3 with x = (ref - cm) - y, expanded in y
+              const double dl = ref - cm;
+              q0 += fma(fma(fma(D, dl, C), dl, B), dl, A);
+              q1 -= fma(fma(3.0 * D, dl, 2.0 * C), dl, B);
+              q2 += fma(3.0 * D, dl, C);
+              q3 -= D;
+            }
+            P0 = group_sum<G>(q0, mask) + wet_sum;
+            P1 = group_sum<G>(q1, mask);
+            P2 = group_sum<G>(q2, mask);
+            P3 = group_sum<G>(q3, mask);
+            ++evals;
+            tev += n_rows;
+            const double ya = va - cm, yb = vb - cm;
+            const double ga = fma(fma(fma(P3, ya, P2), ya, P1), ya, P0) - tgt;
+            const double gb = fma(fma(fma(P3, yb, P2), yb, P1), yb, P0) - tgt;
+            if (gb > 0.0 && okey(vb) < okey(hi)) {  // the root lies above vb
+              vertex_interval(vb, va, vb);
+            } else if (ga < 0.0 && okey(va) > okey(lo)) {  // below va
+              vertex_interval(okey_inv(okey(va) - 1), va, vb);
+            } else {
+              bracketed = true;
+              break;
+            }
+          }
+          if (bracketed) {
+            double ya = va - cm, yb = vb - cm;  // g(ya) >= 0 >= g(yb), g decreasing
+            double y = dmin(dmax(c1 - cm, ya), yb);
+            for (int it = 0; it < 12; ++it) {
+              const double g = fma(fma(fma(P3, y, P2), y, P1), y, P0) - tgt;
+              const uint64_t kf = mag(g * invV);
+              if (kf < kbest) { kbest = kf; c_best = cm + y; }
+              if (g == 0.0) break;
+              if (g > 0.0) ya = y; else yb = y;
+              const double dp = fma(fma(3.0 * P3, y, 2.0 * P2), y, P1);  // dg/dy <= 0
+              double yn = 0.5 * (ya + yb);
+              if (dp < 0.0) {
+                double r = (double)(1.0f / (float)dp);
+                r = fma(r, fma(-dp, r, 1.0), r);
+                const double yt = fma(-g, r, y);
+                if (inside(yt, ya, yb)) yn = yt;
+              }
+              if (yn == y || !inside(yn, ya, yb)) break;
+              y = yn;
+            }
+          }
+          done = kbest <= ktol;
+          if (!done) {
+            status |= VOF_ST_FALLBACK;
+            prepare64();  // bisection over [lo, hi] on every row
+          }
+        } else {
           __syncwarp(mask);
           // FP64 phase on the rows of a window of 2e-3 of the range around the refined point
           // (a thousand times the FP32 refinement's accuracy); every FP64 point stays inside it
@@ -1404,7 +1496,7 @@ int pick_group(const vof_mesh* m, const vof_options& o, int bin) {
 }
 
 template <int G>
-cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                           int bin) {
   const int max_ct = m->bin_max_ct[bin];
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
@@ -1425,14 +1517,14 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   if (bps < 1) bps = 1;
   const int64_t need = (m->bin_cells[bin] + (threads / G) - 1) / (threads / G);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
-  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, learned, bin);
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, mode, bin);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s);  // vof_mlp.cu
-cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                             int bin, int G);
 
 vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s,
@@ -1495,7 +1587,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     e = cudaStreamWaitEvent(sb, m->ev_fork, 0);
     if (e != cudaSuccess) break;
     tm.start(KC_ROOT, sb);
-    e = launch_root_bin(m, d_alpha, opt, sb, learned, b, pick_group(m, opt, b));
+    e = launch_root_bin(m, d_alpha, opt, sb, opt.root_mode, b, pick_group(m, opt, b));
     tm.stop(sb);
     if (e != cudaSuccess) break;
     if (e == cudaSuccess) e = cudaEventRecord(m->ev_join[b], sb);
@@ -1510,15 +1602,15 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   return VOF_OK;
 }
 
-cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int learned,
+cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                             int bin, int G) {
   switch (G) {
-    case 1: return launch_root_g<1>(m, alpha, opt, s, learned, bin);
-    case 2: return launch_root_g<2>(m, alpha, opt, s, learned, bin);
-    case 4: return launch_root_g<4>(m, alpha, opt, s, learned, bin);
-    case 8: return launch_root_g<8>(m, alpha, opt, s, learned, bin);
-    case 16: return launch_root_g<16>(m, alpha, opt, s, learned, bin);
-    default: return launch_root_g<32>(m, alpha, opt, s, learned, bin);
+    case 1: return launch_root_g<1>(m, alpha, opt, s, mode, bin);
+    case 2: return launch_root_g<2>(m, alpha, opt, s, mode, bin);
+    case 4: return launch_root_g<4>(m, alpha, opt, s, mode, bin);
+    case 8: return launch_root_g<8>(m, alpha, opt, s, mode, bin);
+    case 16: return launch_root_g<16>(m, alpha, opt, s, mode, bin);
+    default: return launch_root_g<32>(m, alpha, opt, s, mode, bin);
   }
 }
 
