@@ -134,6 +134,8 @@ def run_ours(args, rank, world, dev):
         for mode in modes:
             opt = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
                                                  "cubic": vof.ROOT_CUBIC}[mode])
+            if mode == "cubic":  # from 1 - alpha: on these workloads the guess costs more than it saves
+                M.set_mlp(None)
             if args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
                 tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
                 M.set_group_sizes(tuned[mode])
@@ -182,8 +184,14 @@ def run_ours(args, rank, world, dev):
             M.timing_enable(False)
             kcnt = M.counts(stream=stream)
             results[mode] = dict(ms=ms, units=units, counts=cnt, kcounts=kcnt, ktime=kt, clocks=clk.summary())
-        # end to end: host buffers through vof_step_host, copies inside the timed region
-        opt_best = vof.default_options(root_mode=vof.ROOT_LEARNED if "learned" in results else vof.ROOT_BISECT)
+        # end to end: host buffers through vof_step_host, copies inside the timed region, in the
+        # headline mode with its own tuned lanes per cell
+        best_mode = "learned" if "learned" in results else ("bisect" if "bisect" in results else "cubic")
+        if best_mode == "learned":
+            vof.load_default_mlp(M)
+        M.set_group_sizes(tuned[best_mode])
+        opt_best = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
+                                                  "cubic": vof.ROOT_CUBIC}[best_mode])
         pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
         ha, hT = pin(a), pin(T)
         hTb = None if pipe else pin(Tb)

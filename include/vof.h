@@ -73,7 +73,8 @@ typedef enum {
 #define VOF_ROOT_BISECT 0  /* plain FP64 bisection on [phi_min, phi_max] */
 #define VOF_ROOT_LEARNED 1 /* BF16 MLP guess, <= max_secant FP64 secant steps, bracketed bisection fallback */
 /* Interval cubic: V_L(c) is one cubic between consecutive vertex values of a cell (Sec. 2.1 with
- * the cell split into tetrahedra of its own vertices); an FP32 refinement picks the interval, one
+ * the cell split into tetrahedra of its own vertices); an FP32 refinement (from the MLP guess when
+ * the mesh has an MLP, else from 1 - alpha) picks the interval, one
  * FP64 pass sums the straddling tetrahedra's pieces into that cubic, and its root follows from
  * the polynomial alone (bisection fallback, counted). The paper has no such mode: it is the
  * scope's next step for the root search. */

@@ -601,7 +601,7 @@ __device__ __forceinline__ void geometry_outputs(const ff* v, double ax, double 
 
 template <int G>
 __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
-                                                   int max_ct, int max_cv, int mode, int bin) {
+                                                   int max_ct, int max_cv, int mode, int use_mlp, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
@@ -723,8 +723,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         // tetrahedron rows in normalised values); then the FP64 phase: evaluations at the
         // refined guess and at a second point next to it, at most max_secant secant steps, and
         // bisection inside the bracket found so far as the counted fallback. The interval-cubic
-        // mode starts the same FP32 refinement from 1 - alpha and replaces the FP64 phase.
-        float u0 = mode == VOF_ROOT_LEARNED ? W.mlp_out[i] : 1.0f - (float)a;
+        // mode runs the same FP32 refinement (from the MLP guess when the mesh has an MLP, else
+        // from 1 - alpha) and replaces the FP64 phase.
+        float u0 = use_mlp ? W.mlp_out[i] : 1.0f - (float)a;
         if (!(u0 >= 0.0f)) {
           status |= VOF_ST_MLP_SKIPPED;
           u0 = 1.0f - (float)a;
@@ -1497,7 +1498,7 @@ int pick_group(const vof_mesh* m, const vof_options& o, int bin) {
 
 template <int G>
 cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
-                          int bin) {
+                          int use_mlp, int bin) {
   const int max_ct = m->bin_max_ct[bin];
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
@@ -1517,7 +1518,7 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   if (bps < 1) bps = 1;
   const int64_t need = (m->bin_cells[bin] + (threads / G) - 1) / (threads / G);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
-  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, mode, bin);
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, mode, use_mlp, bin);
   return cudaGetLastError();
 }
 
@@ -1525,12 +1526,13 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
 
 cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s);  // vof_mlp.cu
 cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
-                            int bin, int G);
+                            int use_mlp, int bin, int G);
 
 vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s,
                               bool early_xmark) {
-  const int learned = opt.root_mode == VOF_ROOT_LEARNED;
-  if (learned && !m->mlp) {
+  // the learned path needs the MLP guess; the interval cubic takes it when the mesh has an MLP
+  const int learned = opt.root_mode == VOF_ROOT_LEARNED || (opt.root_mode == VOF_ROOT_CUBIC && m->mlp);
+  if (opt.root_mode == VOF_ROOT_LEARNED && !m->mlp) {
     set_error("learned root search requested but no MLP weights are set");
     return VOF_ESTATE;
   }
@@ -1587,7 +1589,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     e = cudaStreamWaitEvent(sb, m->ev_fork, 0);
     if (e != cudaSuccess) break;
     tm.start(KC_ROOT, sb);
-    e = launch_root_bin(m, d_alpha, opt, sb, opt.root_mode, b, pick_group(m, opt, b));
+    e = launch_root_bin(m, d_alpha, opt, sb, opt.root_mode, learned, b, pick_group(m, opt, b));
     tm.stop(sb);
     if (e != cudaSuccess) break;
     if (e == cudaSuccess) e = cudaEventRecord(m->ev_join[b], sb);
@@ -1603,14 +1605,14 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
 }
 
 cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
-                            int bin, int G) {
+                            int use_mlp, int bin, int G) {
   switch (G) {
-    case 1: return launch_root_g<1>(m, alpha, opt, s, mode, bin);
-    case 2: return launch_root_g<2>(m, alpha, opt, s, mode, bin);
-    case 4: return launch_root_g<4>(m, alpha, opt, s, mode, bin);
-    case 8: return launch_root_g<8>(m, alpha, opt, s, mode, bin);
-    case 16: return launch_root_g<16>(m, alpha, opt, s, mode, bin);
-    default: return launch_root_g<32>(m, alpha, opt, s, mode, bin);
+    case 1: return launch_root_g<1>(m, alpha, opt, s, mode, use_mlp, bin);
+    case 2: return launch_root_g<2>(m, alpha, opt, s, mode, use_mlp, bin);
+    case 4: return launch_root_g<4>(m, alpha, opt, s, mode, use_mlp, bin);
+    case 8: return launch_root_g<8>(m, alpha, opt, s, mode, use_mlp, bin);
+    case 16: return launch_root_g<16>(m, alpha, opt, s, mode, use_mlp, bin);
+    default: return launch_root_g<32>(m, alpha, opt, s, mode, use_mlp, bin);
   }
 }
 

@@ -59,3 +59,21 @@ def test_interval_cubic_needs_no_mlp_and_matches_bisection():
     ok, err = close(gc["mdot"], gb["mdot"])
     assert ok, err
     assert gc["counts"]["evals_total"] * 10 < gb["counts"]["evals_total"]
+
+
+def test_interval_cubic_takes_the_mlp_guess():
+    """With an MLP attached the interval is picked from the learned guess: fewer FP32 evaluations,
+    the same single FP64 pass, the same bars."""
+    m, a, T, Tb = case("voronoi_film")
+    M = vof.Mesh(m)
+    _, g0 = gpu_step(m, a, T, Tb, dev_mesh=M, root_mode=vof.ROOT_CUBIC)
+    assert vof.load_default_mlp(M)
+    _, g1 = gpu_step(m, a, T, Tb, dev_mesh=M, root_mode=vof.ROOT_CUBIC)
+    assert g1["counts"]["evals32_total"] < g0["counts"]["evals32_total"]
+    assert g1["counts"]["evals_total"] <= 2 * len(g1["iface_idx"])
+    O = oracle.Oracle(m)
+    V = O.geometry()["cell_vol"]
+    for c in g1["iface_idx"]:
+        assert abs(O.liquid_volume(c, g1["phi_v"], g1["iso"][c])["VL"] / V[c] - a[c]) <= 1e-10
+    ok, err = close(g1["mdot"], g0["mdot"])
+    assert ok, err
