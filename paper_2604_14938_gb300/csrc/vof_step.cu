@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   cg::grid_group grid = cg::this_grid();
   constexpr int kPer = kSelTile / kThreads;  // consecutive cells per thread in a tile
   static_assert(kPer >= 1 && kPer <= 32 && kSelTile % kThreads == 0, "tile layout");
-  extern __shared__ int32_t band_buf[];  // (kThreads / 32) * (1 + max faces per cell)
+  extern __shared__ int32_t band_buf[];  // (kThreads / 16) * (1 + max faces per cell)
   __shared__ int64_t s8[kThreads / 32];
   __shared__ int wpre[kThreads / 32 + 1];
   __shared__ int s_bin[kBins], s_nb;
@@ -197,21 +197,25 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
     __syncthreads();
   }
   grid.sync();
-  // (3) a warp per interface cell, eight cells per block pass: lane j takes face j and vertex j
-  // (and j + 32, ...). New band cells go to a shared buffer that one atomic per pass appends to
-  // the band list; a vertex gets its field value from the lane that stamps it first.
+  // (3) kSelLanes lanes per interface cell, kThreads / kSelLanes cells per block pass: lane j takes
+  // face j and vertex j (and j + kSelLanes, ...). New band cells go to a shared buffer that one
+  // atomic per pass appends to the band list; a vertex gets its field value from the lane that
+  // stamps it first.
   {
+    constexpr int kSelLanes = 16;
+    const int sl = threadIdx.x % kSelLanes, scell = threadIdx.x / kSelLanes;
     const int64_t n = W.counters->n_iface;
-    for (int64_t base = (int64_t)blockIdx.x * (kThreads / 32); base < n; base += (int64_t)gridDim.x * (kThreads / 32)) {
+    for (int64_t base = (int64_t)blockIdx.x * (kThreads / kSelLanes); base < n;
+         base += (int64_t)gridDim.x * (kThreads / kSelLanes)) {
       if (threadIdx.x == 0) s_nb = 0;
       __syncthreads();
-      const int64_t i = base + wid;
+      const int64_t i = base + scell;
       if (i < n) {
         const int32_t c = W.iface_idx[i];
-        if (lane == 0 && atomicExch(&W.band_stamp[c], step) != step) band_buf[atomicAdd(&s_nb, 1)] = c;
+        if (sl == 0 && atomicExch(&W.band_stamp[c], step) != step) band_buf[atomicAdd(&s_nb, 1)] = c;
         const int64_t f0 = M.cell_face_off[c], f1 = M.cell_face_off[c + 1];
         const int64_t v0 = M.cell_vert_off[c], v1 = M.cell_vert_off[c + 1];
-        for (int64_t j = lane; j < max(f1 - f0, v1 - v0); j += 32) {
+        for (int64_t j = sl; j < max(f1 - f0, v1 - v0); j += kSelLanes) {
           if (f0 + j < f1) {
             const int32_t fc = M.cell_face[f0 + j] & 0x7fffffff;
             const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
@@ -1541,7 +1545,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   W.alpha_in = d_alpha;
   Timing& tm = m->timing;
   // selection, band, vertex field and bins: one cooperative launch, as many blocks as are resident
-  const size_t sel_smem = (size_t)(kThreads / 32) * (1 + m->max_cf) * sizeof(int32_t);
+  const size_t sel_smem = (size_t)(kThreads / 16) * (1 + m->max_cf) * sizeof(int32_t);  // phase 3's cells per pass
   if (!m->sel_grid) {
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_select, kThreads, sel_smem);
