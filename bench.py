@@ -204,8 +204,11 @@ def run_ours(args, rank, world, dev):
             M.step_host(ha, hT, hTb, synth.PROPS, hm, ht, opt_best, stream=stream)
         e2e_s = time.perf_counter() - t0
         e2e_units = M.counts(stream=stream)["n_iface"] * args.steps
+    # bytes in: alpha and T, and T_bnd at the boundary faces (pinned: the library gathers only
+    # those entries from host memory); out: mdot and the totals
+    n_bnd = sum(int((np.asarray(mm.face_neigh) < 0).sum()) for mm in (meshes if isinstance(meshes, list) else [meshes]))
     info = dict(n_cells=nc, batch=batch, pipe=pipe, tuned=tuned, extra=extra, e2e_units=e2e_units,
-                h2d=8 * (2 * nc + (0 if pipe else M.n_faces)), d2h=8 * (nc + 2))
+                h2d=8 * (2 * nc + (0 if pipe else n_bnd)), d2h=8 * (nc + 2))
     return M, (meshes, a, T, Tb), desc, results, e2e_s, info
 
 

@@ -53,6 +53,16 @@ vof_status read_counters(vof_mesh* m, Counters* c, cudaStream_t s) {
   return VOF_OK;
 }
 
+// dst[idx[i]] = src[idx[i]]: the boundary entries of a per-face array, read through a
+// device-accessible view of pinned host memory
+__global__ void k_gather_faces(int64_t n, const int32_t* idx, const double* src, double* dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int32_t f = idx[i];
+    dst[f] = src[f];
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -152,7 +162,21 @@ vof_status vof_step_host(vof_mesh* m, const double* h_alpha, const double* h_T, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_stream, m->ev_io_start, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, m->io_stream);
-  if (e == cudaSuccess && h_T_bnd) e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, m->io_stream);
+  if (e == cudaSuccess && h_T_bnd) {
+    // only the boundary entries are ever read: when h_T_bnd is pinned and mapped, a kernel gathers
+    // them straight from host memory; otherwise the whole array is copied
+    cudaPointerAttributes pa;
+    const double* view = nullptr;
+    if (cudaPointerGetAttributes(&pa, h_T_bnd) == cudaSuccess && pa.type == cudaMemoryTypeHost)
+      view = static_cast<const double*>(pa.devicePointer);
+    cudaGetLastError();
+    if (view && m->n_bnd > 0) {
+      k_gather_faces<<<(unsigned)((m->n_bnd + 255) / 256), 256, 0, m->io_stream>>>(m->n_bnd, m->bnd_faces, view, W.io_Tb);
+      e = cudaGetLastError();
+    } else if (!view) {
+      e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, m->io_stream);
+    }
+  }
   if (e == cudaSuccess) e = cudaEventRecord(m->ev_io_done, m->io_stream);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   m->io_pending = true;

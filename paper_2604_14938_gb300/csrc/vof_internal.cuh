@@ -168,6 +168,8 @@ struct vof_mesh {
   int num_sms = 0;
   int sel_grid = 0;   // blocks of the cooperative selection launch (all resident)
   int geom_grid = 0;  // blocks of the interface-geometry launch
+  int32_t* bnd_faces = nullptr;  // device list of the boundary faces (face_neigh < 0)
+  int64_t n_bnd = 0;
   vof::MeshView view{};
   vof::Workspace ws{};
   std::vector<void*> allocs;

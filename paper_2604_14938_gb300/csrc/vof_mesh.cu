@@ -370,6 +370,13 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.io_alpha, nc));
   TRY(dev_alloc(m, &W.io_T, nc));
   TRY(dev_alloc(m, &W.io_Tb, nf));
+  {  // boundary faces, for the host-buffer step's gather of T_bnd
+    std::vector<int32_t> bf;
+    for (int64_t f = 0; f < nf; ++f)
+      if (d->face_neigh[f] < 0) bf.push_back((int32_t)f);
+    m->n_bnd = (int64_t)bf.size();
+    TRY(upload(m, &m->bnd_faces, bf.data(), bf.size(), s));
+  }
   TRY(dev_alloc(m, &W.io_mdot, nc));
   TRY(dev_alloc(m, &W.io_Q, nc));
   TRY(dev_alloc(m, &W.io_totals, 2));

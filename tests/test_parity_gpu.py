@@ -197,6 +197,19 @@ def test_host_buffer_step_matches_device_step():
     assert np.array_equal(ht.numpy(), g["totals"])
 
 
+def test_host_buffer_step_from_pageable_memory():
+    """Host buffers that are not pinned take the plain copies (the boundary gather needs a mapped
+    view); the results are those of the device step."""
+    import paper_2604_14938_gb300 as vof
+    m, a, T, Tb = case("pipe_film")
+    M, g = gpu_step(m, a, T, Tb)
+    hm, ht = torch.empty(m.n_cells, dtype=torch.float64), torch.empty(2, dtype=torch.float64)
+    M.step_host(torch.as_tensor(a), torch.as_tensor(T), torch.as_tensor(np.ascontiguousarray(Tb)), synth.PROPS, hm, ht,
+                vof.default_options())
+    assert np.array_equal(hm.numpy(), g["mdot"])
+    assert np.array_equal(ht.numpy(), g["totals"])
+
+
 def test_iteration_cap_sets_status_not_a_fault():
     """A forced bisection cap leaves NOT_CONVERGED bits and counts; the step completes."""
     m, a, T, Tb = case("voronoi_spheres")
