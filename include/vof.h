@@ -143,10 +143,13 @@ vof_status vof_step(vof_mesh* mesh, const double* d_alpha, const double* d_T, co
                     const vof_props* props, const vof_options* opt, double* d_mdot, double* d_Q, double* d_totals,
                     void* stream);
 
-/* The same step from HOST buffers: copies h_alpha, h_T [n_cells] (and h_T_bnd [n_faces] when
- * non-NULL) to the device on the stream, runs vof_step, copies mdot [n_cells] into h_mdot and
- * the totals into h_totals [2], and synchronises. Pinned host memory makes the copies
- * asynchronous. */
+/* The same step from HOST buffers: copies h_alpha, h_T [n_cells] (and the boundary entries of
+ * h_T_bnd [n_faces] when non-NULL) to the device on the stream, runs vof_step, copies mdot
+ * [n_cells] into h_mdot and the totals into h_totals [2], and synchronises. With every buffer in
+ * pinned (mapped) host memory and a stream other than the default one, the boundary entries are
+ * gathered through the mapping and the whole sequence is captured once into a CUDA graph and
+ * replayed while the pointers, properties, options, tuned lanes and MLP stay the same; other
+ * buffers take plain copies and eager launches. */
 vof_status vof_step_host(vof_mesh* mesh, const double* h_alpha, const double* h_T, const double* h_T_bnd,
                          const vof_props* props, const vof_options* opt, double* h_mdot, double* h_totals,
                          void* stream);

@@ -63,6 +63,57 @@ __global__ void k_gather_faces(int64_t n, const int32_t* idx, const double* src,
   }
 }
 
+// The device view of host memory that CUDA maps (pinned allocations), else null.
+const double* mapped_view(const void* p) {
+  cudaPointerAttributes pa;
+  const double* v = nullptr;
+  if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost)
+    v = static_cast<const double*>(pa.devicePointer);
+  cudaGetLastError();
+  return v;
+}
+
+// The host-buffer step, enqueued on s without synchronising: alpha on s; T and T_bnd on the
+// mesh's copy stream, overlapping the reconstruction (the source stage waits for them); T_bnd
+// gathered at the boundary faces through tb_view when there is one; mdot and the totals back.
+vof_status host_step_enqueue(vof_mesh* m, const double* h_alpha, const double* h_T, const double* h_T_bnd,
+                             const double* tb_view, const vof_props* props, const vof_options* opt, double* h_mdot,
+                             double* h_totals, cudaStream_t s) {
+  Workspace& W = m->ws;
+  const size_t nc = (size_t)m->n_cells, nf = (size_t)m->n_faces;
+  cudaError_t e = cudaEventRecord(m->ev_io_start, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_stream, m->ev_io_start, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, m->io_stream);
+  if (e == cudaSuccess && h_T_bnd) {
+    if (tb_view) {
+      if (m->n_bnd > 0) {
+        k_gather_faces<<<(unsigned)((m->n_bnd + 255) / 256), 256, 0, m->io_stream>>>(m->n_bnd, m->bnd_faces, tb_view,
+                                                                                      W.io_Tb);
+        e = cudaGetLastError();
+      }
+    } else {
+      e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, m->io_stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(m->ev_io_done, m->io_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  m->io_pending = true;
+  vof_status st = vof_step(m, W.io_alpha, W.io_T, h_T_bnd ? W.io_Tb : nullptr, props, opt, W.io_mdot, W.io_Q,
+                           W.io_totals, s);
+  if (st) {
+    if (m->io_pending) {  // the step stopped before its source stage: join the copy stream
+      cudaStreamWaitEvent(s, m->ev_io_done, 0);
+      m->io_pending = false;
+    }
+    return st;
+  }
+  e = cudaMemcpyAsync(h_mdot, W.io_mdot, nc * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_totals, W.io_totals, 2 * 8, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  return VOF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -152,47 +203,76 @@ vof_status vof_timing_read(vof_mesh* m, double* ms, int64_t* launches, int n, vo
 vof_status vof_step_host(vof_mesh* m, const double* h_alpha, const double* h_T, const double* h_T_bnd,
                          const vof_props* props, const vof_options* opt, double* h_mdot, double* h_totals,
                          void* stream) {
-  if (!m || !h_alpha || !h_T || !h_mdot || !h_totals) { set_error("null argument"); return VOF_EINVAL; }
+  if (!m || !h_alpha || !h_T || !h_mdot || !h_totals || !props || !opt) {
+    set_error("null argument");
+    return VOF_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace& W = m->ws;
-  const size_t nc = (size_t)m->n_cells, nf = (size_t)m->n_faces;
-  // alpha on the caller's stream; T and T_bnd, needed only by the source stage, on the mesh's copy
-  // stream, overlapping the reconstruction (the source stage waits for them)
-  cudaError_t e = cudaEventRecord(m->ev_io_start, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_alpha, h_alpha, nc * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_stream, m->ev_io_start, 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(W.io_T, h_T, nc * 8, cudaMemcpyHostToDevice, m->io_stream);
-  if (e == cudaSuccess && h_T_bnd) {
-    // only the boundary entries are ever read: when h_T_bnd is pinned and mapped, a kernel gathers
-    // them straight from host memory; otherwise the whole array is copied
-    cudaPointerAttributes pa;
-    const double* view = nullptr;
-    if (cudaPointerGetAttributes(&pa, h_T_bnd) == cudaSuccess && pa.type == cudaMemoryTypeHost)
-      view = static_cast<const double*>(pa.devicePointer);
-    cudaGetLastError();
-    if (view && m->n_bnd > 0) {
-      k_gather_faces<<<(unsigned)((m->n_bnd + 255) / 256), 256, 0, m->io_stream>>>(m->n_bnd, m->bnd_faces, view, W.io_Tb);
-      e = cudaGetLastError();
-    } else if (!view) {
-      e = cudaMemcpyAsync(W.io_Tb, h_T_bnd, nf * 8, cudaMemcpyHostToDevice, m->io_stream);
+  // only the boundary entries of T_bnd are ever read: a mapped (pinned) h_T_bnd is gathered there
+  const double* tb_view = h_T_bnd ? mapped_view(h_T_bnd) : nullptr;
+  const bool pinned = mapped_view(h_alpha) && mapped_view(h_T) && mapped_view(h_mdot) && mapped_view(h_totals) &&
+                      (!h_T_bnd || tb_view);
+  if (!s || !pinned) {
+    vof_status st = host_step_enqueue(m, h_alpha, h_T, h_T_bnd, tb_view, props, opt, h_mdot, h_totals, s);
+    if (st) {
+      cudaStreamSynchronize(s);  // the copies in flight still read the caller's buffers
+      return st;
     }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "host-buffer step");
+    return VOF_OK;
   }
-  if (e == cudaSuccess) e = cudaEventRecord(m->ev_io_done, m->io_stream);
-  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-  m->io_pending = true;
-  vof_status st = vof_step(m, W.io_alpha, W.io_T, h_T_bnd ? W.io_Tb : nullptr, props, opt, W.io_mdot, W.io_Q,
-                           W.io_totals, stream);
-  if (st) {
-    if (m->io_pending) {  // the step stopped before its source stage: let the copies finish
-      cudaStreamSynchronize(m->io_stream);
-      m->io_pending = false;
+  // pinned buffers on a stream of the caller's: the copies, the gather and the step are captured
+  // once and replayed, valid while the arguments they bake in are unchanged
+  std::vector<unsigned char> key;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    key.insert(key.end(), c, c + n);
+  };
+  const void* ptrs[6] = {h_alpha, h_T, h_T_bnd, h_mdot, h_totals, (const void*)m->mlp};
+  put(ptrs, sizeof(ptrs));
+  put(props, sizeof(vof_props));
+  put(opt, sizeof(vof_options));
+  put(m->bin_G, sizeof(m->bin_G));
+  GraphCache& g = m->host_graph;
+  if (!g.exec || g.key.size() != key.size() || std::memcmp(g.key.data(), key.data(), key.size()) != 0) {
+    const bool timing = m->timing.on;
+    m->timing.on = false;  // no event records inside the graph
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { m->timing.on = timing; return cuda_fail(e, "cudaStreamBeginCapture"); }
+    const vof_status st = host_step_enqueue(m, h_alpha, h_T, h_T_bnd, tb_view, props, opt, h_mdot, h_totals, s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    m->timing.on = timing;
+    m->io_pending = false;
+    if (st != VOF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
     }
-    return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if (g.exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+    }
+    if (!g.exec) {
+      e = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        g.exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+      }
+    }
+    cudaGraphDestroy(graph);
+    g.key = key;
+    g.captures += 1;
   }
-  e = cudaMemcpyAsync(h_mdot, W.io_mdot, nc * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_totals, W.io_totals, 2 * 8, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaGraphLaunch(g.exec, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  if (e != cudaSuccess) return cuda_fail(e, "host-buffer step");
   return VOF_OK;
 }
 

@@ -177,7 +177,8 @@ struct vof_mesh {
   vof_mlp* mlp = nullptr;
   bool recon_done = false;
   vof::Timing timing;
-  vof::GraphCache graph;
+  vof::GraphCache graph;       // vof_step_graph
+  vof::GraphCache host_graph;  // vof_step_host with pinned buffers
   // the bins' root searches and geometries run as parallel branches (fork after binning, join
   // before the least squares), so that one bin's slow cells overlap the other bins' work
   cudaStream_t bin_stream[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};

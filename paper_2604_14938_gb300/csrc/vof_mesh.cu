@@ -397,6 +397,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
 void destroy(vof_mesh* m) {
   if (m->graph.exec) cudaGraphExecDestroy(m->graph.exec);
   m->graph.exec = nullptr;
+  if (m->host_graph.exec) cudaGraphExecDestroy(m->host_graph.exec);
+  m->host_graph.exec = nullptr;
   for (cudaEvent_t e : m->timing.ev) cudaEventDestroy(e);
   m->timing.ev.clear();
   for (void* p : m->allocs) cudaFree(p);

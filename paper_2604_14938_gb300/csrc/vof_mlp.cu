@@ -692,7 +692,10 @@ vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp) {
   }
   // a captured step graph bakes in the weights' device address: recapture after any change (a
   // new MLP may even reuse the old handle's host address)
-  if (mesh->mlp != mlp) mesh->graph.key.clear();
+  if (mesh->mlp != mlp) {
+    mesh->graph.key.clear();
+    mesh->host_graph.key.clear();
+  }
   mesh->mlp = mlp;
   return VOF_OK;
 }
