@@ -34,6 +34,10 @@ METRIC = "interface cells/s (recon+LSQ∇T+mdot), learned vs bisection, at |Δα
 UNIT = "interface cells/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step's root-search launches,
+# all bins, measured with ncu --set full on a GB300 for the workload, path and lanes per cell given;
+# the roofline reports null traffic for anything else
+ROOT_TRAFFIC = {("film250k", "learned", (0, 0, 32, 16, 0)): 6_535_168}
 
 
 class Clocks:
@@ -353,7 +357,8 @@ def main():
         "roofline": {"kernel": "k_root (isovalue root search)", "bound": "alu",
                      "flops_per_launch": flops, "flops_per_iface_cell": flops / max(r["kcounts"]["n_iface"], 1),
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                     "traffic": ROOT_TRAFFIC.get((args.workload, best, tuple(info["tuned"][best]))),
                      "peak_source": "FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (2 FMA); no FP64 figure in the "
                                     "measured peaks (an FMA-chain probe measured 1.20 TFLOP/s)"},
         "e2e": {"value": world * info["e2e_units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
