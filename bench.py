@@ -216,6 +216,21 @@ def run_ours(args, rank, world, dev):
     return M, (meshes, a, T, Tb), desc, results, e2e_s, info
 
 
+def job_rate(units: float, seconds: float, device=None) -> tuple[float, float]:
+    """(whole-job rate, slowest rank's seconds): the units of every rank summed and divided by the
+    largest time over the ranks; one process without a process group is its own job."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / seconds, seconds
+    t = torch.tensor([float(units), float(seconds)], dtype=torch.float64, device=device)
+    u = t[:1].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    s = t[1:].clone()
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(s.item()), float(s.item())
+
+
 def _oracle_step(O, a, T, Tb, cells):
     """One oracle pass: (seconds of the whole-mesh parts, seconds of the sampled reconstruction).
     The whole-mesh parts are the vertex field and the downstream steps (selection, band, crossing
@@ -317,13 +332,10 @@ def main():
     best = "learned" if "learned" in res else ("bisect" if "bisect" in res else "cubic")
     r = res[best]
     n_iface = r["counts"]["n_iface"]
-    ms = r["ms"]
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * r["units"] / (ms_max / 1e3)
+    value, s_max = job_rate(r["units"], r["ms"] / 1e3, dev)
+    ms_max = s_max * 1e3
+    paths = {k: job_rate(v["units"], v["ms"] / 1e3, dev) for k, v in res.items()}
+    e2e_value, _ = job_rate(info["e2e_units"], e2e_s, dev)
     # roofline of the dominant kernel (the root search): algorithmic FP64 flops per launch,
     # from the device counters of the same step whose kernel time the events measured
     # per step: the eager timing pass records one selection group per step and one root-search
@@ -346,7 +358,7 @@ def main():
                    "step": "eager launches per step" if info["pipe"] else "CUDA graph replay",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single", **info["extra"]},
-        "paths": {k: {"value": world * v["units"] / (v["ms"] / 1e3), "ms_per_step": v["ms"] / args.steps,
+        "paths": {k: {"value": paths[k][0], "ms_per_step": paths[k][1] * 1e3 / args.steps,
                       "evals_per_cell": v["counts"]["evals_total"] / max(v["counts"]["n_iface"], 1),
                       "fp32_evals_per_cell": v["counts"]["evals32_total"] / max(v["counts"]["n_iface"], 1),
                       "fallbacks": v["counts"]["n_fallback"], "not_converged": v["counts"]["n_not_converged"],
@@ -361,7 +373,7 @@ def main():
                      "traffic": ROOT_TRAFFIC.get((args.workload, best, tuple(info["tuned"][best]))),
                      "peak_source": "FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (2 FMA); no FP64 figure in the "
                                     "measured peaks (an FMA-chain probe measured 1.20 TFLOP/s)"},
-        "e2e": {"value": world * info["e2e_units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
                 "d2h_bytes_per_step": info["d2h"]},
         "gpu_launches": args.steps * per_step,
         "clocks": r["clocks"],
