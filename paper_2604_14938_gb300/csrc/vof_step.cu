@@ -1217,60 +1217,80 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
 }
 
 // ---- interface-modified least squares (R7) on band cells -----------------------------------------
-// L lanes per band cell over its faces; the nine sums of G and b are reduced across the lanes. A
-// crossing face contributes its crossing point x_f (computed first) with T_sat; every face runs the same
-// instructions (the point and the value are selected, not branched on).
+// L lanes per band cell over its faces, a block taking kThreads / L consecutive band cells; a
+// crossing face contributes its crossing point x_f (computed first) with T_sat, and every face runs
+// the same instructions (the point and the value are selected, not branched on). The lanes' nine
+// sums of G and b go to shared memory; then one thread per cell adds them, in the order of the
+// lanes' pairwise tree, and inverts G: the per-cell FP64 work runs with every lane of a warp busy
+// (an FP64 warp instruction costs the same with one active lane as with 32).
 template <int L>
 __device__ void lsq_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
+  constexpr int C = kThreads / L;  // cells per block pass
+  static_assert(L == 4, "the per-cell sum below pairs lanes as (0 + 2) + (1 + 3)");
+  __shared__ double part[C][9][L];
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
-  const int lane = threadIdx.x % L;
-  const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
-  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / L);
+  const int lane = threadIdx.x % L, slot = threadIdx.x / L;
   int nsing = 0;
-  // groups interleaved over the blocks, so that a short band still spreads over every SM
-  for (int64_t j = (int64_t)(threadIdx.x / L) * gridDim.x + blockIdx.x; j < nb; j += groups) {
-    const int32_t c = W.band_idx[j];
-    const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
-    const double TP = a.T[c], aP = a.alpha[c];
-    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
-    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
-      const int32_t f = M.cell_face[k] & 0x7fffffff;
-      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-      const int32_t q = o == c ? nbr : o;
-      if (q < 0 && !a.T_bnd) continue;
-      const bool cross = q >= 0 && (aP - 0.5) * (a.alpha[q] - 0.5) < 0;
-      const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
-      const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
-      const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
-      const double dT = Tq - TP;
-      g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
-      g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
-      b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+  for (int64_t base = (int64_t)blockIdx.x * C; base < nb; base += (int64_t)gridDim.x * C) {
+    {
+      const int64_t j = base + slot;
+      double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+      if (j < nb) {
+        const int32_t c = W.band_idx[j];
+        const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
+        const double TP = a.T[c], aP = a.alpha[c];
+        for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
+          const int32_t f = M.cell_face[k] & 0x7fffffff;
+          const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+          const int32_t q = o == c ? nbr : o;
+          if (q < 0 && !a.T_bnd) continue;
+          const bool cross = q >= 0 && (aP - 0.5) * (a.alpha[q] - 0.5) < 0;
+          const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
+          const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
+          const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
+          const double dT = Tq - TP;
+          g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
+          g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
+          b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+        }
+      }
+      double* p = &part[slot][0][lane];
+      p[0 * L] = g00; p[1 * L] = g01; p[2 * L] = g02; p[3 * L] = g11; p[4 * L] = g12; p[5 * L] = g22;
+      p[6 * L] = b0; p[7 * L] = b1; p[8 * L] = b2;
     }
-    g00 = group_sum<L>(g00, mask); g01 = group_sum<L>(g01, mask);
-    g02 = group_sum<L>(g02, mask); g11 = group_sum<L>(g11, mask);
-    g12 = group_sum<L>(g12, mask); g22 = group_sum<L>(g22, mask);
-    b0 = group_sum<L>(b0, mask); b1 = group_sum<L>(b1, mask); b2 = group_sum<L>(b2, mask);
-    if (lane != 0) continue;
-    // explicit symmetric inverse (cofactors / det), Appendix B
-    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-    const double det = g00 * c00 + g01 * c01 + g02 * c02;
-    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
-    int st = 0;
-    Vec3 g = v3(0, 0, 0);
-    if (det > 1e-12 * tr * tr * tr) {
-      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-      const double id = 1.0 / det;
-      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
-             (c02 * b0 + c12 * b1 + c22 * b2) * id);
-    } else {
-      st = VOF_ST_SINGULAR_LSQ;
-      ++nsing;
+    __syncthreads();
+    if (threadIdx.x < C) {
+      const int sl = threadIdx.x;
+      const int64_t j = base + sl;
+      if (j < nb) {
+        const int32_t c = W.band_idx[j];
+        double v[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] = (part[sl][q][0] + part[sl][q][2]) + (part[sl][q][1] + part[sl][q][3]);
+        const double g00 = v[0], g01 = v[1], g02 = v[2], g11 = v[3], g12 = v[4], g22 = v[5];
+        const double b0 = v[6], b1 = v[7], b2 = v[8];
+        // explicit symmetric inverse (cofactors / det), Appendix B
+        const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+        const double det = g00 * c00 + g01 * c01 + g02 * c02;
+        const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
+        int st = 0;
+        Vec3 g = v3(0, 0, 0);
+        if (det > 1e-12 * tr * tr * tr) {
+          const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+          const double id = 1.0 / det;
+          g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+                 (c02 * b0 + c12 * b1 + c22 * b2) * id);
+        } else {
+          st = VOF_ST_SINGULAR_LSQ;
+          ++nsing;
+        }
+        W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
+        if (W.iface_stamp[c] == step) W.status[c] |= st;
+        else W.status[c] = st;
+      }
     }
-    W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
-    if (W.iface_stamp[c] == step) W.status[c] |= st;
-    else W.status[c] = st;
+    __syncthreads();
   }
   if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
 }
