@@ -60,12 +60,14 @@ def _lib():
         _LIB.orc_reconstruct.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 7)
         _LIB.orc_reconstruct_m.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 7)
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double]
+                                          + [ctypes.c_void_p] * 7)
         _LIB.orc_phase_change.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 6
                                           + [ctypes.c_int] + [ctypes.c_void_p] * 15)
         _LIB.orc_vertex_field.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
         _LIB.orc_geometry.argtypes = [ctypes.c_void_p] * 5
         _LIB.orc_pairwise_sum.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        _LIB.orc_interface_htc.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_double] * 2 + [ctypes.c_void_p] * 2
     return _LIB
 
 
@@ -115,10 +117,12 @@ class Oracle:
         _lib().orc_liquid_volume(self.ref, int(cell), _p(phi), float(c), _p(x), _p(out))
         return dict(VL=out[0], area=out[1], vec_area=out[2:5].copy(), centroid=out[5:8].copy(), nloops=int(out[8]))
 
-    def reconstruct(self, alpha, phi, eps=1e-12, tol=1e-12, max_iter=100, cells=None, method="bisect") -> dict:
+    def reconstruct(self, alpha, phi, eps=1e-12, tol=1e-12, max_iter=100, cells=None, method="bisect",
+                    alpha_iso=0.5) -> dict:
         """R0 + R3 (+ geometry at the root). Arrays over all cells; untouched cells hold nan/0.
         method "bisect": bisection on V_L(c)/V - alpha; "cubic": bisection over the sorted vertex
-        values, then the interval's cubic (interpolated from four evaluations) solved on its own."""
+        values, then the interval's cubic (interpolated from four evaluations) solved on its own;
+        "fixed": the iso-surface at alpha_iso, no volume matching."""
         nc = self.c.n_cells
         a = np.ascontiguousarray(alpha, np.float64)
         r = dict(iso=np.full(nc, np.nan), status=np.zeros(nc, np.int32), evals=np.zeros(nc, np.int32),
@@ -126,7 +130,8 @@ class Oracle:
                  nloops=np.zeros(nc, np.int32))
         cl = None if cells is None else np.ascontiguousarray(cells, np.int64)
         _lib().orc_reconstruct_m(self.ref, _p(a), _p(phi), _p(self.geometry()["cell_vol"]), eps, tol, max_iter,
-                                 _p(cl), 0 if cl is None else len(cl), {"bisect": 0, "cubic": 1}[method],
+                                 _p(cl), 0 if cl is None else len(cl), {"bisect": 0, "cubic": 1, "fixed": 2}[method],
+                                 float(alpha_iso),
                                  *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
         return r
 
@@ -148,6 +153,9 @@ class Oracle:
                                 *[_p(o[k]) for k in ("in_band", "grad", "grad_l", "grad_v", "q_l", "q_v", "mdot", "Q",
                                                      "status", "crossing", "x_f", "d_own", "d_neigh", "A_int_f",
                                                      "totals")])
+        o["a_own"], o["a_neigh"] = np.zeros(nf), np.zeros(nf)
+        _lib().orc_interface_htc(self.ref, _p(arr(alpha)), _p(o["crossing"]), _p(o["A_int_f"]), _p(o["d_own"]),
+                                 _p(o["d_neigh"]), props["k_l"], props["k_v"], _p(o["a_own"]), _p(o["a_neigh"]))
         return o
 
     def run(self, alpha, T, T_bnd, props, eps=1e-12, tol=1e-12, vertex_mode=0, xf_mode=XF_RECON) -> dict:

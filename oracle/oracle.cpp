@@ -344,6 +344,19 @@ RootResult interval_cubic(const OrcMesh& m, int64_t cell, const double* phi, dou
   return r;
 }
 
+// R3, fixed isovalue (the paper's own choice, Sec. 2.1: the iso-surface at a prescribed
+// alpha_iso, typically 0.5; the next row N3 of the scope): no volume matching, c = alpha_iso. A
+// cell whose vertex values all lie on one side of it has no interface there (its area is 0).
+RootResult fixed_iso(const OrcMesh& m, int64_t cell, const double* phi, double iso) {
+  const std::vector<int32_t> vs = cell_vertices(m, cell);
+  double lo = phi[vs[0]], hi = phi[vs[0]];
+  for (int32_t v : vs) { lo = std::min(lo, phi[v]); hi = std::max(hi, phi[v]); }
+  RootResult r;
+  if (hi - lo < 1e-14) { r.c = lo; r.status = ST_DEGENERATE; return r; }
+  r.c = iso;
+  return r;
+}
+
 double pairwise_sum(std::vector<double> a) {
   if (a.empty()) return 0.0;
   size_t n = 1;
@@ -396,9 +409,10 @@ void orc_liquid_volume(const OrcMesh* m, int64_t cell, const double* phi, double
 // R0 + R3 + geometry at the root for every cell with eps < alpha < 1 - eps (other cells get
 // iso = nan, status 0, evals 0, zero geometry). Arrays are [n_cells] or [3 n_cells].
 // `cells`, when non-null, restricts the work to the listed cells (n_list of them).
-// method 0: bisection (R3); method 1: interval cubic (R3, NEXT row N1).
+// method 0: bisection (R3); 1: interval cubic (R3, next row N1); 2: fixed isovalue iso_fixed (N3).
 void orc_reconstruct_m(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
-                       double tol, int max_iter, const int64_t* cells, int64_t n_list, int method, double* iso,
+                       double tol, int max_iter, const int64_t* cells, int64_t n_list, int method, double iso_fixed,
+                       double* iso,
                        int32_t* status, int32_t* evals, double* A_int, double* n_int, double* x_gamma, int32_t* nloops) {
   const OrcMesh& m = *mp;
   std::vector<int64_t> todo;
@@ -411,8 +425,9 @@ void orc_reconstruct_m(const OrcMesh* mp, const double* alpha, const double* phi
 #pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < (int64_t)todo.size(); ++t) {
     const int64_t c = todo[t];
-    const RootResult r = method == 1 ? interval_cubic(m, c, phi, alpha[c], cell_vol[c], tol, max_iter)
-                                     : bisect(m, c, phi, alpha[c], cell_vol[c], tol, max_iter);
+    const RootResult r = method == 1   ? interval_cubic(m, c, phi, alpha[c], cell_vol[c], tol, max_iter)
+                         : method == 2 ? fixed_iso(m, c, phi, iso_fixed)
+                                       : bisect(m, c, phi, alpha[c], cell_vol[c], tol, max_iter);
     iso[c] = r.c;
     status[c] = r.status;
     evals[c] = r.evals;
@@ -431,8 +446,8 @@ void orc_reconstruct_m(const OrcMesh* mp, const double* alpha, const double* phi
 void orc_reconstruct(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
                      double tol, int max_iter, const int64_t* cells, int64_t n_list, double* iso, int32_t* status,
                      int32_t* evals, double* A_int, double* n_int, double* x_gamma, int32_t* nloops) {
-  orc_reconstruct_m(mp, alpha, phi, cell_vol, eps, tol, max_iter, cells, n_list, 0, iso, status, evals, A_int, n_int,
-                    x_gamma, nloops);
+  orc_reconstruct_m(mp, alpha, phi, cell_vol, eps, tol, max_iter, cells, n_list, 0, 0.5, iso, status, evals, A_int,
+                    n_int, x_gamma, nloops);
 }
 
 // R4: crossing point of face f (owner o, neighbour n); returns t along x_o -> x_n, and the cell
@@ -613,6 +628,25 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
   }
   totals[0] = pairwise_sum(mv);
   totals[1] = pairwise_sum(qv);
+}
+
+// Eq. interface_htc (the next row N3 of the scope): on each side of a crossing face the interface
+// heat-transfer coefficient a_f = k_phi A_int,f / d_f, k_phi the conductivity of the phase the cell
+// resides in (liquid when alpha > 1/2) and d_f the cell centre's distance to the crossing point;
+// 0 on other faces. The cell adds a_f to its energy-matrix diagonal and a_f T_sat to its
+// right-hand side (the face itself is detached from the diffusive coupling).
+void orc_interface_htc(const OrcMesh* mp, const double* alpha, const uint8_t* crossing, const double* A_int_f,
+                       const double* d_own, const double* d_neigh, double k_l, double k_v, double* a_own,
+                       double* a_neigh) {
+  const OrcMesh& m = *mp;
+  for (int64_t f = 0; f < m.n_faces; ++f) {
+    a_own[f] = a_neigh[f] = 0;
+    if (!crossing[f]) continue;
+    const double ko = alpha[m.face_owner[f]] > 0.5 ? k_l : k_v;
+    const double kn = alpha[m.face_neigh[f]] > 0.5 ? k_l : k_v;
+    if (d_own[f] > 0) a_own[f] = ko * A_int_f[f] / d_own[f];
+    if (d_neigh[f] > 0) a_neigh[f] = kn * A_int_f[f] / d_neigh[f];
+  }
 }
 
 void orc_pairwise_sum(const double* a, int64_t n, double* out) { *out = pairwise_sum(std::vector<double>(a, a + n)); }

@@ -986,7 +986,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
 // partials in a fixed order: the result does not depend on timing.
 constexpr int kGeomCells = 2;  // at most 4 (two bits of a list entry)
 constexpr int kGeomRed = 32 / kGeomCells;
-constexpr int kGeomWarps = kThreads / 32;
+constexpr int kGeomThreads = 128;  // small blocks: five per SM keep every warp resident at 96 registers
+constexpr int kGeomWarps = kGeomThreads / 32;
 
 struct GeomSlot {
   int64_t v0, t0;  // first vertex / tetrahedron entry of the cell
@@ -1001,7 +1002,7 @@ size_t geom_smem_bytes(int max_ct) {
                                (size_t)kGeomCells * max_ct * sizeof(uint32_t));
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_geom(MeshView M, Workspace W, int max_ct) {
+__global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace W, int max_ct) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
@@ -1574,7 +1575,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   if (!m->geom_grid) {  // the geometry grid: every resident warp of the device
     int bps = 0;
     cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem_bytes(m->max_ct));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_geom, kThreads, geom_smem_bytes(m->max_ct));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_geom, kGeomThreads, geom_smem_bytes(m->max_ct));
     m->geom_grid = m->num_sms * std::max(1, bps);
   }
   {
@@ -1621,7 +1622,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   }
   if (e != cudaSuccess) return cuda_fail(e, "root search kernels");
   tm.start(KC_GEOM, s);
-  k_geom<<<m->geom_grid, kThreads, geom_smem_bytes(m->max_ct), s>>>(M, W, m->max_ct);
+  k_geom<<<m->geom_grid, kGeomThreads, geom_smem_bytes(m->max_ct), s>>>(M, W, m->max_ct);
   tm.stop(s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "interface geometry kernel");

@@ -433,6 +433,52 @@ def test_P7_stefan_flux(frac):
     np.testing.assert_allclose(rec["n_int"][I], np.broadcast_to([1.0, 0, 0], (9, 3)), atol=1e-12)
 
 
+@pytest.mark.parametrize("frac", [0.23, 0.81])
+def test_P12_interface_htc_stefan(frac):
+    """P12 (next row N3, Eq. interface_htc): on the planar Stefan layer the one crossing face per row
+    of cells is the face next to the interface cell; its interface area projected onto the face is
+    the face area h^2, and each side's coefficient is k_phi h^2 / d with d the distance from that
+    cell's centre to the plane x = x_g; every other face has none."""
+    r, I, V, xg, dT = _stefan(frac)
+    pc = r["pc"]
+    m = synth.hex_box(20, 3, 3, lo=(0, 0, 0), hi=(2e-3, 3e-4, 3e-4))
+    cen = oracle.Oracle(m).geometry()["cell_cen"]
+    h = 1e-4
+    cross = np.where(pc["crossing"])[0]
+    assert len(cross) == 9
+    for f in cross:
+        o, n = m.face_owner[f], m.face_neigh[f]
+        for cell, got in ((o, pc["a_own"][f]), (n, pc["a_neigh"][f])):
+            liquid = cen[cell, 0] > xg
+            k = synth.PROPS["k_l"] if liquid else synth.PROPS["k_v"]
+            assert got == pytest.approx(k * h * h / abs(cen[cell, 0] - xg), rel=1e-12)
+    others = np.setdiff1d(np.arange(m.n_faces), cross)
+    assert not np.any(pc["a_own"][others]) and not np.any(pc["a_neigh"][others])
+
+
+def test_P12_fixed_isovalue_planar():
+    """P12 (next row N3): with the vertex field linear in x the alpha_iso = 0.5 surface is the plane
+    where that field is 0.5; its area in each cut cell is the cell's cross-section (1/3)^2, its
+    normal -x (vapour at high x), and the cells it misses have no interface."""
+    m = synth.hex_box(6, 3, 3)
+    O = oracle.Oracle(m)
+    h = 1 / 6  # cell size along x; 1/3 across
+    phi = 0.9 - 1.3 * m.vx  # linear, decreasing in x: the liquid (phi >= c) lies at low x
+    a = np.full(m.n_cells, 0.5)
+    rec = O.reconstruct(a, phi, method="fixed", alpha_iso=0.5)
+    x_iso = (0.9 - 0.5) / 1.3
+    cen = O.geometry()["cell_cen"]
+    for c in range(m.n_cells):
+        cut = abs(cen[c, 0] - x_iso) < h / 2
+        assert rec["status"][c] == 0 and rec["iso"][c] == 0.5
+        if cut:
+            assert rec["A_int"][c] == pytest.approx(1 / 9, rel=1e-12)
+            np.testing.assert_allclose(rec["n_int"][c], [-1.0, 0, 0], atol=1e-12)
+            assert rec["x_gamma"][c][0] == pytest.approx(x_iso, rel=1e-12)
+        else:
+            assert rec["A_int"][c] == 0.0
+
+
 def test_P7_stefan_linear_xf_is_not_exact():
     """P7: with the alpha-interpolated crossing point the flux is not exact."""
     r, I, V, xg, dT = _stefan(0.23, mode=oracle.XF_LINEAR)
