@@ -79,6 +79,10 @@ typedef enum {
  * the polynomial alone (bisection fallback, counted). The paper has no such mode: it is the
  * scope's next step for the root search. */
 #define VOF_ROOT_CUBIC 2
+/* Fixed isovalue: the iso-surface at alpha_iso (Sec. 2.1, typically 0.5), the paper's own
+ * reconstruction, without volume matching; a cell whose vertex values do not straddle it has no
+ * interface there. The scope's next step N3. */
+#define VOF_ROOT_FIXED 3
 
 typedef struct vof_mesh vof_mesh; /* opaque, library-owned */
 
@@ -106,11 +110,14 @@ typedef struct {
   double alpha_eps;  /* interface cells: alpha_eps < alpha < 1 - alpha_eps (default 1e-12) */
   double tol_alpha;  /* root accepted when |V_L(c)/V - alpha| <= tol_alpha (default 1e-12) */
   int max_bisect;    /* bisection iteration cap (default 100) */
-  int root_mode;     /* VOF_ROOT_BISECT, VOF_ROOT_LEARNED or VOF_ROOT_CUBIC */
+  int root_mode;     /* VOF_ROOT_BISECT, VOF_ROOT_LEARNED, VOF_ROOT_CUBIC or VOF_ROOT_FIXED */
   int max_secant;    /* secant steps after the learned guess (default 2) */
   int xf_mode;       /* VOF_XF_* (default VOF_XF_RECON) */
   int vertex_mode;   /* 0 inverse distance to cell centroids (default), 1 plain average */
   int group_size;    /* lanes per cell in the root search: 0 = auto, else 1, 2, 4, 8, 16 or 32 */
+  int htc;           /* 1: also compute the interface heat-transfer coefficients VOF_F_A_OWN and
+                      * VOF_F_A_NEIGH (Eq. interface_htc) on a side branch of the step (default 0) */
+  double alpha_iso;  /* isovalue of VOF_ROOT_FIXED, in (0, 1) (default 0.5) */
 } vof_options;
 
 /* Fills *o with the defaults above. */
@@ -214,7 +221,12 @@ typedef enum {
   VOF_F_FACE_CEN = 21, /* double [n_faces][3] */
   VOF_F_IFACE_STAMP = 22, /* uint32 [n_cells]: equals the step stamp on interface cells */
   VOF_F_BAND_STAMP = 23,  /* uint32 [n_cells]: equals the step stamp on band cells */
-  VOF_F_N = 24
+  VOF_F_A_OWN = 24,    /* double [n_faces]: a_f = k_phi A_int,f / d_own of the owner side (Eq. interface_htc) */
+  VOF_F_A_NEIGH = 25,  /* double [n_faces]: the same for the neighbour side; both on crossing faces next to
+                        * the band, in steps run with options.htc = 1: each side adds a_f to its
+                        * energy-matrix diagonal and a_f T_sat to its right-hand side, the face being
+                        * detached from the diffusive coupling */
+  VOF_F_N = 26
 } vof_field;
 
 /* Element count of a field in the current state (n_iface for the interface list). */

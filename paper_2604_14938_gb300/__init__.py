@@ -18,7 +18,7 @@ _LIB = None
 VOF_ST_DEGENERATE, VOF_ST_NOT_CONVERGED, VOF_ST_FALLBACK = 1, 2, 4
 VOF_ST_SINGULAR_LSQ, VOF_ST_NO_SIDE, VOF_ST_MLP_SKIPPED = 8, 16, 32
 XF_RECON, XF_LINEAR, XF_AS_PRINTED = 0, 1, 2
-ROOT_BISECT, ROOT_LEARNED, ROOT_CUBIC = 0, 1, 2
+ROOT_BISECT, ROOT_LEARNED, ROOT_CUBIC, ROOT_FIXED = 0, 1, 2, 3
 
 FIELDS = {
     "iface_idx": (0, np.int32, 1), "phi_v": (1, np.float64, 1), "iso": (2, np.float64, 1),
@@ -29,6 +29,7 @@ FIELDS = {
     "d_neigh": (15, np.float64, 1), "A_int_f": (16, np.float64, 1), "face_stamp": (17, np.int32, 1),
     "cell_vol": (18, np.float64, 1), "cell_cen": (19, np.float64, 3), "face_area": (20, np.float64, 3),
     "face_cen": (21, np.float64, 3), "iface_stamp": (22, np.int32, 1), "band_stamp": (23, np.int32, 1),
+    "a_own": (24, np.float64, 1), "a_neigh": (25, np.float64, 1),
 }
 
 
@@ -52,7 +53,8 @@ class Props(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("alpha_eps", ctypes.c_double), ("tol_alpha", ctypes.c_double), ("max_bisect", ctypes.c_int),
                 ("root_mode", ctypes.c_int), ("max_secant", ctypes.c_int), ("xf_mode", ctypes.c_int),
-                ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int)]
+                ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int), ("htc", ctypes.c_int),
+                ("alpha_iso", ctypes.c_double)]
 
 
 class Counts(ctypes.Structure):

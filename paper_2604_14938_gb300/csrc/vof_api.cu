@@ -42,6 +42,8 @@ FieldDesc field_of(vof_mesh* m, int f, int64_t n_iface) {
     case VOF_F_FACE_CEN: return {M.face_cen, 3 * nf, 8};
     case VOF_F_IFACE_STAMP: return {W.iface_stamp, nc, 4};
     case VOF_F_BAND_STAMP: return {W.band_stamp, nc, 4};
+    case VOF_F_A_OWN: return {W.a_own, nf, 8};
+    case VOF_F_A_NEIGH: return {W.a_neigh, nf, 8};
     default: return {nullptr, 0, 0};
   }
 }

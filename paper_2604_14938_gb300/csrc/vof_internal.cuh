@@ -90,6 +90,7 @@ struct Workspace {
   double* d_own;           // [n_faces]
   double* d_neigh;         // [n_faces]
   double* A_int_f;         // [n_faces]
+  double *a_own, *a_neigh;  // [n_faces]: interface heat-transfer coefficients of the two sides
   int32_t* xface_list;     // [n_faces] crossing faces next to the band (n_crossing of them this step)
   double* mdotV;           // [n_cells] in interface-list order
   double* QV;              // [n_cells]

@@ -363,6 +363,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.d_own, nf));
   TRY(dev_alloc(m, &W.d_neigh, nf));
   TRY(dev_alloc(m, &W.A_int_f, nf));
+  TRY(dev_alloc(m, &W.a_own, nf));
+  TRY(dev_alloc(m, &W.a_neigh, nf));
   TRY(dev_alloc(m, &W.xface_list, nf));
   TRY(dev_alloc(m, &W.mdotV, nc));
   TRY(dev_alloc(m, &W.QV, nc));
@@ -438,6 +440,8 @@ void vof_default_options(vof_options* o) {
   o->tol_alpha = 1e-12;
   o->max_bisect = 100;
   o->root_mode = VOF_ROOT_BISECT;
+  o->alpha_iso = 0.5;
+  o->htc = 0;
   o->max_secant = 2;
   o->xf_mode = VOF_XF_RECON;
   o->vertex_mode = 0;
@@ -490,7 +494,8 @@ vof_status vof_mesh_bins(const vof_mesh* m, int64_t* cells5) {
 static vof_status check_opt(const vof_options* o) {
   if (!o) { set_error("null options"); return VOF_EINVAL; }
   if (!(o->alpha_eps >= 0 && o->alpha_eps < 0.5) || !(o->tol_alpha > 0) || o->max_bisect < 1 || o->max_bisect > 1000 ||
-      (o->root_mode != VOF_ROOT_BISECT && o->root_mode != VOF_ROOT_LEARNED && o->root_mode != VOF_ROOT_CUBIC) || o->max_secant < 0 || o->max_secant > 8 ||
+      o->root_mode < VOF_ROOT_BISECT || o->root_mode > VOF_ROOT_FIXED || !(o->alpha_iso > 0.0 && o->alpha_iso < 1.0) ||
+      o->max_secant < 0 || o->max_secant > 8 || o->htc < 0 || o->htc > 1 ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {

@@ -977,6 +977,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
 // sectioning its share of the cell's cut tetrahedra in FP32 pair arithmetic. Kept apart from the
 // root search, whose per-cell chain is FP64 latency: here every cell is in flight at once and the
 // chain is one or two sections and the pair sums.
+// Fixed isovalue (VOF_ROOT_FIXED, Sec. 2.1's prescribed alpha_iso): no root search; one thread per
+// interface cell checks the cell's vertex range (degenerate as in the root search) and sets c.
+__global__ void k_fixed_iso(MeshView M, Workspace W, double alpha_iso) {
+  const int64_t n = W.counters->n_iface;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t cell = W.iface_idx[i];
+    uint64_t klo = ~0ull, khi = 0ull;
+    for (int64_t j = M.cell_vert_off[cell]; j < M.cell_vert_off[cell + 1]; ++j) {
+      const uint64_t k = okey(W.phi_v[M.cell_vert[j]]);
+      klo = min(klo, k);
+      khi = max(khi, k);
+    }
+    const double lo = okey_inv(klo), hi = okey_inv(khi);
+    const bool degenerate = hi - lo < 1e-14;
+    W.iso[cell] = degenerate ? lo : alpha_iso;
+    W.status[cell] = degenerate ? VOF_ST_DEGENERATE : 0;
+    W.evals[cell] = 0;
+    if (degenerate) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
+  }
+}
+
 // Interface geometry (paper Sec. 2.1: area, unit normal and centroid of the cut polygons) at the
 // isovalues of the root search, kept apart from it: the root search's per-cell chain is FP64
 // latency, while here every cell is in flight at once. A warp takes kGeomCells consecutive
@@ -1203,8 +1224,9 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
     const Vec3 xn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]);
     const Vec3 xf = xo + (xn - xo) * t;
     W.x_f[3 * f] = xf.x; W.x_f[3 * f + 1] = xf.y; W.x_f[3 * f + 2] = xf.z;
-    W.d_own[f] = norm(xf - xo);
-    W.d_neigh[f] = norm(xf - xn);
+    const double d_o = norm(xf - xo), d_n = norm(xf - xn);
+    W.d_own[f] = d_o;
+    W.d_neigh[f] = d_n;
     const int32_t sc = src >= 0 ? src : (has_plane(W, o, step) ? o : (has_plane(W, nbr, step) ? nbr : -1));
     double af = 0;
     if (sc >= 0) {
@@ -1491,6 +1513,21 @@ __device__ __noinline__ void fold_phase(const MeshView& M, const StepArgs& a, Wo
 
 __global__ void k_xface(MeshView M, const double* alpha, int xf_mode, Workspace W) { xface_phase(M, alpha, xf_mode, W); }
 
+// Eq. interface_htc on each listed crossing face: a_f = k_phi A_int,f / d_f on both sides, k_phi
+// the conductivity of the side's phase. Nothing in the step reads it: it runs on request
+// (options.htc), on a side branch next to the least squares and the source.
+__global__ void k_htc(MeshView M, const double* alpha, double k_l, double k_v, Workspace W) {
+  const int64_t n = W.counters->n_crossing;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f = W.xface_list[j];
+    const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+    const double af = W.A_int_f[f], d_o = W.d_own[f], d_n = W.d_neigh[f];
+    const double ko = alpha[o] > 0.5 ? k_l : k_v, kn = alpha[nbr] > 0.5 ? k_l : k_v;
+    W.a_own[f] = d_o > 0 ? ko * af / d_o : 0.0;
+    W.a_neigh[f] = d_n > 0 ? kn * af / d_n : 0.0;
+  }
+}
+
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_lsq(MeshView M, StepArgs a, Workspace W) { lsq_phase<L>(M, a, W); }
 
@@ -1607,8 +1644,13 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
   // one branch per non-empty bin (root search); the branches join on s, then the geometry
-  e = cudaEventRecord(m->ev_fork, s);
-  for (int b = 0; b < kBins && e == cudaSuccess; ++b) {
+  if (opt.root_mode == VOF_ROOT_FIXED) {
+    tm.start(KC_ROOT, s);
+    k_fixed_iso<<<m->num_sms * 2, kThreads, 0, s>>>(M, W, opt.alpha_iso);
+    tm.stop(s);
+  }
+  e = opt.root_mode == VOF_ROOT_FIXED ? cudaSuccess : cudaEventRecord(m->ev_fork, s);
+  for (int b = 0; b < kBins && e == cudaSuccess && opt.root_mode != VOF_ROOT_FIXED; ++b) {
     if (!m->bin_cells[b]) continue;
     cudaStream_t sb = m->bin_stream[b];
     e = cudaStreamWaitEvent(sb, m->ev_fork, 0);
@@ -1655,9 +1697,16 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
   tm.stop(s);
   tm.start(KC_SOURCE, s);
   k_xface<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
+  if (a.opt.htc) {  // the interface heat-transfer coefficients on a side branch, joined after the source
+    cudaEventRecord(m->ev_xfork, s);
+    cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
+    k_htc<<<m->num_sms * 2, kThreads, 0, m->xm_stream>>>(M, a.alpha, a.props.k_l, a.props.k_v, W);
+    cudaEventRecord(m->ev_xjoin, m->xm_stream);
+  }
   k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
+  if (a.opt.htc) cudaStreamWaitEvent(s, m->ev_xjoin, 0);  // the side branch (k_htc) joins here
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "source kernels");
   return VOF_OK;

@@ -23,7 +23,7 @@ CASES = ["hex_sphere", "voronoi_film", "voronoi_spheres", "tet_sphere", "prism_s
 @pytest.fixture(scope="module", params=CASES)
 def run(request):
     m, a, T, Tb = case(request.param)
-    M, g = gpu_step(m, a, T, Tb)
+    M, g = gpu_step(m, a, T, Tb, htc=1)
     O = oracle.Oracle(m)
     r = O.run(a, T, Tb, synth.PROPS)
     return request.param, m, a, T, Tb, g, O, r
@@ -78,7 +78,7 @@ def test_crossing_faces(run):
     exp = pc["crossing"].astype(bool) & (band[m.face_owner] | band[np.maximum(m.face_neigh, 0)])
     got = g["face_stamp"] == g["counts"]["step"]
     assert np.array_equal(got, exp)
-    for k in ("d_own", "d_neigh", "A_int_f"):
+    for k in ("d_own", "d_neigh", "A_int_f", "a_own", "a_neigh"):
         ok, err = close(g[k][exp], pc[k][exp])
         assert ok, (k, err)
     ok, err = close(g["x_f"][exp], pc["x_f"][exp])
@@ -151,7 +151,7 @@ def test_edge_degenerate_and_uniform():
     m = synth.hex_box(6)
     a = np.full(m.n_cells, 0.3)
     T, Tb = synth.temperature(m, {}, dict(kind="linear", T0=370.0, g=[1.0, 2.0, 3.0]))
-    M, g = gpu_step(m, a, T, Tb)
+    M, g = gpu_step(m, a, T, Tb, htc=1)
     assert g["counts"]["n_iface"] == m.n_cells
     assert g["counts"]["n_degenerate"] == m.n_cells
     assert np.all(g["A_int"] == 0) and np.all(g["mdot"] == 0)
@@ -187,7 +187,7 @@ def test_repeated_steps_are_bitwise_reproducible():
 def test_host_buffer_step_matches_device_step():
     import paper_2604_14938_gb300 as vof
     m, a, T, Tb = case("voronoi_film")
-    M, g = gpu_step(m, a, T, Tb)
+    M, g = gpu_step(m, a, T, Tb, htc=1)
     pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
     ha, hT, hTb = pin(a), pin(T), pin(Tb)
     hm = torch.empty(m.n_cells, dtype=torch.float64).pin_memory()
@@ -202,7 +202,7 @@ def test_host_buffer_step_from_pageable_memory():
     view); the results are those of the device step."""
     import paper_2604_14938_gb300 as vof
     m, a, T, Tb = case("pipe_film")
-    M, g = gpu_step(m, a, T, Tb)
+    M, g = gpu_step(m, a, T, Tb, htc=1)
     hm, ht = torch.empty(m.n_cells, dtype=torch.float64), torch.empty(2, dtype=torch.float64)
     M.step_host(torch.as_tensor(a), torch.as_tensor(T), torch.as_tensor(np.ascontiguousarray(Tb)), synth.PROPS, hm, ht,
                 vof.default_options())

@@ -77,3 +77,36 @@ def test_interval_cubic_takes_the_mlp_guess():
         assert abs(O.liquid_volume(c, g1["phi_v"], g1["iso"][c])["VL"] / V[c] - a[c]) <= 1e-10
     ok, err = close(g1["mdot"], g0["mdot"])
     assert ok, err
+
+
+@pytest.mark.parametrize("name", ["hex_sphere", "voronoi_film", "tet_sphere", "pipe_film"])
+def test_fixed_isovalue_mode(name):
+    """The paper's own reconstruction (iso-surface at alpha_iso = 0.5, the scope's next row N3):
+    the geometry at 0.5 and the downstream steps match the oracle's, and the interface
+    heat-transfer coefficients a_f = k_phi A_int,f / d_f of both sides of every crossing face next
+    to the band match too."""
+    m, a, T, Tb = case(name)
+    M, g = gpu_step(m, a, T, Tb, root_mode=vof.ROOT_FIXED, htc=1)
+    O = oracle.Oracle(m)
+    I = g["iface_idx"]
+    live = I[(g["status"][I] & 1) == 0]
+    assert np.all(g["iso"][live] == 0.5)
+    assert g["counts"]["evals_total"] == 0
+    rf = O.reconstruct(a, g["phi_v"], cells=I, method="fixed")
+    V = O.geometry()["cell_vol"]
+    for c in live:
+        assert rf["A_int"][c] == pytest.approx(g["A_int"][c], rel=1e-9, abs=1e-13 * V[c] ** (2 / 3))
+        if rf["A_int"][c] > 1e-9 * V[c] ** (2 / 3):
+            np.testing.assert_allclose(g["n_int"][c], rf["n_int"][c], atol=1e-8)
+            np.testing.assert_allclose(g["x_gamma"][c], rf["x_gamma"][c], atol=1e-9 * V[c] ** (1 / 3))
+    rec = dict(status=g["status"], A_int=g["A_int"], n_int=g["n_int"], x_gamma=g["x_gamma"])
+    pc = O.phase_change(a, rec, T, Tb, synth.PROPS)
+    for k in ("mdot", "q_l", "q_v"):
+        ok, err = close(g[k][I], pc[k][I], rel=1e-10)
+        assert ok, (k, err)
+    band = pc["in_band"].astype(bool)
+    exp = pc["crossing"].astype(bool) & (band[m.face_owner] | band[np.maximum(m.face_neigh, 0)])
+    assert np.array_equal(g["face_stamp"] == g["counts"]["step"], exp)
+    for k in ("a_own", "a_neigh"):
+        ok, err = close(g[k][exp], pc[k][exp], rel=1e-10)
+        assert ok, (k, err)
