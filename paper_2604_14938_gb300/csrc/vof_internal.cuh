@@ -180,8 +180,8 @@ struct vof_mesh {
   vof::Timing timing;
   vof::GraphCache graph;       // vof_step_graph
   vof::GraphCache host_graph;  // vof_step_host with pinned buffers
-  // the bins' root searches and geometries run as parallel branches (fork after binning, join
-  // before the least squares), so that one bin's slow cells overlap the other bins' work
+  // the bins' root searches run as parallel branches (fork after binning, join before the
+  // interface geometry), so that one bin's slow cells overlap the other bins' work
   cudaStream_t bin_stream[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[vof::kBins] = {nullptr, nullptr, nullptr, nullptr, nullptr};

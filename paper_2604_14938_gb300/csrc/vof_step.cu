@@ -1,6 +1,7 @@
-// Step kernels of the hot path: interface selection, vertex field, isovalue root search with the
-// interface geometry, interface-modified least squares, per-side gradients and phase-change
-// source, deterministic totals.
+// Step kernels of the hot path: interface selection, vertex field, isovalue root search (bisection,
+// learned guess with secant steps, interval cubic, or a fixed isovalue), interface geometry,
+// crossing faces and their heat-transfer coefficients, interface-modified least squares, per-side
+// gradients and phase-change source, deterministic totals.
 //
 // Cut volume (paper Sec. 2.1, Eq. edge_intersection; reading: tetrahedralisation by the cell's
 // own vertices, phi linear per tetrahedron): for a tetrahedron with corner values p_i and k corners
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   }
 }
 
-// ---- isovalue root search + interface geometry (R2, R3) ------------------------------------------
+// ---- isovalue root search (R2, R3); the interface geometry follows in k_geom -----------------------
 // Once per cell and step every tetrahedron's corner values are sorted (s0 >= s1 >= s2 >= s3) and
 // its wet volume is written, for each number k of corners at or above c, as a cubic in a local
 // variable x = ref_k - c:
