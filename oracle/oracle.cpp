@@ -22,8 +22,9 @@
 //   R7  interface-modified least squares gradient (Appendix B), explicit symmetric inverse
 //   R8  totals by a fixed pairwise tree
 //
-// Functions with no independent pin: R1 on general meshes (invariants only), R5 (a reading of
-// the extrapolation step), the both-interface-cells rule of R4 — these are "parity unpinned".
+// Pinned only in special cases (invariants otherwise): R1 (the plain mean on a uniform hex mesh),
+// R5, a reading of the extrapolation step (equal neighbour gradients), R4 (a point on the common
+// plane); R4's choice between two different planes has no independent pin ("parity unpinned").
 #include <algorithm>
 #include <array>
 #include <cmath>

@@ -319,9 +319,24 @@ def test_P5_linear_field_exact_modified(axis):
     prof = dict(kind="linear", T0=synth.T_SAT - 7.0 * xg, g=gvec)
     T, Tb = synth.temperature(m, {}, prof)
     r = O.run(a, T, Tb, synth.PROPS)
-    band = r["pc"]["in_band"].astype(bool)
+    pc = r["pc"]
+    band = pc["in_band"].astype(bool)
     assert band.sum() > 0
-    np.testing.assert_allclose(r["pc"]["grad"][band], np.broadcast_to(gvec, (band.sum(), 3)), atol=1e-9)
+    np.testing.assert_allclose(pc["grad"][band], np.broadcast_to(gvec, (band.sum(), 3)), atol=1e-9)
+    # R4 and R5 in the same setting: both interface cells of a crossing face carry the same plane,
+    # so the crossing point lies on x_axis = x_g whichever is chosen; and the other side's gradient,
+    # an upwind average of equal neighbour gradients, is that gradient again: q_l and q_v follow in
+    # closed form (n = +e_axis, the liquid side high; A_int = the cross-section 1/n^2)
+    cross = np.where(pc["crossing"])[0]
+    assert len(cross) == n * n
+    # the plane's position carries the root's volume tolerance 1e-12 (in units of the cell width)
+    np.testing.assert_allclose(pc["x_f"][cross][:, axis], xg, rtol=0, atol=2e-12 / n)
+    I = np.where((a > 1e-12) & (a < 1 - 1e-12))[0]
+    for k in ("grad_l", "grad_v"):
+        np.testing.assert_allclose(pc[k][I], np.broadcast_to(gvec, (len(I), 3)), atol=1e-9)
+    np.testing.assert_allclose(pc["q_l"][I], synth.PROPS["k_l"] * 7.0 / n ** 2, rtol=1e-10)
+    np.testing.assert_allclose(pc["q_v"][I], -synth.PROPS["k_v"] * 7.0 / n ** 2, rtol=1e-10)
+    assert not np.any(pc["status"][I] & oracle.ST_NO_SIDE)
 
 
 def _column(d_over_h, T_P, T_far, Ts=373.15, h=1.0, standard=False):
@@ -524,6 +539,23 @@ def test_P9_special_cases(hex_sphere):
     Tc = np.full(m.n_cells, synth.T_SAT)
     r2 = O.phase_change(a, r["recon"], Tc, np.full(m.n_faces, synth.T_SAT), synth.PROPS)
     assert np.all(r2["mdot"] == 0.0) and r2["totals"][0] == 0.0
+
+
+def test_R1_uniform_hex_is_the_plain_mean():
+    """R1, a special case with a textbook answer: on a uniform hex mesh an interior vertex is
+    equidistant from its eight cell centroids, so the inverse-distance field is their plain mean;
+    a boundary vertex of a face's centre line is equidistant from its two or four cells too."""
+    m = synth.hex_box(4)
+    O = oracle.Oracle(m)
+    a = np.random.default_rng(5).uniform(size=m.n_cells)
+    phi = O.vertex_field(a)
+    cells_of = [[] for _ in range(m.n_verts)]
+    for c in range(m.n_cells):
+        for v in cell_vertex_ids(m, c):
+            cells_of[v].append(c)
+    for v, cs in enumerate(cells_of):
+        assert phi[v] == pytest.approx(np.mean(a[cs]), rel=1e-14), v
+    np.testing.assert_allclose(phi, O.vertex_field(a, mode=1), rtol=1e-14)
 
 
 def test_R1_vertex_field_invariants():
