@@ -34,6 +34,10 @@ METRIC = "interface cells/s (recon+LSQ∇T+mdot), learned vs bisection, at |Δα
 UNIT = "interface cells/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
+# Algorithmic work of one FP64 cut-volume evaluation of a Voronoi cell of about 14 faces: 36
+# straddle tests, ~15 cut points and ~90 fan tetrahedra at ~20 flops, about 2 kFLOP (the survey's
+# per-unit figure; a learned cell needs 3-4 such evaluations, a bisection cell about 40)
+ALG_FLOPS_PER_EVAL = 2000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step's root-search launches,
 # all bins, measured with ncu --set full on a GB300 for the workload, path and lanes per cell given;
 # the roofline reports null traffic for anything else
@@ -342,7 +346,10 @@ def main():
     # launch per non-empty bin (bins run as parallel branches: their launch times are summed)
     nst = max(r["ktime"]["select"][1], 1)
     root_ms = r["ktime"]["root"][0] / nst
-    flops = M.root_flops(r["kcounts"])
+    # algorithmic work: the per-evaluation figure times the FP64 evaluations the step made (device
+    # counter); the kernel's own count of its FP64 arithmetic is reported beside it
+    flops = ALG_FLOPS_PER_EVAL * r["kcounts"]["evals_total"]
+    counted = M.root_flops(r["kcounts"])
     achieved = flops / (root_ms / 1e3) / 1e12 if root_ms and flops else None
     ksum = sum(v[0] for v in r["ktime"].values())
     share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
@@ -368,6 +375,9 @@ def main():
         "kernel_share": share,
         "roofline": {"kernel": "k_root (isovalue root search)", "bound": "alu",
                      "flops_per_launch": flops, "flops_per_iface_cell": flops / max(r["kcounts"]["n_iface"], 1),
+                     "flops_basis": f"{ALG_FLOPS_PER_EVAL} algorithmic flops per FP64 cut-volume evaluation x "
+                                    "the evaluations of one step (all bins)",
+                     "flops_counted_per_iface_cell": counted / max(r["kcounts"]["n_iface"], 1),
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                      "traffic": ROOT_TRAFFIC.get((args.workload, best, tuple(info["tuned"][best]))),
