@@ -46,6 +46,11 @@ class _OrcMesh(ctypes.Structure):
                 ("cell_face_off", ctypes.c_void_p), ("cell_face", ctypes.c_void_p)]
 
 
+class _OrcExtrap(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("dtau", ctypes.c_double),
+                ("iters", ctypes.c_int32 * 6)]
+
+
 class _OrcProps(ctypes.Structure):
     _fields_ = [("k_l", ctypes.c_double), ("k_v", ctypes.c_double), ("h_lv", ctypes.c_double),
                 ("T_sat", ctypes.c_double)]
@@ -63,7 +68,10 @@ def _lib():
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double]
                                           + [ctypes.c_void_p] * 7)
         _LIB.orc_phase_change.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 6
-                                          + [ctypes.c_int] + [ctypes.c_void_p] * 15)
+                                          + [ctypes.c_int] + [ctypes.c_void_p] * 16)
+        _LIB.orc_extrap_dtau.argtypes = [ctypes.c_void_p] * 4
+        _LIB.orc_extrapolate.argtypes = ([ctypes.c_void_p] * 7 + [ctypes.c_double, ctypes.c_int, ctypes.c_double]
+                                         + [ctypes.c_void_p] * 3)
         _LIB.orc_vertex_field.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
         _LIB.orc_geometry.argtypes = [ctypes.c_void_p] * 5
         _LIB.orc_pairwise_sum.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
@@ -135,8 +143,33 @@ class Oracle:
                                  *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
         return r
 
-    def phase_change(self, alpha, recon: dict, T, T_bnd, props: dict, eps=1e-12, xf_mode=XF_RECON) -> dict:
-        """R4-R8 given a reconstruction (oracle's own, or another one to be judged)."""
+    def extrap_dtau(self) -> float:
+        """Pseudo-time step of Eq. (extrapolation): min over faces of |d_f|."""
+        g = self.geometry()
+        out = np.zeros(1)
+        _lib().orc_extrap_dtau(self.ref, _p(g["cell_cen"]), _p(g["face_cen"]), _p(out))
+        return float(out[0])
+
+    def extrapolate(self, alpha, iface, n_int, grad, dtau=None, max_iter=120, tol=1e-3) -> dict:
+        """The pseudo-time solve of Eq. (extrapolation) alone, on a given gradient field: the other
+        side's gradient of every cell with iface != 0 (g_other), the six iteration counts (iters) and
+        the no-side flags (status)."""
+        g = self.geometry()
+        nc = self.c.n_cells
+        o = dict(g_other=np.zeros((nc, 3)), iters=np.zeros(6, np.int32), status=np.zeros(nc, np.int32))
+        arr = lambda x: np.ascontiguousarray(x, np.float64)
+        _lib().orc_extrapolate(self.ref, _p(g["face_area"]), _p(g["cell_vol"]), _p(arr(alpha)),
+                               _p(np.ascontiguousarray(iface, np.uint8)), _p(arr(n_int)), _p(arr(grad)),
+                               self.extrap_dtau() if dtau is None else float(dtau), int(max_iter), float(tol),
+                               _p(o["g_other"]), _p(o["iters"]), _p(o["status"]))
+        return o
+
+    def phase_change(self, alpha, recon: dict, T, T_bnd, props: dict, eps=1e-12, xf_mode=XF_RECON,
+                     extrap=None) -> dict:
+        """R4-R8 given a reconstruction (oracle's own, or another one to be judged). `extrap`: None for
+        R5's single upwind sweep, else a dict (max_iter, tol, dtau; dtau <= 0 or absent: the mesh's)
+        for the pseudo-time solve of Eq. (extrapolation); its six iteration counts come back as
+        `extrap_iters` (liquid x, y, z, vapour x, y, z)."""
         g = self.geometry()
         nc, nf = self.c.n_cells, self.c.n_faces
         o = dict(in_band=np.zeros(nc, np.uint8), grad=np.zeros((nc, 3)), grad_l=np.zeros((nc, 3)),
@@ -146,13 +179,20 @@ class Oracle:
                  totals=np.zeros(2))
         pr = _OrcProps(props["k_l"], props["k_v"], props["h_lv"], props["T_sat"])
         arr = lambda x: np.ascontiguousarray(x, np.float64)
+        ex = None
+        if extrap is not None:
+            ex = _OrcExtrap(int(extrap.get("max_iter", 120)), float(extrap.get("tol", 1e-3)),
+                            float(extrap.get("dtau", 0.0)))
         _lib().orc_phase_change(self.ref, _p(g["face_area"]), _p(g["face_cen"]), _p(g["cell_vol"]),
                                 _p(g["cell_cen"]), _p(arr(alpha)), eps, _p(arr(recon["A_int"])),
                                 _p(arr(recon["n_int"])), _p(arr(recon["x_gamma"])), _p(arr(T)),
                                 None if T_bnd is None else _p(arr(T_bnd)), ctypes.byref(pr), xf_mode,
                                 *[_p(o[k]) for k in ("in_band", "grad", "grad_l", "grad_v", "q_l", "q_v", "mdot", "Q",
                                                      "status", "crossing", "x_f", "d_own", "d_neigh", "A_int_f",
-                                                     "totals")])
+                                                     "totals")],
+                                None if ex is None else ctypes.byref(ex))
+        if ex is not None:
+            o["extrap_iters"] = np.array(ex.iters[:], np.int32)
         o["a_own"], o["a_neigh"] = np.zeros(nf), np.zeros(nf)
         _lib().orc_interface_htc(self.ref, _p(arr(alpha)), _p(o["crossing"]), _p(o["A_int_f"]), _p(o["d_own"]),
                                  _p(o["d_neigh"]), props["k_l"], props["k_v"], _p(o["a_own"]), _p(o["a_neigh"]))

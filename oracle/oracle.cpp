@@ -17,7 +17,8 @@
 //       sorted vertex values, then the cubic V_L has between two of them, solved on its own)
 //   R4  crossing point x_f on faces with (alpha_P - 1/2)(alpha_Q - 1/2) < 0
 //   R5  per-side gradients: own phase from the modified LSQ gradient, other phase from one upwind
-//       sweep over the neighbours on that side
+//       sweep over the neighbours on that side; or (the next row N2 of the scope) from the full
+//       pseudo-time solve of Eq. (extrapolation), first-order upwind, per side and component
 //   R6  q_l, q_v, mdot, Q_phase
 //   R7  interface-modified least squares gradient (Appendix B), explicit symmetric inverse
 //   R8  totals by a fixed pairwise tree
@@ -47,6 +48,15 @@ struct OrcMesh {
 
 struct OrcProps {
   double k_l, k_v, h_lv, T_sat;
+};
+
+// Options of the pseudo-time extrapolation (N2); iters[] returns the iterations each of the six
+// solves took (liquid side x, y, z, then vapour side x, y, z).
+struct OrcExtrap {
+  int max_iter;
+  double tol;   // K/m, absolute, on the largest change of one iteration
+  double dtau;  // pseudo-time step; <= 0: the mesh's min_f |d_f|
+  int32_t iters[6];
 };
 
 }  // extern "C"
@@ -482,9 +492,93 @@ double crossing_t(const OrcMesh& m, int64_t f, const double* alpha, const double
   return *src >= 0 ? best_t : t_lin;
 }
 
+// Pseudo-time step of Eq. (extrapolation): the smallest |d_f| over the mesh's faces, d_f the vector
+// from a face's owner centroid to its neighbour centroid (to the face centroid on a boundary face,
+// where the boundary value sits).
+double extrap_dtau(const OrcMesh& m, const double* cell_cen, const double* face_cen) {
+  double d = INFINITY;
+  for (int64_t f = 0; f < m.n_faces; ++f) {
+    const int32_t o = m.face_owner[f], n = m.face_neigh[f];
+    const V3 xo = {cell_cen[3 * o], cell_cen[3 * o + 1], cell_cen[3 * o + 2]};
+    const V3 xn = n >= 0 ? V3{cell_cen[3 * n], cell_cen[3 * n + 1], cell_cen[3 * n + 2]}
+                         : V3{face_cen[3 * f], face_cen[3 * f + 1], face_cen[3 * f + 2]};
+    d = std::min(d, norm(sub(xn, xo)));
+  }
+  return d;
+}
+
+// N2: Eq. (extrapolation) in pseudo-time, once per side and per gradient component. The field phi
+// starts as the modified LSQ gradient component of every cell. Information travels from the bulk
+// of a side towards and across the interface (the text's direction): the liquid side moves along
+// -n_int, the vapour side along +n_int. The unknowns of a side are the interface cells (A_int > 0)
+// of the other phase; every cell of the side itself keeps its gradient. First-order upwind: at an
+// unknown P the inflow faces are those whose outward area A_f has w = sigma n_P . A_f > 0
+// (sigma = +1 for the liquid side, -1 for the vapour side), and a face counts when its neighbour
+// is a cell of the side (known) or an unknown of the same solve; others carry no value of this
+// side and are left out. One explicit step (Jacobi: every unknown from the previous iterate):
+//   phi_P <- phi_P + (dtau_P / V_P) sum_f w_f (phi_Q - phi_P),
+// dtau_P = min(dtau, V_P / sum_f w_f): the global step, limited where it would exceed the cell's
+// upwind Courant limit, so that each step is a convex combination. The solve stops after the
+// iteration whose largest change over its unknowns is below tol, or after max_iter. An unknown
+// with no counted inflow face keeps its initial value and is flagged ST_NO_SIDE.
+void extrapolate(const OrcMesh& m, const double* face_area, const double* cell_vol, const double* alpha,
+                 const uint8_t* iface, const double* n_int, const double* grad, double dtau, int max_iter, double tol,
+                 double* g_other, int32_t* iters, int32_t* status) {
+  const int64_t nc = m.n_cells;
+  for (int side = 0; side < 2; ++side) {  // 0 liquid, 1 vapour
+    const double sigma = side == 0 ? 1.0 : -1.0;
+    auto of_side = [&](int64_t c) { return (alpha[c] > 0.5) == (side == 0); };
+    std::vector<uint8_t> unknown(nc, 0);
+    for (int64_t c = 0; c < nc; ++c) unknown[c] = iface[c] && !of_side(c);
+    for (int j = 0; j < 3; ++j) {
+      std::vector<double> phi(nc);
+      for (int64_t c = 0; c < nc; ++c) phi[c] = grad[3 * c + j];
+      int k = 1;
+      for (;; ++k) {
+        std::vector<double> next = phi;
+        double change = 0;
+        for (int64_t P = 0; P < nc; ++P) {
+          if (!unknown[P]) continue;
+          const V3 nn = {n_int[3 * P], n_int[3 * P + 1], n_int[3 * P + 2]};
+          std::vector<std::pair<double, int32_t>> in;  // (w_f, Q) of the counted inflow faces
+          double wsum = 0;
+          for (int64_t e = m.cell_face_off[P]; e < m.cell_face_off[P + 1]; ++e) {
+            const int32_t fe = m.cell_face[e];
+            const int32_t f = fe & 0x7fffffff;
+            const int32_t Q = m.face_owner[f] == P ? m.face_neigh[f] : m.face_owner[f];
+            if (Q < 0) continue;
+            V3 Af = {face_area[3 * f], face_area[3 * f + 1], face_area[3 * f + 2]};
+            if (fe < 0) Af = mul(Af, -1.0);  // outward from P
+            const double w = sigma * dot(nn, Af);
+            if (!(w > 0)) continue;
+            if (!of_side(Q) && !unknown[Q]) continue;
+            in.push_back({w, Q});
+            wsum += w;
+          }
+          if (wsum == 0) {
+            if (j == 0 && k == 1) status[P] |= ST_NO_SIDE;
+            continue;
+          }
+          const double dtau_P = std::min(dtau, cell_vol[P] / wsum);
+          double s = 0;
+          for (const auto& [w, Q] : in) s += w * (phi[Q] - phi[P]);
+          next[P] = phi[P] + dtau_P / cell_vol[P] * s;
+          change = std::max(change, std::fabs(next[P] - phi[P]));
+        }
+        phi.swap(next);
+        if (change < tol || k >= max_iter) break;
+      }
+      iters[3 * side + j] = k;
+      for (int64_t c = 0; c < nc; ++c)
+        if (unknown[c]) g_other[3 * c + j] = phi[c];
+    }
+  }
+}
+
 // R4-R8. Inputs: geometry (from orc_geometry), alpha, reconstruction (iso/status/A_int/n_int/
 // x_gamma arrays from orc_reconstruct), T at cells, T at boundary faces (may be null: boundary
-// faces then stay out of the stencil), properties.
+// faces then stay out of the stencil), properties; ex = null for R5's single sweep, else the
+// options of the pseudo-time solve (N2), whose iteration counts it returns.
 // Outputs ([n_cells] or [3 n_cells]): band flag, grad (modified LSQ) on band cells, grad_l,
 // grad_v, q_l, q_v, mdot, Q on interface cells, status bits (ORed into `status`);
 // per face: crossing flag, x_f, d_own, d_neigh, A_int_f; totals[0..1] = sum mdot V, sum Q V.
@@ -493,7 +587,7 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
                       const double* x_gamma, const double* T, const double* T_bnd, const OrcProps* pr, int xf_mode,
                       uint8_t* in_band, double* grad, double* grad_l, double* grad_v, double* q_l, double* q_v,
                       double* mdot, double* Qph, int32_t* status, uint8_t* crossing, double* x_f, double* d_own,
-                      double* d_neigh, double* A_int_f, double* totals) {
+                      double* d_neigh, double* A_int_f, double* totals, OrcExtrap* ex) {
   const OrcMesh& m = *mp;
   const int64_t nc = m.n_cells;
   std::vector<uint8_t> iface(nc, 0);
@@ -588,6 +682,14 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
     Gi[2][1] = Gi[1][2];
     for (int i = 0; i < 3; ++i) grad[3 * c + i] = Gi[i][0] * b[0] + Gi[i][1] * b[1] + Gi[i][2] * b[2];
   }
+  // N2 (when asked): the other side's gradient of every interface cell from the pseudo-time solve
+  std::vector<double> g_n2;
+  if (ex) {
+    g_n2.assign(3 * nc, 0.0);
+    const double dtau = ex->dtau > 0 ? ex->dtau : extrap_dtau(m, cell_cen, face_cen);
+    extrapolate(m, face_area, cell_vol, alpha, iface.data(), n_int, grad, dtau, ex->max_iter, ex->tol, g_n2.data(),
+                ex->iters, status);
+  }
   // R5 + R6 on interface cells
   std::vector<double> mv, qv;
   for (int64_t c = 0; c < nc; ++c) {
@@ -613,7 +715,8 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
         wsum += w;
       }
       V3 g_other = {0, 0, 0};
-      if (wsum > 0) g_other = mul(acc, 1.0 / wsum);
+      if (ex) g_other = {g_n2[3 * c], g_n2[3 * c + 1], g_n2[3 * c + 2]};
+      else if (wsum > 0) g_other = mul(acc, 1.0 / wsum);
       else status[c] |= ST_NO_SIDE;
       const V3 g_own = {grad[3 * c], grad[3 * c + 1], grad[3 * c + 2]};
       const V3 gl = P_liquid ? g_own : g_other;
@@ -648,6 +751,18 @@ void orc_interface_htc(const OrcMesh* mp, const double* alpha, const uint8_t* cr
     if (d_own[f] > 0) a_own[f] = ko * A_int_f[f] / d_own[f];
     if (d_neigh[f] > 0) a_neigh[f] = kn * A_int_f[f] / d_neigh[f];
   }
+}
+
+// N2 alone, on a given gradient field: g_other [3 n_cells] receives the other side's gradient of
+// every interface cell (iface[c] != 0; its phase: liquid when alpha > 1/2), iters[6] the counts.
+void orc_extrapolate(const OrcMesh* m, const double* face_area, const double* cell_vol, const double* alpha,
+                     const uint8_t* iface, const double* n_int, const double* grad, double dtau, int max_iter,
+                     double tol, double* g_other, int32_t* iters, int32_t* status) {
+  extrapolate(*m, face_area, cell_vol, alpha, iface, n_int, grad, dtau, max_iter, tol, g_other, iters, status);
+}
+
+void orc_extrap_dtau(const OrcMesh* m, const double* cell_cen, const double* face_cen, double* out) {
+  *out = extrap_dtau(*m, cell_cen, face_cen);
 }
 
 void orc_pairwise_sum(const double* a, int64_t n, double* out) { *out = pairwise_sum(std::vector<double>(a, a + n)); }
