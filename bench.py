@@ -136,15 +136,22 @@ def run_ours(args, rank, world, dev):
         btot = torch.empty((B.n, 2), dtype=torch.float64, device=dev) if batch else None
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
         learned_ok = args.root in ("auto", "learned") and vof.load_default_mlp(M)
+        # learned_extrap: the learned path with the pseudo-time solve of Eq. (extrapolation) for the
+        # other-side gradients instead of the single upwind sweep (same lanes per cell as learned)
         modes = ((["bisect"] if args.root in ("auto", "bisect") else []) + (["learned"] if learned_ok else [])
+                 + (["learned_extrap"] if learned_ok and args.root == "auto" else [])
                  + (["cubic"] if args.root in ("auto", "cubic") else []))
         tuned = {}
         for mode in modes:
             opt = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
-                                                 "cubic": vof.ROOT_CUBIC}[mode])
+                                                 "learned_extrap": vof.ROOT_LEARNED, "cubic": vof.ROOT_CUBIC}[mode],
+                                      extrap=int(mode == "learned_extrap"))
             if mode == "cubic":  # from 1 - alpha: on these workloads the guess costs more than it saves
                 M.set_mlp(None)
-            if args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
+            if mode == "learned_extrap":
+                tuned[mode] = tuned["learned"]
+                M.set_group_sizes(tuned[mode])
+            elif args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
                 tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
                 M.set_group_sizes(tuned[mode])
             else:
@@ -369,7 +376,10 @@ def main():
                       "evals_per_cell": v["counts"]["evals_total"] / max(v["counts"]["n_iface"], 1),
                       "fp32_evals_per_cell": v["counts"]["evals32_total"] / max(v["counts"]["n_iface"], 1),
                       "fallbacks": v["counts"]["n_fallback"], "not_converged": v["counts"]["n_not_converged"],
-                      "mlp_skipped": v["counts"]["n_mlp_skipped"], "group_sizes_by_bin": info["tuned"][k]}
+                      "mlp_skipped": v["counts"]["n_mlp_skipped"], "group_sizes_by_bin": info["tuned"][k],
+                      **({"extrap_iters": v["counts"]["extrap_iters"],
+                          "extrap_kernel_ms": v["ktime"]["extrap"][0] / max(v["ktime"]["select"][1], 1)}
+                         if k == "learned_extrap" else {})}
                   for k, v in res.items()},
         "kernel_ms_per_step": {k: v[0] / nst for k, v in r["ktime"].items() if v[1]},
         "kernel_share": share,

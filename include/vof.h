@@ -61,7 +61,8 @@ typedef enum {
 #define VOF_ST_NOT_CONVERGED 2 /* |V_L(c)/V - alpha| > tol after the iteration cap */
 #define VOF_ST_FALLBACK 4      /* learned guess + secant missed tol; bracketed bisection finished it */
 #define VOF_ST_SINGULAR_LSQ 8  /* det(G) <= 1e-12 (tr G / 3)^3: gradient set to 0 */
-#define VOF_ST_NO_SIDE 16      /* no face neighbour looks into the other phase: its gradient is 0 */
+#define VOF_ST_NO_SIDE 16      /* no face neighbour looks into the other phase: its gradient is 0
+                                * (options.extrap = 1: no counted inflow face, it keeps its own) */
 #define VOF_ST_MLP_SKIPPED 32  /* more than 32 vertices: learned guess not used */
 
 /* Crossing-point modes (Eq. front_interpolation). */
@@ -118,6 +119,22 @@ typedef struct {
   int htc;           /* 1: also compute the interface heat-transfer coefficients VOF_F_A_OWN and
                       * VOF_F_A_NEIGH (Eq. interface_htc) on a side branch of the step (default 0) */
   double alpha_iso;  /* isovalue of VOF_ROOT_FIXED, in (0, 1) (default 0.5) */
+  /* Other-side gradient of an interface cell (Sec. 2.3, Eq. extrapolation):
+   *   0 (default): one upwind sweep, the weighted mean of the gradients of the face neighbours on
+   *     that side, weights max(0, +-n_int . A_f);
+   *   1: the pseudo-time solve of Eq. (extrapolation), first-order upwind, one solve per side and
+   *     gradient component. Unknowns: the interface cells of the other phase; every cell of the
+   *     side keeps its modified least-squares gradient, which is also the unknowns' start value.
+   *     The liquid side moves along -n_int, the vapour side along +n_int (from the bulk of the side
+   *     towards the interface). Step dtau = min over faces of |d_f| (owner centroid to neighbour
+   *     centroid, or to the face centroid on a boundary face: VOF_F_DTAU), limited per cell to
+   *     V_P / sum of its inflow weights. A solve stops after the iteration whose largest change is
+   *     below extrap_tol, or after extrap_max_iter; vof_counts.extrap_iters holds the counts.
+   *     Needs cells of at most 64 faces (VOF_EINVAL otherwise). In a batch the step is the
+   *     smallest over all meshes of the batch (the batch is one mesh to the step). */
+  int extrap;
+  int extrap_max_iter; /* 1 .. 1000 (default 120) */
+  double extrap_tol;   /* K/m, absolute, > 0 (default 1e-3) */
 } vof_options;
 
 /* Fills *o with the defaults above. */
@@ -226,7 +243,8 @@ typedef enum {
                         * the band, in steps run with options.htc = 1: each side adds a_f to its
                         * energy-matrix diagonal and a_f T_sat to its right-hand side, the face being
                         * detached from the diffusive coupling */
-  VOF_F_N = 26
+  VOF_F_DTAU = 26,     /* double [1]: pseudo-time step of Eq. (extrapolation), min over faces of |d_f| */
+  VOF_F_N = 27
 } vof_field;
 
 /* Element count of a field in the current state (n_iface for the interface list). */
@@ -246,6 +264,9 @@ typedef struct {
    * interface */
   int64_t tet_evals, tets_prepared, tets_sectioned;
   int64_t evals32_total; /* FP32 evaluations of the learned path's refinement */
+  /* iterations of the six pseudo-time solves of options.extrap = 1 (liquid side x, y, z, then
+   * vapour side x, y, z); 0 in steps with options.extrap = 0 */
+  int64_t extrap_iters[6];
 } vof_counts;
 vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
 
@@ -318,7 +339,7 @@ vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, do
  * milliseconds and the launch count since the last read (at most 8192 records are kept).
  * Classes: 0 selection, band and vertex field, 2 root search, 3 list of the crossing faces,
  * 4 crossing faces, least squares, per-side gradients, source and totals, 6 learned guess,
- * 7 interface geometry; 1 and 5 are unused. */
+ * 7 interface geometry, 8 pseudo-time extrapolation (options.extrap = 1); 1 and 5 are unused. */
 vof_status vof_timing_enable(vof_mesh* mesh, int on);
 vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
 

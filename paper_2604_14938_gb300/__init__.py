@@ -29,7 +29,7 @@ FIELDS = {
     "d_neigh": (15, np.float64, 1), "A_int_f": (16, np.float64, 1), "face_stamp": (17, np.int32, 1),
     "cell_vol": (18, np.float64, 1), "cell_cen": (19, np.float64, 3), "face_area": (20, np.float64, 3),
     "face_cen": (21, np.float64, 3), "iface_stamp": (22, np.int32, 1), "band_stamp": (23, np.int32, 1),
-    "a_own": (24, np.float64, 1), "a_neigh": (25, np.float64, 1),
+    "a_own": (24, np.float64, 1), "a_neigh": (25, np.float64, 1), "dtau": (26, np.float64, 1),
 }
 
 
@@ -54,14 +54,16 @@ class Options(ctypes.Structure):
     _fields_ = [("alpha_eps", ctypes.c_double), ("tol_alpha", ctypes.c_double), ("max_bisect", ctypes.c_int),
                 ("root_mode", ctypes.c_int), ("max_secant", ctypes.c_int), ("xf_mode", ctypes.c_int),
                 ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int), ("htc", ctypes.c_int),
-                ("alpha_iso", ctypes.c_double)]
+                ("alpha_iso", ctypes.c_double), ("extrap", ctypes.c_int), ("extrap_max_iter", ctypes.c_int),
+                ("extrap_tol", ctypes.c_double)]
 
 
 class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("step", "n_iface", "n_band", "n_crossing", "n_degenerate",
                                                "n_not_converged", "n_fallback", "n_singular", "n_no_side",
                                                "n_mlp_skipped", "evals_total", "tet_evals", "tets_prepared",
-                                               "tets_sectioned", "evals32_total")]
+                                               "tets_sectioned", "evals32_total")] + [
+        ("extrap_iters", ctypes.c_int64 * 6)]
 
 
 def lib():
@@ -195,7 +197,7 @@ class Mesh:
         _check(lib().vof_copy_field(self.h, fid, _ptr(out), cnt.value, _stream(stream)), "vof_copy_field")
         return out.view(-1, width) if width > 1 else out
 
-    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp", "geom")
+    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp", "geom", "extrap")
 
     def timing_enable(self, on: bool = True):
         _check(lib().vof_timing_enable(self.h, int(on)), "vof_timing_enable")
@@ -227,7 +229,9 @@ class Mesh:
     def counts(self, stream=None) -> dict:
         c = Counts()
         _check(lib().vof_get_counts(self.h, ctypes.byref(c), _stream(stream)), "vof_get_counts")
-        return {n: getattr(c, n) for n, _ in Counts._fields_}
+        out = {n: getattr(c, n) for n, _ in Counts._fields_}
+        out["extrap_iters"] = list(c.extrap_iters)
+        return out
 
 
 # ---------------------------------------------------------------------------------- learned guess

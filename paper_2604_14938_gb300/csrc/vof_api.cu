@@ -44,6 +44,7 @@ FieldDesc field_of(vof_mesh* m, int f, int64_t n_iface) {
     case VOF_F_BAND_STAMP: return {W.band_stamp, nc, 4};
     case VOF_F_A_OWN: return {W.a_own, nf, 8};
     case VOF_F_A_NEIGH: return {W.a_neigh, nf, 8};
+    case VOF_F_DTAU: return {W.ex_dtau, 1, 8};
     default: return {nullptr, 0, 0};
   }
 }
@@ -164,6 +165,7 @@ vof_status vof_get_counts(vof_mesh* m, vof_counts* out, void* stream) {
   out->tets_prepared = c.tets_prepared;
   out->tets_sectioned = c.tets_sectioned;
   out->evals32_total = c.evals32_total;
+  for (int k = 0; k < 6; ++k) out->extrap_iters[k] = c.extrap_iters[k];
   return VOF_OK;
 }
 

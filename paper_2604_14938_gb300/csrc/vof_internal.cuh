@@ -36,6 +36,7 @@ struct Counters {
   int64_t evals32_total;  // FP32 evaluations of the learned path's refinement
   int64_t bin_count[5];   // interface cells per tetrahedron-count bin
   int64_t bin_next[5];    // next bin-list position to take (cells fetched dynamically by the root search)
+  int64_t extrap_iters[6];  // iterations of the pseudo-time solves (liquid x, y, z, vapour x, y, z)
 };
 
 // Everything a step kernel reads or writes, by value (device pointers).
@@ -66,6 +67,7 @@ struct MeshView {
 struct Workspace {
   Counters* counters;
   int32_t* iface_idx;      // [n_cells]
+  int32_t* iface_slot;     // [n_cells] position of an interface cell in iface_idx (valid on this step's)
   uint32_t* iface_stamp;   // [n_cells]
   uint32_t* band_stamp;    // [n_cells]
   uint32_t* vert_stamp;    // [n_verts]
@@ -102,6 +104,14 @@ struct Workspace {
   float* mlp_x;            // [n_cells][40] features of interface cells (allocated with an MLP)
   int32_t* mlp_ok;         // [n_cells] 1 where the cell has features
   float* mlp_y;            // [n_cells] raw MLP outputs
+  // pseudo-time extrapolation (options.extrap = 1), per interface-list slot
+  double* ex_x;            // [2][n_cells][4] iterates of the slot's other-side gradient (ping-pong, padded)
+  double* ex_k;            // [n_cells][5]: C = sum of step weights, f = dtau_P / V_P, b (3) = known inflow
+  int32_t* ex_nb;          // [n_cells][kExCap] slots of the first unknown neighbours (-1: none)
+  double* ex_g;            // [n_cells][kExCap] their step weights f_P w_f
+  unsigned long long* ex_mask;  // [n_cells] face positions of further unknown neighbours
+  unsigned long long* ex_itmax; // [kExMaxIter + 1] per iteration: barrier word (arrivals, blocks still moving)
+  double* ex_dtau;         // [1] min over faces of |d_f|
   // device staging for the host-buffer step
   double *io_alpha, *io_T, *io_Tb, *io_mdot, *io_Q, *io_totals;
 };
@@ -114,6 +124,9 @@ __host__ __device__ inline int bin_of(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 
 constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
 constexpr int kSrcTile = 16;        // interface cells per source tile (an aligned subtree of the totals)
 constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
+constexpr int kExMaxIter = 1000;    // cap of options.extrap_max_iter
+constexpr int kExMaxFaces = 64;     // faces per cell the extrapolation's face masks cover
+constexpr int kExCap = 8;           // unknown neighbours per slot gathered once (the rest: face mask)
 
 struct StepArgs {
   const double* alpha;
@@ -130,7 +143,7 @@ struct StepArgs {
 
 namespace vof {
 // Optional per-kernel device timing: pairs of CUDA events recorded on the launch stream.
-enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_GEOM, KC_N };
+enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_GEOM, KC_EXTRAP, KC_N };
 struct Timing {
   bool on = false;
   int cap = 0, used = 0;
@@ -169,6 +182,7 @@ struct vof_mesh {
   int num_sms = 0;
   int sel_grid = 0;   // blocks of the cooperative selection launch (all resident)
   int geom_grid = 0;  // blocks of the interface-geometry launch
+  int ex_grid = 0;    // blocks of the cooperative extrapolation launch
   int32_t* bnd_faces = nullptr;  // device list of the boundary faces (face_neigh < 0)
   int64_t n_bnd = 0;
   vof::MeshView view{};

@@ -103,6 +103,20 @@ __global__ void k_rel_pos(int64_t nc, const int64_t* cvo, const int32_t* cv, con
 }
 
 // Inverse-distance weights of the cells around each vertex, normalised to sum 1.
+// |d_f| of each face: owner centroid to neighbour centroid, or to the face centroid on a boundary
+// face; the minimum over the faces by atomicMin on the raw bits.
+__global__ void k_dtau_init(double* out) { *out = INFINITY; }
+__global__ void k_dtau(int64_t nf, const int32_t* own, const int32_t* nei, const double* cen, const double* fcen,
+                       double* out) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int32_t o = own[f], n = nei[f];
+  const double* xn = n >= 0 ? cen + 3 * n : fcen + 3 * f;
+  const double dx = xn[0] - cen[3 * o], dy = xn[1] - cen[3 * o + 1], dz = xn[2] - cen[3 * o + 2];
+  const double d = sqrt(dx * dx + dy * dy + dz * dz);
+  atomicMin((unsigned long long*)out, (unsigned long long)__double_as_longlong(d));
+}
+
 __global__ void k_idw(int64_t nv, const int64_t* vco, const int32_t* vc, const double* vx, const double* vy,
                       const double* vz, const double* cen, double* w) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -384,6 +398,18 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.io_totals, 2));
   TRY(dev_alloc(m, &W.mlp_out, nc));
   TRY(dev_alloc(m, &W.bin_list, (size_t)kBins * nc));
+  TRY(dev_alloc(m, &W.iface_slot, nc));
+  TRY(dev_alloc(m, &W.ex_x, 8 * (size_t)nc));
+  TRY(dev_alloc(m, &W.ex_k, 5 * (size_t)nc));
+  TRY(dev_alloc(m, &W.ex_nb, kExCap * (size_t)nc));
+  TRY(dev_alloc(m, &W.ex_g, kExCap * (size_t)nc));
+  TRY(dev_alloc(m, &W.ex_mask, nc));
+  TRY(dev_alloc(m, &W.ex_itmax, 6 * (size_t)(kExMaxIter + 1)));
+  TRY(dev_alloc(m, &W.ex_dtau, 1));
+  // pseudo-time step of the extrapolation: min over faces of |d_f|, by an atomic minimum of the
+  // raw bits (non-negative doubles order as their bit patterns)
+  k_dtau_init<<<1, 1, 0, s>>>(W.ex_dtau);
+  k_dtau<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_own, d_nei, d_cen, d_fc, W.ex_dtau);
   cudaMemsetAsync(W.counters, 0, sizeof(Counters), s);
   cudaMemsetAsync(W.iface_stamp, 0, nc * sizeof(uint32_t), s);
   cudaMemsetAsync(W.band_stamp, 0, nc * sizeof(uint32_t), s);
@@ -446,6 +472,9 @@ void vof_default_options(vof_options* o) {
   o->xf_mode = VOF_XF_RECON;
   o->vertex_mode = 0;
   o->group_size = 0;
+  o->extrap = 0;
+  o->extrap_max_iter = 120;
+  o->extrap_tol = 1e-3;
 }
 
 vof_status vof_mesh_create(const vof_mesh_desc* desc, void* stream, vof_mesh** out) {
@@ -495,7 +524,9 @@ static vof_status check_opt(const vof_options* o) {
   if (!o) { set_error("null options"); return VOF_EINVAL; }
   if (!(o->alpha_eps >= 0 && o->alpha_eps < 0.5) || !(o->tol_alpha > 0) || o->max_bisect < 1 || o->max_bisect > 1000 ||
       o->root_mode < VOF_ROOT_BISECT || o->root_mode > VOF_ROOT_FIXED || !(o->alpha_iso > 0.0 && o->alpha_iso < 1.0) ||
-      o->max_secant < 0 || o->max_secant > 8 || o->htc < 0 || o->htc > 1 ||
+      o->max_secant < 0 || o->max_secant > 8 || o->htc < 0 || o->htc > 1 || o->extrap < 0 || o->extrap > 1 ||
+      o->extrap_max_iter < 1 || o->extrap_max_iter > kExMaxIter || !(o->extrap_tol > 0) ||
+      !std::isfinite(o->extrap_tol) ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {
@@ -518,6 +549,10 @@ static vof_status check_source_args(const vof_mesh* m, const double* d_alpha, co
                                     const double* d_totals) {
   if (!m || !d_alpha || !d_T || !props || !d_mdot || !d_Q || !d_totals) { set_error("null argument"); return VOF_EINVAL; }
   if (vof_status st = check_opt(opt)) return st;
+  if (opt->extrap && m->max_cf > kExMaxFaces) {
+    set_error("options.extrap = 1 needs cells of at most 64 faces");
+    return VOF_EINVAL;
+  }
   if (!(props->h_lv > 0) || !(props->k_l >= 0) || !(props->k_v >= 0) || !std::isfinite(props->T_sat)) {
     set_error("bad properties");
     return VOF_EINVAL;

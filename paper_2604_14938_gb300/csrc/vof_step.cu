@@ -88,6 +88,7 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
   cn->evals_total = 0;
   cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
   for (int b = 0; b < kBins; ++b) cn->bin_count[b] = cn->bin_next[b] = 0;
+  for (int k = 0; k < 6; ++k) cn->extrap_iters[k] = 0;
 }
 
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
       if ((f >> k) & 1u) {
         const int64_t c = c0 + k;
         W.iface_idx[p + __popc(f & ((1u << k) - 1u))] = (int32_t)c;
+        W.iface_slot[c] = (int32_t)(p + __popc(f & ((1u << k) - 1u)));
         W.iface_stamp[c] = step;
         const int b = bin_of((int)(M.cell_tet_off[c + 1] - M.cell_tet_off[c]));
         bslot[k] = (b << 24) | atomicAdd(&s_bin[b], 1);
@@ -1379,7 +1381,7 @@ __device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W)
     {
       const int64_t i = tile * kSrcTile + slot;
       double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-      if (i < n) {
+      if (i < n && !a.opt.extrap) {  // with the pseudo-time solve the other side is already known
         const int32_t c = W.iface_idx[i];
         if (W.A_int[c] > 0) {
           const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
@@ -1431,11 +1433,15 @@ __device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W)
           const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
           gl = liq ? gown : go;
           gv = liq ? go : gown;
+          if (a.opt.extrap) {  // both sides written by the pseudo-time solve
+            gl = v3(W.grad_l[3 * c], W.grad_l[3 * c + 1], W.grad_l[3 * c + 2]);
+            gv = v3(W.grad_v[3 * c], W.grad_v[3 * c + 1], W.grad_v[3 * c + 2]);
+          }
           ql = a.props.k_l * dot(gl, nn) * Aint;
           qv = -a.props.k_v * dot(gv, nn) * Aint;
           mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
           Q = -mdot * a.props.h_lv;
-          if (!(ws > 0)) {
+          if (!(ws > 0) && !a.opt.extrap) {
             W.status[c] |= VOF_ST_NO_SIDE;
             ++nside;
           }
@@ -1526,6 +1532,317 @@ __global__ void k_htc(MeshView M, const double* alpha, double k_l, double k_v, W
     const double ko = alpha[o] > 0.5 ? k_l : k_v, kn = alpha[nbr] > 0.5 ? k_l : k_v;
     W.a_own[f] = d_o > 0 ? ko * af / d_o : 0.0;
     W.a_neigh[f] = d_n > 0 ? kn * af / d_n : 0.0;
+  }
+}
+
+// ---- pseudo-time extrapolation of the per-side gradients (Eq. extrapolation) ------------------
+// One solve per side and gradient component, all six in one cooperative launch. The unknowns of
+// a side are the interface cells of the other phase, one per interface-list slot (its other
+// side), and they start from the slot's own modified least-squares gradient. First-order upwind
+// explicit step (Jacobi): x <- x + f_P sum_f w_f (x_Q - x), w_f = sigma n_P . A_f > 0 over the
+// inflow faces whose neighbour is a cell of the side (fixed value: its gradient) or an unknown of
+// the same solve (its previous iterate); sigma = +1 for the liquid side, -1 for the vapour side,
+// so that each side moves from its bulk towards the interface; f_P = min(dtau, V_P / sum w_f) / V_P.
+// Written as x <- x + b - C x + sum over the unknown neighbours of g_Q x_Q: the fixed part b,
+// C = f_P sum w_f and the first kExCap unknown neighbours (slot, g_Q = f_P w_f) are gathered once
+// (further unknown faces, rare, are walked on the mesh each iteration from a bit mask).
+//
+// Layout for the FP64 pipe: a warp instruction holds its sub-partition's FP64 unit for the same
+// time whatever its active lanes, so an iteration costs FP64 warp instructions, not lanes. Each
+// slot takes three lanes (one per component; ten slots per warp), which cuts a warp's FP64
+// instructions per iteration about threefold, and the grid spreads the warps over every SM. When
+// the grid has a lane per component of every slot, a lane keeps its constants and iterate in
+// registers.
+//
+// Iterations end at a grid barrier of its own that also carries the stopping test: each block
+// adds 1 + sum over the solves it saw move by tol or more of 1 << (16 + 8 j) to the iteration's
+// 64-bit word (low 16 bits: arrivals; 8 bits per solve: blocks still moving), then polls the word
+// until every block has arrived. A solve stops after the first iteration in which no block saw a
+// change of tol or more (its largest change is below tol), or after max_iter; a stopped solve's
+// components are carried forward unchanged. The poll gives up after kExSpinLimit reads: the
+// block then stops iterating and the step reports -1 iterations for every solve (results invalid).
+constexpr int kExThreads = 256;
+constexpr int kExSlotsPerWarp = 10;  // three lanes each; lanes 30 and 31 idle
+constexpr long long kExSpinLimit = 1ll << 22;
+
+struct ExSlot {
+  double C, f, b0, b1, b2;
+  double g[kExCap];
+  int32_t nb[kExCap];        // slots of the first unknown neighbours (-1: none)
+  unsigned long long mask;   // face positions of further unknown neighbours
+  int32_t c;
+  int side;                  // 0: an unknown of the liquid side (a vapour cell), 1: of the vapour side
+};
+
+// The constants of slot i (step weights, fixed inflow part, unknown neighbours); flags and counts a
+// slot without inflow.
+__device__ __forceinline__ ExSlot ex_prep(const MeshView& M, const Workspace& W, const double* alpha, double eps,
+                                          double dtau, int64_t i, int& nside) {
+  ExSlot s;
+  const int32_t c = W.iface_idx[i];
+  s.c = c;
+  s.side = alpha[c] > 0.5 ? 1 : 0;  // a liquid cell is an unknown of the vapour side, and the reverse
+  s.C = s.f = s.b0 = s.b1 = s.b2 = 0.0;
+  s.mask = 0;
+#pragma unroll
+  for (int t = 0; t < kExCap; ++t) {
+    s.g[t] = 0.0;
+    s.nb[t] = -1;
+  }
+  if (!(W.A_int[c] > 0)) return s;
+  const bool liq = s.side == 1;
+  const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+  const int64_t e0 = M.cell_face_off[c], e1 = M.cell_face_off[c + 1];
+  double ws = 0;
+  int cnt = 0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int32_t fe = M.cell_face[e];
+    const int32_t fc = fe & 0x7fffffff;
+    const int32_t q = M.face_owner[fc] == c ? M.face_neigh[fc] : M.face_owner[fc];
+    if (q < 0) continue;
+    const Vec3 Af = v3(M.face_area[3 * fc], M.face_area[3 * fc + 1], M.face_area[3 * fc + 2]);
+    const double w = flip_if(dot(nn, Af), (fe < 0) != liq);  // sigma n . (outward area of c)
+    if (!(w > 0)) continue;
+    const double aq = alpha[q];
+    if ((aq > 0.5) != liq) {  // a cell of the side: fixed value
+      ws += w;
+      s.b0 = fma(w, W.grad[3 * q], s.b0);
+      s.b1 = fma(w, W.grad[3 * q + 1], s.b1);
+      s.b2 = fma(w, W.grad[3 * q + 2], s.b2);
+    } else if (is_iface(aq, eps) && W.A_int[q] > 0) {  // an unknown of the same solve
+      ws += w;
+      if (cnt < kExCap) {
+#pragma unroll
+        for (int t = 0; t < kExCap; ++t)
+          if (t == cnt) {
+            s.g[t] = w;
+            s.nb[t] = W.iface_slot[q];
+          }
+        ++cnt;
+      } else {
+        s.mask |= 1ull << (e - e0);
+      }
+    }
+  }
+  if (ws > 0) {
+    const double V = M.cell_vol[c];
+    s.f = fmin(dtau, V / ws) / V;
+    s.C = s.f * ws;
+    s.b0 *= s.f;
+    s.b1 *= s.f;
+    s.b2 *= s.f;
+#pragma unroll
+    for (int t = 0; t < kExCap; ++t) s.g[t] *= s.f;
+  } else {
+    W.status[c] |= VOF_ST_NO_SIDE;  // no inflow: keeps its start value
+    ++nside;
+  }
+  return s;
+}
+
+struct ExLane {
+  double C, f, b;
+  double g[kExCap];
+  int32_t nb[kExCap];        // slots of the first unknown neighbours (-1: none)
+  unsigned long long mask;   // face positions of further unknown neighbours
+  int32_t c;
+  int side;                  // 0: an unknown of the liquid side (a vapour cell), 1: of the vapour side
+};
+
+__device__ __forceinline__ ExLane ex_lane_load(const Workspace& W, const double* alpha, int64_t i, int comp) {
+  ExLane s;
+  const double* k5 = W.ex_k + 5 * i;
+  s.C = k5[0];
+  s.f = k5[1];
+  s.b = k5[2 + comp];
+#pragma unroll
+  for (int t = 0; t < kExCap; ++t) {
+    s.nb[t] = W.ex_nb[kExCap * i + t];
+    s.g[t] = W.ex_g[kExCap * i + t];
+  }
+  s.mask = W.ex_mask[i];
+  s.c = W.iface_idx[i];
+  s.side = alpha[s.c] > 0.5 ? 1 : 0;
+  return s;
+}
+
+// One Jacobi step of one component of a slot from the previous iterates Xo ([slot][4]); x in, new
+// iterate out; the solve's bit ORed into `moved` when it moved by tol or more.
+__device__ __forceinline__ void ex_update(const MeshView& M, const Workspace& W, const ExLane& s, int comp,
+                                          const double* Xo, unsigned active, double tol, double& x,
+                                          unsigned& moved) {
+  const int j = 3 * s.side + comp;
+  if (!(s.C > 0) || !((active >> j) & 1u)) return;
+  double a = fma(-s.C, x, x + s.b);
+#pragma unroll
+  for (int t = 0; t < kExCap; ++t)
+    if (s.nb[t] >= 0) a = fma(s.g[t], __ldcg(Xo + 4 * (int64_t)s.nb[t] + comp), a);
+  if (s.mask) {
+    const bool liq = s.side == 1;
+    const Vec3 nn = v3(W.n_int[3 * s.c], W.n_int[3 * s.c + 1], W.n_int[3 * s.c + 2]);
+    const int64_t e0 = M.cell_face_off[s.c];
+    unsigned long long mask = s.mask;
+    while (mask) {
+      const int jf = __ffsll((long long)mask) - 1;
+      mask &= mask - 1;
+      const int32_t fe = M.cell_face[e0 + jf];
+      const int32_t fc = fe & 0x7fffffff;
+      const int32_t q = M.face_owner[fc] == s.c ? M.face_neigh[fc] : M.face_owner[fc];
+      const Vec3 Af = v3(M.face_area[3 * fc], M.face_area[3 * fc + 1], M.face_area[3 * fc + 2]);
+      const double g = s.f * flip_if(dot(nn, Af), (fe < 0) != liq);
+      a = fma(g, __ldcg(Xo + 4 * (int64_t)W.iface_slot[q] + comp), a);
+    }
+  }
+  if (fabs(a - x) >= tol) moved |= 1u << j;
+  x = a;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double* alpha, double eps, int max_iter,
+                                                        double tol, Workspace W) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ unsigned s_or[2];
+  __shared__ unsigned s_dec;
+  const int64_t n = W.counters->n_iface;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  double* Xa = W.ex_x;  // [slot][4]: x0, x1, x2, pad
+  double* Xb = W.ex_x + 4 * M.n_cells;
+  // (0) a thread per slot: fixed inflow part, step weights, unknown neighbours, start value
+  int nside = 0;
+  const double dtau = *W.ex_dtau;
+  for (int64_t i = t0; i < n; i += nthr) {
+    const ExSlot sl = ex_prep(M, W, alpha, eps, dtau, i, nside);
+    double* k5 = W.ex_k + 5 * i;
+    k5[0] = sl.C; k5[1] = sl.f; k5[2] = sl.b0; k5[3] = sl.b1; k5[4] = sl.b2;
+#pragma unroll
+    for (int t = 0; t < kExCap; ++t) {
+      W.ex_nb[kExCap * i + t] = sl.nb[t];
+      W.ex_g[kExCap * i + t] = sl.g[t];
+    }
+    W.ex_mask[i] = sl.mask;
+    Xa[4 * i] = W.grad[3 * sl.c];
+    Xa[4 * i + 1] = W.grad[3 * sl.c + 1];
+    Xa[4 * i + 2] = W.grad[3 * sl.c + 2];
+  }
+  if (nside) atomicAdd((unsigned long long*)&W.counters->n_no_side, (unsigned long long)nside);
+  for (int64_t j = t0; j <= max_iter; j += nthr) W.ex_itmax[j] = 0ull;
+  if (threadIdx.x < 2) s_or[threadIdx.x] = 0u;
+  grid.sync();
+  // (1) the iterations: three lanes per slot
+  const int64_t warp = t0 >> 5, nwarps = nthr >> 5;
+  const int sw = lane / 3, comp = lane - 3 * (lane / 3);
+  const int64_t ngroups = (n + kExSlotsPerWarp - 1) / kExSlotsPerWarp;
+  const bool one = ngroups <= nwarps;  // a lane per component of every slot: registers
+  const int64_t im = warp * kExSlotsPerWarp + sw;
+  const bool mine_ok = one && sw < kExSlotsPerWarp && im < n;
+  ExLane mine;
+  double xm = 0;
+  if (mine_ok) {
+    mine = ex_lane_load(W, alpha, im, comp);
+    xm = Xa[4 * im + comp];
+  }
+  unsigned active = 0x3fu;
+  int K[6] = {max_iter, max_iter, max_iter, max_iter, max_iter, max_iter};
+  bool failed = false;
+  const double* Xo = Xa;
+  double* Xn = Xb;
+  for (int k = 1; k <= max_iter; ++k) {
+    unsigned moved = 0;
+    if (one) {
+      if (mine_ok) {
+        ex_update(M, W, mine, comp, Xo, active, tol, xm, moved);
+        Xn[4 * im + comp] = xm;
+      }
+    } else if (sw < kExSlotsPerWarp) {
+      for (int64_t gi = warp; gi < ngroups; gi += nwarps) {
+        const int64_t i = gi * kExSlotsPerWarp + sw;
+        if (i >= n) continue;
+        const ExLane sl = ex_lane_load(W, alpha, i, comp);
+        double x = __ldcg(Xo + 4 * i + comp);
+        ex_update(M, W, sl, comp, Xo, active, tol, x, moved);
+        Xn[4 * i + comp] = x;
+      }
+    }
+    moved = __reduce_or_sync(0xffffffffu, moved);
+    if (lane == 0 && moved) atomicOr(&s_or[k & 1], moved);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned v = s_or[k & 1];
+      s_or[(k + 1) & 1] = 0u;  // the next iteration's word: cleared before this block's barrier below
+      unsigned long long add = 1ull;
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        if ((v >> j) & 1u) add += 1ull << (16 + 8 * j);
+      __threadfence();  // this block's iterates before its arrival
+      atomicAdd(W.ex_itmax + k, add);
+      unsigned long long cur = 0;
+      long long spins = 0;
+      do {
+        cur = ld_acquire_gpu(W.ex_itmax + k);
+      } while ((cur & 0xffffull) < gridDim.x && ++spins < kExSpinLimit);
+      __threadfence();  // the other blocks' iterates after their arrivals
+      unsigned dec = 0;
+      if ((cur & 0xffffull) < gridDim.x) {
+        dec = 0x80000000u;  // gave up waiting
+      } else {
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+          if ((cur >> (16 + 8 * j)) & 0xffull) dec |= 1u << j;
+      }
+      s_dec = dec;
+    }
+    __syncthreads();
+    const unsigned still = s_dec;
+    if (still & 0x80000000u) {
+      failed = true;
+      break;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (((active >> j) & 1u) && !((still >> j) & 1u)) K[j] = k;
+    active &= still;
+    const double* t = Xo;
+    Xo = Xn;
+    Xn = const_cast<double*>(t);
+    if (!active) break;
+  }
+  // (2) both sides of every interface cell with an interface (iterates of the last iteration, in
+  // this thread's registers or, for the other slots, written before the last barrier)
+  if (one) {
+    if (mine_ok && W.A_int[mine.c] > 0) {
+      double* own = mine.side ? W.grad_l : W.grad_v;
+      double* oth = mine.side ? W.grad_v : W.grad_l;
+      own[3 * mine.c + comp] = W.grad[3 * mine.c + comp];
+      oth[3 * mine.c + comp] = xm;
+    }
+  } else if (sw < kExSlotsPerWarp) {
+    for (int64_t gi = warp; gi < ngroups; gi += nwarps) {
+      const int64_t i = gi * kExSlotsPerWarp + sw;
+      if (i >= n) continue;
+      const int32_t c = W.iface_idx[i];
+      if (!(W.A_int[c] > 0)) continue;
+      const bool liq = alpha[c] > 0.5;
+      double* own = liq ? W.grad_l : W.grad_v;
+      double* oth = liq ? W.grad_v : W.grad_l;
+      own[3 * c + comp] = W.grad[3 * c + comp];
+      oth[3 * c + comp] = __ldcg(Xo + 4 * i + comp);
+    }
+  }
+  // counts (zeroed at the step's start): a block that gave up marks every solve -1, which a count
+  // written by block 0 never overwrites
+  unsigned long long* it = (unsigned long long*)W.counters->extrap_iters;
+  if (failed) {
+    if (threadIdx.x == 0)
+      for (int j = 0; j < 6; ++j) atomicExch(it + j, (unsigned long long)-1ll);
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int j = 0; j < 6; ++j) atomicCAS(it + j, 0ull, (unsigned long long)K[j]);
   }
 }
 
@@ -1705,6 +2022,25 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
   }
   k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+  if (a.opt.extrap) {
+    // the pseudo-time solve: one cooperative launch
+    if (!m->ex_grid) {  // a block per SM (the barrier word counts at most 255 blocks)
+      int bps = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_extrap, kExThreads, 0);
+      m->ex_grid = std::max(1, std::min(std::min(m->num_sms, m->num_sms * std::max(1, bps)), 255));
+    }
+    tm.stop(s);
+    tm.start(KC_EXTRAP, s);
+    MeshView Mv = M;
+    const double* al = a.alpha;
+    double eps = a.opt.alpha_eps, tol = a.opt.extrap_tol;
+    int mi = a.opt.extrap_max_iter;
+    void* args[] = {&Mv, (void*)&al, &eps, &mi, &tol, &W};
+    cudaError_t el = cudaLaunchCooperativeKernel((const void*)k_extrap, dim3(m->ex_grid), dim3(kExThreads), args, 0, s);
+    tm.stop(s);
+    if (el != cudaSuccess) return cuda_fail(el, "extrapolation kernel (cooperative launch)");
+    tm.start(KC_SOURCE, s);
+  }
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   if (a.opt.htc) cudaStreamWaitEvent(s, m->ev_xjoin, 0);  // the side branch (k_htc) joins here

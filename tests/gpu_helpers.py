@@ -52,6 +52,12 @@ def case(name):
         reg = dict(type="pipe", r0=0.9, a=0.04, lam=0.5, t=0.0)
         a = synth.alpha(m, reg, mode="subtet", level=2)
         prof = dict(kind="pipe", dT=8.0, radius=1.0)
+    elif name == "voronoi_many_spheres":  # about 15.0k interface cells
+        from synth.workloads import spheres
+        m = synth.voronoi_bcc(36, seed=7)
+        reg = dict(type="spheres", spheres=spheres(np.random.default_rng(7), 130, 0.04, 0.09))
+        a = synth.alpha(m, reg, mode="subtet", level=1)
+        prof = dict(kind="radial", dT=5.0)
     else:
         raise KeyError(name)
     T, Tb = synth.temperature(m, reg, prof)
@@ -93,20 +99,20 @@ def rel_err(x, y):
     return dn / np.where(scale == 0, 1.0, scale)
 
 
-def ulp_spread(O, a, rec, T, Tb, props, keys, draws=2, seed=0):
+def ulp_spread(O, a, rec, T, Tb, props, keys, draws=2, seed=0, **pc_kw):
     """The oracle's own conditioning, cell by cell: the largest rel_err of its downstream outputs
     when every cell centroid is moved by at most one ulp (random sign). Returns (unperturbed
-    outputs, {key: spread per row})."""
+    outputs, {key: spread per row}); pc_kw goes to the oracle's phase_change."""
     g = O.geometry()
     cen0 = g["cell_cen"].copy()
-    pc0 = O.phase_change(a, rec, T, Tb, props)
+    pc0 = O.phase_change(a, rec, T, Tb, props, **pc_kw)
     rng = np.random.default_rng(seed)
     spread = {k: np.zeros(len(pc0[k])) for k in keys}
     try:
         for _ in range(draws):
             s = rng.integers(-1, 2, cen0.shape)
             g["cell_cen"][:] = np.where(s > 0, np.nextafter(cen0, np.inf), np.where(s < 0, np.nextafter(cen0, -np.inf), cen0))
-            pc = O.phase_change(a, rec, T, Tb, props)
+            pc = O.phase_change(a, rec, T, Tb, props, **pc_kw)
             for k in keys:
                 spread[k] = np.maximum(spread[k], rel_err(pc[k], pc0[k]))
     finally:
