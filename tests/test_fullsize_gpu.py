@@ -34,9 +34,9 @@ def _dev(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def _run(M, a, T, Tb, n_cells, mode, graph, batch=None):
+def _run(M, a, T, Tb, n_cells, mode, graph, batch=None, **kw):
     """Autotune for `mode`, then one step as the benchmark takes it; numpy outputs."""
-    opt = vof.default_options(root_mode=mode)
+    opt = vof.default_options(root_mode=mode, **kw)
     s = torch.cuda.Stream()  # graph capture needs a stream of its own
     with torch.cuda.stream(s):
         ta, tT = _dev(a), _dev(T)
@@ -170,6 +170,27 @@ def test_full_size_other_root_modes(full, mode):
         assert per_cell(g) * 5 < per_cell(gb), (per_cell(g), per_cell(gb))
     else:
         assert per_cell(gb) <= 1.5, per_cell(gb)
+
+
+def test_full_size_extrapolation(full):
+    """The pseudo-time solve of Eq. (extrapolation) at full size, learned path, graph replay: the six
+    iteration counts exact, the per-side gradients and the sources within the bars, against the
+    oracle's solve starting from the GPU reconstruction and least-squares inputs."""
+    name, m, a, T, Tb, g, M = full
+    if name == "pipe8m":
+        pytest.skip("the moving film is timed with the single sweep")
+    ge = _run(M, a, T, Tb, m.n_cells, vof.ROOT_LEARNED, graph=True, extrap=1)
+    O = oracle.Oracle(m)
+    rec = dict(status=ge["status"], A_int=ge["A_int"], n_int=ge["n_int"], x_gamma=ge["x_gamma"])
+    keys = ("grad_l", "grad_v", "q_l", "q_v", "mdot", "Q")
+    pc, spread = ulp_spread(O, a, rec, T, Tb, synth.PROPS, keys, extrap={})
+    assert list(ge["counts"]["extrap_iters"]) == list(pc["extrap_iters"])
+    I = ge["iface_idx"]
+    assert np.array_equal(ge["status"][I] & 16, pc["status"][I] & 16)
+    for k in keys:
+        ok, worst = within(ge[k][I], pc[k][I], spread[k][I])
+        assert ok, (k, worst)
+    np.testing.assert_allclose(ge["totals"], pc["totals"], rtol=1e-10)
 
 
 def test_full_size_batch64():
