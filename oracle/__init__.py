@@ -70,6 +70,9 @@ def _lib():
         _LIB.orc_phase_change.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 6
                                           + [ctypes.c_int] + [ctypes.c_void_p] * 16)
         _LIB.orc_extrap_dtau.argtypes = [ctypes.c_void_p] * 4
+        _LIB.orc_lsq_study.argtypes = ([ctypes.c_void_p] * 6 + [ctypes.c_double] + [ctypes.c_void_p] * 3
+                                       + [ctypes.c_int] + [ctypes.c_void_p] * 3)
+        _LIB.orc_sym3_eigenvalues.argtypes = [ctypes.c_void_p] * 2
         _LIB.orc_extrapolate.argtypes = ([ctypes.c_void_p] * 7 + [ctypes.c_double, ctypes.c_int, ctypes.c_double]
                                          + [ctypes.c_void_p] * 3)
         _LIB.orc_vertex_field.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
@@ -143,6 +146,22 @@ class Oracle:
                                  *[_p(r[k]) for k in ("iso", "status", "evals", "A_int", "n_int", "x_gamma", "nloops")])
         return r
 
+    def lsq_study(self, alpha, pc: dict, T, T_bnd, props: dict, variant: int) -> dict:
+        """Appendix B's least squares on the band with the stencil-anisotropy study's variants (bits:
+        1 standard stencil, 2 inverse-distance weights 1/|r|^2, 4 vertex neighbours), given a
+        phase_change output `pc` (its crossing flags, x_f and band); returns grad, cond(G_P) and
+        the singular flags (status)."""
+        g = self.geometry()
+        nc = self.c.n_cells
+        o = dict(grad=np.zeros((nc, 3)), cond=np.zeros(nc), status=np.zeros(nc, np.int32))
+        arr = lambda x: np.ascontiguousarray(x, np.float64)
+        _lib().orc_lsq_study(self.ref, _p(g["face_cen"]), _p(g["cell_cen"]), _p(arr(alpha)), _p(arr(T)),
+                             None if T_bnd is None else _p(arr(T_bnd)), float(props["T_sat"]),
+                             _p(np.ascontiguousarray(pc["crossing"], np.uint8)), _p(arr(pc["x_f"])),
+                             _p(np.ascontiguousarray(pc["in_band"], np.uint8)), int(variant),
+                             _p(o["grad"]), _p(o["cond"]), _p(o["status"]))
+        return o
+
     def extrap_dtau(self) -> float:
         """Pseudo-time step of Eq. (extrapolation): min over faces of |d_f|."""
         g = self.geometry()
@@ -204,6 +223,13 @@ class Oracle:
         rec = self.reconstruct(alpha, phi, eps, tol)
         pc = self.phase_change(alpha, rec, T, T_bnd, props, eps, xf_mode)
         return dict(phi=phi, recon=rec, pc=pc)
+
+
+def sym3_eigenvalues(A) -> np.ndarray:
+    """Eigenvalues (ascending) of a symmetric 3x3 matrix by the oracle's Jacobi rotations."""
+    out = np.zeros(3)
+    _lib().orc_sym3_eigenvalues(_p(np.ascontiguousarray(A, np.float64).reshape(9)), _p(out))
+    return out
 
 
 def pairwise_sum(a: np.ndarray) -> float:

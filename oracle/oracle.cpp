@@ -22,6 +22,8 @@
 //   R6  q_l, q_v, mdot, Q_phase
 //   R7  interface-modified least squares gradient (Appendix B), explicit symmetric inverse
 //   R8  totals by a fixed pairwise tree
+//   S   stencil variants of R7 for the stencil-anisotropy study (the next row N4 of the scope):
+//       standard (unmodified) stencil, inverse-distance weights, vertex neighbours; cond(G_P)
 //
 // Pinned only in special cases (invariants otherwise): R1 (the plain mean on a uniform hex mesh),
 // R5, a reading of the extrapolation step (equal neighbour gradients), R4 (a point on the common
@@ -378,6 +380,144 @@ double pairwise_sum(std::vector<double> a) {
     n /= 2;
   }
   return a[0];
+}
+
+// ------------------------------------------------------------------------------ S (study)
+// Eigenvalues of a symmetric 3x3 matrix by the cyclic Jacobi method (plane rotations that zero
+// one off-diagonal entry at a time, swept until the off-diagonal part is negligible).
+std::array<double, 3> sym3_eigenvalues(double A[3][3]) {
+  double a[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) a[i][j] = A[i][j];
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-34 * dia) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (a[p][q] == 0) continue;
+        // rotation angle that zeroes a[p][q]: tan(2 phi) = 2 a_pq / (a_qq - a_pp)
+        const double theta = (a[q][q] - a[p][p]) / (2 * a[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        const double c = 1 / std::sqrt(t * t + 1), sn = t * c;
+        double b[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) b[i][j] = a[i][j];
+        for (int k = 0; k < 3; ++k) {  // columns p, q of A R
+          b[k][p] = c * a[k][p] - sn * a[k][q];
+          b[k][q] = sn * a[k][p] + c * a[k][q];
+        }
+        for (int k = 0; k < 3; ++k) {  // rows p, q of R^T (A R)
+          a[p][k] = c * b[p][k] - sn * b[q][k];
+          a[q][k] = sn * b[p][k] + c * b[q][k];
+          if (k != p && k != q) {
+            a[k][p] = b[k][p];
+            a[k][q] = b[k][q];
+          }
+        }
+        a[p][q] = a[q][p] = 0;
+      }
+  }
+  std::array<double, 3> e = {a[0][0], a[1][1], a[2][2]};
+  std::sort(e.begin(), e.end());
+  return e;
+}
+
+// R7 with the study's variants (bits of `variant`): 1 the standard stencil (neighbours across the
+// interface enter with their own centroid and temperature), 2 inverse-distance weights w = 1/|r|^2
+// on every stencil entry, 4 the stencil of every cell sharing a vertex (boundary faces as in R7);
+// in the modified stencil a vertex-only neighbour across the interface enters at the linear
+// interpolation of alpha along the centroid connection (t = (alpha_P - 1/2)/(alpha_P - alpha_Q)),
+// a face neighbour at the face's x_f. cond receives lambda_max / lambda_min of G_P (inf when
+// lambda_min <= 0); grad and the singular flag as R7.
+void lsq_study(const OrcMesh& m, const double* face_cen, const double* cell_cen, const double* alpha, const double* T,
+               const double* T_bnd, double T_sat, const uint8_t* crossing, const double* x_f, const uint8_t* in_band,
+               int variant, double* grad, double* cond, int32_t* status) {
+  const bool standard = variant & 1, idw = variant & 2, ext = variant & 4;
+  const int64_t nc = m.n_cells;
+  std::vector<std::vector<int32_t>> cells_of(ext ? m.n_verts : 0);
+  if (ext)
+    for (int64_t c = 0; c < nc; ++c)
+      for (int32_t v : cell_vertices(m, c)) cells_of[v].push_back((int32_t)c);
+  for (int64_t c = 0; c < nc; ++c) {
+    grad[3 * c] = grad[3 * c + 1] = grad[3 * c + 2] = 0;
+    cond[c] = 0;
+    if (!in_band[c]) continue;
+    const V3 xP = {cell_cen[3 * c], cell_cen[3 * c + 1], cell_cen[3 * c + 2]};
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0};
+    auto add_entry = [&](const V3& r, double dT) {
+      const double w = idw ? 1.0 / dot(r, r) : 1.0;
+      for (int i = 0; i < 3; ++i) {
+        b[i] += w * r[i] * dT;
+        for (int j = 0; j < 3; ++j) G[i][j] += w * r[i] * r[j];
+      }
+    };
+    std::map<int32_t, int32_t> face_to;  // face neighbour -> face
+    for (int64_t k = m.cell_face_off[c]; k < m.cell_face_off[c + 1]; ++k) {
+      const int32_t f = m.cell_face[k] & 0x7fffffff;
+      const int32_t q = m.face_owner[f] == c ? m.face_neigh[f] : m.face_owner[f];
+      if (q < 0) {
+        if (T_bnd) add_entry(sub({face_cen[3 * f], face_cen[3 * f + 1], face_cen[3 * f + 2]}, xP), T_bnd[f] - T[c]);
+        continue;
+      }
+      face_to[q] = f;
+    }
+    std::vector<int32_t> nbrs;
+    if (ext) {
+      std::vector<int32_t> all;
+      for (int32_t v : cell_vertices(m, c))
+        for (int32_t q : cells_of[v])
+          if (q != c) all.push_back(q);
+      std::sort(all.begin(), all.end());
+      all.erase(std::unique(all.begin(), all.end()), all.end());
+      nbrs = all;
+    } else {
+      for (int64_t k = m.cell_face_off[c]; k < m.cell_face_off[c + 1]; ++k) {
+        const int32_t f = m.cell_face[k] & 0x7fffffff;
+        const int32_t q = m.face_owner[f] == c ? m.face_neigh[f] : m.face_owner[f];
+        if (q >= 0) nbrs.push_back(q);
+      }
+    }
+    for (int32_t q : nbrs) {
+      const V3 xQ = {cell_cen[3 * q], cell_cen[3 * q + 1], cell_cen[3 * q + 2]};
+      const bool across = (alpha[c] - 0.5) * (alpha[q] - 0.5) < 0;
+      if (standard || !across) {
+        add_entry(sub(xQ, xP), T[q] - T[c]);
+        continue;
+      }
+      const auto it = face_to.find(q);
+      V3 xs;
+      if (it != face_to.end() && crossing[it->second]) {
+        const int32_t f = it->second;
+        xs = {x_f[3 * f], x_f[3 * f + 1], x_f[3 * f + 2]};
+      } else {
+        const double t = (alpha[c] - 0.5) / (alpha[c] - alpha[q]);
+        xs = add(xP, mul(sub(xQ, xP), t));
+      }
+      add_entry(sub(xs, xP), T_sat - T[c]);
+    }
+    const auto ev = sym3_eigenvalues(G);
+    cond[c] = ev[0] > 0 ? ev[2] / ev[0] : INFINITY;
+    const double det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                       G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                       G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    const double tr = (G[0][0] + G[1][1] + G[2][2]) / 3.0;
+    if (!(det > 1e-12 * tr * tr * tr)) {
+      status[c] |= ST_SINGULAR_LSQ;
+      continue;
+    }
+    double Gi[3][3];
+    Gi[0][0] = (G[1][1] * G[2][2] - G[1][2] * G[2][1]) / det;
+    Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) / det;
+    Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) / det;
+    Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) / det;
+    Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) / det;
+    Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) / det;
+    Gi[1][0] = Gi[0][1];
+    Gi[2][0] = Gi[0][2];
+    Gi[2][1] = Gi[1][2];
+    for (int i = 0; i < 3; ++i) grad[3 * c + i] = Gi[i][0] * b[0] + Gi[i][1] * b[1] + Gi[i][2] * b[2];
+  }
 }
 
 }  // namespace
@@ -759,6 +899,20 @@ void orc_extrapolate(const OrcMesh* m, const double* face_area, const double* ce
                      const uint8_t* iface, const double* n_int, const double* grad, double dtau, int max_iter,
                      double tol, double* g_other, int32_t* iters, int32_t* status) {
   extrapolate(*m, face_area, cell_vol, alpha, iface, n_int, grad, dtau, max_iter, tol, g_other, iters, status);
+}
+
+// S: the study's least-squares variants on the band (see lsq_study).
+void orc_lsq_study(const OrcMesh* m, const double* face_cen, const double* cell_cen, const double* alpha,
+                   const double* T, const double* T_bnd, double T_sat, const uint8_t* crossing, const double* x_f,
+                   const uint8_t* in_band, int variant, double* grad, double* cond, int32_t* status) {
+  lsq_study(*m, face_cen, cell_cen, alpha, T, T_bnd, T_sat, crossing, x_f, in_band, variant, grad, cond, status);
+}
+
+void orc_sym3_eigenvalues(const double* A9, double* out3) {
+  double A[3][3];
+  for (int i = 0; i < 9; ++i) A[i / 3][i % 3] = A9[i];
+  const auto e = sym3_eigenvalues(A);
+  for (int i = 0; i < 3; ++i) out3[i] = e[i];
 }
 
 void orc_extrap_dtau(const OrcMesh* m, const double* cell_cen, const double* face_cen, double* out) {
