@@ -135,6 +135,18 @@ typedef struct {
   int extrap;
   int extrap_max_iter; /* 1 .. 1000 (default 120) */
   double extrap_tol;   /* K/m, absolute, > 0 (default 1e-3) */
+  /* Least-squares variants of the stencil-anisotropy study (Sec. 3, Fig. stencil_polar; Appendix B),
+   * bits (default 0: the interface-modified face stencil, unweighted):
+   *   1 the standard stencil: neighbours across the interface enter with their own centroid and
+   *     temperature (no crossing point, no T_sat);
+   *   2 inverse-distance weights w = 1/|r|^2 on every stencil entry (G = sum w r r^T, b = sum w r dT);
+   *   4 the stencil of every cell sharing a vertex with the cell (boundary faces as before); in
+   *     the modified stencil a neighbour across the interface that shares no face enters at the
+   *     linear interpolation of alpha along the centroid connection, t = (a_P - 1/2)/(a_P - a_Q);
+   *   8 also write cond(G_P) = lambda_max / lambda_min to VOF_F_LSQ_COND (band cells).
+   * Any bit set runs the study's least-squares kernel (a thread per band cell) in place of the
+   * path's; VOF_F_GRAD and everything downstream follow the chosen stencil. */
+  int lsq_variant;
 } vof_options;
 
 /* Fills *o with the defaults above. */
@@ -244,7 +256,9 @@ typedef enum {
                         * energy-matrix diagonal and a_f T_sat to its right-hand side, the face being
                         * detached from the diffusive coupling */
   VOF_F_DTAU = 26,     /* double [1]: pseudo-time step of Eq. (extrapolation), min over faces of |d_f| */
-  VOF_F_N = 27
+  VOF_F_LSQ_COND = 27, /* double [n_cells]: cond(G_P) of band cells, in steps run with options.lsq_variant bit 8
+                        * (inf where G_P has no positive smallest eigenvalue) */
+  VOF_F_N = 28
 } vof_field;
 
 /* Element count of a field in the current state (n_iface for the interface list). */

@@ -30,6 +30,7 @@ FIELDS = {
     "cell_vol": (18, np.float64, 1), "cell_cen": (19, np.float64, 3), "face_area": (20, np.float64, 3),
     "face_cen": (21, np.float64, 3), "iface_stamp": (22, np.int32, 1), "band_stamp": (23, np.int32, 1),
     "a_own": (24, np.float64, 1), "a_neigh": (25, np.float64, 1), "dtau": (26, np.float64, 1),
+    "lsq_cond": (27, np.float64, 1),
 }
 
 
@@ -55,7 +56,7 @@ class Options(ctypes.Structure):
                 ("root_mode", ctypes.c_int), ("max_secant", ctypes.c_int), ("xf_mode", ctypes.c_int),
                 ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int), ("htc", ctypes.c_int),
                 ("alpha_iso", ctypes.c_double), ("extrap", ctypes.c_int), ("extrap_max_iter", ctypes.c_int),
-                ("extrap_tol", ctypes.c_double)]
+                ("extrap_tol", ctypes.c_double), ("lsq_variant", ctypes.c_int)]
 
 
 class Counts(ctypes.Structure):

@@ -112,6 +112,7 @@ struct Workspace {
   unsigned long long* ex_mask;  // [n_cells] face positions of further unknown neighbours
   unsigned long long* ex_itmax; // [kExMaxIter + 1] per iteration: barrier word (arrivals, blocks still moving)
   double* ex_dtau;         // [1] min over faces of |d_f|
+  double* lsq_cond;        // [n_cells] cond(G_P) of band cells (least-squares study variants)
   // device staging for the host-buffer step
   double *io_alpha, *io_T, *io_Tb, *io_mdot, *io_Q, *io_totals;
 };

@@ -406,6 +406,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.ex_mask, nc));
   TRY(dev_alloc(m, &W.ex_itmax, 6 * (size_t)(kExMaxIter + 1)));
   TRY(dev_alloc(m, &W.ex_dtau, 1));
+  TRY(dev_alloc(m, &W.lsq_cond, nc));
   // pseudo-time step of the extrapolation: min over faces of |d_f|, by an atomic minimum of the
   // raw bits (non-negative doubles order as their bit patterns)
   k_dtau_init<<<1, 1, 0, s>>>(W.ex_dtau);
@@ -475,6 +476,7 @@ void vof_default_options(vof_options* o) {
   o->extrap = 0;
   o->extrap_max_iter = 120;
   o->extrap_tol = 1e-3;
+  o->lsq_variant = 0;
 }
 
 vof_status vof_mesh_create(const vof_mesh_desc* desc, void* stream, vof_mesh** out) {
@@ -526,7 +528,7 @@ static vof_status check_opt(const vof_options* o) {
       o->root_mode < VOF_ROOT_BISECT || o->root_mode > VOF_ROOT_FIXED || !(o->alpha_iso > 0.0 && o->alpha_iso < 1.0) ||
       o->max_secant < 0 || o->max_secant > 8 || o->htc < 0 || o->htc > 1 || o->extrap < 0 || o->extrap > 1 ||
       o->extrap_max_iter < 1 || o->extrap_max_iter > kExMaxIter || !(o->extrap_tol > 0) ||
-      !std::isfinite(o->extrap_tol) ||
+      !std::isfinite(o->extrap_tol) || o->lsq_variant < 0 || o->lsq_variant > 15 ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {

@@ -13,6 +13,7 @@
 // with w = p - c on wet corners and u = c - p on dry corners: every denominator is a product of
 // (wet - dry) differences, so no term is singular and nothing cancels.
 #include <cooperative_groups.h>
+#include <math_constants.h>
 #include <cstring>
 
 #include "vof_internal.cuh"
@@ -1846,6 +1847,131 @@ __global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double*
   }
 }
 
+// ---- least-squares variants of the stencil-anisotropy study (options.lsq_variant) -------------
+// A thread per band cell: G = sum w r r^T, b = sum w r dT over the chosen stencil (bits: 1 the
+// standard stencil, 2 weights w = 1/|r|^2, 4 every cell sharing a vertex, 8 also cond(G_P)), then
+// the same explicit inverse and singular test as the path's kernel. In the vertex stencil a
+// neighbour reached through several shared vertices is counted at the first of the cell's
+// (sorted) vertices it contains; across the interface a face neighbour enters at the face's
+// crossing point, any other at the linear interpolation of alpha along the centroid connection.
+// cond = lambda_max / lambda_min from the eigenvalues of G_P by cyclic Jacobi rotations (Golub and
+// Van Loan, Sec. 8.5: each rotation zeroes one off-diagonal pair; at most eight sweeps of the three
+// pairs), accurate also where two eigenvalues coincide.
+__device__ __forceinline__ void jacobi_rotate(double& dp, double& dq, double& apq, double& arp, double& arq) {
+  // the plane rotation that zeroes apq: tan(2 phi) = 2 apq / (dq - dp); off-pair entries rotate
+  if (apq == 0.0) return;
+  const double th = (dq - dp) / (2.0 * apq);
+  const double t = fabs(th) > 1e150 ? 0.5 / th : copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+  const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+  dp -= t * apq;
+  dq += t * apq;
+  apq = 0.0;
+  const double rp = arp, rq = arq;
+  arp = c * rp - s * rq;
+  arq = s * rp + c * rq;
+}
+
+__device__ double sym3_cond(double a00, double a01, double a02, double a11, double a12, double a22) {
+  double d0 = a00, d1 = a11, d2 = a22, e01 = a01, e02 = a02, e12 = a12;
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    if (e01 * e01 + e02 * e02 + e12 * e12 <= 1e-34 * (d0 * d0 + d1 * d1 + d2 * d2)) break;
+    jacobi_rotate(d0, d1, e01, e02, e12);  // pair (0, 1); the third index is 2
+    jacobi_rotate(d0, d2, e02, e01, e12);  // pair (0, 2); the third index is 1
+    jacobi_rotate(d1, d2, e12, e01, e02);  // pair (1, 2); the third index is 0
+  }
+  const double lmax = fmax(d0, fmax(d1, d2)), lmin = fmin(d0, fmin(d1, d2));
+  return lmin > 0 ? lmax / lmin : CUDART_INF;
+}
+
+__global__ void __launch_bounds__(kThreads) k_lsq_study(MeshView M, StepArgs a, Workspace W) {
+  const int variant = a.opt.lsq_variant;
+  const bool standard = variant & 1, idw = variant & 2, ext = variant & 4, want_cond = variant & 8;
+  const uint32_t step = W.counters->step;
+  const int64_t nb = W.counters->n_band;
+  int nsing = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = W.band_idx[j];
+    const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
+    const double TP = a.T[c], aP = a.alpha[c];
+    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+    auto entry = [&](const Vec3& r, double dT) {
+      const double w = idw ? 1.0 / dot(r, r) : 1.0;
+      const double wx = w * r.x, wy = w * r.y, wz = w * r.z;
+      g00 = fma(wx, r.x, g00); g01 = fma(wx, r.y, g01); g02 = fma(wx, r.z, g02);
+      g11 = fma(wy, r.y, g11); g12 = fma(wy, r.z, g12); g22 = fma(wz, r.z, g22);
+      b0 = fma(wx, dT, b0); b1 = fma(wy, dT, b1); b2 = fma(wz, dT, b2);
+    };
+    // a neighbour q (face f, or -1 when it shares no face with c)
+    auto neighbour = [&](int32_t q, int32_t f) {
+      const double aq = a.alpha[q];
+      const Vec3 xQ = v3(M.cell_cen[3 * q], M.cell_cen[3 * q + 1], M.cell_cen[3 * q + 2]);
+      if (standard || !((aP - 0.5) * (aq - 0.5) < 0)) {
+        entry(xQ - xP, a.T[q] - TP);
+      } else if (f >= 0) {
+        entry(v3(W.x_f[3 * f], W.x_f[3 * f + 1], W.x_f[3 * f + 2]) - xP, a.props.T_sat - TP);
+      } else {
+        const double t = (aP - 0.5) / (aP - aq);
+        entry((xQ - xP) * t, a.props.T_sat - TP);
+      }
+    };
+    const int64_t f0 = M.cell_face_off[c], f1 = M.cell_face_off[c + 1];
+    for (int64_t k = f0; k < f1; ++k) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
+      if (q < 0) {
+        if (a.T_bnd) entry(v3(M.face_cen[3 * f], M.face_cen[3 * f + 1], M.face_cen[3 * f + 2]) - xP, a.T_bnd[f] - TP);
+      } else if (!ext) {
+        neighbour(q, f);
+      }
+    }
+    if (ext) {
+      const int64_t v0 = M.cell_vert_off[c], v1 = M.cell_vert_off[c + 1];
+      for (int64_t kv = v0; kv < v1; ++kv) {
+        const int32_t v = M.cell_vert[kv];
+        for (int64_t e = M.vert_cell_off[v]; e < M.vert_cell_off[v + 1]; ++e) {
+          const int32_t q = M.vert_cell[e];
+          if (q == c) continue;
+          bool seen = false;  // q already reached through an earlier vertex of c
+          for (int64_t k2 = v0; k2 < kv && !seen; ++k2) {
+            const int32_t v2 = M.cell_vert[k2];
+            for (int64_t e2 = M.vert_cell_off[v2]; e2 < M.vert_cell_off[v2 + 1]; ++e2)
+              if (M.vert_cell[e2] == q) {
+                seen = true;
+                break;
+              }
+          }
+          if (seen) continue;
+          int32_t fq = -1;  // the face shared with q, if any
+          for (int64_t k = f0; k < f1 && fq < 0; ++k) {
+            const int32_t f = M.cell_face[k] & 0x7fffffff;
+            if ((M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f]) == q) fq = f;
+          }
+          neighbour(q, fq);
+        }
+      }
+    }
+    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    const double det = g00 * c00 + g01 * c01 + g02 * c02;
+    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
+    int st = 0;
+    Vec3 g = v3(0, 0, 0);
+    if (det > 1e-12 * tr * tr * tr) {
+      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+      const double id = 1.0 / det;
+      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+             (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    } else {
+      st = VOF_ST_SINGULAR_LSQ;
+      ++nsing;
+    }
+    W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
+    if (want_cond) W.lsq_cond[c] = sym3_cond(g00, g01, g02, g11, g12, g22);
+    if (W.iface_stamp[c] == step) W.status[c] |= st;
+    else W.status[c] = st;
+  }
+  if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
+}
+
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_lsq(MeshView M, StepArgs a, Workspace W) { lsq_phase<L>(M, a, W); }
 
@@ -2021,7 +2147,10 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
     k_htc<<<m->num_sms * 2, kThreads, 0, m->xm_stream>>>(M, a.alpha, a.props.k_l, a.props.k_v, W);
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
   }
-  k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+  if (a.opt.lsq_variant)  // the stencil-anisotropy study's variants
+    k_lsq_study<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+  else
+    k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   if (a.opt.extrap) {
     // the pseudo-time solve: one cooperative launch
     if (!m->ex_grid) {  // a block per SM (the barrier word counts at most 255 blocks)
