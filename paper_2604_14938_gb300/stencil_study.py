@@ -9,9 +9,10 @@ widths of the sphere, in the equatorial slab |z - z_c| < h. Per variant the scri
 |grad T| / G by the azimuth and reports the bin means' minimum / maximum ratio (the paper's
 anisotropy measure), the relative amplitude of the bin means' four-fold Fourier mode, the mean
 ratio and the median cond(G_P). On a Voronoi mesh the vertex stencil equals the face stencil: the
-four cells around a Voronoi vertex form a Delaunay tetrahedron, so every two of them share a face. Everything runs on the GPU through the library (one step per variant).
+four cells around a Voronoi vertex form a Delaunay tetrahedron, so every two of them share a face.
+Everything runs on the GPU through the library (one step per variant).
 
-    python -m paper_2604_14938_gb300.stencil_study [--n 48] [--json out.json]
+    python -m paper_2604_14938_gb300.stencil_study [--n 64] [--json out.json]
 """
 import argparse
 import json
@@ -45,7 +46,7 @@ def analytic_T(x: np.ndarray, R: float, G: float, T_sat: float) -> np.ndarray:
     return np.where(r > R, T_sat + G * (r - R), T_sat)
 
 
-def study(kind: str = "hex", n: int = 48, R: float = 0.3, G: float = 1000.0, bins: int = 36) -> dict:
+def study(kind: str = "hex", n: int = 64, R: float = 0.3, G: float = 1000.0, bins: int = 24) -> dict:
     import torch
     import synth
     from . import Mesh, default_options
@@ -88,7 +89,7 @@ def study(kind: str = "hex", n: int = 48, R: float = 0.3, G: float = 1000.0, bin
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, default=48, help="hexahedra per box edge (the polyhedral mesh matches the count)")
+    ap.add_argument("--n", type=int, default=64, help="hexahedra per box edge (the polyhedral mesh matches the count)")
     ap.add_argument("--R", type=float, default=0.3)
     ap.add_argument("--json", default="")
     args = ap.parse_args()
