@@ -279,7 +279,9 @@ typedef struct {
   int64_t tet_evals, tets_prepared, tets_sectioned;
   int64_t evals32_total; /* FP32 evaluations of the learned path's refinement */
   /* iterations of the six pseudo-time solves of options.extrap = 1 (liquid side x, y, z, then
-   * vapour side x, y, z); 0 in steps with options.extrap = 0 */
+   * vapour side x, y, z); 0 in steps with options.extrap = 0; -1 for every solve when a block of the
+   * launch gave up waiting at the iteration barrier (a bounded poll; the step's per-side
+   * gradients and sources are then invalid) */
   int64_t extrap_iters[6];
 } vof_counts;
 vof_status vof_get_counts(vof_mesh* mesh, vof_counts* out, void* stream);
