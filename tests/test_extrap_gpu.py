@@ -102,3 +102,13 @@ def test_extrap_options_rejected(bad):
     m, a, T, Tb = case("hex_sphere")
     with pytest.raises(RuntimeError):
         gpu_step(m, a, T, Tb, **bad)
+
+
+def test_extrap_without_interface():
+    """No interface cell: every solve stops after its first iteration, no source anywhere."""
+    m, a, T, Tb = case("hex_sphere")
+    a = np.ones(m.n_cells)
+    M, g = gpu_step(m, a, T, Tb, extrap=1)
+    assert g["counts"]["n_iface"] == 0
+    assert list(g["counts"]["extrap_iters"]) == [1] * 6
+    assert not np.any(g["mdot"]) and not np.any(g["totals"])
