@@ -130,8 +130,9 @@ typedef struct {
    *     centroid, or to the face centroid on a boundary face: VOF_F_DTAU), limited per cell to
    *     V_P / sum of its inflow weights. A solve stops after the iteration whose largest change is
    *     below extrap_tol, or after extrap_max_iter; vof_counts.extrap_iters holds the counts.
-   *     Needs cells of at most 64 faces (VOF_EINVAL otherwise). In a batch the step is the
-   *     smallest over all meshes of the batch (the batch is one mesh to the step). */
+   *     Needs cells of at most 64 faces (VOF_EINVAL otherwise). A batch is one mesh to the
+   *     step: its dtau is the smallest over all its meshes, and a solve stops only when no mesh
+   *     of the batch moves by extrap_tol or more. */
   int extrap;
   int extrap_max_iter; /* 1 .. 1000 (default 120) */
   double extrap_tol;   /* K/m, absolute, > 0 (default 1e-3) */
