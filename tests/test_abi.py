@@ -74,3 +74,30 @@ def test_null_arguments(vof):
     assert L.vof_mesh_destroy(None) == 1
     o = vof.default_options()
     assert o.tol_alpha == 1e-12 and o.max_bisect == 100 and o.xf_mode == 0
+
+
+def _c_layout(struct: str, fields: list[str], tmp_path) -> dict:
+    """Offsets and size of a struct of include/vof.h, from a small C program compiled with gcc."""
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vof.h"', "int main(void) {",
+             f'  printf("size %zu\\n", sizeof({struct}));']
+    lines += [f'  printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("name", ["Options", "Counts", "Props", "_Desc"])
+def test_struct_layouts_match_the_header(vof, name, tmp_path):
+    """The binding's ctypes structures have the header's field offsets and size."""
+    py = getattr(vof, name)
+    struct = {"Options": "vof_options", "Counts": "vof_counts", "Props": "vof_props", "_Desc": "vof_mesh_desc"}[name]
+    fields = [f for f, _ in py._fields_]
+    c = _c_layout(struct, fields, tmp_path)
+    assert c["size"] == ctypes.sizeof(py)
+    for f in fields:
+        assert c[f] == getattr(py, f).offset, f
