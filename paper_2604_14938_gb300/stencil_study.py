@@ -46,6 +46,19 @@ def analytic_T(x: np.ndarray, R: float, G: float, T_sat: float) -> np.ndarray:
     return np.where(r > R, T_sat + G * (r - R), T_sat)
 
 
+def anisotropy(theta: np.ndarray, ratio: np.ndarray, bins: int) -> tuple[float, float]:
+    """(min / max of the azimuth-bin means of ratio, relative amplitude of the bin means'
+    four-fold Fourier mode). The bin means weigh every bin alike, so that the mesh's uneven
+    angular sampling does not enter; the amplitude of m(theta) = m0 (1 + eps cos 4 (theta - c))
+    is eps."""
+    k = np.clip(((theta + np.pi) / (2 * np.pi) * bins).astype(int), 0, bins - 1)
+    filled = [b for b in range(bins) if np.any(k == b)]
+    means = np.array([ratio[k == b].mean() for b in filled])
+    centres = -np.pi + (np.array(filled) + 0.5) * (2 * np.pi / bins)
+    four = 2 * np.abs(np.mean((means - means.mean()) * np.exp(4j * centres))) / means.mean()
+    return float(means.min() / means.max()), float(four)
+
+
 def study(kind: str = "hex", n: int = 64, R: float = 0.3, G: float = 1000.0, bins: int = 24) -> dict:
     import torch
     import synth
@@ -72,17 +85,10 @@ def study(kind: str = "hex", n: int = 64, R: float = 0.3, G: float = 1000.0, bin
         sel = band & (a > 0.5) & (rr > R) & (rr - R < 1.5 * h) & (np.abs(cen[:, 2] - 0.5) < h)
         g = M.field("grad").cpu().numpy()[sel]
         ratio = np.linalg.norm(g, axis=1) / G
-        th = theta[sel]
-        k = np.clip(((th + np.pi) / (2 * np.pi) * bins).astype(int), 0, bins - 1)
-        filled = [b for b in range(bins) if np.any(k == b)]
-        means = np.array([ratio[k == b].mean() for b in filled])
-        centres = -np.pi + (np.array(filled) + 0.5) * (2 * np.pi / bins)
-        # the four-fold Fourier mode of the bin means (equal weight per bin, so that the mesh's
-        # uneven angular sampling does not enter), relative to their mean
-        four = 2 * np.abs(np.mean((means - means.mean()) * np.exp(4j * centres))) / means.mean()
+        mm, four = anisotropy(theta[sel], ratio, bins)
         cond = M.field("lsq_cond").cpu().numpy()[sel]
         out["variants"][name] = dict(cells=int(sel.sum()), mean_ratio=float(ratio.mean()),
-                                     min_over_max=float(means.min() / means.max()), fourfold=float(four),
+                                     min_over_max=mm, fourfold=four,
                                      median_cond=float(np.median(cond)), max_cond=float(cond.max()))
     return out
 
