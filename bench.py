@@ -35,8 +35,8 @@ UNIT = "interface cells/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 # Algorithmic work of one FP64 cut-volume evaluation of a Voronoi cell of about 14 faces: 36
-# straddle tests, ~15 cut points and ~90 fan tetrahedra at ~20 flops, about 2 kFLOP (the survey's
-# per-unit figure; a learned cell needs 3-4 such evaluations, a bisection cell about 40)
+# straddle tests, ~15 cut points and ~90 fan tetrahedra at ~20 flops, about 2 kFLOP, the per-unit
+# figure of the roofline (a learned cell needs 3-4 such evaluations, a bisection cell about 40)
 ALG_FLOPS_PER_EVAL = 2000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step's root-search launches,
 # all bins, measured with ncu --set full on a GB300 for the workload, path and lanes per cell given;

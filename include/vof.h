@@ -210,8 +210,8 @@ vof_status vof_autotune(vof_mesh* mesh, const double* d_alpha, const vof_options
                         void* stream);
 vof_status vof_set_group_sizes(vof_mesh* mesh, const int* h_G);
 
-/* ---- batches of independent meshes (spec: many meshes of uneven size and cell type in one
- * launch) ----
+/* ---- batches of independent meshes (many meshes of uneven size and cell type in one launch)
+ * ----
  * A batch is the disjoint union of n meshes: cells, faces and vertices renumbered with the offsets
  * vof_batch_offsets returns (host arrays of n + 1). vof_batch_mesh gives the union mesh, stepped
  * like any mesh (vof_step, vof_step_graph; alpha, T, T_bnd, mdot, Q concatenated in mesh order).
@@ -297,7 +297,7 @@ vof_status vof_mesh_info(const vof_mesh* mesh, int64_t* out5);
  * No counterpart in the paper (launch layout of this implementation). */
 vof_status vof_mesh_bins(const vof_mesh* mesh, int64_t* cells5);
 
-/* ---- learned isovalue guess (the benchmark spec's learned part; the paper fixes no such model) ----
+/* ---- learned isovalue guess (the learned part of the path; the paper fixes no such model) ----
  * A 40 -> 64 -> 64 -> 64 -> 1 GELU MLP predicting the normalised isovalue position
  * t = (c - phi_min)/(phi_max - phi_min) of an interface cell. BF16 operands with FP32
  * accumulation (forward on the tensor cores), FP32 master weights and Adam.

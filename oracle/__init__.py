@@ -185,7 +185,7 @@ class Oracle:
 
     def phase_change(self, alpha, recon: dict, T, T_bnd, props: dict, eps=1e-12, xf_mode=XF_RECON,
                      extrap=None) -> dict:
-        """R4-R8 given a reconstruction (oracle's own, or another one to be judged). `extrap`: None for
+        """R4-R8 given a reconstruction (oracle's own, or another one to be checked). `extrap`: None for
         R5's single upwind sweep, else a dict (max_iter, tol, dtau; dtau <= 0 or absent: the mesh's)
         for the pseudo-time solve of Eq. (extrapolation); its six iteration counts come back as
         `extrap_iters` (liquid x, y, z, vapour x, y, z)."""

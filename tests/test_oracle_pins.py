@@ -74,8 +74,8 @@ MESHES = {
 @pytest.mark.parametrize("kind", sorted(MESHES))
 def test_P1_planar_interface_exact(kind):
     """P1: a linear vertex field phi = d - n.x with alpha = exact half-space fraction reproduces
-    c = 0, n_int = -n (vapour -> liquid), A_int = section area (spec: planar interfaces
-    reproduced exactly)."""
+    c = 0, n_int = -n (vapour -> liquid), A_int = section area (the method reproduces planar
+    interfaces exactly)."""
     m = MESHES[kind]()
     O = oracle.Oracle(m)
     rng = np.random.default_rng(11)
@@ -191,8 +191,7 @@ def _tet_root(f, alpha):
 
 def test_P4_bisection_matches_closed_form_root():
     """P4: on tetrahedra with a linear field the bisection root equals the closed-form root of the
-    cut-volume cubic, and |V_L(c)/V - alpha| <= 1e-12 (spec: cut volume equal to alpha V to
-    1e-12)."""
+    cut-volume cubic, and |V_L(c)/V - alpha| <= 1e-12 (the root's volume tolerance)."""
     m = synth.tet_box(2)
     O = oracle.Oracle(m)
     rng = np.random.default_rng(8)

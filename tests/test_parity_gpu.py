@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
 
-Bars (the benchmark spec): |V_L^oracle(c_GPU)/V - alpha| <= 1e-10 on every interface cell (the oracle
+Bars: |V_L^oracle(c_GPU)/V - alpha| <= 1e-10 on every interface cell (the oracle
 re-evaluates the GPU's isovalue, since several c can be correct to rounding); relative error
 <= 1e-8 on gradients, heat rates and mdot (relative to max(|x|, 1e-3 max|x|)); integer and index
 outputs bit-exact.
