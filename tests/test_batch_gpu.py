@@ -95,3 +95,39 @@ def test_autotune_choices_keep_parity():
         phi = g["phi_v"][voff:B.vert_off[i + 1]]
         for c in np.where((ai > 1e-12) & (ai < 1 - 1e-12))[0]:
             assert abs(O.liquid_volume(c, phi, g["iso"][off + c])["VL"] / V[c] - ai[c]) <= 1e-10
+
+
+def test_batch_extrapolation_shares_step_and_stop():
+    """The pseudo-time extrapolation in a batch: one mesh to the step, so dtau is the smallest over
+    the meshes and each solve stops when no mesh moves by tol or more. The step's homogeneous
+    iteration matrix is non-negative with row sums <= 1, so a mesh's largest change never grows:
+    the batch's count of a solve is the largest of the meshes' counts at the batch's dtau, and each
+    mesh's values are the oracle's after exactly that many iterations."""
+    names = ["voronoi_spheres", "hex_sphere", "prism_sphere"]
+    cases = [case(n) for n in names]
+    B = vof.Batch([c[0] for c in cases])
+    a = np.concatenate([c[1] for c in cases])
+    T = np.concatenate([c[2] for c in cases])
+    Tb = np.concatenate([c[3] for c in cases])
+    _run(B.mesh, a, T, Tb, B.mesh.n_cells, extrap=1)
+    K = B.mesh.counts()["extrap_iters"]
+    dtau = float(B.mesh.field("dtau").cpu().numpy()[0])
+    f = {k: B.mesh.field(k).cpu().numpy() for k in ("status", "A_int", "n_int", "x_gamma", "grad_l", "grad_v")}
+    own_K = []
+    for i, (m, ai, Ti, Tbi) in enumerate(cases):
+        O = oracle.Oracle(m)
+        assert O.extrap_dtau() >= dtau
+        c0, c1 = B.cell_off[i], B.cell_off[i + 1]
+        I = np.where((ai > 1e-12) & (ai < 1 - 1e-12))[0]  # the fields hold values on interface cells
+        rec = {k: f[k][c0:c1] for k in ("status", "A_int", "n_int", "x_gamma")}
+        own_K.append(O.phase_change(ai, rec, Ti, Tbi, synth.PROPS, extrap=dict(dtau=dtau))["extrap_iters"])
+        for k_it in sorted(set(K)):
+            pc = O.phase_change(ai, rec, Ti, Tbi, synth.PROPS, extrap=dict(dtau=dtau, max_iter=k_it, tol=0.0))
+            for j in range(6):
+                if K[j] != k_it:
+                    continue
+                side, comp = ("grad_l", "grad_v")[j // 3], j % 3
+                g, o = f[side][c0:c1, comp][I], pc[side][I, comp]
+                scale = max(np.abs(o).max(), 1e-300)
+                assert np.abs(g - o).max() <= 1e-8 * scale, (names[i], j)
+    assert list(K) == list(np.max(np.array(own_K), axis=0))
