@@ -5,9 +5,11 @@ oracle.cpp) plus an FP64 NumPy restatement of the isovalue-guess MLP (oracle.mlp
 check the CUDA library: only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import it. It shares no code with the library.
 
-Parity unpinned (no independent reference exists, only invariants): the inverse-distance vertex
-field on general meshes, the one-sweep per-side gradient, and the rule for faces whose two cells
-are both interface cells.
+Pinned only in special cases (no independent reference exists for general inputs): the one-sweep
+per-side gradient (closed forms when the neighbour gradients are equal; its upwind weights also
+enter the pseudo-time solve, whose first step at a Courant number of 1 reproduces it). The
+inverse-distance vertex field and the choice between two interface planes on one face are pinned
+by cases worked by hand (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

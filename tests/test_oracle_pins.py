@@ -597,3 +597,109 @@ def test_geometry_closed_cells():
     i = np.arange(4)
     exp = np.stack(np.meshgrid((i + 0.5) / 4, (i + 0.5) / 4, (i + 0.5) / 4, indexing="ij")[::-1], -1).reshape(-1, 3)
     np.testing.assert_allclose(g["cell_cen"], exp, atol=1e-15)
+
+
+def stretched_hex(xs, ys, zs):
+    """A hex mesh whose grid lines sit at the given node coordinates (a uniform hex box with each
+    coordinate mapped piecewise linearly onto the nodes): cells of different sizes, exact box
+    centroids."""
+    m = synth.hex_box(len(xs) - 1, len(ys) - 1, len(zs) - 1)
+    for attr, nodes in (("vx", xs), ("vy", ys), ("vz", zs)):
+        u = np.linspace(0.0, 1.0, len(nodes))
+        setattr(m, attr, np.interp(getattr(m, attr), u, np.asarray(nodes, np.float64)))
+    return m
+
+
+def box_cell(m, lo, hi):
+    """The cell of a stretched hex mesh whose vertices span the box [lo, hi] (found by its vertices)."""
+    for c in range(m.n_cells):
+        P = xyz(m, cell_vertex_ids(m, c))
+        if np.allclose(P.min(0), lo) and np.allclose(P.max(0), hi):
+            return c
+    raise KeyError((lo, hi))
+
+
+def vertex_at(m, x):
+    d = (m.vx - x[0]) ** 2 + (m.vy - x[1]) ** 2 + (m.vz - x[2]) ** 2
+    v = int(np.argmin(d))
+    assert d[v] == 0.0
+    return v
+
+
+def test_R1_inverse_distance_unequal_cells():
+    """R1 on cells of four different sizes, worked by hand. Grid lines x = 0, 1, 3 and y = 0, 1/2, 2,
+    one layer 0 <= z <= 1. The vertex (1, 1/2, 0) touches the four cells, whose box centroids are
+    (1/2, 1/4, 1/2), (2, 1/4, 1/2), (1/2, 5/4, 1/2) and (2, 5/4, 1/2), at distances 3/4, sqrt(21)/4,
+    sqrt(17)/4 and sqrt(29)/4; so phi_v = (a0/3 + a1/sqrt21 + a2/sqrt17 + a3/sqrt29) /
+    (1/3 + 1/sqrt21 + 1/sqrt17 + 1/sqrt29). The boundary vertex (1, 0, 0) touches the first two cells
+    at distances 3/4 and sqrt(21)/4: phi_v = (a0/3 + a1/sqrt21)/(1/3 + 1/sqrt21). A corner vertex
+    takes its one cell's alpha. Weights 1/|x|^2 or the plain mean give other values."""
+    m = stretched_hex([0.0, 1.0, 3.0], [0.0, 0.5, 2.0], [0.0, 1.0])
+    O = oracle.Oracle(m)
+    cells = [box_cell(m, (0, 0, 0), (1, 0.5, 1)), box_cell(m, (1, 0, 0), (3, 0.5, 1)),
+             box_cell(m, (0, 0.5, 0), (1, 2, 1)), box_cell(m, (1, 0.5, 0), (3, 2, 1))]
+    a = np.zeros(m.n_cells)
+    a[cells] = [0.2, 0.9, 0.55, 0.05]
+    phi = O.vertex_field(a)
+    w = np.array([1 / 3, 1 / math.sqrt(21), 1 / math.sqrt(17), 1 / math.sqrt(29)])
+    assert phi[vertex_at(m, (1, 0.5, 0))] == pytest.approx((w @ a[cells]) / w.sum(), rel=1e-14)
+    assert phi[vertex_at(m, (1, 0, 0))] == pytest.approx((0.2 / 3 + 0.9 / math.sqrt(21)) / w[:2].sum(), rel=1e-14)
+    assert phi[vertex_at(m, (3, 2, 1))] == 0.05
+    # the same vertex with the plain average (vertex_mode 1)
+    assert O.vertex_field(a, mode=1)[vertex_at(m, (1, 0.5, 0))] == pytest.approx(np.mean(a[cells]), rel=1e-14)
+
+
+def _two_cell_recon(m, cells, planes):
+    """A reconstruction given by hand: planes[k] = (A_int, n_int, x_gamma) of cells[k]."""
+    nc = m.n_cells
+    rec = dict(status=np.zeros(nc, np.int32), A_int=np.zeros(nc), n_int=np.zeros((nc, 3)), x_gamma=np.zeros((nc, 3)))
+    for c, (A, n, xg) in zip(cells, planes):
+        rec["A_int"][c] = A
+        rec["n_int"][c] = np.asarray(n, np.float64) / np.linalg.norm(n)
+        rec["x_gamma"][c] = xg
+    return rec
+
+
+def _shared_face(m, p, q):
+    for f in range(m.n_faces):
+        if {int(m.face_owner[f]), int(m.face_neigh[f])} == {p, q}:
+            return f
+    raise KeyError((p, q))
+
+
+@pytest.mark.parametrize("case", ["owner_nearer", "neighbour_nearer", "owner_outside", "both_outside"])
+def test_R4_two_interface_cells_nearest_plane(case):
+    """R4 when both cells of a crossing face are interface cells with different planes, worked by
+    hand. Cells [0, 1] and [1, 3] along x (unit cross-section), centroids x = 1/2 and x = 2, so the
+    centroid segment is x = 1/2 + 3/2 t; the face centroid is at x = 1. alpha = 0.7 | 0.3 (liquid on
+    the left: n_int = -e_x). A plane x = p crosses at t = (p - 1/2)/(3/2), at distance |p - 1| from
+    the face centroid; the plane nearer the face centroid gives x_f, one whose t leaves [0, 1] does
+    not count, and with neither the linear interpolation t = (0.7 - 0.5)/(0.7 - 0.3) = 1/2 applies.
+    The projected area A_int,f = |A_int n_int . n_f| follows the plane that was used. Tilted planes
+    (normal (-1, -1, 0)) cross the centre line y = 1/2 at the same x."""
+    m = stretched_hex([0.0, 1.0, 3.0], [0.0, 1.0], [0.0, 1.0])
+    p, q = box_cell(m, (0, 0, 0), (1, 1, 1)), box_cell(m, (1, 0, 0), (3, 1, 1))
+    a = np.zeros(m.n_cells)
+    a[p], a[q] = 0.7, 0.3
+    xp, xq = {"owner_nearer": (0.8, 1.5), "neighbour_nearer": (0.6, 1.1), "owner_outside": (0.2, 1.9),
+              "both_outside": (0.1, 2.9)}[case]
+    # cell p: axis-normal plane, area 1; cell q: tilted plane through (xq, 1/2, 1/2), area 0.5
+    rec = _two_cell_recon(m, [p, q], [(1.0, (-1, 0, 0), (xp, 0.5, 0.5)), (0.5, (-1, -1, 0), (xq, 0.5, 0.5))])
+    T = np.full(m.n_cells, synth.T_SAT)
+    pc = oracle.Oracle(m).phase_change(a, rec, T, None, synth.PROPS)
+    f = _shared_face(m, p, q)
+    assert pc["crossing"][f] == 1
+    tp, tq = (xp - 0.5) / 1.5, (xq - 0.5) / 1.5
+    cand = [(abs(x - 1.0), x, A) for x, t, A in ((xp, tp, 1.0), (xq, tq, 0.5 / math.sqrt(2))) if 0 <= t <= 1]
+    o = int(m.face_owner[f])
+    if cand:
+        _, x_exp, Af_exp = min(cand)
+    else:  # linear interpolation; the projected area then comes from the owner's plane
+        x_exp, Af_exp = 0.5 + 1.5 * 0.5, 1.0 if o == p else 0.5 / math.sqrt(2)
+    want = {"owner_nearer": 0.8, "neighbour_nearer": 1.1, "owner_outside": 1.9, "both_outside": 1.25}[case]
+    assert x_exp == want
+    np.testing.assert_allclose(pc["x_f"][f], [x_exp, 0.5, 0.5], rtol=0, atol=1e-15)
+    d_o, d_n = (x_exp - 0.5, 2.0 - x_exp) if o == p else (2.0 - x_exp, x_exp - 0.5)
+    assert pc["d_own"][f] == pytest.approx(d_o, rel=1e-14)
+    assert pc["d_neigh"][f] == pytest.approx(d_n, rel=1e-14)
+    assert pc["A_int_f"][f] == pytest.approx(Af_exp, rel=1e-14)
