@@ -81,6 +81,7 @@ def _lib():
         _LIB.orc_geometry.argtypes = [ctypes.c_void_p] * 5
         _LIB.orc_pairwise_sum.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         _LIB.orc_interface_htc.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_double] * 2 + [ctypes.c_void_p] * 2
+        _LIB.orc_htc_cell_sums.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_double] + [ctypes.c_void_p] * 2
     return _LIB
 
 
@@ -217,6 +218,11 @@ class Oracle:
         o["a_own"], o["a_neigh"] = np.zeros(nf), np.zeros(nf)
         _lib().orc_interface_htc(self.ref, _p(arr(alpha)), _p(o["crossing"]), _p(o["A_int_f"]), _p(o["d_own"]),
                                  _p(o["d_neigh"]), props["k_l"], props["k_v"], _p(o["a_own"]), _p(o["a_neigh"]))
+        # each cell's energy-matrix contributions of its detached faces: diagonal sum a_f, right-hand
+        # side sum a_f T_sat
+        o["htc_diag"], o["htc_rhs"] = np.zeros(nc), np.zeros(nc)
+        _lib().orc_htc_cell_sums(self.ref, _p(o["crossing"]), _p(o["a_own"]), _p(o["a_neigh"]), float(props["T_sat"]),
+                                 _p(o["htc_diag"]), _p(o["htc_rhs"]))
         return o
 
     def run(self, alpha, T, T_bnd, props, eps=1e-12, tol=1e-12, vertex_mode=0, xf_mode=XF_RECON) -> dict:

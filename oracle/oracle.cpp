@@ -893,6 +893,27 @@ void orc_interface_htc(const OrcMesh* mp, const double* alpha, const uint8_t* cr
   }
 }
 
+// Eq. interface_htc's place in the energy equation (next row N3): a cell whose face f is detached
+// from the diffusive coupling by the interface adds a_f to its matrix diagonal and a_f T_sat to its
+// right-hand side. Per cell, over its faces in the cell's face order: diag = sum a_f, rhs =
+// sum a_f T_sat, with a_f the coefficient of the cell's own side of the face.
+void orc_htc_cell_sums(const OrcMesh* mp, const uint8_t* crossing, const double* a_own, const double* a_neigh,
+                       double T_sat, double* diag, double* rhs) {
+  const OrcMesh& m = *mp;
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    double d = 0, r = 0;
+    for (int64_t k = m.cell_face_off[c]; k < m.cell_face_off[c + 1]; ++k) {
+      const int32_t f = m.cell_face[k] & 0x7fffffff;
+      if (!crossing[f]) continue;
+      const double a = m.face_owner[f] == c ? a_own[f] : a_neigh[f];
+      d += a;
+      r += a * T_sat;
+    }
+    diag[c] = d;
+    rhs[c] = r;
+  }
+}
+
 // N2 alone, on a given gradient field: g_other [3 n_cells] receives the other side's gradient of
 // every interface cell (iface[c] != 0; its phase: liquid when alpha > 1/2), iters[6] the counts.
 void orc_extrapolate(const OrcMesh* m, const double* face_area, const double* cell_vol, const double* alpha,

@@ -470,6 +470,55 @@ def test_P12_interface_htc_stefan(frac):
     assert not np.any(pc["a_own"][others]) and not np.any(pc["a_neigh"][others])
 
 
+@pytest.mark.parametrize("frac", [0.23, 0.81])
+def test_P12_energy_matrix_terms_stefan(frac):
+    """P12 (next row N3, Eq. interface_htc in the energy equation): on the planar Stefan layer each
+    cell next to the interface has exactly one detached face, so its diagonal term is k_phi h^2 / d
+    (d its centre's distance to the plane x = x_g) and its right-hand side that times T_sat; every
+    other cell has none."""
+    r, I, V, xg, dT = _stefan(frac)
+    pc = r["pc"]
+    m = synth.hex_box(20, 3, 3, lo=(0, 0, 0), hi=(2e-3, 3e-4, 3e-4))
+    cen = oracle.Oracle(m).geometry()["cell_cen"]
+    h = 1e-4
+    touched = set()
+    for f in np.where(pc["crossing"])[0]:
+        touched |= {int(m.face_owner[f]), int(m.face_neigh[f])}
+    assert len(touched) == 18
+    for c in range(m.n_cells):
+        if c in touched:
+            k = synth.PROPS["k_l"] if cen[c, 0] > xg else synth.PROPS["k_v"]
+            assert pc["htc_diag"][c] == pytest.approx(k * h * h / abs(cen[c, 0] - xg), rel=1e-12)
+            assert pc["htc_rhs"][c] == pytest.approx(pc["htc_diag"][c] * synth.T_SAT, rel=1e-15)
+        else:
+            assert pc["htc_diag"][c] == 0.0 and pc["htc_rhs"][c] == 0.0
+
+
+def test_P12_energy_matrix_terms_two_faces():
+    """P12 with a cell detached on two faces, worked by hand. Cells [0, 1], [1, 3], [3, 4] along x
+    (unit cross-section, centroids x = 1/2, 2, 7/2), alpha = 0.3 | 0.9 | 0.1, all interface cells,
+    linear crossing points (Eq. front_interpolation read as linear interpolation): the face x = 1
+    has t = 1/3, so x_f = 1 and d = 1/2 | 1; the face x = 3 has t = 1/2, so x_f = 11/4 and
+    d = 3/4 | 3/4. Each face's projected area comes from its owner's plane: 1 on the first
+    (normal e_x), 0.8 |n . e_x| = 0.8/sqrt2 on the second (normal (1, 1, 0)/sqrt2). So the
+    diagonal terms are 2 k_v, k_l + k_l 0.8/(0.75 sqrt2) and k_v 0.8/(0.75 sqrt2); the right-hand
+    sides are those times T_sat."""
+    m = stretched_hex([0.0, 1.0, 3.0, 4.0], [0.0, 1.0], [0.0, 1.0])
+    cells = [box_cell(m, (0, 0, 0), (1, 1, 1)), box_cell(m, (1, 0, 0), (3, 1, 1)), box_cell(m, (3, 0, 0), (4, 1, 1))]
+    a = np.zeros(m.n_cells)
+    a[cells] = [0.3, 0.9, 0.1]
+    assert all(int(m.face_owner[_shared_face(m, cells[i], cells[i + 1])]) == cells[i] for i in range(2))
+    rec = _two_cell_recon(m, cells, [(1.0, (1, 0, 0), (0.9, 0.5, 0.5)), (0.8, (1, 1, 0), (2.9, 0.5, 0.5)),
+                                     (0.5, (-1, 0, 0), (3.1, 0.5, 0.5))])
+    T = np.full(m.n_cells, synth.T_SAT)
+    pc = oracle.Oracle(m).phase_change(a, rec, T, None, synth.PROPS, xf_mode=oracle.XF_LINEAR)
+    kl, kv = synth.PROPS["k_l"], synth.PROPS["k_v"]
+    g = 0.8 / (0.75 * math.sqrt(2.0))
+    for c, want in zip(cells, (2 * kv, kl + kl * g, kv * g)):
+        assert pc["htc_diag"][c] == pytest.approx(want, rel=1e-14)
+        assert pc["htc_rhs"][c] == pytest.approx(want * synth.T_SAT, rel=1e-14)
+
+
 def test_P12_fixed_isovalue_planar():
     """P12 (next row N3): with the vertex field linear in x the alpha_iso = 0.5 surface is the plane
     where that field is 0.5; its area in each cut cell is the cell's cross-section (1/3)^2, its
