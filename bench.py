@@ -5,9 +5,11 @@ One step = reconstruct (interface cells, vertex field, isovalue root search, int
 geometry) + phase-change source (interface-modified least-squares gradient on the band, per-side
 gradients, q_l, q_v, mdot, Q, totals) over one synthetic input, through the library's C ABI.
 
-Default workload: jittered-BCC Voronoi mesh, 2 * 50^3 = 250,000 cells on the unit cube (seed 1,
-jitter +-h/4), wavy liquid film z < 0.3 + 0.03 sin(2 pi x) sin(2 pi y), T linear across the film
-from T_sat + 10 K at the wall to T_sat at the interface, water/steam properties.
+Default workload: the large annular case, learned and batched. An extruded jittered 2D Voronoi
+disk of radius 1, 600 layers over length 6 (7,903,200 cells), with a wall liquid film
+r > 0.9 - 0.04 sin(2 pi (z - t)/0.5) that moves one layer per step; T falls linearly from
+T_sat + 8 K at the wall to T_sat at the interface. 100 consecutive steps' alpha and T are
+resident on the device, and step k reads pair k mod 100.
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle instead (host cores).
 Multi-GPU (torchrun, N > 1): every rank processes its own replica of the workload (replicas;
@@ -18,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -32,16 +35,20 @@ from synth.workloads import NAMES as WORKLOADS, workload  # noqa: E402
 
 METRIC = "interface cells/s (recon+LSQ∇T+mdot), learned vs bisection, at |Δα|≤1e-10"
 UNIT = "interface cells/s"
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
+FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
-# Algorithmic work of one FP64 cut-volume evaluation of a Voronoi cell of about 14 faces: 36
-# straddle tests, ~15 cut points and ~90 fan tetrahedra at ~20 flops, about 2 kFLOP, the per-unit
-# figure of the roofline (a learned cell needs 3-4 such evaluations, a bisection cell about 40)
-ALG_FLOPS_PER_EVAL = 2000
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step's root-search launches,
-# all bins, measured with ncu --set full on a GB300 for the workload, path and lanes per cell given;
-# the roofline reports null traffic for anything else
-ROOT_TRAFFIC = {("film250k", "learned", (0, 0, 32, 16, 0)): 6_535_168}
+RESIDENT_STEPS = 100  # device-resident input pairs of the moving-film workload (default)
+# The survey's per-unit figure, kept as a secondary basis: about 2 kFLOP per FP64 cut-volume
+# evaluation of a Voronoi cell of about 14 faces (36 straddle tests, ~15 cut points, ~90 fan
+# tetrahedra at ~20 flops). The roofline's own basis is the FP64 work the kernel counts on the
+# device (prepared rows, three-FMA evaluations of the straddling rows).
+SURVEY_FLOPS_PER_EVAL = 2000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per root-search launch, from ncu
+# captures of the workload (and layers), path and lanes per cell given; null for anything else
+ROOT_TRAFFIC: dict = {}
+# path name -> (root mode, pseudo-time extrapolation, guess option)
+PATHS = {"bisect": (0, 0, 0), "learned": (1, 0, 0), "learned_nomlp": (1, 0, 1), "cubic": (2, 0, 1),
+         "learned_extrap": (1, 1, 0)}
 
 
 class Clocks:
@@ -104,12 +111,49 @@ class Clocks:
                 "window_s": round((self.t1 or 0) - (self.t0 or 0), 3)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def n_interface(a) -> int:
+    return int(np.count_nonzero((a > 1e-12) & (a < 1 - 1e-12)))
+
+
+def bench_config(args, desc, n_cells, a, extra) -> dict:
+    """The workload as both arms report it (same dict for the GPU path and the oracle arm)."""
+    return {"workload": args.workload, "description": desc, "n_cells": int(n_cells), "n_iface": n_interface(a),
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)",
+            "parallelism": "replicas" if args.gpus > 1 else "single", **extra,
+            **({"resident_steps": args.resident} if args.workload == "pipe8m" else {})}
+
+
+def path_options(vof, name):
+    mode, extrap, guess = PATHS[name]
+    return vof.default_options(root_mode=mode, extrap=extrap, guess=guess)
+
+
 def run_ours(args, rank, world, dev):
     import torch
     import paper_2604_14938_gb300 as vof
     import synth
 
-    meshes, a, T, Tb, desc, extra = workload(args.workload)
+    meshes, a, T, Tb, desc, extra = workload(args.workload, layers=args.layers)
     batch = isinstance(meshes, list)
     if batch:
         B = vof.Batch(meshes)
@@ -123,10 +167,10 @@ def run_ours(args, rank, world, dev):
     with torch.cuda.stream(stream):
         d = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
         if pipe:
-            # 100 device-resident steps: the film translates one layer (n2d cells) per step
+            # device-resident steps: the film translates one layer (n2d cells) per step
             n2d = nc // extra["layers"]
-            ta_k = [d(np.roll(a, k * n2d)) for k in range(100)]
-            tT_k = [d(np.roll(T, k * n2d)) for k in range(100)]
+            ta_k = [d(np.roll(a, k * n2d)) for k in range(args.resident)]
+            tT_k = [d(np.roll(T, k * n2d)) for k in range(args.resident)]
             tTb = None
         else:
             ta_k, tT_k, tTb = [d(a)], [d(T)], d(Tb)
@@ -135,25 +179,21 @@ def run_ours(args, rank, world, dev):
         tot = torch.empty(2, dtype=torch.float64, device=dev)
         btot = torch.empty((B.n, 2), dtype=torch.float64, device=dev) if batch else None
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-        learned_ok = args.root in ("auto", "learned", "learned_extrap") and vof.load_default_mlp(M)
-        # learned_extrap: the learned path with the pseudo-time solve of Eq. (extrapolation) for the
-        # other-side gradients instead of the single upwind sweep (same lanes per cell as learned)
-        modes = ((["bisect"] if args.root in ("auto", "bisect") else [])
-                 + (["learned"] if learned_ok and args.root != "learned_extrap" else [])
-                 + (["learned_extrap"] if learned_ok and args.root in ("auto", "learned_extrap") else [])
-                 + (["cubic"] if args.root in ("auto", "cubic") else []))
+        have_mlp = vof.load_default_mlp(M)
+        if args.root == "auto":
+            modes = ["bisect"] + (["learned", "learned_nomlp"] if have_mlp else []) + ["cubic"] + \
+                    (["learned_extrap"] if have_mlp and not args.no_extrap else [])
+        else:
+            modes = [args.root]
+            if args.root in ("learned", "learned_extrap") and not have_mlp:
+                raise RuntimeError("the learned path needs the shipped MLP weights (mlp_iso.npy)")
+        fp64 = vof.fp64_peak(stream=stream)  # the FP64 roofline's denominator, measured in this run
         tuned = {}
         for mode in modes:
-            opt = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
-                                                 "learned_extrap": vof.ROOT_LEARNED, "cubic": vof.ROOT_CUBIC}[mode],
-                                      extrap=int(mode == "learned_extrap"))
-            if mode == "cubic":  # from 1 - alpha: on these workloads the guess costs more than it saves
-                M.set_mlp(None)
-            if mode == "learned_extrap" and "learned" in tuned:
+            opt = path_options(vof, mode)
+            if mode == "learned_extrap" and "learned" in tuned:  # the same root search as the learned path
                 tuned[mode] = tuned["learned"]
                 M.set_group_sizes(tuned[mode])
-            elif mode == "learned_extrap" and not args.group_sizes:  # the lanes per cell do not depend on it
-                tuned[mode] = M.autotune(ta_k[0], vof.default_options(root_mode=vof.ROOT_LEARNED), reps=10)
             elif args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
                 tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
                 M.set_group_sizes(tuned[mode])
@@ -192,25 +232,26 @@ def run_ours(args, rank, world, dev):
             ms = sum(s0.elapsed_time(e0) for s0, e0 in ev)
             cnt = M.counts(stream=stream)
             units = sum(iface) if pipe else cnt["n_iface"] * args.steps
-            # one more pass, eager with per-kernel events, for the kernel times of the roofline
+            # one more pass, eager with per-kernel events, for the kernel times of the roofline; the
+            # device counters are read after every step (they are reset by the next one)
             M.timing_enable(True)
+            ksum = {}
             for k in range(min(args.steps, 5)):
-                opt_e = opt
                 ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
-                M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt_e, stream=stream)
+                flush.fill_(k & 0xFF)
+                M.step(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt, stream=stream)
+                c = M.counts(stream=stream)
+                for key in ("n_iface", "evals_total", "tet_evals", "tets_prepared", "evals32_total"):
+                    ksum[key] = ksum.get(key, 0) + c[key]
             kt = M.timing_read(stream=stream)
             M.timing_enable(False)
-            kcnt = M.counts(stream=stream)
-            results[mode] = dict(ms=ms, units=units, counts=cnt, kcounts=kcnt, ktime=kt, clocks=clk.summary())
+            results[mode] = dict(ms=ms, units=units, counts=cnt, ksum=ksum, ktime=kt, clocks=clk.summary(),
+                                 mean_iface=units / args.steps)
         # end to end: host buffers through vof_step_host, copies inside the timed region, in the
         # headline mode with its own tuned lanes per cell
         best_mode = headline_mode(results)
-        if best_mode in ("learned", "learned_extrap"):
-            vof.load_default_mlp(M)
         M.set_group_sizes(tuned[best_mode])
-        opt_best = vof.default_options(root_mode={"bisect": vof.ROOT_BISECT, "learned": vof.ROOT_LEARNED,
-                                                  "learned_extrap": vof.ROOT_LEARNED, "cubic": vof.ROOT_CUBIC}[best_mode],
-                                       extrap=int(best_mode == "learned_extrap"))
+        opt_best = path_options(vof, best_mode)
         pin = lambda x: torch.as_tensor(np.ascontiguousarray(x)).pin_memory()
         ha, hT = pin(a), pin(T)
         hTb = None if pipe else pin(Tb)
@@ -226,15 +267,16 @@ def run_ours(args, rank, world, dev):
     # bytes in: alpha and T, and T_bnd at the boundary faces (pinned: the library gathers only
     # those entries from host memory); out: mdot and the totals
     n_bnd = sum(int((np.asarray(mm.face_neigh) < 0).sum()) for mm in (meshes if isinstance(meshes, list) else [meshes]))
-    info = dict(n_cells=nc, batch=batch, pipe=pipe, tuned=tuned, extra=extra, e2e_units=e2e_units,
+    info = dict(n_cells=nc, batch=batch, pipe=pipe, tuned=tuned, extra=extra, e2e_units=e2e_units, fp64=fp64,
                 h2d=8 * (2 * nc + (0 if pipe else n_bnd)), d2h=8 * (nc + 2))
     return M, (meshes, a, T, Tb), desc, results, e2e_s, info
 
 
 def headline_mode(results) -> str:
     """The path the headline value reports: learned when it ran, else bisection, the interval
-    cubic, or the learned path with the pseudo-time extrapolation."""
-    return next(k for k in ("learned", "bisect", "cubic", "learned_extrap") if k in results)
+    cubic, the learned path without its network, or the learned path with the pseudo-time
+    extrapolation."""
+    return next(k for k in ("learned", "bisect", "cubic", "learned_nomlp", "learned_extrap") if k in results)
 
 
 def job_rate(units: float, seconds: float, device=None) -> tuple[float, float]:
@@ -268,23 +310,36 @@ def _oracle_step(O, a, T, Tb, cells):
     return (t1 - t0) + (t3 - t2), t2 - t1
 
 
+def _sample_note(tf, tr, n, n_all, reps, cores):
+    return (f"vertex field and downstream steps over the whole mesh, one thread ({tf:.2f} s per pass); FP64 "
+            f"bisection reconstruction (OpenMP, {cores} threads) of {n} of {n_all} interface cells (index-order "
+            f"prefix, {tr:.2f} s per pass) scaled to all of them; {reps} passes")
+
+
+def _oracle_sample(O, a, T, Tb, I, step_budget_s):
+    """Index-order prefix of the interface cells whose reconstruction takes about step_budget_s
+    minus the whole-mesh parts (at least 256 cells). Returns (n, whole-mesh seconds, seconds of
+    the sampled reconstruction) of the last sizing pass."""
+    n = min(len(I), 256)
+    while True:
+        fixed, rec = _oracle_step(O, a, T, Tb, I[:n])
+        want = max(step_budget_s - fixed, 0.25)
+        if n >= len(I) or rec > 0.6 * want:
+            return n, fixed, rec
+        n = min(len(I), int(n * min(8.0, max(1.5, want / max(rec, 1e-3)))))
+
+
 def cpu_baseline(m, a, T, Tb, budget_s=12.0):
     """The oracle as it stands on the host cores, timed with perf_counter to about budget_s
     seconds of work: the whole-mesh parts in full, the reconstruction on an index-order prefix
-    sample of the interface cells, scaled to all of them. Returns (line, sample size, seconds of
-    one whole-workload pass)."""
+    sample of the interface cells, scaled to all of them."""
     import oracle
 
     O = oracle.Oracle(m)
     O.geometry()  # mesh geometry is set-up work, as on the GPU
     I = np.where((a > 1e-12) & (a < 1 - 1e-12))[0]
-    n = min(len(I), 256)
-    while True:
-        fixed, rec = _oracle_step(O, a, T, Tb, I[:n])
-        if n >= len(I) or rec > budget_s / 8:
-            break
-        n = min(len(I), int(n * max(2.0, budget_s / 8 / max(rec, 1e-3))))
-    reps = max(1, int(budget_s / max(fixed + rec, 1e-3)))
+    n, fixed, rec = _oracle_sample(O, a, T, Tb, I, budget_s / 3)
+    reps = max(1, int(budget_s / max(fixed + rec, 1e-3)) - 1)
     tf = tr = 0.0
     for _ in range(reps):
         f, r = _oracle_step(O, a, T, Tb, I[:n])
@@ -292,23 +347,62 @@ def cpu_baseline(m, a, T, Tb, budget_s=12.0):
         tr += r / reps
     whole = tf + tr * len(I) / max(n, 1)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dict(value=len(I) / whole, unit=UNIT, cores=cores, kind="oracle",
-                sample=f"vertex field and downstream steps over the whole mesh ({tf:.2f} s), FP64 bisection "
-                       f"reconstruction of {n} of {len(I)} interface cells (index-order prefix, {tr:.2f} s) "
-                       f"scaled to all of them; {reps} repetitions"), n, whole
+    return dict(value=len(I) / whole, unit=UNIT, cores=cores, kind="oracle", cpu=cpu_model(),
+                sample=_sample_note(tf, tr, n, len(I), reps, cores))
+
+
+def reference_arm(args):
+    """The oracle on the host cores as the reference arm: each step one oracle pass over a
+    bounded sample of the workload (whole-mesh parts in full, the reconstruction on a prefix of
+    the interface cells, scaled to all of them), sized so that warm-up and timed steps together
+    take about three minutes."""
+    m, a, T, Tb, desc, extra = workload(args.workload, layers=args.layers)
+    if isinstance(m, list):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers single-mesh workloads"}))
+        return
+    import oracle
+    if args.workload == "pipe8m":
+        Tb = None  # the moving-film steps leave the boundary faces out of the stencil, as the GPU arm does
+    O = oracle.Oracle(m)
+    O.geometry()
+    I = np.where((a > 1e-12) & (a < 1 - 1e-12))[0]
+    n, _, _ = _oracle_sample(O, a, T, Tb, I, 180.0 / (args.warmup + args.steps))
+    tf, tr = [], []
+    for k in range(args.warmup + args.steps):
+        f, r = _oracle_step(O, a, T, Tb, I[:n])
+        if k >= args.warmup:
+            tf.append(f)
+            tr.append(r)
+    # one step = the whole workload: the sampled reconstruction scaled to every interface cell
+    step_s = (sum(tf) + sum(tr) * len(I) / max(n, 1)) / len(tf)
+    v = len(I) / step_s
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cb = dict(value=v, unit=UNIT, cores=cores, kind="oracle", cpu=cpu_model(),
+              sample=_sample_note(sum(tf) / len(tf), sum(tr) / len(tr), n, len(I), len(tf), cores))
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": bench_config(args, desc, m.n_cells, a, extra),
+                      "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="film250k", choices=list(WORKLOADS))
-    ap.add_argument("--root", default="auto", choices=["auto", "bisect", "learned", "cubic", "learned_extrap"],
-                    help="auto: every path, the learned one as the headline; learned_extrap: the learned path "
-                         "with the pseudo-time solve of Eq. (extrapolation) alone")
+    ap.add_argument("--workload", default="pipe8m", choices=list(WORKLOADS))
+    ap.add_argument("--layers", type=int, default=600,
+                    help="layers of the pipe workload (600: the full case; fewer: a smaller case for profiling)")
+    ap.add_argument("--resident", type=int, default=RESIDENT_STEPS,
+                    help="device-resident input pairs of the pipe workload (fewer: a smaller device footprint for "
+                         "profiling)")
+    ap.add_argument("--root", default="auto", choices=["auto"] + list(PATHS),
+                    help="auto: every path, the learned one as the headline; otherwise that path alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extrap", action="store_true", help="auto without the pseudo-time extrapolation path")
     ap.add_argument("--group-sizes", default="",
                     help="lanes per cell of the five tetrahedron-count bins, comma-separated (skips the autotuner)")
     args = ap.parse_args()
@@ -317,32 +411,8 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        m, a, T, Tb, desc, _ = workload(args.workload)
-        if isinstance(m, list):
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers single-mesh workloads"}))
-            return
-        base, n, _ = cpu_baseline(m, a, T, Tb, budget_s=6.0)
-        import oracle
-        O = oracle.Oracle(m)
-        I = np.where((a > 1e-12) & (a < 1 - 1e-12))[0]
-        tf, tr = [], []
-        for k in range(args.warmup + args.steps):
-            f, r = _oracle_step(O, a, T, Tb, I[:n])
-            if k >= args.warmup:
-                tf.append(f)
-                tr.append(r)
-        # one step = the whole workload: the sampled reconstruction scaled to every interface cell
-        step_s = (sum(tf) + sum(tr) * len(I) / max(n, 1)) / len(tf)
-        v = len(I) / step_s
-        cb = dict(base, value=v)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": args.workload, "description": desc},
-                          "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                                      "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            reference_arm(args)
         return
 
     import torch
@@ -354,67 +424,72 @@ def main():
     M, fields, desc, res, e2e_s, info = run_ours(args, rank, world, dev)
     best = headline_mode(res)
     r = res[best]
-    n_iface = r["counts"]["n_iface"]
     value, s_max = job_rate(r["units"], r["ms"] / 1e3, dev)
     ms_max = s_max * 1e3
     paths = {k: job_rate(v["units"], v["ms"] / 1e3, dev) for k, v in res.items()}
     e2e_value, _ = job_rate(info["e2e_units"], e2e_s, dev)
-    # roofline of the dominant kernel (the root search): algorithmic FP64 flops per launch,
-    # from the device counters of the same step whose kernel time the events measured
-    # per step: the eager timing pass records one selection group per step and one root-search
-    # launch per non-empty bin (bins run as parallel branches: their launch times are summed)
-    nst = max(r["ktime"]["select"][1], 1)
-    root_ms = r["ktime"]["root"][0] / nst
-    # algorithmic work: the per-evaluation figure times the FP64 evaluations the step made (device
-    # counter); the kernel's own count of its FP64 arithmetic is reported beside it
-    flops = ALG_FLOPS_PER_EVAL * r["kcounts"]["evals_total"]
-    counted = M.root_flops(r["kcounts"])
-    achieved = flops / (root_ms / 1e3) / 1e12 if root_ms and flops else None
-    ksum = sum(v[0] for v in r["ktime"].values())
-    share = {k: round(v[0] / max(ksum, 1e-30), 4) for k, v in r["ktime"].items() if v[1]}
+    # roofline of the root search: the FP64 work the kernel counts on the device over the eager
+    # timing pass, over the summed durations of its launches (one per non-empty bin and step; the
+    # bins run as parallel branches), against the FP64 rate measured in this run
+    kt, ks = r["ktime"], r["ksum"]
+    nst = max(kt["select"][1], 1)
+    root_ms, root_launches = kt["root"]
+    counted = M.root_flops(ks)
+    survey = SURVEY_FLOPS_PER_EVAL * ks["evals_total"]
+    peak = info["fp64"]["tflops"]
+    achieved = counted / (root_ms / 1e3) / 1e12 if root_ms and counted else None
+    survey_tf = survey / (root_ms / 1e3) / 1e12 if root_ms and survey else None
+    ktot = sum(v[0] for v in kt.values())
+    share = {k: round(v[0] / max(ktot, 1e-30), 4) for k, v in kt.items() if v[1]}
     nbins = sum(1 for c in M.bin_cells if c)  # the root search launches once per non-empty bin
-    # selection, crossing list, crossing faces, least squares, source, geometry; guess (2); the
-    # pseudo-time extrapolation; batch totals
-    per_step = (6 + nbins + (2 if best in ("learned", "learned_extrap") else 0) + (1 if best == "learned_extrap" else 0)
+    mlp_used = best in ("learned", "learned_extrap")
+    # selection, crossing list, crossing points, least squares, source, geometry; root search per
+    # bin; MLP features and forward; the pseudo-time extrapolation; batch totals
+    per_step = (6 + nbins + (2 if mlp_used else 0) + (1 if best == "learned_extrap" else 0)
                 + (1 if info["batch"] else 0))
+    config = bench_config(args, desc, info["n_cells"], fields[1], info["extra"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n_cells": info["n_cells"], "n_iface": n_iface,
-                   "root": best, "group_sizes_by_bin": info["tuned"][best],
-                   "step": "eager launches per step" if info["pipe"] else "CUDA graph replay",
-                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single", **info["extra"]},
+        "dtype": "f64", "data": "synthetic", "config": config,
+        "path": {"root": best, "group_sizes_by_bin": info["tuned"][best], "n_iface_mean": r["mean_iface"],
+                 "step": ("eager launches per step (a different resident input pair every step)" if info["pipe"]
+                          else "CUDA graph replay")},
         "paths": {k: {"value": paths[k][0], "ms_per_step": paths[k][1] * 1e3 / args.steps,
                       "evals_per_cell": v["counts"]["evals_total"] / max(v["counts"]["n_iface"], 1),
                       "fp32_evals_per_cell": v["counts"]["evals32_total"] / max(v["counts"]["n_iface"], 1),
                       "fallbacks": v["counts"]["n_fallback"], "not_converged": v["counts"]["n_not_converged"],
                       "mlp_skipped": v["counts"]["n_mlp_skipped"], "group_sizes_by_bin": info["tuned"][k],
-                      **({"extrap_iters": v["counts"]["extrap_iters"],
-                          "extrap_kernel_ms": v["ktime"]["extrap"][0] / max(v["ktime"]["select"][1], 1)}
-                         if k == "learned_extrap" else {})}
+                      "kernel_ms_per_step": {kk: vv[0] / max(v["ktime"]["select"][1], 1)
+                                             for kk, vv in v["ktime"].items() if vv[1]},
+                      **({"extrap_iters": v["counts"]["extrap_iters"]} if k == "learned_extrap" else {})}
                   for k, v in res.items()},
-        "kernel_ms_per_step": {k: v[0] / nst for k, v in r["ktime"].items() if v[1]},
+        "kernel_ms_per_step": {k: v[0] / nst for k, v in kt.items() if v[1]},
         "kernel_share": share,
         "roofline": {"kernel": "k_root (isovalue root search)", "bound": "alu",
-                     "flops_per_launch": flops, "flops_per_iface_cell": flops / max(r["kcounts"]["n_iface"], 1),
-                     "flops_basis": f"{ALG_FLOPS_PER_EVAL} algorithmic flops per FP64 cut-volume evaluation x "
-                                    "the evaluations of one step (all bins)",
-                     "flops_counted_per_iface_cell": counted / max(r["kcounts"]["n_iface"], 1),
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                     "traffic": ROOT_TRAFFIC.get((args.workload, best, tuple(info["tuned"][best]))),
-                     "peak_source": "FP64: 152 SMs x 2070 MHz x 4 flop/clk/SM (2 FMA); no FP64 figure in the "
-                                    "measured peaks (an FMA-chain probe measured 1.20 TFLOP/s)"},
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": ROOT_TRAFFIC.get((args.workload, args.layers, best, tuple(info["tuned"][best]))),
+                     "flops_per_launch": counted / max(root_launches, 1),
+                     "flops_per_iface_cell": counted / max(ks["n_iface"], 1),
+                     "launches": root_launches, "ms_per_launch": root_ms / max(root_launches, 1),
+                     "flops_basis": "FP64 work counted on the device: 8 flops per tetrahedron row evaluation, 24 per "
+                                    "row prepared, 2 per evaluation (summed over the eager timing pass)",
+                     "peak_source": (f"FP64 FMA-chain probe in this run (vof_probe_fp64_fma: 8 independent chains per "
+                                     f"thread, every SM at full occupancy, best of 3): {peak:.4f} TFLOP/s of measured; "
+                                     f"nominal 152 SMs x 2070 MHz x 4 flop/clk = {FP64_NOMINAL_TFLOPS:.4f}"),
+                     "survey_basis": {"flops_per_eval": SURVEY_FLOPS_PER_EVAL, "achieved": survey_tf,
+                                      "frac": survey_tf / peak if survey_tf else None,
+                                      "note": "the survey's 2 kFLOP per FP64 cut-volume evaluation of a ~14-face cell "
+                                              "x the evaluations made; it credits the windowed rows' saving, so it "
+                                              "can exceed the peak on small cells"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
                 "d2h_bytes_per_step": info["d2h"]},
         "gpu_launches": args.steps * per_step,
         "clocks": r["clocks"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not info["batch"]:
-        cb, _, _ = cpu_baseline(fields[0], fields[1], fields[2], None if info["pipe"] else fields[3])
-        line["cpu_baseline"] = cb
+        line["cpu_baseline"] = cpu_baseline(fields[0], fields[1], fields[2], None if info["pipe"] else fields[3])
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -117,7 +117,8 @@ typedef struct {
   int vertex_mode;   /* 0 inverse distance to cell centroids (default), 1 plain average */
   int group_size;    /* lanes per cell in the root search: 0 = auto, else 1, 2, 4, 8, 16 or 32 */
   int htc;           /* 1: also compute the interface heat-transfer coefficients VOF_F_A_OWN and
-                      * VOF_F_A_NEIGH (Eq. interface_htc) on a side branch of the step (default 0) */
+                      * VOF_F_A_NEIGH (Eq. interface_htc) and each band cell's energy-matrix terms
+                      * VOF_F_HTC_DIAG and VOF_F_HTC_RHS on a side branch of the step (default 0) */
   double alpha_iso;  /* isovalue of VOF_ROOT_FIXED, in (0, 1) (default 0.5) */
   /* Other-side gradient of an interface cell (Sec. 2.3, Eq. extrapolation):
    *   0 (default): one upwind sweep, the weighted mean of the gradients of the face neighbours on
@@ -148,6 +149,18 @@ typedef struct {
    * Any bit set runs the study's least-squares kernel (a thread per band cell) in place of the
    * path's; VOF_F_GRAD and everything downstream follow the chosen stencil. */
   int lsq_variant;
+  /* Start of the FP32 refinement of VOF_ROOT_LEARNED and VOF_ROOT_CUBIC:
+   *   0 (default): the MLP guess when the mesh has an MLP (VOF_ROOT_LEARNED requires one), else
+   *     u0 = 1 - alpha;
+   *   1: u0 = 1 - alpha for every cell, with or without an MLP: the learned path's refinement,
+   *     FP64 window, secant steps and fallback without the network (no feature or MLP kernel
+   *     runs), which measures what the network gains. */
+  int guess;
+  /* Reads of the pseudo-time extrapolation's per-iteration barrier word before a block stops
+   * waiting (options.extrap = 1; default 4194304, range 1 .. 2^30). A block that stops waiting
+   * ends the solve: every solve reports -1 iterations and the step's per-side gradients and
+   * sources are invalid; the kernel returns normally and the next step is unaffected. */
+  int extrap_poll_limit;
 } vof_options;
 
 /* Fills *o with the defaults above. */
@@ -255,11 +268,18 @@ typedef enum {
   VOF_F_A_NEIGH = 25,  /* double [n_faces]: the same for the neighbour side; both on crossing faces next to
                         * the band, in steps run with options.htc = 1: each side adds a_f to its
                         * energy-matrix diagonal and a_f T_sat to its right-hand side, the face being
-                        * detached from the diffusive coupling */
+                        * detached from the diffusive coupling (per-cell sums: VOF_F_HTC_DIAG/RHS) */
   VOF_F_DTAU = 26,     /* double [1]: pseudo-time step of Eq. (extrapolation), min over faces of |d_f| */
   VOF_F_LSQ_COND = 27, /* double [n_cells]: cond(G_P) of band cells, in steps run with options.lsq_variant bit 8
                         * (inf where G_P has no positive smallest eigenvalue) */
-  VOF_F_N = 28
+  /* Energy-matrix terms of Eq. interface_htc (Sec. 2.3, heat source/sink), in steps run with
+   * options.htc = 1, valid on band cells (VOF_F_BAND_STAMP): per cell, over its faces detached by the
+   * interface (the crossing faces of the step) in the cell's face order, the sum of its own side's
+   * a_f (added to the cell's diagonal) and the sum of a_f T_sat (added to its right-hand side).
+   * No cell outside the band has such a face with a non-zero coefficient. */
+  VOF_F_HTC_DIAG = 28, /* double [n_cells] */
+  VOF_F_HTC_RHS = 29,  /* double [n_cells] */
+  VOF_F_N = 30
 } vof_field;
 
 /* Element count of a field in the current state (n_iface for the interface list). */
@@ -343,7 +363,8 @@ vof_status vof_mlp_features(vof_mesh* mesh, const double* d_alpha, float* d_X, i
  * cells in cell order). It allocates nothing: its chunk sums live in a 32 KB file-scope device
  * array that every GPU loading the library holds until exit. The first call made with a device
  * current looks up that array's address (cudaGetSymbolAddress); make that first call before any
- * stream capture. Every call shares the array and zeroes its block counter before launching, so
+ * stream capture. The address is kept per device for the life of the process: do not call the
+ * function on a device after cudaDeviceReset on it (the kept address would be stale). Every call shares the array and zeroes its block counter before launching, so
  * calls that overlap on the GPU (two streams, or two host threads) race; order them on one stream.
  * n > VOF_TOTALS_STATIC_MAX_N returns VOF_EINVAL. */
 #define VOF_TOTALS_STATIC_MAX_N 4194304
@@ -354,11 +375,22 @@ vof_status vof_totals_static(const double* d_a, const double* d_b, int64_t n, do
  * vof_timing_enable(mesh, 1) creates the events on first use and resets the record;
  * vof_timing_read synchronises the stream and returns, per kernel class, the summed
  * milliseconds and the launch count since the last read (at most 8192 records are kept).
- * Classes: 0 selection, band and vertex field, 2 root search, 3 list of the crossing faces,
- * 4 crossing faces, least squares, per-side gradients, source and totals, 6 learned guess,
- * 7 interface geometry, 8 pseudo-time extrapolation (options.extrap = 1); 1 and 5 are unused. */
+ * Classes, one per kernel: 0 selection, band and vertex field; 1 features of the learned guess;
+ * 2 root search (one launch per non-empty bin, on parallel branches: their times add up);
+ * 3 list of the crossing faces (a side branch in vof_step); 4 crossing points; 5 least squares;
+ * 6 MLP forward pass of the learned guess; 7 interface geometry; 8 pseudo-time extrapolation
+ * (options.extrap = 1); 9 per-side gradients, source and totals; 10 heat-transfer coefficients
+ * (options.htc = 1, a side branch). */
 vof_status vof_timing_enable(vof_mesh* mesh, int on);
 vof_status vof_timing_read(vof_mesh* mesh, double* ms, int64_t* launches, int n, void* stream);
+
+/* FP64 FMA throughput of the current device, the denominator of the roofline of the FP64-bound
+ * kernels (measurement support; the paper has no counterpart). Launches a kernel whose threads
+ * each run 8 independent FMA chains of `iters` steps, every SM at full occupancy: one untimed
+ * launch, then `reps` launches timed with CUDA events on the stream. *h_ms = the fastest launch,
+ * *h_flops = its FP64 flops (2 per FMA). Allocates a small output buffer for the launch's lifetime
+ * and synchronises; iters < 1 or reps < 1 returns VOF_EINVAL. */
+vof_status vof_probe_fp64_fma(int64_t iters, int reps, double* h_ms, double* h_flops, void* stream);
 
 const char* vof_last_error(void);
 

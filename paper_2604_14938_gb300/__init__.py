@@ -30,7 +30,7 @@ FIELDS = {
     "cell_vol": (18, np.float64, 1), "cell_cen": (19, np.float64, 3), "face_area": (20, np.float64, 3),
     "face_cen": (21, np.float64, 3), "iface_stamp": (22, np.int32, 1), "band_stamp": (23, np.int32, 1),
     "a_own": (24, np.float64, 1), "a_neigh": (25, np.float64, 1), "dtau": (26, np.float64, 1),
-    "lsq_cond": (27, np.float64, 1),
+    "lsq_cond": (27, np.float64, 1), "htc_diag": (28, np.float64, 1), "htc_rhs": (29, np.float64, 1),
 }
 
 
@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
                 ("root_mode", ctypes.c_int), ("max_secant", ctypes.c_int), ("xf_mode", ctypes.c_int),
                 ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int), ("htc", ctypes.c_int),
                 ("alpha_iso", ctypes.c_double), ("extrap", ctypes.c_int), ("extrap_max_iter", ctypes.c_int),
-                ("extrap_tol", ctypes.c_double), ("lsq_variant", ctypes.c_int)]
+                ("extrap_tol", ctypes.c_double), ("lsq_variant", ctypes.c_int), ("guess", ctypes.c_int),
+                ("extrap_poll_limit", ctypes.c_int)]
 
 
 class Counts(ctypes.Structure):
@@ -198,7 +199,8 @@ class Mesh:
         _check(lib().vof_copy_field(self.h, fid, _ptr(out), cnt.value, _stream(stream)), "vof_copy_field")
         return out.view(-1, width) if width > 1 else out
 
-    KERNEL_CLASSES = ("select", "vertex", "root", "lsq", "source", "totals", "mlp", "geom", "extrap")
+    KERNEL_CLASSES = ("select", "mlp_features", "root", "xmark", "xface", "lsq", "mlp_forward", "geom", "extrap",
+                      "source", "htc")
 
     def timing_enable(self, on: bool = True):
         _check(lib().vof_timing_enable(self.h, int(on)), "vof_timing_enable")
@@ -233,6 +235,18 @@ class Mesh:
         out = {n: getattr(c, n) for n, _ in Counts._fields_}
         out["extrap_iters"] = list(c.extrap_iters)
         return out
+
+
+def fp64_peak(iters: int = 20000, reps: int = 3, stream=None) -> dict:
+    """vof_probe_fp64_fma: the FP64 FMA rate of the current device (TFLOP/s), the best of `reps`
+    timed launches of independent FMA chains at full occupancy."""
+    L = lib()
+    f = L.vof_probe_fp64_fma
+    f.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    _check(f(iters, reps, ctypes.byref(ms), ctypes.byref(fl), _stream(stream)), "vof_probe_fp64_fma")
+    return {"tflops": fl.value / (ms.value * 1e-3) / 1e12, "ms": ms.value, "flops": fl.value}
 
 
 # ---------------------------------------------------------------------------------- learned guess

@@ -46,6 +46,8 @@ FieldDesc field_of(vof_mesh* m, int f, int64_t n_iface) {
     case VOF_F_A_NEIGH: return {W.a_neigh, nf, 8};
     case VOF_F_DTAU: return {W.ex_dtau, 1, 8};
     case VOF_F_LSQ_COND: return {W.lsq_cond, nc, 8};
+    case VOF_F_HTC_DIAG: return {W.htc_diag, nc, 8};
+    case VOF_F_HTC_RHS: return {W.htc_rhs, nc, 8};
     default: return {nullptr, 0, 0};
   }
 }

@@ -93,6 +93,7 @@ struct Workspace {
   double* d_neigh;         // [n_faces]
   double* A_int_f;         // [n_faces]
   double *a_own, *a_neigh;  // [n_faces]: interface heat-transfer coefficients of the two sides
+  double *htc_diag, *htc_rhs;  // [n_cells]: sum of a_f, sum of a_f T_sat over a band cell's detached faces
   int32_t* xface_list;     // [n_faces] crossing faces next to the band (n_crossing of them this step)
   double* mdotV;           // [n_cells] in interface-list order
   double* QV;              // [n_cells]
@@ -144,7 +145,11 @@ struct StepArgs {
 
 namespace vof {
 // Optional per-kernel device timing: pairs of CUDA events recorded on the launch stream.
-enum KernelClass { KC_SELECT = 0, KC_VERTEX, KC_ROOT, KC_LSQ, KC_SOURCE, KC_TOTALS, KC_MLP, KC_GEOM, KC_EXTRAP, KC_N };
+// one class per kernel of the step (the root search: one launch per non-empty bin)
+enum KernelClass {
+  KC_SELECT = 0, KC_MLP_FEATURES, KC_ROOT, KC_XMARK, KC_XFACE, KC_LSQ, KC_MLP_FORWARD, KC_GEOM, KC_EXTRAP,
+  KC_SOURCE, KC_HTC, KC_N
+};
 struct Timing {
   bool on = false;
   int cap = 0, used = 0;

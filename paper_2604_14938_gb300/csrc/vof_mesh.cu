@@ -379,6 +379,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.A_int_f, nf));
   TRY(dev_alloc(m, &W.a_own, nf));
   TRY(dev_alloc(m, &W.a_neigh, nf));
+  TRY(dev_alloc(m, &W.htc_diag, nc));
+  TRY(dev_alloc(m, &W.htc_rhs, nc));
   TRY(dev_alloc(m, &W.xface_list, nf));
   TRY(dev_alloc(m, &W.mdotV, nc));
   TRY(dev_alloc(m, &W.QV, nc));
@@ -477,6 +479,8 @@ void vof_default_options(vof_options* o) {
   o->extrap_max_iter = 120;
   o->extrap_tol = 1e-3;
   o->lsq_variant = 0;
+  o->guess = 0;
+  o->extrap_poll_limit = 1 << 22;
 }
 
 vof_status vof_mesh_create(const vof_mesh_desc* desc, void* stream, vof_mesh** out) {
@@ -528,7 +532,8 @@ static vof_status check_opt(const vof_options* o) {
       o->root_mode < VOF_ROOT_BISECT || o->root_mode > VOF_ROOT_FIXED || !(o->alpha_iso > 0.0 && o->alpha_iso < 1.0) ||
       o->max_secant < 0 || o->max_secant > 8 || o->htc < 0 || o->htc > 1 || o->extrap < 0 || o->extrap > 1 ||
       o->extrap_max_iter < 1 || o->extrap_max_iter > kExMaxIter || !(o->extrap_tol > 0) ||
-      !std::isfinite(o->extrap_tol) || o->lsq_variant < 0 || o->lsq_variant > 15 ||
+      !std::isfinite(o->extrap_tol) || o->lsq_variant < 0 || o->lsq_variant > 15 || o->guess < 0 || o->guess > 1 ||
+      o->extrap_poll_limit < 1 || o->extrap_poll_limit > (1 << 30) ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {

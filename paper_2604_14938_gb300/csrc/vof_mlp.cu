@@ -572,15 +572,19 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   vof_mlp* mlp = (vof_mlp*)m->mlp;
   float* X = m->ws.mlp_x;
   int32_t* ok = m->ws.mlp_ok;
+  m->timing.start(KC_MLP_FEATURES, s);
   k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
+  m->timing.stop(s);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float)));
     attr = true;
   }
+  m->timing.start(KC_MLP_FORWARD, s);
   k_mlp_forward_iface<<<m->num_sms * 2, kFwdThreads, sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float), s>>>(
       mlp->w, X, ok, m->ws);
+  m->timing.stop(s);
   return cudaGetLastError();
 }
 

@@ -1327,8 +1327,9 @@ constexpr int kSrcLanes = 16;  // lanes per interface cell over its faces
 // The totals are the pairwise tree over the interface list (cell order) padded with zeros to a
 // power of two. Each block takes aligned tiles of kSrcTile interface cells: it computes their
 // sources (kSrcLanes lanes per cell over its faces), then the tile's subtree from shared memory;
-// after a grid barrier block 0 folds the tile sums in subtrees of 2 kThreads leaves, level by
-// level, so the pairing is the whole tree's. Cells outside the interface get mdot = Q = 0.
+// the last block to finish (an atomic count of finished blocks) folds the tile sums in subtrees of
+// 2 kThreads leaves, level by level, so the pairing is the whole tree's. Cells outside the
+// interface get mdot = Q = 0.
 
 // Pairwise tree of x[base, base + 2 T) (zeros past n) in a block of T threads (T a multiple of 32,
 // at most 1024); the result is valid in thread 0. Thread t pairs leaves 2t and 2t+1, lanes then
@@ -1491,7 +1492,7 @@ __device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W)
     }
 }
 
-// Block 0 folds the tile sums into the two totals.
+// The last block to finish folds the tile sums into the two totals.
 __device__ __noinline__ void fold_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
   __shared__ double sw[kThreads / 32];
   const int64_t n = W.counters->n_iface;
@@ -1536,6 +1537,30 @@ __global__ void k_htc(MeshView M, const double* alpha, double k_l, double k_v, W
   }
 }
 
+// Eq. interface_htc in the energy equation: each band cell adds a_f to its matrix diagonal and
+// a_f T_sat to its right-hand side for every face the interface detaches from the diffusive
+// coupling (the crossing faces of this step), a_f being the coefficient of the cell's own side. A
+// thread per band cell over its faces in the cell's face order; other cells have no such face with
+// a non-zero coefficient (a crossing face next to no band cell has no interface plane on either
+// side, so A_int,f = 0 there).
+__global__ void k_htc_cells(MeshView M, double T_sat, Workspace W) {
+  const uint32_t step = W.counters->step;
+  const int64_t nb = W.counters->n_band;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = W.band_idx[j];
+    double d = 0, r = 0;
+    for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      if (W.face_stamp[f] != step) continue;
+      const double a = M.face_owner[f] == c ? W.a_own[f] : W.a_neigh[f];
+      d += a;
+      r += a * T_sat;
+    }
+    W.htc_diag[c] = d;
+    W.htc_rhs[c] = r;
+  }
+}
+
 // ---- pseudo-time extrapolation of the per-side gradients (Eq. extrapolation) ------------------
 // One solve per side and gradient component, all six in one cooperative launch. The unknowns of
 // a side are the interface cells of the other phase, one per interface-list slot (its other
@@ -1560,11 +1585,11 @@ __global__ void k_htc(MeshView M, const double* alpha, double k_l, double k_v, W
 // 64-bit word (low 16 bits: arrivals; 8 bits per solve: blocks still moving), then polls the word
 // until every block has arrived. A solve stops after the first iteration in which no block saw a
 // change of tol or more (its largest change is below tol), or after max_iter; a stopped solve's
-// components are carried forward unchanged. The poll gives up after kExSpinLimit reads: the
-// block then stops iterating and the step reports -1 iterations for every solve (results invalid).
+// components are carried forward unchanged. The poll gives up after poll_limit reads
+// (options.extrap_poll_limit): the block then stops iterating, and the step reports -1 iterations
+// for every solve (results invalid).
 constexpr int kExThreads = 256;
 constexpr int kExSlotsPerWarp = 10;  // three lanes each; lanes 30 and 31 idle
-constexpr long long kExSpinLimit = 1ll << 22;
 
 struct ExSlot {
   double C, f, b0, b1, b2;
@@ -1705,7 +1730,7 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
 }
 
 __global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double* alpha, double eps, int max_iter,
-                                                        double tol, Workspace W) {
+                                                        double tol, int poll_limit, Workspace W) {
   cg::grid_group grid = cg::this_grid();
   __shared__ unsigned s_or[2];
   __shared__ unsigned s_dec;
@@ -1787,7 +1812,7 @@ __global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double*
       long long spins = 0;
       do {
         cur = ld_acquire_gpu(W.ex_itmax + k);
-      } while ((cur & 0xffffull) < gridDim.x && ++spins < kExSpinLimit);
+      } while ((cur & 0xffffull) < gridDim.x && ++spins < poll_limit);
       __threadfence();  // the other blocks' iterates after their arrivals
       unsigned dec = 0;
       if ((cur & 0xffffull) < gridDim.x) {
@@ -2036,9 +2061,10 @@ cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options&
 
 vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_options& opt, cudaStream_t s,
                               bool early_xmark) {
-  // the learned path needs the MLP guess; the interval cubic takes it when the mesh has an MLP
-  const int learned = opt.root_mode == VOF_ROOT_LEARNED || (opt.root_mode == VOF_ROOT_CUBIC && m->mlp);
-  if (opt.root_mode == VOF_ROOT_LEARNED && !m->mlp) {
+  // the learned path needs the MLP guess; the interval cubic takes it when the mesh has an MLP;
+  // guess = 1 starts both from 1 - alpha without the network
+  const int learned = opt.guess == 0 && (opt.root_mode == VOF_ROOT_LEARNED || (opt.root_mode == VOF_ROOT_CUBIC && m->mlp));
+  if (opt.root_mode == VOF_ROOT_LEARNED && opt.guess == 0 && !m->mlp) {
     set_error("learned root search requested but no MLP weights are set");
     return VOF_ESTATE;
   }
@@ -2074,7 +2100,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     // crossing faces next to the band: needed only by the least squares
     cudaEventRecord(m->ev_xfork, s);
     cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
-    tm.start(KC_LSQ, m->xm_stream);
+    tm.start(KC_XMARK, m->xm_stream);
     k_xmark<<<m->num_sms * 4, kThreads, 0, m->xm_stream>>>(M, d_alpha, W);
     tm.stop(m->xm_stream);
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
@@ -2082,9 +2108,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "selection kernels");
   if (learned) {
-    tm.start(KC_MLP, s);
-    e = launch_mlp_guess(m, s);
-    tm.stop(s);
+    e = launch_mlp_guess(m, s);  // times its two kernels itself
     if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
   // one branch per non-empty bin (root search); the branches join on s, then the geometry
@@ -2136,21 +2160,29 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
     cudaStreamWaitEvent(s, m->ev_io_done, 0);
     m->io_pending = false;
   }
-  tm.start(KC_LSQ, s);
-  if (!xmark_done) k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
-  tm.stop(s);
-  tm.start(KC_SOURCE, s);
+  if (!xmark_done) {
+    tm.start(KC_XMARK, s);
+    k_xmark<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, W);
+    tm.stop(s);
+  }
+  tm.start(KC_XFACE, s);
   k_xface<<<m->num_sms * 4, kThreads, 0, s>>>(M, a.alpha, a.opt.xf_mode, W);
+  tm.stop(s);
   if (a.opt.htc) {  // the interface heat-transfer coefficients on a side branch, joined after the source
     cudaEventRecord(m->ev_xfork, s);
     cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
+    tm.start(KC_HTC, m->xm_stream);
     k_htc<<<m->num_sms * 2, kThreads, 0, m->xm_stream>>>(M, a.alpha, a.props.k_l, a.props.k_v, W);
+    k_htc_cells<<<m->num_sms * 2, kThreads, 0, m->xm_stream>>>(M, a.props.T_sat, W);
+    tm.stop(m->xm_stream);
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
   }
+  tm.start(KC_LSQ, s);
   if (a.opt.lsq_variant)  // the stencil-anisotropy study's variants
     k_lsq_study<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   else
     k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+  tm.stop(s);
   if (a.opt.extrap) {
     // the pseudo-time solve: one cooperative launch
     if (!m->ex_grid) {  // a block per SM (the barrier word counts at most 255 blocks)
@@ -2158,18 +2190,17 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_extrap, kExThreads, 0);
       m->ex_grid = std::max(1, std::min(std::min(m->num_sms, m->num_sms * std::max(1, bps)), 255));
     }
-    tm.stop(s);
     tm.start(KC_EXTRAP, s);
     MeshView Mv = M;
     const double* al = a.alpha;
     double eps = a.opt.alpha_eps, tol = a.opt.extrap_tol;
-    int mi = a.opt.extrap_max_iter;
-    void* args[] = {&Mv, (void*)&al, &eps, &mi, &tol, &W};
+    int mi = a.opt.extrap_max_iter, poll = a.opt.extrap_poll_limit;
+    void* args[] = {&Mv, (void*)&al, &eps, &mi, &tol, &poll, &W};
     cudaError_t el = cudaLaunchCooperativeKernel((const void*)k_extrap, dim3(m->ex_grid), dim3(kExThreads), args, 0, s);
     tm.stop(s);
     if (el != cudaSuccess) return cuda_fail(el, "extrapolation kernel (cooperative launch)");
-    tm.start(KC_SOURCE, s);
   }
+  tm.start(KC_SOURCE, s);
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   if (a.opt.htc) cudaStreamWaitEvent(s, m->ev_xjoin, 0);  // the side branch (k_htc) joins here

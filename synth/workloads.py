@@ -2,13 +2,14 @@
 benchmark times and the full-size parity tests check. Inputs only: nothing here computes any
 part of the reconstruction or the phase-change source.
 
-    film250k    jittered-BCC Voronoi, 2 x 50^3 cells, wavy liquid film (the benchmark default)
+    film250k    jittered-BCC Voronoi, 2 x 50^3 cells, wavy liquid film
     sphere32    uniform hex 32^3, one vapour sphere R = 0.25 at the centre
     batch64     64 meshes of four kinds, log-uniform sizes 8k-500k cells, 1-6 spheres each
     voronoi2m   jittered-BCC Voronoi, 2 x 100^3 cells (spacing 0.01), 200 vapour spheres with
                 R ~ U[0.01, 0.05]: the application case of the learned isovalue guess
     pipe8m      extruded jittered 2D Voronoi disk, 600 layers (about 7.9M cells), wall film with
-                axial waves moving one layer per step
+                axial waves moving one layer per step (the benchmark default: the largest
+                single-GPU case, learned and batched over 100 resident steps)
 """
 from __future__ import annotations
 
@@ -30,9 +31,11 @@ def spheres(rng, k, r_lo=0.05, r_hi=0.2):
     return out
 
 
-def workload(name: str):
+def workload(name: str, layers: int = 600):
     """(mesh or list of meshes, alpha, T, T_bnd, description, extra). For a list of meshes the
-    fields are concatenated in mesh order."""
+    fields are concatenated in mesh order. `layers` shortens the pipe (same cross-section and
+    layer height 0.01, so every layer's cells are those of the full pipe): a smaller case of the
+    same kernels for profiling."""
     if name == "film250k":
         m = voronoi_bcc(50, jitter=0.25, seed=1)
         reg = dict(type="film", z0=0.3, a=0.03)
@@ -77,11 +80,12 @@ def workload(name: str):
         return m, a, T, Tb, ("jittered-BCC Voronoi 2x100^3=2M cells (seed 100, +-h/4), 200 non-overlapping vapour "
                              "spheres R~U[0.01,0.05], alpha from 64 sub-tetrahedra per fan tetrahedron, radial T"), {}
     if name == "pipe8m":
-        m = pipe(spacing=0.01537, layers=600, radius=1.0, length=6.0, seed=5)
+        m = pipe(spacing=0.01537, layers=layers, radius=1.0, length=6.0 * layers / 600, seed=5)
         reg = dict(type="pipe", r0=0.9, a=0.04, lam=0.5, t=0.0)
         a = alpha(m, reg, mode="subtet", level=2)
         T, Tb = temperature(m, reg, dict(kind="pipe", dT=8.0, radius=1.0))
-        return m, a, T, Tb, ("extruded jittered 2D Voronoi disk (radius 1, 600 layers over length 6, "
-                             f"{m.n_cells} cells), wall film r > 0.9 - 0.04 sin(2pi(z-t)/0.5) moving one layer "
-                             "(dz = 0.01 = phase velocity x dt) per step, T_sat+8 K at the wall"), {"layers": 600}
+        return m, a, T, Tb, (f"extruded jittered 2D Voronoi disk (radius 1, {layers} layers over length "
+                             f"{6.0 * layers / 600:g}, {m.n_cells} cells), wall film r > 0.9 - 0.04 sin(2pi(z-t)/0.5) "
+                             "moving one layer (dz = 0.01 = phase velocity x dt) per step, T_sat+8 K at the wall"), \
+            {"layers": layers}
     raise KeyError(f"unknown workload {name}")

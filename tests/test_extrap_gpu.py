@@ -112,3 +112,24 @@ def test_extrap_without_interface():
     assert g["counts"]["n_iface"] == 0
     assert list(g["counts"]["extrap_iters"]) == [1] * 6
     assert not np.any(g["mdot"]) and not np.any(g["totals"])
+
+
+def test_barrier_poll_limit_reports_and_recovers():
+    """The extrapolation's per-iteration barrier is a bounded poll: with a limit of one read per
+    block (options.extrap_poll_limit = 1), a block that finds the barrier not yet full stops
+    waiting, the kernel returns, and the step reports -1 iterations for all six solves; the next
+    step with the default limit is exact again (same counts and outputs as before)."""
+    m, a, T, Tb = case("voronoi_spheres")
+    M, g1 = gpu_step(m, a, T, Tb, extrap=1)
+    assert min(g1["counts"]["extrap_iters"]) > 0
+    gave_up = None
+    for _ in range(20):  # a launch in which every block found every barrier full is possible, not likely
+        _, gf = gpu_step(m, a, T, Tb, dev_mesh=M, extrap=1, extrap_poll_limit=1)
+        if list(gf["counts"]["extrap_iters"]) == [-1] * 6:
+            gave_up = gf
+            break
+    assert gave_up is not None
+    _, g2 = gpu_step(m, a, T, Tb, dev_mesh=M, extrap=1)
+    assert list(g2["counts"]["extrap_iters"]) == list(g1["counts"]["extrap_iters"])
+    for k in ("grad_l", "grad_v", "mdot", "Q", "totals"):
+        assert np.array_equal(g2[k], g1[k]), k

@@ -110,3 +110,27 @@ def test_fixed_isovalue_mode(name):
     for k in ("a_own", "a_neigh"):
         ok, err = close(g[k][exp], pc[k][exp], rel=1e-10)
         assert ok, (k, err)
+    # each band cell's energy-matrix terms: its own side's a_f and a_f T_sat summed over its
+    # detached faces
+    for k in ("htc_diag", "htc_rhs"):
+        ok, err = close(g[k][band], pc[k][band], rel=1e-10)
+        assert ok, (k, err)
+
+
+@pytest.mark.parametrize("name", ["voronoi_film", "prism_sphere"])
+def test_energy_matrix_terms_volume_matched(name):
+    """Eq. interface_htc's energy-matrix terms (options.htc = 1) on the volume-matched
+    reconstruction: per band cell, the diagonal sum of a_f and the right-hand side sum of
+    a_f T_sat over its detached faces match the oracle's, computed from the GPU's reconstruction."""
+    m, a, T, Tb = case(name)
+    M, g = gpu_step(m, a, T, Tb, root_mode=vof.ROOT_BISECT, htc=1)
+    O = oracle.Oracle(m)
+    rec = dict(status=g["status"], A_int=g["A_int"], n_int=g["n_int"], x_gamma=g["x_gamma"])
+    pc = O.phase_change(a, rec, T, Tb, synth.PROPS)
+    band = pc["in_band"].astype(bool)
+    assert np.array_equal(band, g["band_stamp"] == g["counts"]["step"])
+    assert np.count_nonzero(pc["htc_diag"][band]) > 0
+    assert not np.any(pc["htc_diag"][~band])
+    for k in ("htc_diag", "htc_rhs"):
+        ok, err = close(g[k][band], pc[k][band], rel=1e-10)
+        assert ok, (k, err)
