@@ -346,11 +346,13 @@ vof_status vof_mlp_train_step(vof_mlp* mlp, const float* d_X, const float* d_t, 
 /* The gradient of the batch loss (device float [VOF_MLP_N_PARAMS]) without an update. */
 vof_status vof_mlp_grad(vof_mlp* mlp, const float* d_X, const float* d_t, int64_t n, float* d_grad, float* d_loss,
                         void* stream);
-/* Attaches an MLP (or NULL) to a mesh for VOF_ROOT_LEARNED; allocates the mesh's feature buffers
- * on first use. The MLP must outlive its use by the mesh. */
+/* Attaches an MLP (or NULL) to a mesh for VOF_ROOT_LEARNED; on first use allocates the mesh's
+ * feature buffers and computes every cell's mesh-only features (faces / 32 and the six shape
+ * features) once, synchronising the device. The MLP must outlive its use by the mesh. */
 vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp);
 /* Features of the interface cells of the last reconstruction, made with that reconstruction's
- * d_alpha: d_X [n_iface][40], d_ok [n_iface] (1 where the cell has features). */
+ * d_alpha: d_X [n_iface][40], d_ok [n_iface] (1 where the cell has features). On a mesh without an
+ * MLP attached, the first call allocates the buffer of the mesh-only features and fills it. */
 vof_status vof_mlp_features(vof_mesh* mesh, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream);
 
 /* ---- totals without allocation (no counterpart in the paper: a variant of the totals step) ----

@@ -62,6 +62,8 @@ struct MeshView {
   const double* cell_cen;    // [n][3]
   const double* face_area;   // [n][3] outward from owner
   const double* face_cen;    // [n][3]
+  const double* face_len;    // [n] |x_neigh - x_owner| (0 on boundary faces)
+  const double* face_iarea;  // [n] 1 / |face_area|
 };
 
 struct Workspace {
@@ -105,6 +107,7 @@ struct Workspace {
   float* mlp_x;            // [n_cells][40] features of interface cells (allocated with an MLP)
   int32_t* mlp_ok;         // [n_cells] 1 where the cell has features
   float* mlp_y;            // [n_cells] raw MLP outputs
+  float* mlp_static;       // [n_cells][8] faces / 32 and the six shape features (allocated with an MLP)
   // pseudo-time extrapolation (options.extrap = 1), per interface-list slot
   double* ex_x;            // [2][n_cells][4] iterates of the slot's other-side gradient (ping-pong, padded)
   double* ex_k;            // [n_cells][5]: C = sum of step weights, f = dtau_P / V_P, b (3) = known inflow
@@ -124,7 +127,7 @@ constexpr int kBins = 5;
 constexpr int kBinMaxTets[kBins] = {4, 8, 24, 64, 192};
 __host__ __device__ inline int bin_of(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 1 : (nt <= 24 ? 2 : (nt <= 64 ? 3 : 4))); }
 constexpr int kReduceChunk = 2048;  // leaves per reduction block (power of two)
-constexpr int kSrcTile = 16;        // interface cells per source tile (an aligned subtree of the totals)
+constexpr int kSrcTile = 256;       // interface cells per source tile (an aligned subtree of the totals)
 constexpr int kMaxPartials = 8192;  // reduction blocks (n_iface <= 16.7 M)
 constexpr int kExMaxIter = 1000;    // cap of options.extrap_max_iter
 constexpr int kExMaxFaces = 64;     // faces per cell the extrapolation's face masks cover
@@ -208,6 +211,10 @@ struct vof_mesh {
   // side branch of a whole step: crossing-face list, from the band to the least squares
   cudaStream_t xm_stream = nullptr;
   cudaEvent_t ev_xfork = nullptr, ev_xjoin = nullptr;
+  // zeros of mdot and Q (every cell; the source then writes the interface cells): a memset on
+  // its own branch, forked when the source stage starts and joined before the source kernel
+  cudaStream_t z_stream = nullptr;
+  cudaEvent_t ev_zfork = nullptr, ev_zjoin = nullptr;
   // host-buffer step: T and T_bnd are copied on their own stream while the reconstruction runs;
   // the source stage waits for ev_io_done when io_pending is set
   cudaStream_t io_stream = nullptr;

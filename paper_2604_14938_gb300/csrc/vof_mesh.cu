@@ -117,6 +117,23 @@ __global__ void k_dtau(int64_t nf, const int32_t* own, const int32_t* nei, const
   atomicMin((unsigned long long*)out, (unsigned long long)__double_as_longlong(d));
 }
 
+// Per face: the owner-to-neighbour centroid distance (0 on a boundary face) and the reciprocal of
+// the face's area, for the crossing points of the steps.
+__global__ void k_face_static(int64_t nf, const int32_t* own, const int32_t* nei, const double* cen, const double* fa,
+                              double* len, double* iarea) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int32_t o = own[f], n = nei[f];
+  double L = 0;
+  if (n >= 0) {
+    const double dx = cen[3 * n] - cen[3 * o], dy = cen[3 * n + 1] - cen[3 * o + 1], dz = cen[3 * n + 2] - cen[3 * o + 2];
+    L = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  len[f] = L;
+  const double ax = fa[3 * f], ay = fa[3 * f + 1], az = fa[3 * f + 2];
+  iarea[f] = 1.0 / sqrt(ax * ax + ay * ay + az * az);
+}
+
 __global__ void k_idw(int64_t nv, const int64_t* vco, const int32_t* vc, const double* vx, const double* vy,
                       const double* vz, const double* cen, double* w) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -285,6 +302,9 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xfork, cudaEventDisableTiming);
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_xjoin, cudaEventDisableTiming);
     if (es == cudaSuccess) es = cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaStreamCreateWithFlags(&m->z_stream, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_zfork, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_zjoin, cudaEventDisableTiming);
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_io_start, cudaEventDisableTiming);
     if (es == cudaSuccess) es = cudaEventCreateWithFlags(&m->ev_io_done, cudaEventDisableTiming);
     for (int b = 0; b < kBins && es == cudaSuccess; ++b) {
@@ -328,6 +348,9 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &d_fa, 3 * nf));
   TRY(dev_alloc(m, &d_fc, 3 * nf));
   TRY(dev_alloc(m, &d_w, vc.size()));
+  double *d_flen, *d_fia;
+  TRY(dev_alloc(m, &d_flen, nf));
+  TRY(dev_alloc(m, &d_fia, nf));
   TRY(dev_alloc(m, &d_bad, 1));
   cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
   k_face_geom<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_fvo, d_fv, d_vx, d_vy, d_vz, d_fa, d_fc);
@@ -335,6 +358,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
                                                             d_tvf, d_vol, d_ivol, d_cen, d_bad);
   k_rel_pos<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_vx, d_vy, d_vz, d_rel);
   k_idw<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, d_vco, d_vc, d_vx, d_vy, d_vz, d_cen, d_w);
+  k_face_static<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_own, d_nei, d_cen, d_fa, d_flen, d_fia);
   int32_t h_bad = 0;
   cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
@@ -347,6 +371,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   V.rel_pos = d_rel;
   V.vert_cell_off = d_vco; V.vert_cell = d_vc; V.vert_w = d_w;
   V.cell_vol = d_vol; V.cell_ivol = d_ivol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
+  V.face_len = d_flen; V.face_iarea = d_fia;
   // ---- workspace
   Workspace& W = m->ws;
   m->n_sel_blocks = (int)((nc + kSelTile - 1) / kSelTile);
@@ -447,6 +472,11 @@ void destroy(vof_mesh* m) {
   if (m->ev_xjoin) cudaEventDestroy(m->ev_xjoin);
   m->xm_stream = nullptr;
   m->ev_xfork = m->ev_xjoin = nullptr;
+  if (m->z_stream) cudaStreamDestroy(m->z_stream);
+  if (m->ev_zfork) cudaEventDestroy(m->ev_zfork);
+  if (m->ev_zjoin) cudaEventDestroy(m->ev_zjoin);
+  m->z_stream = nullptr;
+  m->ev_zfork = m->ev_zjoin = nullptr;
   if (m->io_stream) cudaStreamDestroy(m->io_stream);
   if (m->ev_io_start) cudaEventDestroy(m->ev_io_start);
   if (m->ev_io_done) cudaEventDestroy(m->ev_io_done);

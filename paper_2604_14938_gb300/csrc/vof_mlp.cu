@@ -51,6 +51,19 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// (hi, lo) float pair and its sum by Knuth's two-sum (for vertex-value differences in FP32)
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float t = __fadd_rn(__fadd_rn(e, a.lo), b.lo);
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -222,64 +235,25 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward(WeightsBF16* w, const
 }
 
 // ---- features of interface cells, written as float32 [n_iface][40]; flag[i] = 0 when skipped ---
-// One warp per cell: lane j holds vertex j (at most 32); the normalised values are sorted
-// descending by a bitonic network over the warp; differences are taken in FP64 (relative to the
-// cell's range and first vertex), everything after that in FP32.
-__global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, float* X, int32_t* ok) {
-  const int64_t n = W.counters->n_iface;
+// The shape features do not change from step to step: k_mlp_static writes, once per mesh, each
+// cell's face count / 32 and its six extent features (coordinates relative to the cell's first
+// vertex, the leading FP32 parts of the mesh's relative positions): bounding-box extents / V^(1/3)
+// and (vertex mean - bounding-box centre) / V^(1/3), a warp per cell. Entry 7 is unused.
+__global__ void k_mlp_static(MeshView M, float* S) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-    const int32_t c = W.iface_idx[i];
+  for (int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < M.n_cells; c += warps) {
     const int64_t v0 = M.cell_vert_off[c];
     const int nv = (int)(M.cell_vert_off[c + 1] - v0);
-    if (nv > 32) {
-      if (lane == 0) ok[i] = 0;
-      continue;
+    float mnx = 3.4e38f, mny = 3.4e38f, mnz = 3.4e38f, mxx = -3.4e38f, mxy = -3.4e38f, mxz = -3.4e38f;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int j = lane; j < nv; j += 32) {
+      const float2* rp = M.rel_pos + 3 * (v0 + j);
+      const float rx = rp[0].x, ry = rp[1].x, rz = rp[2].x;
+      mnx = fminf(mnx, rx); mny = fminf(mny, ry); mnz = fminf(mnz, rz);
+      mxx = fmaxf(mxx, rx); mxy = fmaxf(mxy, ry); mxz = fmaxf(mxz, rz);
+      sx += rx; sy += ry; sz += rz;
     }
-    const bool has = lane < nv;
-    const int32_t v = has ? M.cell_vert[v0 + lane] : M.cell_vert[v0];
-    const double p = W.phi_v[v];
-    // range by integer min/max of the order keys (no FP64 compares)
-    uint64_t klo = okey(p), khi = klo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      klo = min(klo, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)klo, o));
-      khi = max(khi, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)khi, o));
-    }
-    const double lo = okey_inv(klo), range = okey_inv(khi) - lo;
-    if (!(range >= 1e-14)) {
-      if (lane == 0) ok[i] = 0;
-      continue;
-    }
-    // normalised value from the (hi, lo) float pairs of the vertex values (no FP64 instruction:
-    // each costs 64 FP32 issue slots on this part); missing lanes hold -1 so that they sort last
-    const float2 pf = W.phi_ff[v];
-    const int src = __ffs(__ballot_sync(0xffffffffu, okey(p) == klo)) - 1;
-    const float lox = __shfl_sync(0xffffffffu, pf.x, src), loy = __shfl_sync(0xffffffffu, pf.y, src);
-    const float irange = 1.0f / (float)range;
-    float u = has ? ((pf.x - lox) + (pf.y - loy)) * irange : -1.0f;
-    // bitonic sort, descending
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const float other = __shfl_xor_sync(0xffffffffu, u, j);
-        const bool up = ((lane & k) == 0);   // this block of the network sorts descending
-        const bool lower = ((lane & j) == 0);
-        const bool take_max = (up == lower);
-        u = take_max ? fmaxf(u, other) : fminf(u, other);
-      }
-    }
-    const float smallest = __shfl_sync(0xffffffffu, u, nv - 1);
-    float* x = X + i * kIn;
-    x[2 + lane] = lane < nv ? u : smallest;
-    // shape: coordinates relative to the first vertex (the leading FP32 parts of the mesh's
-    // relative positions, that is the FP64 differences rounded to FP32)
-    const float2* rp = M.rel_pos + 3 * (v0 + (has ? lane : 0));
-    float rx = rp[0].x, ry = rp[1].x, rz = rp[2].x;
-    float mnx = rx, mny = ry, mnz = rz, mxx = rx, mxy = ry, mxz = rz;
-    float sx = has ? rx : 0.f, sy = has ? ry : 0.f, sz = has ? rz : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
@@ -294,15 +268,87 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, flo
     }
     if (lane == 0) {
       const float is = 1.0f / cbrtf((float)M.cell_vol[c]);
-      x[0] = (float)alpha[c];
-      x[1] = (float)(M.cell_face_off[c + 1] - M.cell_face_off[c]) * (1.0f / 32.0f);
-      x[34] = (mxx - mnx) * is;
-      x[35] = (mxy - mny) * is;
-      x[36] = (mxz - mnz) * is;
-      x[37] = (sx / nv - 0.5f * (mnx + mxx)) * is;
-      x[38] = (sy / nv - 0.5f * (mny + mxy)) * is;
-      x[39] = (sz / nv - 0.5f * (mnz + mxz)) * is;
-      ok[i] = 1;
+      float* x = S + 8 * c;
+      x[0] = (float)(M.cell_face_off[c + 1] - M.cell_face_off[c]) * (1.0f / 32.0f);
+      x[1] = (mxx - mnx) * is;
+      x[2] = (mxy - mny) * is;
+      x[3] = (mxz - mnz) * is;
+      x[4] = (sx / nv - 0.5f * (mnx + mxx)) * is;
+      x[5] = (sy / nv - 0.5f * (mny + mxy)) * is;
+      x[6] = (sz / nv - 0.5f * (mnz + mxz)) * is;
+      x[7] = 0.f;
+    }
+  }
+}
+
+// Per step: a warp takes a batch of 32 interface cells. Lane j reads cell j's alpha (one FP32
+// conversion for the batch: conversions run on the FP64 unit) and its static features; then the
+// warp takes the cells one by one, lane j holding vertex j (at most 32): the range comes from the
+// order keys of the FP64 vertex values (integer min / max), the normalised values from the values'
+// (hi, lo) float pairs in FP32 (no FP64 instruction), sorted descending by a bitonic network over
+// the warp. A cell whose range is below 1e-14 (as a float pair difference) gets no features.
+__global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, const float* S, float* X, int32_t* ok) {
+  const int64_t n = W.counters->n_iface;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t b0 = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; b0 < n; b0 += warps * 32) {
+    const int64_t ib = b0 + lane;
+    const int32_t cb = ib < n ? W.iface_idx[ib] : 0;
+    const float ab = ib < n ? (float)alpha[cb] : 0.f;
+    const int nb = n - b0 < 32 ? (int)(n - b0) : 32;
+    int okb = 0;
+    for (int j = 0; j < nb; ++j) {
+      const int32_t c = __shfl_sync(0xffffffffu, cb, j);
+      const int64_t v0 = M.cell_vert_off[c];
+      const int nv = (int)(M.cell_vert_off[c + 1] - v0);
+      if (nv > 32) continue;
+      const bool has = lane < nv;
+      const int32_t v = has ? M.cell_vert[v0 + lane] : M.cell_vert[v0];
+      const uint64_t kp = okey(W.phi_v[v]);
+      const float2 pf = W.phi_ff[v];
+      // extreme vertices by integer min / max of the order keys
+      uint64_t klo = kp, khi = kp;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        klo = min(klo, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)klo, o));
+        khi = max(khi, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)khi, o));
+      }
+      const int slo = __ffs(__ballot_sync(0xffffffffu, kp == klo)) - 1;
+      const int shi = __ffs(__ballot_sync(0xffffffffu, kp == khi)) - 1;
+      const ff lo = {__shfl_sync(0xffffffffu, pf.x, slo), __shfl_sync(0xffffffffu, pf.y, slo)};
+      const ff hi = {__shfl_sync(0xffffffffu, pf.x, shi), __shfl_sync(0xffffffffu, pf.y, shi)};
+      const ff rg = ff_add(hi, ff{-lo.hi, -lo.lo});
+      const float range = rg.hi + rg.lo;
+      if (!(range >= 1e-14f)) continue;
+      const float irange = 1.0f / range;
+      float u = has ? ((pf.x - lo.hi) + (pf.y - lo.lo)) * irange : -1.0f;  // missing lanes sort last
+      // bitonic sort, descending
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          const float other = __shfl_xor_sync(0xffffffffu, u, jj);
+          const bool up = ((lane & k) == 0);  // this block of the network sorts descending
+          const bool lower = ((lane & jj) == 0);
+          u = (up == lower) ? fmaxf(u, other) : fminf(u, other);
+        }
+      }
+      const float smallest = __shfl_sync(0xffffffffu, u, nv - 1);
+      X[(b0 + j) * kIn + 2 + lane] = lane < nv ? u : smallest;
+      if (lane == j) okb = 1;
+    }
+    // alpha, faces / 32 and the shape features, a cell per lane
+    if (ib < n) {
+      float* x = X + ib * kIn;
+      if (okb) {
+        const float4 s0 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)cb);
+        const float4 s1 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)cb + 4);
+        x[0] = ab;
+        x[1] = s0.x;
+        x[34] = s0.y; x[35] = s0.z; x[36] = s0.w;
+        x[37] = s1.x; x[38] = s1.y; x[39] = s1.z;
+      }
+      ok[ib] = okb;
     }
   }
 }
@@ -573,17 +619,17 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   float* X = m->ws.mlp_x;
   int32_t* ok = m->ws.mlp_ok;
   m->timing.start(KC_MLP_FEATURES, s);
-  k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, X, ok);
+  k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, m->ws.mlp_static, X, ok);
   m->timing.stop(s);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float)));
-    attr = true;
+  const size_t fwd_smem = sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float);
+  static int fwd_bps = 0;  // resident blocks per SM of the forward pass
+  if (!fwd_bps) {
+    cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_bps, k_mlp_forward_iface, kFwdThreads, fwd_smem);
+    if (fwd_bps < 1) fwd_bps = 1;
   }
   m->timing.start(KC_MLP_FORWARD, s);
-  k_mlp_forward_iface<<<m->num_sms * 2, kFwdThreads, sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float), s>>>(
-      mlp->w, X, ok, m->ws);
+  k_mlp_forward_iface<<<m->num_sms * fwd_bps, kFwdThreads, fwd_smem, s>>>(mlp->w, X, ok, m->ws);
   m->timing.stop(s);
   return cudaGetLastError();
 }
@@ -694,6 +740,15 @@ vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp) {
     mesh->allocs.push_back(W.mlp_ok);
     mesh->allocs.push_back(W.mlp_y);
   }
+  if (mlp && !W.mlp_static) {
+    // the features that depend on the mesh alone, once
+    cudaError_t e = cudaMalloc(&W.mlp_static, (size_t)mesh->n_cells * 8 * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "vof_mesh_set_mlp");
+    mesh->allocs.push_back(W.mlp_static);
+    k_mlp_static<<<mesh->num_sms * 8, 256>>>(mesh->view, W.mlp_static);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "vof_mesh_set_mlp (static features)");
+  }
   // a captured step graph bakes in the weights' device address: recapture after any change (a
   // new MLP may even reuse the old handle's host address)
   if (mesh->mlp != mlp) {
@@ -707,7 +762,14 @@ vof_status vof_mesh_set_mlp(vof_mesh* mesh, vof_mlp* mlp) {
 vof_status vof_mlp_features(vof_mesh* m, const double* d_alpha, float* d_X, int32_t* d_ok, void* stream) {
   if (!m || !d_alpha || !d_X || !d_ok) { set_error("null argument"); return VOF_EINVAL; }
   if (!m->recon_done) { set_error("vof_mlp_features needs a reconstruction"); return VOF_ESTATE; }
-  k_mlp_features<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, d_X, d_ok);
+  if (!m->ws.mlp_static) {  // the mesh-only features, once (also without an MLP attached)
+    cudaError_t e = cudaMalloc(&m->ws.mlp_static, (size_t)m->n_cells * 8 * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_features");
+    m->allocs.push_back(m->ws.mlp_static);
+    k_mlp_static<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, m->ws.mlp_static);
+  }
+  k_mlp_features<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, m->ws.mlp_static, d_X,
+                                                                  d_ok);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_features");
   return VOF_OK;

@@ -94,6 +94,28 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
 
 __device__ __forceinline__ bool is_iface(double a, double eps) { return a > eps && a < 1.0 - eps; }
 
+// Phase tests of alpha on its bits (integer pipe; same results as the FP64 comparisons): liquid
+// iff alpha > 1/2, vapour iff alpha < 1/2; NaN is neither, and so is alpha = 1/2.
+constexpr uint64_t kKeyHalf = 0xbfe0000000000000ull;  // okey(0.5)
+__device__ __forceinline__ bool not_nan(double a) {
+  return ((uint64_t)__double_as_longlong(a) & 0x7fffffffffffffffull) <= 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool liquid(double a) { return okey(a) > kKeyHalf && not_nan(a); }
+__device__ __forceinline__ bool vapour(double a) { return okey(a) < kKeyHalf && not_nan(a); }
+// (alpha_P - 1/2)(alpha_Q - 1/2) < 0: one strictly above 1/2, the other strictly below
+__device__ __forceinline__ bool crossing_pair(double aP, double aQ) {
+  return (liquid(aP) && vapour(aQ)) || (vapour(aP) && liquid(aQ));
+}
+// eps < alpha < 1 - eps on the bits, with the two bounds' keys computed once per thread
+struct IfaceKeys {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ IfaceKeys iface_keys(double eps) { return {okey(eps), okey(1.0 - eps)}; }
+__device__ __forceinline__ bool is_iface_k(double a, IfaceKeys k) {
+  const uint64_t x = okey(a);
+  return x > k.lo && x < k.hi && not_nan(a);
+}
+
 // ---- the step's selection as one cooperative kernel ----------------------------------------------
 // Three phases separated by grid-wide barriers (the launch is cooperative, so every block is
 // resident): (1) step stamp and counters, interface cells per tile of kSelTile cells (each thread
@@ -112,11 +134,12 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* s8) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* alpha, double eps, int vertex_mode,
-                                                     Workspace W) {
+                                                     int max_cf, Workspace W) {
   cg::grid_group grid = cg::this_grid();
   constexpr int kPer = kSelTile / kThreads;  // consecutive cells per thread in a tile
   static_assert(kPer >= 1 && kPer <= 32 && kSelTile % kThreads == 0, "tile layout");
-  extern __shared__ int32_t band_buf[];  // (kThreads / 16) * (1 + max faces per cell)
+  // (kThreads / 16) * (1 + max faces per cell) band cells, then (kThreads / 16) * max vertices per cell
+  extern __shared__ int32_t band_buf[];
   __shared__ int64_t s8[kThreads / 32];
   __shared__ int wpre[kThreads / 32 + 1];
   __shared__ int s_bin[kBins], s_nb;
@@ -125,12 +148,13 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   const int64_t ntiles = (nc + kSelTile - 1) / kSelTile;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // interface flags of this thread's kPer cells of tile t
+  const IfaceKeys ik = iface_keys(eps);
   auto flags = [&](int64_t t) {
     unsigned f = 0;
     const int64_t c0 = t * kSelTile + (int64_t)threadIdx.x * kPer;
 #pragma unroll
     for (int k = 0; k < kPer; ++k)
-      if (c0 + k < nc && is_iface(alpha[c0 + k], eps)) f |= 1u << k;
+      if (c0 + k < nc && is_iface_k(alpha[c0 + k], ik)) f |= 1u << k;
     return f;
   };
   // (1)
@@ -202,16 +226,19 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   }
   grid.sync();
   // (3) kSelLanes lanes per interface cell, kThreads / kSelLanes cells per block pass: lane j takes
-  // face j and vertex j (and j + kSelLanes, ...). New band cells go to a shared buffer that one
-  // atomic per pass appends to the band list; a vertex gets its field value from the lane that
-  // stamps it first.
+  // face j and vertex j (and j + kSelLanes, ...). New band cells and newly stamped vertices go to
+  // shared buffers; one atomic per pass appends the band cells to the band list, and the block then
+  // computes the field value of each vertex it stamped first, a thread per vertex (full warps on
+  // the FP64 pipe).
   {
     constexpr int kSelLanes = 16;
+    int32_t* vert_buf = band_buf + (kThreads / kSelLanes) * (1 + max_cf);
+    __shared__ int s_nv;
     const int sl = threadIdx.x % kSelLanes, scell = threadIdx.x / kSelLanes;
     const int64_t n = W.counters->n_iface;
     for (int64_t base = (int64_t)blockIdx.x * (kThreads / kSelLanes); base < n;
          base += (int64_t)gridDim.x * (kThreads / kSelLanes)) {
-      if (threadIdx.x == 0) s_nb = 0;
+      if (threadIdx.x == 0) s_nb = s_nv = 0;
       __syncthreads();
       const int64_t i = base + scell;
       if (i < n) {
@@ -227,37 +254,38 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
           }
           if (v0 + j < v1) {
             const int32_t v = M.cell_vert[v0 + j];
-            if (atomicExch(&W.vert_stamp[v], step) != step) {
-              // vertex field (R1): inverse-distance weights, or the plain mean
-              const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
-              double sum = 0;
-              if (vertex_mode == 0) {
-                // four cells' loads in flight at a time; the sum keeps the cell order
-                int64_t k = k0;
-                for (; k + 4 <= k1; k += 4) {
-                  const int32_t ca = M.vert_cell[k], cb = M.vert_cell[k + 1], cc = M.vert_cell[k + 2],
-                                cd = M.vert_cell[k + 3];
-                  const double wa = M.vert_w[k], wb = M.vert_w[k + 1], wc = M.vert_w[k + 2], wd = M.vert_w[k + 3];
-                  const double aa = alpha[ca], ab = alpha[cb], ac = alpha[cc], ad = alpha[cd];
-                  sum = fma(wa, aa, sum);
-                  sum = fma(wb, ab, sum);
-                  sum = fma(wc, ac, sum);
-                  sum = fma(wd, ad, sum);
-                }
-                for (; k < k1; ++k) sum = fma(M.vert_w[k], alpha[M.vert_cell[k]], sum);
-              } else {
-                for (int64_t k = k0; k < k1; ++k) sum += alpha[M.vert_cell[k]];
-                sum /= (double)(k1 - k0);
-              }
-              W.phi_v[v] = sum;
-              const float h = __double2float_rn(sum);
-              W.phi_ff[v] = make_float2(h, __double2float_rn(sum - (double)h));
-            }
+            if (atomicExch(&W.vert_stamp[v], step) != step) vert_buf[atomicAdd(&s_nv, 1)] = v;
           }
         }
       }
       __syncthreads();
       if (threadIdx.x == 0) s_gb = s_nb ? atomicAdd((unsigned long long*)&W.counters->n_band, (unsigned long long)s_nb) : 0ull;
+      // vertex field (R1): inverse-distance weights, or the plain mean
+      for (int k = threadIdx.x; k < s_nv; k += blockDim.x) {
+        const int32_t v = vert_buf[k];
+        const int64_t k0 = M.vert_cell_off[v], k1 = M.vert_cell_off[v + 1];
+        double sum = 0;
+        if (vertex_mode == 0) {
+          // four cells' loads in flight at a time; the sum keeps the cell order
+          int64_t e = k0;
+          for (; e + 4 <= k1; e += 4) {
+            const int32_t ca = M.vert_cell[e], cb = M.vert_cell[e + 1], cc = M.vert_cell[e + 2], cd = M.vert_cell[e + 3];
+            const double wa = M.vert_w[e], wb = M.vert_w[e + 1], wc = M.vert_w[e + 2], wd = M.vert_w[e + 3];
+            const double aa = alpha[ca], ab = alpha[cb], ac = alpha[cc], ad = alpha[cd];
+            sum = fma(wa, aa, sum);
+            sum = fma(wb, ab, sum);
+            sum = fma(wc, ac, sum);
+            sum = fma(wd, ad, sum);
+          }
+          for (; e < k1; ++e) sum = fma(M.vert_w[e], alpha[M.vert_cell[e]], sum);
+        } else {
+          for (int64_t e = k0; e < k1; ++e) sum += alpha[M.vert_cell[e]];
+          sum /= (double)(k1 - k0);
+        }
+        W.phi_v[v] = sum;
+        const float h = __double2float_rn(sum);
+        W.phi_ff[v] = make_float2(h, __double2float_rn(sum - (double)h));
+      }
       __syncthreads();
       for (int k = threadIdx.x; k < s_nb; k += blockDim.x) W.band_idx[s_gb + k] = band_buf[k];
       __syncthreads();
@@ -1022,30 +1050,40 @@ struct GeomSlot {
   int32_t nt;      // tetrahedra (0 for a degenerate cell)
 };
 
+constexpr int kGeomBatch = 32;  // interface cells whose per-cell set-up and outputs a warp does lane per cell
+
 size_t geom_smem_bytes(int max_ct) {
-  return (size_t)kGeomWarps * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomCells * sizeof(GeomSlot) +
-                               (size_t)kGeomCells * max_ct * sizeof(uint32_t));
+  return (size_t)kGeomWarps * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomBatch * sizeof(GeomSlot) +
+                               (size_t)kGeomBatch * 7 * sizeof(float2) + (size_t)kGeomCells * max_ct * sizeof(uint32_t));
 }
 
+// A warp takes a batch of B consecutive interface cells (B up to kGeomBatch, fewer when the step has
+// too few interface cells to give every resident warp a full batch): the per-cell set-up (isovalue
+// as a pair, apex value minus it) and the final FP64 outputs run a cell per lane, so that their
+// FP64 instructions serve B cells at once; the sections in between take kGeomCells cells at a time.
 __global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace W, int max_ct) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
-  float2* part = reinterpret_cast<float2*>(smem) + (size_t)warp * kGeomCells * 7 * 32;  // [cell][k][lane]
-  GeomSlot* slot = reinterpret_cast<GeomSlot*>(reinterpret_cast<float2*>(smem) + (size_t)kGeomWarps * kGeomCells * 7 * 32) +
-                   warp * kGeomCells;
-  uint32_t* lst = reinterpret_cast<uint32_t*>(reinterpret_cast<GeomSlot*>(reinterpret_cast<float2*>(smem) +
-                                                                          (size_t)kGeomWarps * kGeomCells * 7 * 32) +
-                                              kGeomWarps * kGeomCells) +
-                  (size_t)warp * kGeomCells * max_ct;
+  unsigned char* wbase = smem + (size_t)warp * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomBatch * sizeof(GeomSlot) +
+                                                (size_t)kGeomBatch * 7 * sizeof(float2) +
+                                                (size_t)kGeomCells * max_ct * sizeof(uint32_t));
+  float2* part = reinterpret_cast<float2*>(wbase);                                  // [cell][k][lane]
+  GeomSlot* bslot = reinterpret_cast<GeomSlot*>(part + kGeomCells * 7 * 32);        // [batch cell]
+  float2* res = reinterpret_cast<float2*>(bslot + kGeomBatch);                      // [batch cell][7]
+  uint32_t* lst = reinterpret_cast<uint32_t*>(res + kGeomBatch * 7);                // [kGeomCells * max_ct]
   const int64_t n = W.counters->n_iface;
+  const int64_t nwarps = (int64_t)gridDim.x * kGeomWarps;
+  const int64_t per_warp = n / (nwarps > 0 ? nwarps : 1);
+  int B = per_warp >= kGeomBatch ? kGeomBatch : (per_warp <= kGeomCells ? kGeomCells : (int)per_warp);
+  B -= B % kGeomCells;
   int64_t sect = 0;
-  for (int64_t i0 = ((int64_t)blockIdx.x * kGeomWarps + warp) * kGeomCells; i0 < n;
-       i0 += (int64_t)gridDim.x * kGeomWarps * kGeomCells) {
-    if (lane < kGeomCells) {
+  for (int64_t b0 = ((int64_t)blockIdx.x * kGeomWarps + warp) * B; b0 < n; b0 += nwarps * B) {
+    // set-up of the batch's cells, a cell per lane
+    if (lane < B) {
       GeomSlot g = {0, 0, 0.0, make_float2(0.f, 0.f), make_float2(0.f, 0.f), -1, 0};
-      if (i0 + lane < n) {
-        g.cell = W.iface_idx[i0 + lane];
+      if (b0 + lane < n) {
+        g.cell = W.iface_idx[b0 + lane];
         g.v0 = M.cell_vert_off[g.cell];
         if (!(W.status[g.cell] & VOF_ST_DEGENERATE)) {
           g.t0 = M.cell_tet_off[g.cell];
@@ -1057,84 +1095,97 @@ __global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace 
           g.w0 = make_float2(w0.hi, w0.lo);
         }
       }
-      slot[lane] = g;
+      bslot[lane] = g;
     }
-#pragma unroll
-    for (int k = 0; k < kGeomCells * 7; ++k) part[k * 32 + lane] = make_float2(0.f, 0.f);
     __syncwarp();
-    int off[kGeomCells + 1];
-    off[0] = 0;
+    for (int p0 = 0; p0 < B; p0 += kGeomCells) {
+      const GeomSlot* slot = bslot + p0;
 #pragma unroll
-    for (int q = 0; q < kGeomCells; ++q) off[q + 1] = off[q] + slot[q].nt;
-    // the cut tetrahedra of the warp's cells, by integer order keys
-    int n_cut = 0;
-    for (int r0 = 0; r0 < off[kGeomCells]; r0 += 32) {
-      const int q = r0 + lane;
-      bool cut = false;
-      uint32_t ent = 0;
-      if (q < off[kGeomCells]) {
-        int sl = 0, base = 0;
+      for (int k = 0; k < kGeomCells * 7; ++k) part[k * 32 + lane] = make_float2(0.f, 0.f);
+      __syncwarp();
+      int off[kGeomCells + 1];
+      off[0] = 0;
 #pragma unroll
-        for (int k = 1; k < kGeomCells; ++k)
-          if (q >= off[k]) { sl = k; base = off[k]; }
+      for (int q = 0; q < kGeomCells; ++q) off[q + 1] = off[q] + slot[q].nt;
+      // the cut tetrahedra of the pair's cells, by integer order keys
+      int n_cut = 0;
+      for (int r0 = 0; r0 < off[kGeomCells]; r0 += 32) {
+        const int q = r0 + lane;
+        bool cut = false;
+        uint32_t ent = 0;
+        if (q < off[kGeomCells]) {
+          int sl = 0, base = 0;
+#pragma unroll
+          for (int k = 1; k < kGeomCells; ++k)
+            if (q >= off[k]) { sl = k; base = off[k]; }
+          const GeomSlot& g = slot[sl];
+          const int t = q - base;
+          const uint64_t kc = okey(g.c);
+          const int32_t* cv = M.cell_vert + g.v0;
+          const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
+          const unsigned m = (unsigned)(okey(W.phi_v[cv[0]]) >= kc) | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
+                             ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
+                             ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
+          cut = m != 0u && m != 15u;
+          ent = ((uint32_t)t << 6) | ((uint32_t)sl << 4) | m;
+        }
+        const unsigned bal = __ballot_sync(full, cut);
+        if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = ent;
+        n_cut += __popc(bal);
+      }
+      __syncwarp();
+      // sections, each added to this lane's partials of its cell
+      for (int jj = lane; jj < n_cut; jj += 32) {
+        const uint32_t e = lst[jj];
+        const int sl = (int)((e >> 4) & 3u), t = (int)(e >> 6);
         const GeomSlot& g = slot[sl];
-        const int t = q - base;
-        const uint64_t kc = okey(g.c);
         const int32_t* cv = M.cell_vert + g.v0;
         const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
-        const unsigned m = (unsigned)(okey(W.phi_v[cv[0]]) >= kc) | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
-                           ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
-                           ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
-        cut = m != 0u && m != 15u;
-        ent = ((uint32_t)t << 6) | ((uint32_t)sl << 4) | m;
+        const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
+        const float2* rp = M.rel_pos + 3 * g.v0;
+        const ff cf = ff_make(g.cf);
+        ff3 tA, tm;
+        ff ta;
+        tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), ff_make(g.w0),
+                       ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
+                       ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
+        const ff add[7] = {tA.x, tA.y, tA.z, ta, tm.x, tm.y, tm.z};
+        float2* pc = part + (size_t)sl * 7 * 32 + lane;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          const ff r = ff_add(ff_make(pc[k * 32]), add[k]);
+          pc[k * 32] = make_float2(r.hi, r.lo);
+        }
       }
-      const unsigned bal = __ballot_sync(full, cut);
-      if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = ent;
-      n_cut += __popc(bal);
-    }
-    __syncwarp();
-    // sections, each added to this lane's partials of its cell
-    for (int jj = lane; jj < n_cut; jj += 32) {
-      const uint32_t e = lst[jj];
-      const int sl = (int)((e >> 4) & 3u), t = (int)(e >> 6);
-      const GeomSlot& g = slot[sl];
-      const int32_t* cv = M.cell_vert + g.v0;
-      const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
-      const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
-      const float2* rp = M.rel_pos + 3 * g.v0;
-      const ff cf = ff_make(g.cf);
-      ff3 tA, tm;
-      ff ta;
-      tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), ff_make(g.w0),
-                     ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
-                     ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
-      const ff add[7] = {tA.x, tA.y, tA.z, ta, tm.x, tm.y, tm.z};
-      float2* pc = part + (size_t)sl * 7 * 32 + lane;
+      sect += n_cut;
+      __syncwarp();
+      // per cell: kGeomRed lanes add the 32 partials (lane l takes l, l + kGeomRed, ...), then a tree
+      const int sl = lane / kGeomRed, l = lane % kGeomRed;
+      ff v[7];
 #pragma unroll
       for (int k = 0; k < 7; ++k) {
-        const ff r = ff_add(ff_make(pc[k * 32]), add[k]);
-        pc[k * 32] = make_float2(r.hi, r.lo);
+        const float2* pc = part + ((size_t)sl * 7 + k) * 32;
+        ff acc = ff_make(pc[l]);
+#pragma unroll
+        for (int j = 1; j < 32 / kGeomRed; ++j) acc = ff_add(acc, ff_make(pc[l + j * kGeomRed]));
+        v[k] = acc;
       }
+#pragma unroll
+      for (int o = kGeomRed / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = ff_add(v[k], ff{__shfl_xor_sync(full, v[k].hi, o), __shfl_xor_sync(full, v[k].lo, o)});
+      if (l == 0) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) res[(p0 + sl) * 7 + k] = make_float2(v[k].hi, v[k].lo);
+      }
+      __syncwarp();
     }
-    sect += n_cut;
-    __syncwarp();
-    // per cell: kGeomRed lanes add the 32 partials (lane l takes l, l + kGeomRed, ...), then a tree
-    const int sl = lane / kGeomRed, l = lane % kGeomRed;
-    ff v[7];
+    // outputs, a cell per lane
+    if (lane < B && bslot[lane].cell >= 0) {
+      const GeomSlot& g = bslot[lane];
+      ff v[7];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const float2* pc = part + ((size_t)sl * 7 + k) * 32;
-      ff acc = ff_make(pc[l]);
-#pragma unroll
-      for (int j = 1; j < 32 / kGeomRed; ++j) acc = ff_add(acc, ff_make(pc[l + j * kGeomRed]));
-      v[k] = acc;
-    }
-#pragma unroll
-    for (int o = kGeomRed / 2; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) v[k] = ff_add(v[k], ff{__shfl_xor_sync(full, v[k].hi, o), __shfl_xor_sync(full, v[k].lo, o)});
-    const GeomSlot& g = slot[sl];
-    if (l == 0 && g.cell >= 0) {
+      for (int k = 0; k < 7; ++k) v[k] = ff_make(res[lane * 7 + k]);
       const int32_t a = M.cell_vert[g.v0];
       double area;
       Vec3 nrm, xg;
@@ -1159,16 +1210,14 @@ __device__ __forceinline__ bool has_plane(const Workspace& W, int32_t c, uint32_
   return W.iface_stamp[c] == step && W.A_int[c] > 0;
 }
 
-// t along x_owner -> x_neigh; *src = the interface cell whose plane gave it, or -1
+// t along x_owner -> x_neigh (dn = x_neigh - x_owner); *src = the interface cell whose plane gave
+// it, or -1
 __device__ double crossing_t(const MeshView& M, const Workspace& W, const double* alpha, int32_t f, int xf_mode,
-                             uint32_t step, int32_t* src) {
+                             uint32_t step, const Vec3& xo, const Vec3& dn, int32_t* src) {
   const int32_t o = M.face_owner[f], n = M.face_neigh[f];
   *src = -1;
   if (xf_mode == VOF_XF_AS_PRINTED) return fabs(alpha[n] - 0.5) / fabs(alpha[o] - alpha[n]);
-  const double t_lin = (alpha[o] - 0.5) / (alpha[o] - alpha[n]);
-  if (xf_mode == VOF_XF_LINEAR) return t_lin;
-  const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
-  const Vec3 xn = v3(M.cell_cen[3 * n], M.cell_cen[3 * n + 1], M.cell_cen[3 * n + 2]);
+  if (xf_mode == VOF_XF_LINEAR) return (alpha[o] - 0.5) / (alpha[o] - alpha[n]);
   const Vec3 xfc = v3(M.face_cen[3 * f], M.face_cen[3 * f + 1], M.face_cen[3 * f + 2]);
   double best_t = 0, best_d = 0;
   const int32_t cand[2] = {o, n};
@@ -1177,20 +1226,19 @@ __device__ double crossing_t(const MeshView& M, const Workspace& W, const double
     if (!has_plane(W, c, step)) continue;
     const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
     const Vec3 xg = v3(W.x_gamma[3 * c], W.x_gamma[3 * c + 1], W.x_gamma[3 * c + 2]);
-    const double den = dot(nn, xn - xo);
+    const double den = dot(nn, dn);
     if (den == 0) continue;
     const double t = dot(nn, xg - xo) / den;
     if (!(t >= 0 && t <= 1)) continue;
-    const double d = norm(xo + (xn - xo) * t - xfc);
+    const double d = norm(xo + dn * t - xfc);
     if (*src < 0 || d < best_d) { best_t = t; best_d = d; *src = c; }
   }
-  return *src >= 0 ? best_t : t_lin;
+  return *src >= 0 ? best_t : (alpha[o] - 0.5) / (alpha[o] - alpha[n]);
 }
 
 // ---- crossing faces next to the band (R4): list, then one thread per face ------------------------
 // A face is listed once: by its owner when the owner is a band cell, else by its neighbour.
 constexpr int kLsqLanes = 8;
-constexpr int kLsqCellLanes = 4;  // lanes per band cell in the least squares
 
 __global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
   const uint32_t step = W.counters->step;
@@ -1205,7 +1253,7 @@ __global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
       const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
       if (nbr < 0) continue;
       const int32_t q = o == c ? nbr : o;
-      if (!((aP - 0.5) * (alpha[q] - 0.5) < 0)) continue;
+      if (!crossing_pair(aP, alpha[q])) continue;
       if (o == c || W.band_stamp[o] != step) {
         const unsigned long long slot = atomicAdd((unsigned long long*)&W.counters->n_crossing, 1ull);
         W.xface_list[slot] = f;
@@ -1222,21 +1270,23 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
   for (int64_t j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t f = W.xface_list[j];
     const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-    int32_t src;
-    const double t = crossing_t(M, W, alpha, f, xf_mode, step, &src);
     const Vec3 xo = v3(M.cell_cen[3 * o], M.cell_cen[3 * o + 1], M.cell_cen[3 * o + 2]);
-    const Vec3 xn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]);
-    const Vec3 xf = xo + (xn - xo) * t;
+    const Vec3 dn = v3(M.cell_cen[3 * nbr], M.cell_cen[3 * nbr + 1], M.cell_cen[3 * nbr + 2]) - xo;
+    int32_t src;
+    const double t = crossing_t(M, W, alpha, f, xf_mode, step, xo, dn, &src);
+    const Vec3 xf = xo + dn * t;
     W.x_f[3 * f] = xf.x; W.x_f[3 * f + 1] = xf.y; W.x_f[3 * f + 2] = xf.z;
-    const double d_o = norm(xf - xo), d_n = norm(xf - xn);
-    W.d_own[f] = d_o;
-    W.d_neigh[f] = d_n;
+    // t lies in [0, 1] in every mode (the two cells are on opposite sides of 1/2), so the distances
+    // to the two centroids are t |dn| and (1 - t) |dn|
+    const double L = M.face_len[f];
+    W.d_own[f] = t * L;
+    W.d_neigh[f] = (1.0 - t) * L;
     const int32_t sc = src >= 0 ? src : (has_plane(W, o, step) ? o : (has_plane(W, nbr, step) ? nbr : -1));
     double af = 0;
     if (sc >= 0) {
       const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
       const Vec3 nn = v3(W.n_int[3 * sc], W.n_int[3 * sc + 1], W.n_int[3 * sc + 2]);
-      af = fabs(W.A_int[sc] * dot(nn, Af) / norm(Af));
+      af = fabs(W.A_int[sc] * dot(nn, Af) * M.face_iarea[f]);
     }
     W.A_int_f[f] = af;
     W.face_stamp[f] = step;
@@ -1244,92 +1294,64 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
 }
 
 // ---- interface-modified least squares (R7) on band cells -----------------------------------------
-// L lanes per band cell over its faces, a block taking kThreads / L consecutive band cells; a
-// crossing face contributes its crossing point x_f (computed first) with T_sat, and every face runs
-// the same instructions (the point and the value are selected, not branched on). The lanes' nine
-// sums of G and b go to shared memory; then one thread per cell adds them, in the order of the
-// lanes' pairwise tree, and inverts G: the per-cell FP64 work runs with every lane of a warp busy
-// (an FP64 warp instruction costs the same with one active lane as with 32).
-template <int L>
+// A thread per band cell over its faces: a crossing face contributes its crossing point x_f
+// (computed first) with T_sat, and every face runs the same FP64 instructions (the point and the
+// value are selected, the crossing test is on alpha's bits). One cell per lane keeps every lane of
+// the FP64 warp instructions busy, the per-cell inverse included (an FP64 warp instruction costs
+// the same with one active lane as with 32); no block barrier.
 __device__ void lsq_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
-  constexpr int C = kThreads / L;  // cells per block pass
-  static_assert(L == 4, "the per-cell sum below pairs lanes as (0 + 2) + (1 + 3)");
-  __shared__ double part[C][9][L];
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
-  const int lane = threadIdx.x % L, slot = threadIdx.x / L;
   int nsing = 0;
-  for (int64_t base = (int64_t)blockIdx.x * C; base < nb; base += (int64_t)gridDim.x * C) {
-    {
-      const int64_t j = base + slot;
-      double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
-      if (j < nb) {
-        const int32_t c = W.band_idx[j];
-        const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
-        const double TP = a.T[c], aP = a.alpha[c];
-        for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
-          const int32_t f = M.cell_face[k] & 0x7fffffff;
-          const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-          const int32_t q = o == c ? nbr : o;
-          if (q < 0 && !a.T_bnd) continue;
-          const bool cross = q >= 0 && (aP - 0.5) * (a.alpha[q] - 0.5) < 0;
-          const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
-          const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
-          const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
-          const double dT = Tq - TP;
-          g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
-          g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
-          b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
-        }
-      }
-      double* p = &part[slot][0][lane];
-      p[0 * L] = g00; p[1 * L] = g01; p[2 * L] = g02; p[3 * L] = g11; p[4 * L] = g12; p[5 * L] = g22;
-      p[6 * L] = b0; p[7 * L] = b1; p[8 * L] = b2;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = W.band_idx[j];
+    const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
+    const double TP = a.T[c], aP = a.alpha[c];
+    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+      const int32_t q = o == c ? nbr : o;
+      if (q < 0 && !a.T_bnd) continue;
+      const bool cross = q >= 0 && crossing_pair(aP, a.alpha[q]);
+      const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
+      const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
+      const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
+      const double dT = Tq - TP;
+      g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
+      g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
+      b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
     }
-    __syncthreads();
-    if (threadIdx.x < C) {
-      const int sl = threadIdx.x;
-      const int64_t j = base + sl;
-      if (j < nb) {
-        const int32_t c = W.band_idx[j];
-        double v[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) v[q] = (part[sl][q][0] + part[sl][q][2]) + (part[sl][q][1] + part[sl][q][3]);
-        const double g00 = v[0], g01 = v[1], g02 = v[2], g11 = v[3], g12 = v[4], g22 = v[5];
-        const double b0 = v[6], b1 = v[7], b2 = v[8];
-        // explicit symmetric inverse (cofactors / det), Appendix B
-        const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-        const double det = g00 * c00 + g01 * c01 + g02 * c02;
-        const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
-        int st = 0;
-        Vec3 g = v3(0, 0, 0);
-        if (det > 1e-12 * tr * tr * tr) {
-          const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-          const double id = 1.0 / det;
-          g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
-                 (c02 * b0 + c12 * b1 + c22 * b2) * id);
-        } else {
-          st = VOF_ST_SINGULAR_LSQ;
-          ++nsing;
-        }
-        W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
-        if (W.iface_stamp[c] == step) W.status[c] |= st;
-        else W.status[c] = st;
-      }
+    // explicit symmetric inverse (cofactors / det), Appendix B
+    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    const double det = g00 * c00 + g01 * c01 + g02 * c02;
+    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
+    int st = 0;
+    Vec3 g = v3(0, 0, 0);
+    if (det > 1e-12 * tr * tr * tr) {
+      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+      const double id = 1.0 / det;
+      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+             (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    } else {
+      st = VOF_ST_SINGULAR_LSQ;
+      ++nsing;
     }
-    __syncthreads();
+    W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
+    if (W.iface_stamp[c] == step) W.status[c] |= st;
+    else W.status[c] = st;
   }
   if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
 }
 
 // ---- per-side gradients and source (R5, R6) on interface cells, totals (R8) -----------------------
-constexpr int kSrcLanes = 16;  // lanes per interface cell over its faces
 // The totals are the pairwise tree over the interface list (cell order) padded with zeros to a
-// power of two. Each block takes aligned tiles of kSrcTile interface cells: it computes their
-// sources (kSrcLanes lanes per cell over its faces), then the tile's subtree from shared memory;
-// the last block to finish (an atomic count of finished blocks) folds the tile sums in subtrees of
-// 2 kThreads leaves, level by level, so the pairing is the whole tree's. Cells outside the
-// interface get mdot = Q = 0.
+// power of two. A thread per interface cell computes its source (a loop over its faces, one cell
+// per lane so that the FP64 warp instructions keep every lane busy); a block takes aligned tiles
+// of kSrcTile = blockDim interface cells and sums each tile's subtree (warp shuffles, then the
+// warp sums); the last block to finish (an atomic count of finished blocks) folds the tile sums in
+// subtrees of 2 kThreads leaves, level by level, so the pairing is the whole tree's. The zeros of
+// the cells outside the interface are written by a memset on a side branch of the step.
 
 // Pairwise tree of x[base, base + 2 T) (zeros past n) in a block of T threads (T a multiple of 32,
 // at most 1024); the result is valid in thread 0. Thread t pairs leaves 2t and 2t+1, lanes then
@@ -1360,40 +1382,67 @@ __device__ double block_tree(const double* x, int64_t n, int64_t base, double* s
   return r;
 }
 
-constexpr int kSrcThreads = kThreads;  // threads of a source pass: kSrcTile cells x kSrcLanes lanes
-
 __device__ __forceinline__ double flip_if(double x, bool f) {  // -x when f, by the sign bit
   return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
 }
 
+// Sum of the aligned leaves [tile * kThreads, (tile + 1) * kThreads) in thread order: each warp's
+// 32 leaves by shuffles (lane t + 2^k joins lane t), then warp 0 pairs the warp sums. Valid in
+// thread 0.
+__device__ __forceinline__ double tile_tree(double v, double* sw) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double w = __shfl_down_sync(0xffffffffu, v, o);
+    if ((lane & (2 * o - 1)) == 0) v += w;
+  }
+  if (lane == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x < 32) {
+    v = lane < kThreads / 32 ? sw[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < kThreads / 32; o <<= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      if ((lane & (2 * o - 1)) == 0) v += w;
+    }
+    r = v;
+  }
+  __syncthreads();
+  return r;
+}
+
 __device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
-  constexpr int L = kSrcLanes;
-  static_assert(kSrcTile * L == kSrcThreads, "one tile per block pass");
-  __shared__ double part[kSrcTile][L][4];  // per lane: other-side gradient sum (3), weight sum
-  __shared__ double tm[kSrcTile], tq[kSrcTile];
-  const uint32_t step = W.counters->step;
+  static_assert(kSrcTile == kThreads, "a tile per block pass, a cell per thread");
+  __shared__ double swm[kThreads / 32], swq[kThreads / 32];
   const int64_t n = W.counters->n_iface;
   const int64_t ntiles = (n + kSrcTile - 1) / kSrcTile;
   const int64_t tcap = (M.n_cells + kSrcTile - 1) / kSrcTile;
-  const int lane = threadIdx.x % L, slot = threadIdx.x / L;
+  const double inv_hlv = 1.0 / a.props.h_lv;
   int nside = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // (1) L lanes per cell over its faces: weights max(0, n . A_f) towards the other phase and the
-    // weighted gradients of the neighbours there
-    {
-      const int64_t i = tile * kSrcTile + slot;
-      double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-      if (i < n && !a.opt.extrap) {  // with the pseudo-time solve the other side is already known
-        const int32_t c = W.iface_idx[i];
-        if (W.A_int[c] > 0) {
-          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
-          const bool liq = a.alpha[c] > 0.5;  // the other side is vapour (weights of -n) or liquid (+n)
-          for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += L) {
+    const int64_t i = tile * kSrcTile + threadIdx.x;
+    double mV = 0, qV = 0;
+    if (i < n) {
+      const int32_t c = W.iface_idx[i];
+      double mdot = 0, Q = 0, ql = 0, qv = 0;
+      Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
+      const double Aint = W.A_int[c];
+      if (positive(Aint)) {
+        const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
+        const bool liq = liquid(a.alpha[c]);  // the other side is vapour (weights of -n) or liquid (+n)
+        if (a.opt.extrap) {  // both sides written by the pseudo-time solve
+          gl = v3(W.grad_l[3 * c], W.grad_l[3 * c + 1], W.grad_l[3 * c + 2]);
+          gv = v3(W.grad_v[3 * c], W.grad_v[3 * c + 1], W.grad_v[3 * c + 2]);
+        } else {
+          // R5: weights max(0, n . A_f) towards the other phase, the weighted mean of the
+          // neighbours' gradients there
+          double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+          for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
             const int32_t fe = M.cell_face[k];
             const int32_t f = fe & 0x7fffffff;
             const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
-            if (q < 0) continue;
-            if ((a.alpha[q] > 0.5) == liq) continue;
+            if (q < 0 || liquid(a.alpha[q]) == liq) continue;
             const Vec3 Af = v3(M.face_area[3 * f], M.face_area[3 * f + 1], M.face_area[3 * f + 2]);
             double w = flip_if(dot(nn, Af), (fe < 0) != liq);  // outward area of c, towards the other side
             w = positive(w) ? w : 0.0;
@@ -1402,94 +1451,42 @@ __device__ void source_phase(const MeshView& M, const StepArgs& a, Workspace& W)
             p2 = fma(W.grad[3 * q + 2], w, p2);
             p3 += w;
           }
-        }
-      }
-      part[slot][lane][0] = p0;
-      part[slot][lane][1] = p1;
-      part[slot][lane][2] = p2;
-      part[slot][lane][3] = p3;
-    }
-    __syncthreads();
-    // (2) one thread per cell: the lane sums in lane order, then the cell's source
-    if (threadIdx.x < kSrcTile) {
-      const int sl = threadIdx.x;
-      const int64_t i = tile * kSrcTile + sl;
-      double mV = 0, qV = 0;
-      if (i < n) {
-        const int32_t c = W.iface_idx[i];
-        double mdot = 0, Q = 0, ql = 0, qv = 0;
-        Vec3 gl = v3(0, 0, 0), gv = v3(0, 0, 0);
-        const double Aint = W.A_int[c];
-        if (Aint > 0) {
-          Vec3 acc = v3(0, 0, 0);
-          double ws = 0;
-#pragma unroll 2
-          for (int l = 0; l < L; ++l) {
-            acc = acc + v3(part[sl][l][0], part[sl][l][1], part[sl][l][2]);
-            ws += part[sl][l][3];
-          }
-          const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
-          const bool liq = a.alpha[c] > 0.5;
           Vec3 go = v3(0, 0, 0);
-          if (ws > 0) go = acc * (1.0 / ws);
-          const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
-          gl = liq ? gown : go;
-          gv = liq ? go : gown;
-          if (a.opt.extrap) {  // both sides written by the pseudo-time solve
-            gl = v3(W.grad_l[3 * c], W.grad_l[3 * c + 1], W.grad_l[3 * c + 2]);
-            gv = v3(W.grad_v[3 * c], W.grad_v[3 * c + 1], W.grad_v[3 * c + 2]);
-          }
-          ql = a.props.k_l * dot(gl, nn) * Aint;
-          qv = -a.props.k_v * dot(gv, nn) * Aint;
-          mdot = (ql + qv) / (a.props.h_lv * M.cell_vol[c]);
-          Q = -mdot * a.props.h_lv;
-          if (!(ws > 0) && !a.opt.extrap) {
+          if (positive(p3)) {
+            const double r = 1.0 / p3;
+            go = v3(p0 * r, p1 * r, p2 * r);
+          } else {
             W.status[c] |= VOF_ST_NO_SIDE;
             ++nside;
           }
+          const Vec3 gown = v3(W.grad[3 * c], W.grad[3 * c + 1], W.grad[3 * c + 2]);
+          gl = liq ? gown : go;
+          gv = liq ? go : gown;
         }
-        mV = mdot * M.cell_vol[c];
-        qV = Q * M.cell_vol[c];
-        a.mdot[c] = mdot;
-        a.Q[c] = Q;
-        W.q_l[c] = ql;
-        W.q_v[c] = qv;
-        W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
-        W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
-        W.mdotV[i] = mV;
-        W.QV[i] = qV;
+        ql = a.props.k_l * dot(gl, nn) * Aint;
+        qv = -a.props.k_v * dot(gv, nn) * Aint;
+        mdot = (ql + qv) * inv_hlv * M.cell_ivol[c];
+        Q = -mdot * a.props.h_lv;
       }
-      tm[sl] = mV;
-      tq[sl] = qV;
+      const double V = M.cell_vol[c];
+      mV = mdot * V;
+      qV = Q * V;
+      a.mdot[c] = mdot;
+      a.Q[c] = Q;
+      W.q_l[c] = ql;
+      W.q_v[c] = qv;
+      W.grad_l[3 * c] = gl.x; W.grad_l[3 * c + 1] = gl.y; W.grad_l[3 * c + 2] = gl.z;
+      W.grad_v[3 * c] = gv.x; W.grad_v[3 * c + 1] = gv.y; W.grad_v[3 * c + 2] = gv.z;
+      W.mdotV[i] = mV;
+      W.QV[i] = qV;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      // the tile's subtree: lane t pairs leaves 2t and 2t+1, then the levels across the lanes
-      const int t = threadIdx.x;
-      double vm = t < kSrcTile / 2 ? tm[2 * t] + tm[2 * t + 1] : 0.0;
-      double vq = t < kSrcTile / 2 ? tq[2 * t] + tq[2 * t + 1] : 0.0;
-#pragma unroll
-      for (int o = 1; o < kSrcTile / 2; o <<= 1) {
-        const double wm = __shfl_down_sync(0xffffffffu, vm, o), wq = __shfl_down_sync(0xffffffffu, vq, o);
-        if ((t & (2 * o - 1)) == 0) {
-          vm += wm;
-          vq += wq;
-        }
-      }
-      if (t == 0) {
-        W.tile_part[tile] = vm;
-        W.tile_part[tcap + tile] = vq;
-      }
+    const double tm = tile_tree(mV, swm), tq = tile_tree(qV, swq);
+    if (threadIdx.x == 0) {
+      W.tile_part[tile] = tm;
+      W.tile_part[tcap + tile] = tq;
     }
-    __syncthreads();
   }
   if (nside) atomicAdd((unsigned long long*)&W.counters->n_no_side, (unsigned long long)nside);
-  // every other cell: no source
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.n_cells; c += (int64_t)gridDim.x * blockDim.x)
-    if (W.iface_stamp[c] != step) {
-      a.mdot[c] = 0.0;
-      a.Q[c] = 0.0;
-    }
 }
 
 // The last block to finish folds the tile sums into the two totals.
@@ -1997,8 +1994,7 @@ __global__ void __launch_bounds__(kThreads) k_lsq_study(MeshView M, StepArgs a, 
   if (nsing) atomicAdd((unsigned long long*)&W.counters->n_singular, (unsigned long long)nsing);
 }
 
-template <int L>
-__global__ void __launch_bounds__(kThreads) k_lsq(MeshView M, StepArgs a, Workspace W) { lsq_phase<L>(M, a, W); }
+__global__ void __launch_bounds__(kThreads) k_lsq(MeshView M, StepArgs a, Workspace W) { lsq_phase(M, a, W); }
 
 // Sources and tile sums; the last block to finish folds the totals.
 __global__ void __launch_bounds__(kThreads) k_source(MeshView M, StepArgs a, Workspace W) {
@@ -2073,7 +2069,8 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   W.alpha_in = d_alpha;
   Timing& tm = m->timing;
   // selection, band, vertex field and bins: one cooperative launch, as many blocks as are resident
-  const size_t sel_smem = (size_t)(kThreads / 16) * (1 + m->max_cf) * sizeof(int32_t);  // phase 3's cells per pass
+  // phase 3's band cells and vertices per pass
+  const size_t sel_smem = (size_t)(kThreads / 16) * (1 + m->max_cf + m->max_cv) * sizeof(int32_t);
   if (!m->sel_grid) {
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_select, kThreads, sel_smem);
@@ -2087,9 +2084,9 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   }
   {
     const double eps = opt.alpha_eps;
-    int vmode = opt.vertex_mode;
+    int vmode = opt.vertex_mode, max_cf = m->max_cf;
     MeshView Mv = M;
-    void* args[] = {&Mv, (void*)&d_alpha, (void*)&eps, &vmode, &W};
+    void* args[] = {&Mv, (void*)&d_alpha, (void*)&eps, &vmode, &max_cf, &W};
     tm.start(KC_SELECT, s);
     cudaError_t el = cudaLaunchCooperativeKernel((const void*)k_select, dim3(m->sel_grid), dim3(kThreads),
                                                  args, sel_smem, s);
@@ -2155,6 +2152,12 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
   const MeshView& M = m->view;
   Workspace& W = m->ws;
   Timing& tm = m->timing;
+  // zeros of mdot and Q on a side branch, joined before the source kernel writes the interface cells
+  cudaEventRecord(m->ev_zfork, s);
+  cudaStreamWaitEvent(m->z_stream, m->ev_zfork, 0);
+  cudaMemsetAsync(a.mdot, 0, (size_t)m->n_cells * sizeof(double), m->z_stream);
+  cudaMemsetAsync(a.Q, 0, (size_t)m->n_cells * sizeof(double), m->z_stream);
+  cudaEventRecord(m->ev_zjoin, m->z_stream);
   if (xmark_done) cudaStreamWaitEvent(s, m->ev_xjoin, 0);
   if (m->io_pending) {  // T and T_bnd of a host-buffer step, copied on the side
     cudaStreamWaitEvent(s, m->ev_io_done, 0);
@@ -2181,7 +2184,7 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
   if (a.opt.lsq_variant)  // the stencil-anisotropy study's variants
     k_lsq_study<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   else
-    k_lsq<kLsqCellLanes><<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
+    k_lsq<<<m->num_sms * 8, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
   if (a.opt.extrap) {
     // the pseudo-time solve: one cooperative launch
@@ -2200,6 +2203,7 @@ vof_status launch_source(vof_mesh* m, const StepArgs& a, cudaStream_t s, bool xm
     tm.stop(s);
     if (el != cudaSuccess) return cuda_fail(el, "extrapolation kernel (cooperative launch)");
   }
+  cudaStreamWaitEvent(s, m->ev_zjoin, 0);
   tm.start(KC_SOURCE, s);
   k_source<<<m->num_sms * 4, kThreads, 0, s>>>(M, a, W);
   tm.stop(s);
