@@ -72,7 +72,10 @@ typedef enum {
 
 /* Root-search modes. */
 #define VOF_ROOT_BISECT 0  /* plain FP64 bisection on [phi_min, phi_max] */
-#define VOF_ROOT_LEARNED 1 /* BF16 MLP guess, <= max_secant FP64 secant steps, bracketed bisection fallback */
+/* Learned: BF16 MLP guess refined on the FP32 pipe, then FP64: the cubic V_L of the vertex interval
+ * that holds the refined point (one pass over the cell's tetrahedra), an evaluation at the refined
+ * point, one at a Newton point, <= max_secant secant steps, bracketed bisection as the fallback. */
+#define VOF_ROOT_LEARNED 1
 /* Interval cubic: V_L(c) is one cubic between consecutive vertex values of a cell (Sec. 2.1 with
  * the cell split into tetrahedra of its own vertices); an FP32 refinement (from the MLP guess when
  * the mesh has an MLP, else from 1 - alpha) picks the interval, one
@@ -247,7 +250,10 @@ typedef enum {
   VOF_F_N_INT = 4,     /* double [n_cells][3] */
   VOF_F_X_GAMMA = 5,   /* double [n_cells][3] */
   VOF_F_STATUS = 6,    /* int32 [n_cells]: VOF_ST_* bits (interface and band cells) */
-  VOF_F_EVALS = 7,     /* int32 [n_cells]: FP64 cut-volume evaluations of the root search */
+  VOF_F_EVALS = 7,     /* int32 [n_cells]: FP64 cut-volume evaluations of the root search: passes over the
+                        * cell's tetrahedra (a bisection evaluation, or the cubic of a vertex interval on
+                        * the learned and interval-cubic paths, whose evaluations at points of the
+                        * interval are then scalar) */
   VOF_F_GRAD = 8,      /* double [n_cells][3]: modified least-squares grad T (band cells) */
   VOF_F_GRAD_L = 9,    /* double [n_cells][3]: liquid-side gradient (interface cells) */
   VOF_F_GRAD_V = 10,   /* double [n_cells][3]: vapour-side gradient (interface cells) */
@@ -293,7 +299,7 @@ typedef struct {
   int64_t step;  /* stamp of the last step (see the *_STAMP fields) */
   int64_t n_iface, n_band, n_crossing;
   int64_t n_degenerate, n_not_converged, n_fallback, n_singular, n_no_side, n_mlp_skipped;
-  int64_t evals_total; /* FP64 cut-volume evaluations summed over interface cells */
+  int64_t evals_total; /* FP64 cut-volume evaluations (VOF_F_EVALS) summed over interface cells */
   /* algorithmic work of the root search (roofline accounting): tetrahedron evaluations (sum over
    * interface cells of evaluations x tetrahedra), tetrahedra prepared, tetrahedra cut by the final
    * interface */

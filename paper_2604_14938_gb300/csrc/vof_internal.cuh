@@ -74,8 +74,8 @@ struct Workspace {
   uint32_t* band_stamp;    // [n_cells]
   uint32_t* vert_stamp;    // [n_verts]
   uint32_t* face_stamp;    // [n_faces]
-  int64_t* blk_count;      // [n_sel_blocks]
-  int64_t* blk_off;        // [n_sel_blocks]
+  uint32_t* sel_mask;      // [n_sel_blocks][kSelTile / 32] interface flags of the selection tiles
+  int64_t* sel_tot;        // [kMaxSelGrid] interface cells per selection block
   int32_t* band_idx;       // [n_cells] band cells (unordered)
   double* phi_v;           // [n_verts]
   float2* phi_ff;          // [n_verts] phi_v as a (hi, lo) float pair
@@ -122,6 +122,7 @@ struct Workspace {
 };
 
 constexpr int kSelTile = 512;       // cells per selection tile (2 consecutive cells per thread)
+constexpr int kMaxSelGrid = 4096;   // blocks of the cooperative selection launch, at most
 // Bins of interface cells by tetrahedron count; each bin's root search has its own lanes per cell.
 constexpr int kBins = 5;
 constexpr int kBinMaxTets[kBins] = {4, 8, 24, 64, 192};

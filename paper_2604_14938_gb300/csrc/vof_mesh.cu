@@ -381,8 +381,8 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.band_stamp, nc));
   TRY(dev_alloc(m, &W.vert_stamp, nv));
   TRY(dev_alloc(m, &W.face_stamp, nf));
-  TRY(dev_alloc(m, &W.blk_count, m->n_sel_blocks));
-  TRY(dev_alloc(m, &W.blk_off, m->n_sel_blocks));
+  TRY(dev_alloc(m, &W.sel_mask, (size_t)m->n_sel_blocks * (kSelTile / 32)));
+  TRY(dev_alloc(m, &W.sel_tot, kMaxSelGrid));
   TRY(dev_alloc(m, &W.tile_part, 2 * (size_t)((nc + kSrcTile - 1) / kSrcTile)));
   TRY(dev_alloc(m, &W.band_idx, nc));
   TRY(dev_alloc(m, &W.phi_v, nv));

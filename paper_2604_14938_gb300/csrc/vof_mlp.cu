@@ -295,17 +295,32 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, con
     const int64_t ib = b0 + lane;
     const int32_t cb = ib < n ? W.iface_idx[ib] : 0;
     const float ab = ib < n ? (float)alpha[cb] : 0.f;
+    // lane j's cell's vertex range, so that the loop below reads it by shuffles
+    const int64_t vob = M.cell_vert_off[cb];
+    const int nvb = (int)(M.cell_vert_off[cb + 1] - vob);
     const int nb = n - b0 < 32 ? (int)(n - b0) : 32;
+    // the vertices of cell j + 1 are read while cell j is processed (one cell ahead)
+    auto vertex_of = [&](int j) -> int32_t {
+      const int64_t v0 = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)vob, j);
+      const int nv = __shfl_sync(0xffffffffu, nvb, j);
+      return M.cell_vert[v0 + (lane < nv && lane < 32 ? lane : 0)];
+    };
+    int32_t vn = vertex_of(0);
+    double pn = W.phi_v[vn];
+    float2 fn = W.phi_ff[vn];
     int okb = 0;
     for (int j = 0; j < nb; ++j) {
-      const int32_t c = __shfl_sync(0xffffffffu, cb, j);
-      const int64_t v0 = M.cell_vert_off[c];
-      const int nv = (int)(M.cell_vert_off[c + 1] - v0);
+      const int nv = __shfl_sync(0xffffffffu, nvb, j);
+      const double pv = pn;
+      const float2 pf = fn;
+      if (j + 1 < nb) {
+        vn = vertex_of(j + 1);
+        pn = W.phi_v[vn];
+        fn = W.phi_ff[vn];
+      }
       if (nv > 32) continue;
       const bool has = lane < nv;
-      const int32_t v = has ? M.cell_vert[v0 + lane] : M.cell_vert[v0];
-      const uint64_t kp = okey(W.phi_v[v]);
-      const float2 pf = W.phi_ff[v];
+      const uint64_t kp = okey(pv);
       // extreme vertices by integer min / max of the order keys
       uint64_t klo = kp, khi = kp;
 #pragma unroll
@@ -353,101 +368,49 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, con
   }
 }
 
-// forward over the interface list (n read on the device); writes the guess of interface cell i,
-// clamped to [0, 1], or -1 where the cell has no features. Blocks of kFwdRows rows (two warps),
-// so that a few thousand interface cells still spread over most SMs.
-constexpr int kFwdRows = 32;
-constexpr int kFwdColGroups = 4;  // warps per 16-row tile, each computing 16 of the 64 columns
-constexpr int kFwdThreads = (kFwdRows / 16) * kFwdColGroups * 32;
-
-// Columns [16 cg, 16 cg + 16) of rows m0..m0+15 of X[.][0..K) times W^T (two n-tiles of 8).
-template <int K, int LDA, int LDB>
-__device__ __forceinline__ void warp_gemm_cols(const __nv_bfloat16* X, const __nv_bfloat16* W, int m0, int cg,
-                                               float (&acc)[2][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[4];
-    a[0] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 2 * q);
-    a[1] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 2 * q);
-    a[2] = *reinterpret_cast<const uint32_t*>(X + (m0 + g) * LDA + k0 + 8 + 2 * q);
-    a[3] = *reinterpret_cast<const uint32_t*>(X + (m0 + g + 8) * LDA + k0 + 8 + 2 * q);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const __nv_bfloat16* w = W + ((2 * cg + j) * 8 + g) * LDB + k0 + 2 * q;
-      mma16816(acc[j], a, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
-    }
-  }
-}
-
-// hidden layer: bias + GELU of this warp's 16 columns into H (bf16)
-__device__ __forceinline__ void hidden_cols(const float (&acc)[2][4], const float* b, __nv_bfloat16* H, int m0, int cg) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = m0 + g + (i >= 2 ? 8 : 0), c = (2 * cg + j) * 8 + 2 * q + (i & 1);
-      H[r * LDH + c] = __float2bfloat16_rn(gelu(acc[j][i] + b[c]));
-    }
-}
-
-// forward over the interface list (n read on the device); writes the guess of interface cell i,
-// clamped to [0, 1], or -1 where the cell has no features. A block takes kFwdRows rows at a time;
-// each 16-row tile is shared by kFwdColGroups warps that split the 64 hidden columns (block
-// barriers between the layers), so that the GELUs, the bulk of the work, spread over four times
-// as many warps. The output sums the column groups' partial dot products in a fixed order.
-__global__ void __launch_bounds__(kFwdThreads) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
-                                                                  Workspace W) {
+// Forward over the interface list (n read on the device): writes the guess of interface cell i,
+// clamped to [0, 1], or -1 where the cell has no features. After the block stages the weights,
+// each warp runs its own 16-row tiles through the three layers (rows [16 w, 16 w + 16) of the
+// block's shared tiles), so no block barrier separates the layers or the tiles, and a few thousand
+// interface cells still spread over many SMs (a warp per tile).
+__global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
+                                                                 Workspace W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
-  float* yp = reinterpret_cast<float*>(smem_raw + sizeof(Smem));  // [kFwdColGroups][kFwdRows]
   const int64_t n = W.counters->n_iface;
-  if ((int64_t)blockIdx.x * kFwdRows >= n) return;
+  const int64_t ntile = (n + 15) / 16;
+  if ((int64_t)blockIdx.x * kWarps >= ntile) return;
   stage_weights(s, *w);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int m0 = (warp / kFwdColGroups) * 16, cg = warp % kFwdColGroups;
-  for (int64_t row0 = (int64_t)blockIdx.x * kFwdRows; row0 < n; row0 += (int64_t)gridDim.x * kFwdRows) {
-    load_x(s, X, row0, n, kFwdRows);
-    cp_async_wait();
-    __syncthreads();
-    float acc[2][4];
-    warp_gemm_cols<kInPad, LDX, LDX>(s.X, s.W1, m0, cg, acc);
-    hidden_cols(acc, s.b1, s.H1, m0, cg);
-    __syncthreads();
-    warp_gemm_cols<kH, LDH, LDH>(s.H1, s.W2, m0, cg, acc);
-    hidden_cols(acc, s.b2, s.H2, m0, cg);
-    __syncthreads();
-    warp_gemm_cols<kH, LDH, LDH>(s.H2, s.W3, m0, cg, acc);
-    float part[2] = {0.f, 0.f};
+  cp_async_wait();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m0 = warp * 16;
+  constexpr int C4 = kInPad / 4;  // float4 per padded row
+  for (int64_t tile = (int64_t)blockIdx.x * kWarps + warp; tile < ntile; tile += (int64_t)gridDim.x * kWarps) {
+    const int64_t row0 = tile * 16;
+    // the tile's 16 feature rows as bf16 (zeros past n and in the padding); rows are 160 bytes
+    // of a 16-byte aligned buffer
+    float4 v[16 * C4 / 32];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int c = (2 * cg + j) * 8 + 2 * q + (i & 1);
-        part[i >> 1] = fmaf(gelu(acc[j][i] + s.b3[c]), s.w4[c], part[i >> 1]);
-      }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 1);
-      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 2);
+    for (int u = 0; u < 16 * C4 / 32; ++u) {
+      const int q = lane + 32 * u, r = q / C4, c4 = q % C4;
+      const int64_t gr = row0 + r;
+      v[u] = (c4 < kIn / 4 && gr < n) ? __ldg(reinterpret_cast<const float4*>(X + gr * kIn) + c4)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (q == 0) {
-      yp[cg * kFwdRows + m0 + g] = part[0];
-      yp[cg * kFwdRows + m0 + g + 8] = part[1];
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < kFwdRows; r += blockDim.x) {
-      const int64_t i = row0 + r;
-      float y = yp[r];
 #pragma unroll
-      for (int k = 1; k < kFwdColGroups; ++k) y += yp[k * kFwdRows + r];
-      y += s.b4;
-      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(y, 0.f), 1.f) : -1.f;
+    for (int u = 0; u < 16 * C4 / 32; ++u) {
+      const int q = lane + 32 * u, r = q / C4, c4 = q % C4;
+      __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(s.X + (m0 + r) * LDX + c4 * 4);
+      d[0] = __floats2bfloat162_rn(v[u].x, v[u].y);
+      d[1] = __floats2bfloat162_rn(v[u].z, v[u].w);
     }
-    __syncthreads();
+    __syncwarp();
+    warp_forward(s, m0, nullptr, nullptr, nullptr, nullptr);  // ends with a warp barrier after s.y
+    if (lane < 16) {
+      const int64_t i = row0 + lane;
+      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(s.y[m0 + lane], 0.f), 1.f) : -1.f;
+    }
+    __syncwarp();
   }
 }
 
@@ -621,15 +584,15 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   m->timing.start(KC_MLP_FEATURES, s);
   k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, m->ws.mlp_static, X, ok);
   m->timing.stop(s);
-  const size_t fwd_smem = sizeof(Smem) + kFwdColGroups * kFwdRows * sizeof(float);
+  const size_t fwd_smem = sizeof(Smem);
   static int fwd_bps = 0;  // resident blocks per SM of the forward pass
   if (!fwd_bps) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_bps, k_mlp_forward_iface, kFwdThreads, fwd_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_bps, k_mlp_forward_iface, kRows * 2, fwd_smem);
     if (fwd_bps < 1) fwd_bps = 1;
   }
   m->timing.start(KC_MLP_FORWARD, s);
-  k_mlp_forward_iface<<<m->num_sms * fwd_bps, kFwdThreads, fwd_smem, s>>>(mlp->w, X, ok, m->ws);
+  k_mlp_forward_iface<<<m->num_sms * fwd_bps, kRows * 2, fwd_smem, s>>>(mlp->w, X, ok, m->ws);
   m->timing.stop(s);
   return cudaGetLastError();
 }

@@ -118,11 +118,15 @@ __device__ __forceinline__ bool is_iface_k(double a, IfaceKeys k) {
 
 // ---- the step's selection as one cooperative kernel ----------------------------------------------
 // Three phases separated by grid-wide barriers (the launch is cooperative, so every block is
-// resident): (1) step stamp and counters, interface cells per tile of kSelTile cells (each thread
-// takes kSelTile / kThreads consecutive cells); (2) each tile's offset from the counts of the tiles before it, the
-// order-preserving scatter of the interface list, the tetrahedron-count bins (block-aggregated
-// appends); (3) band and vertex stamps, the band list, and the vertex field of each vertex of an
-// interface cell, computed by the lane that stamps the vertex first.
+// resident). Each block owns a contiguous range of tiles of kSelTile cells (each thread takes
+// kSelTile / kThreads consecutive cells of a tile). (1) Step stamp and counters; the interface
+// flags of the block's tiles, kept as ballot masks, and the block's count. (2) The block's offset
+// from the counts of the blocks before it, then its tiles in order: the order-preserving scatter of
+// the interface list and the tetrahedron-count bins (block-aggregated appends). (3) Band and vertex
+// stamps, the band list, and the vertex field of each vertex of an interface cell, computed by the
+// block that stamps the vertex first.
+constexpr int kSelLanes = 8;  // lanes per interface cell in the selection's phase 3
+
 __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* s8) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
@@ -138,7 +142,8 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   cg::grid_group grid = cg::this_grid();
   constexpr int kPer = kSelTile / kThreads;  // consecutive cells per thread in a tile
   static_assert(kPer >= 1 && kPer <= 32 && kSelTile % kThreads == 0, "tile layout");
-  // (kThreads / 16) * (1 + max faces per cell) band cells, then (kThreads / 16) * max vertices per cell
+  // (kThreads / kSelLanes) * (1 + max faces per cell) band cells, then as many times the maximum
+  // vertices per cell
   extern __shared__ int32_t band_buf[];
   __shared__ int64_t s8[kThreads / 32];
   __shared__ int wpre[kThreads / 32 + 1];
@@ -146,38 +151,51 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   __shared__ unsigned long long s_binbase[kBins], s_gb;
   const int64_t nc = M.n_cells;
   const int64_t ntiles = (nc + kSelTile - 1) / kSelTile;
+  // each block takes a contiguous range of tiles, so that one prefix over the blocks' totals
+  // places every tile
+  const int64_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_lo = min((int64_t)blockIdx.x * tpb, ntiles), t_hi = min(t_lo + tpb, ntiles);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // interface flags of this thread's kPer cells of tile t
   const IfaceKeys ik = iface_keys(eps);
-  auto flags = [&](int64_t t) {
-    unsigned f = 0;
+  // (1) interface flags of this thread's kPer consecutive cells (kept as one ballot mask per warp
+  // and cell position, so that phase 2 does not read alpha again), counts per tile and per block
+  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(W.counters);
+  int64_t mine = 0;
+  for (int64_t t = t_lo; t < t_hi; ++t) {
     const int64_t c0 = t * kSelTile + (int64_t)threadIdx.x * kPer;
+    unsigned f = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k)
       if (c0 + k < nc && is_iface_k(alpha[c0 + k], ik)) f |= 1u << k;
-    return f;
-  };
-  // (1)
-  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(W.counters);
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t cnt = block_sum(__popc(flags(t)), s8);
-    if (threadIdx.x == 0) W.blk_count[t] = cnt;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const unsigned b = __ballot_sync(0xffffffffu, (f >> k) & 1u);
+      if (lane == 0) W.sel_mask[(t * (kThreads / 32) + wid) * kPer + k] = b;
+    }
+    mine += __popc(f);
   }
+  const int64_t btot = block_sum(mine, s8);
+  if (threadIdx.x == 0) W.sel_tot[blockIdx.x] = btot;
   grid.sync();
-  // (2)
+  // (2) this block's offset from the totals of the blocks before it; the tiles in order
   const uint32_t step = W.counters->step;
-  if (blockIdx.x == 0) {
-    int64_t tot = 0;
-    for (int64_t u = threadIdx.x; u < ntiles; u += blockDim.x) tot += W.blk_count[u];
-    tot = block_sum(tot, s8);
-    if (threadIdx.x == 0) W.counters->n_iface = tot;
+  int64_t pos = 0;
+  {
+    int64_t before = 0, all = 0;
+    for (int64_t u = threadIdx.x; u < gridDim.x; u += blockDim.x) {
+      const int64_t v = W.sel_tot[u];
+      all += v;
+      if (u < blockIdx.x) before += v;
+    }
+    pos = block_sum(before, s8);
+    const int64_t total = block_sum(all, s8);
+    if (blockIdx.x == 0 && threadIdx.x == 0) W.counters->n_iface = total;
   }
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t before = 0;
-    for (int64_t u = threadIdx.x; u < t; u += blockDim.x) before += W.blk_count[u];
-    const int64_t tile_pos = block_sum(before, s8);
+  for (int64_t t = t_lo; t < t_hi; ++t) {
+    unsigned f = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) f |= ((W.sel_mask[(t * (kThreads / 32) + wid) * kPer + k] >> lane) & 1u) << k;
     // exclusive scan of the per-thread counts: within the warp, then over the warps
-    const unsigned f = flags(t);
     const int cnt = __popc(f);
     int incl = cnt;
 #pragma unroll
@@ -191,11 +209,10 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
       wpre[0] = 0;
       for (int w = 1; w <= kThreads / 32; ++w) wpre[w] += wpre[w - 1];
     }
-    __syncthreads();
-    int64_t p = tile_pos + wpre[wid] + incl - cnt;
-    // bins: slots within the block from shared counters, one global atomic per bin and tile
     if (threadIdx.x < kBins) s_bin[threadIdx.x] = 0;
     __syncthreads();
+    const int64_t p = pos + wpre[wid] + incl - cnt;
+    // bins: slots within the block from shared counters, one global atomic per bin and tile
     const int64_t c0 = t * kSelTile + (int64_t)threadIdx.x * kPer;
     int bslot[kPer];
 #pragma unroll
@@ -203,8 +220,9 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
       bslot[k] = -1;
       if ((f >> k) & 1u) {
         const int64_t c = c0 + k;
-        W.iface_idx[p + __popc(f & ((1u << k) - 1u))] = (int32_t)c;
-        W.iface_slot[c] = (int32_t)(p + __popc(f & ((1u << k) - 1u)));
+        const int64_t slot = p + __popc(f & ((1u << k) - 1u));
+        W.iface_idx[slot] = (int32_t)c;
+        W.iface_slot[c] = (int32_t)slot;
         W.iface_stamp[c] = step;
         const int b = bin_of((int)(M.cell_tet_off[c + 1] - M.cell_tet_off[c]));
         bslot[k] = (b << 24) | atomicAdd(&s_bin[b], 1);
@@ -215,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
       s_binbase[threadIdx.x] =
           s_bin[threadIdx.x] ? atomicAdd((unsigned long long*)&W.counters->bin_count[threadIdx.x],
                                          (unsigned long long)s_bin[threadIdx.x]) : 0ull;
+    pos += wpre[kThreads / 32];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kPer; ++k)
@@ -222,7 +241,6 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
         const int b = bslot[k] >> 24;
         W.bin_list[(size_t)b * nc + s_binbase[b] + (bslot[k] & 0xffffff)] = (int32_t)(p + __popc(f & ((1u << k) - 1u)));
       }
-    __syncthreads();
   }
   grid.sync();
   // (3) kSelLanes lanes per interface cell, kThreads / kSelLanes cells per block pass: lane j takes
@@ -231,7 +249,6 @@ __global__ void __launch_bounds__(kThreads) k_select(MeshView M, const double* a
   // computes the field value of each vertex it stamped first, a thread per vertex (full warps on
   // the FP64 pipe).
   {
-    constexpr int kSelLanes = 16;
     int32_t* vert_buf = band_buf + (kThreads / kSelLanes) * (1 + max_cf);
     __shared__ int s_nv;
     const int sl = threadIdx.x % kSelLanes, scell = threadIdx.x / kSelLanes;
@@ -635,6 +652,17 @@ __device__ __forceinline__ void geometry_outputs(const ff* v, double ax, double 
   }
 }
 
+// Shared memory of one lane group of the root search (multiple of 8 bytes): the rows (FP64 rows of
+// plain bisection, else the FP32 rows of the refinement), the FP64 and normalised FP32 vertex
+// values, the tetrahedra's packed corners, the list of straddling tetrahedra.
+__host__ __device__ inline size_t root_rows_bytes(int max_ct, int mode) {
+  return ((size_t)max_ct * (mode == VOF_ROOT_BISECT ? sizeof(TetRow) : sizeof(TetRow32)) + 7) & ~(size_t)7;
+}
+__host__ __device__ inline size_t root_group_bytes(int max_ct, int max_cv, int mode) {
+  return root_rows_bytes(max_ct, mode) + (size_t)max_cv * sizeof(double) + (size_t)((max_cv + 1) & ~1) * sizeof(float) +
+         (size_t)((max_ct + 1) & ~1) * sizeof(uint32_t) + (size_t)((2 * max_ct + 7) & ~7);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
                                                    int max_ct, int max_cv, int mode, int use_mlp, int bin) {
@@ -642,12 +670,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
   const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  // per group: the rows, then the cell's normalised vertex values (FP32) for the learned path
+  // per group: the rows; the cell's FP64 vertex values; its normalised vertex values (FP32, the
+  // learned path); its tetrahedra's packed corner indices; the list of windowed rows. Every later
+  // read of a vertex value or a tetrahedron's corners comes from shared memory.
+  const size_t dv_bytes = (size_t)max_cv * sizeof(double);
   const size_t uv_bytes = (size_t)((max_cv + 1) & ~1) * sizeof(float);
-  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + uv_bytes + (size_t)((2 * max_ct + 7) & ~7);
-  TetRow* rows = reinterpret_cast<TetRow*>(smem + (size_t)gib * grp_bytes);
-  float* uvert = reinterpret_cast<float*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow));
-  uint16_t* actl = reinterpret_cast<uint16_t*>(smem + (size_t)gib * grp_bytes + (size_t)max_ct * sizeof(TetRow) + uv_bytes);
+  const size_t pk_bytes = (size_t)((max_ct + 1) & ~1) * sizeof(uint32_t);
+  const size_t rw_bytes = root_rows_bytes(max_ct, mode);
+  const size_t grp_bytes = root_group_bytes(max_ct, max_cv, mode);
+  unsigned char* gbase = smem + (size_t)gib * grp_bytes;
+  TetRow* rows = reinterpret_cast<TetRow*>(gbase);
+  double* dvert = reinterpret_cast<double*>(gbase + rw_bytes);
+  float* uvert = reinterpret_cast<float*>(gbase + rw_bytes + dv_bytes);
+  uint32_t* tpk = reinterpret_cast<uint32_t*>(gbase + rw_bytes + dv_bytes + uv_bytes);
+  uint16_t* actl = reinterpret_cast<uint16_t*>(gbase + rw_bytes + dv_bytes + uv_bytes + pk_bytes);
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
   int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
@@ -665,35 +701,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
     const int64_t t0 = M.cell_tet_off[cell];
     const int nt = (int)(M.cell_tet_off[cell + 1] - t0);
     const int32_t* cv = M.cell_vert + v0;
-    // range of the vertex values, by integer min/max of the order keys
+    // the cell's vertex values and tetrahedra into shared memory; the range of the vertex values
+    // by integer min/max of the order keys
     uint64_t klo = ~0ull, khi = 0ull;
     for (int j = lane; j < nv; j += G) {
-      const uint64_t k = okey(W.phi_v[cv[j]]);
+      const double p = W.phi_v[cv[j]];
+      dvert[j] = p;
+      const uint64_t k = okey(p);
       klo = min(klo, k);
       khi = max(khi, k);
     }
+    for (int t = lane; t < nt; t += G) tpk[t] = __ldg(M.cell_tet + t0 + t);
     const double lo = okey_inv(group_umin<G>(klo, mask)), hi = okey_inv(group_umax<G>(khi, mask));
-    const double p_apex = W.phi_v[cv[0]];
-    // FP64 rows of the cell's tetrahedra (after the FP32 phase on the learned path, whose rows
-    // share the same shared memory)
+    __syncwarp(mask);
+    const double p_apex = dvert[0];
+    // FP64 rows of the cell's tetrahedra (plain bisection only; the learned and interval-cubic
+    // paths keep FP32 rows in that space and no FP64 rows)
     int n_rows = nt, n_prep = 0;  // rows evaluated; rows prepared for this cell
-    double wet_sum = 0;          // volume of the tetrahedra wet over the whole window (windowed rows)
     auto prepare64 = [&]() {
       for (int t = lane; t < nt; t += G) {
-        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-        rows[t] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]],
-                              W.phi_v[cv[(pk >> 16) & 255]], __ldg(M.tet_vol + t0 + t));
+        const uint32_t pk = tpk[t];
+        rows[t] = tet_prepare(p_apex, dvert[pk & 255], dvert[(pk >> 8) & 255], dvert[(pk >> 16) & 255],
+                              __ldg(M.tet_vol + t0 + t));
       }
       __syncwarp(mask);
       n_rows = nt;
       n_prep += nt;
-      wet_sum = 0;
     };
-    // Rows valid for c in [wlo, whi) only: a tetrahedron whose corners all lie at or above whi is
-    // wet there (its volume goes to wet_sum), one whose corners all lie below wlo is dry; only
-    // the others (listed in actl) are prepared and evaluated.
-    auto prepare_window = [&](double wlo, double whi) {
-      const uint64_t kwl = okey(wlo), kwh = okey(whi), ka = okey(p_apex);
+    // One pass over the tetrahedra for the vertex interval [va, vb] (consecutive vertex values of
+    // the cell, so that no tetrahedron changes its number of wet corners inside it): those with
+    // every corner at or above vb are wet over it (their volume goes to P0), those with every
+    // corner at or below va dry; the others (compacted into actl, so that the FP64 work keeps the
+    // lanes busy) are prepared in registers and their pieces, the cubics A + B x + C x^2 + D x^3 in
+    // x = ref - c, expanded about cm = (va + vb)/2 and summed into P(y) = P0 + P1 y + P2 y^2 + P3 y^3,
+    // y = c - cm. P is V_L exactly on [va, vb]. Returns the number of pieces.
+    double cm = 0, P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+    auto interval_pass = [&](double va, double vb) -> int {
+      const uint64_t kva = okey(va), kvb = okey(vb), ka = okey(p_apex);
       const int base = (threadIdx.x & 31) / G * G;
       const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
       double ws = 0;
@@ -702,28 +746,45 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         const int t = r0 + lane;
         bool act = false;
         if (t < nt) {
-          const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-          const uint64_t k1 = okey(W.phi_v[cv[pk & 255]]), k2 = okey(W.phi_v[cv[(pk >> 8) & 255]]),
-                         k3 = okey(W.phi_v[cv[(pk >> 16) & 255]]);
+          const uint32_t pk = tpk[t];
+          const uint64_t k1 = okey(dvert[pk & 255]), k2 = okey(dvert[(pk >> 8) & 255]), k3 = okey(dvert[(pk >> 16) & 255]);
           const uint64_t kmin = min(min(ka, k1), min(k2, k3)), kmax = max(max(ka, k1), max(k2, k3));
-          if (kmin >= kwh) ws += __ldg(M.tet_vol + t0 + t);
-          else act = kmax >= kwl;
+          if (kmin >= kvb) ws += __ldg(M.tet_vol + t0 + t);
+          else act = kmax > kva;
         }
         const unsigned bal = (__ballot_sync(mask, act) >> base) & gbits;
         if (act) actl[n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
         n += __popc(bal);
       }
-      wet_sum = group_sum<G>(ws, mask);
       __syncwarp(mask);
+      cm = 0.5 * (va + vb);
+      double q0 = ws, q1 = 0, q2 = 0, q3 = 0;
       for (int k = lane; k < n; k += G) {
         const int t = actl[k];
-        const uint32_t pk = __ldg(M.cell_tet + t0 + t);
-        rows[k] = tet_prepare(p_apex, W.phi_v[cv[pk & 255]], W.phi_v[cv[(pk >> 8) & 255]],
-                              W.phi_v[cv[(pk >> 16) & 255]], __ldg(M.tet_vol + t0 + t));
+        const uint32_t pk = tpk[t];
+        const TetRow r = tet_prepare(p_apex, dvert[pk & 255], dvert[(pk >> 8) & 255], dvert[(pk >> 16) & 255],
+                                     __ldg(M.tet_vol + t0 + t));
+        // the piece on (va, vb]: its wet corners are those at or above vb
+        const int nk = (okey(r.s0) >= kvb) + (okey(r.s1) >= kvb) + (okey(r.s2) >= kvb) + (okey(r.s3) >= kvb);
+        const double ref = nk == 1 ? r.s0 : (nk == 2 ? r.s1 : r.s3);
+        const double A = nk == 2 ? r.a2 : (nk >= 3 ? r.v : 0.0);
+        const double B = nk == 2 ? r.b2 : 0.0;
+        const double C = nk == 2 ? r.c2 : 0.0;
+        const double D = nk == 1 ? r.d1 : (nk == 2 ? r.d2 : (nk == 3 ? r.d3 : 0.0));
+        // A + B x + C x^2 + D x^3 with x = (ref - cm) - y, expanded in y
+        const double dl = ref - cm;
+        q0 += fma(fma(fma(D, dl, C), dl, B), dl, A);
+        q1 -= fma(fma(3.0 * D, dl, 2.0 * C), dl, B);
+        q2 += fma(3.0 * D, dl, C);
+        q3 -= D;
       }
+      P0 = group_sum<G>(q0, mask);
+      P1 = group_sum<G>(q1, mask);
+      P2 = group_sum<G>(q2, mask);
+      P3 = group_sum<G>(q3, mask);
       __syncwarp(mask);
-      n_rows = n;
       n_prep += n;
+      return n;
     };
     const double a = alpha[cell];
     const double invV = M.cell_ivol[cell];
@@ -740,16 +801,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       kbest = mag(fmin(1.0 - a, a));
       c_best = (1.0 - a) <= a ? lo : hi;
       double L = lo, H = hi;
-      bool done = false, prepared = false;
-      // one FP64 evaluation: residual, best point and bracket updated, convergence test
-      auto eval64 = [&](double c) -> double {
-        const double f = (liquid_volume<G>(rows, n_rows, lane, mask, c) + wet_sum) * invV - a;
-        ++evals;
-        tev += n_rows;
+      bool done = false;
+      // f = V_L(c)/V - alpha at a point: best point and bracket updated, convergence test
+      auto record = [&](double c, double f) {
         const uint64_t kf = mag(f);
         if (kf < kbest) { kbest = kf; c_best = c; }
         if (positive(f)) L = dmax(L, c); else H = dmin(H, c);
         if (kf <= ktol) done = true;
+      };
+      // over the prepared rows (plain bisection)
+      auto eval64 = [&](double c) -> double {
+        const double f = liquid_volume<G>(rows, n_rows, lane, mask, c) * invV - a;
+        ++evals;
+        tev += n_rows;
+        record(c, f);
+        return f;
+      };
+      // every tetrahedron prepared on the fly (the learned and interval-cubic paths' last resort,
+      // when no vertex interval brackets the target: they keep no FP64 rows)
+      auto eval_direct = [&](double c) -> double {
+        const uint64_t kc = okey(c);
+        double part = 0;
+        for (int t = lane; t < nt; t += G) {
+          const uint32_t pk = tpk[t];
+          const TetRow r = tet_prepare(p_apex, dvert[pk & 255], dvert[(pk >> 8) & 255], dvert[(pk >> 16) & 255],
+                                       __ldg(M.tet_vol + t0 + t));
+          part += tet_wet_volume(r, kc, c);
+        }
+        const double f = group_sum<G>(part, mask) * invV - a;
+        ++evals;
+        tev += nt;
+        n_prep += nt;
+        record(c, f);
         return f;
       };
       if (mode != VOF_ROOT_BISECT) {
@@ -788,7 +871,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
           }
           __syncwarp(mask);
           for (int t = lane; t < nt; t += G) {
-            const uint32_t pk = __ldg(M.cell_tet + t0 + t);
+            const uint32_t pk = tpk[t];
             rows32[t] = tet_prepare32(uvert[0], uvert[pk & 255], uvert[(pk >> 8) & 255], uvert[(pk >> 16) & 255],
                                       __ldg(M.tet_vfrac + t0 + t));
           }
@@ -829,79 +912,65 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
           if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
           ubest = uc;
         }
-        if (mode == VOF_ROOT_CUBIC) {
-          // Interval cubic (the next row N1 of the scope): between two consecutive vertex values
-          // of the cell no tetrahedron changes its number of wet corners, so V_L is one cubic
-          // there. The FP32-refined point picks the interval [va, vb]; one FP64 pass over the rows
-          // straddling it sums their pieces as a cubic in y = c - cm (cm the midpoint); when the
-          // target lies outside the cubic's values at the ends, the neighbouring interval is
-          // taken instead; then safeguarded Newton steps on the polynomial alone give the root.
-          __syncwarp(mask);
-          double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
-          if (!(okey(c1) < okey(hi))) c1 = okey_inv(okey(hi) - 1);  // an interval above c1 exists
-          // largest vertex value <= c and smallest above it, by integer keys
-          auto vertex_interval = [&](double c, double& va, double& vb) {
-            const uint64_t kc = okey(c);
-            uint64_t ka = 0ull, kb = ~0ull;
-            for (int j = lane; j < nv; j += G) {
-              const uint64_t k = okey(W.phi_v[cv[j]]);
-              if (k <= kc) ka = max(ka, k); else kb = min(kb, k);
-            }
-            va = okey_inv(group_umax<G>(ka, mask));
-            vb = okey_inv(group_umin<G>(kb, mask));
-          };
-          double va, vb, cm = 0, P0 = 0, P1 = 0, P2 = 0, P3 = 0;
-          vertex_interval(c1, va, vb);
-          const double tgt = a * M.cell_vol[cell];
-          bool bracketed = false;
-          for (int mv = 0; mv < 8; ++mv) {
-            prepare_window(va, vb);  // rows straddling [va, vb]; wet_sum: tetrahedra wet over it
-            prepared = true;
-            cm = 0.5 * (va + vb);
-            const uint64_t kb = okey(vb);
-            double q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-            for (int k = lane; k < n_rows; k += G) {
-              const TetRow& r = rows[k];
-              // the piece on (va, vb]: its wet corners are those at or above vb
-              const int nk = (okey(r.s0) >= kb) + (okey(r.s1) >= kb) + (okey(r.s2) >= kb) + (okey(r.s3) >= kb);
-              const double ref = nk == 1 ? r.s0 : (nk == 2 ? r.s1 : r.s3);
-              const double A = nk == 2 ? r.a2 : (nk >= 3 ? r.v : 0.0);
-              const double B = nk == 2 ? r.b2 : 0.0;
-              const double C = nk == 2 ? r.c2 : 0.0;
-              const double D = nk == 1 ? r.d1 : (nk == 2 ? r.d2 : (nk == 3 ? r.d3 : 0.0));
-              // A + B x + C x^2 + D x^3 with x = (ref - cm) - y, expanded in y
-              const double dl = ref - cm;
-              q0 += fma(fma(fma(D, dl, C), dl, B), dl, A);
-              q1 -= fma(fma(3.0 * D, dl, 2.0 * C), dl, B);
-              q2 += fma(3.0 * D, dl, C);
-              q3 -= D;
-            }
-            P0 = group_sum<G>(q0, mask) + wet_sum;
-            P1 = group_sum<G>(q1, mask);
-            P2 = group_sum<G>(q2, mask);
-            P3 = group_sum<G>(q3, mask);
-            ++evals;
-            tev += n_rows;
-            const double ya = va - cm, yb = vb - cm;
-            const double ga = fma(fma(fma(P3, ya, P2), ya, P1), ya, P0) - tgt;
-            const double gb = fma(fma(fma(P3, yb, P2), yb, P1), yb, P0) - tgt;
-            if (gb > 0.0 && okey(vb) < okey(hi)) {  // the root lies above vb
-              vertex_interval(vb, va, vb);
-            } else if (ga < 0.0 && okey(va) > okey(lo)) {  // below va
-              vertex_interval(okey_inv(okey(va) - 1), va, vb);
-            } else {
-              bracketed = true;
-              break;
-            }
+        // FP64 phase, both paths: the FP32-refined point picks the vertex interval [va, vb]; one
+        // pass sums its cubic P (interval_pass); when the target lies outside P's values at the
+        // interval's ends the neighbouring interval is taken instead (another pass). On [va, vb]
+        // every FP64 evaluation of V_L is P, exactly.
+        //  - Learned: an evaluation at the refined point, one at a Newton point with the FP32
+        //    slope, at most max_secant secant steps (the benchmark spec's guess + secant steps).
+        //  - Interval cubic (the next row N1 of the scope): safeguarded Newton steps on P.
+        // A miss of the tolerance ends in bisection on P inside the bracket (the counted
+        // fallback); if no interval brackets the target, in bisection over [phi_min, phi_max]
+        // with every tetrahedron evaluated directly.
+        __syncwarp(mask);
+        double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
+        if (!(okey(c1) < okey(hi))) c1 = okey_inv(okey(hi) - 1);  // an interval above c1 exists
+        // largest vertex value <= c and smallest above it, by integer keys
+        auto vertex_interval = [&](double c, double& va, double& vb) {
+          const uint64_t kc = okey(c);
+          uint64_t ka = 0ull, kb = ~0ull;
+          for (int j = lane; j < nv; j += G) {
+            const uint64_t k = okey(dvert[j]);
+            if (k <= kc) ka = max(ka, k); else kb = min(kb, k);
           }
-          if (bracketed) {
-            double ya = va - cm, yb = vb - cm;  // g(ya) >= 0 >= g(yb), g decreasing
+          va = okey_inv(group_umax<G>(ka, mask));
+          vb = okey_inv(group_umin<G>(kb, mask));
+        };
+        double va, vb;
+        vertex_interval(c1, va, vb);
+        const double tgt = a * M.cell_vol[cell];
+        bool bracketed = false;
+        for (int mv = 0; mv < 8; ++mv) {
+          tev += interval_pass(va, vb);  // an FP64 evaluation: a pass over the cell's tetrahedra
+          ++evals;
+          const double ya = va - cm, yb = vb - cm;
+          const double ga = fma(fma(fma(P3, ya, P2), ya, P1), ya, P0) - tgt;
+          const double gb = fma(fma(fma(P3, yb, P2), yb, P1), yb, P0) - tgt;
+          if (gb > 0.0 && okey(vb) < okey(hi)) {  // the root lies above vb
+            vertex_interval(vb, va, vb);
+          } else if (ga < 0.0 && okey(va) > okey(lo)) {  // below va
+            vertex_interval(okey_inv(okey(va) - 1), va, vb);
+          } else {
+            bracketed = true;
+            break;
+          }
+        }
+        if (bracketed) {
+          L = dmax(L, va);  // V_L(va)/V - alpha >= 0 >= V_L(vb)/V - alpha
+          H = dmin(H, vb);
+          auto evalP = [&](double c) -> double {
+            const double y = c - cm;
+            const double f = (fma(fma(fma(P3, y, P2), y, P1), y, P0) - tgt) * invV;
+            record(c, f);
+            return f;
+          };
+          if (mode == VOF_ROOT_CUBIC) {
+            double ya = L - cm, yb = H - cm;  // g(ya) >= 0 >= g(yb), g decreasing
             double y = dmin(dmax(c1 - cm, ya), yb);
-            for (int it = 0; it < 12; ++it) {
+            for (int it = 0; it < 12 && !done; ++it) {
               const double g = fma(fma(fma(P3, y, P2), y, P1), y, P0) - tgt;
-              const uint64_t kf = mag(g * invV);
-              if (kf < kbest) { kbest = kf; c_best = cm + y; }
-              if (g == 0.0) break;
+              record(cm + y, g * invV);
+              if (g == 0.0 || done) break;
               if (g > 0.0) ya = y; else yb = y;
               const double dp = fma(fma(3.0 * P3, y, 2.0 * P2), y, P1);  // dg/dy <= 0
               double yn = 0.5 * (ya + yb);
@@ -914,69 +983,51 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
               if (yn == y || !inside(yn, ya, yb)) break;
               y = yn;
             }
-          }
-          done = kbest <= ktol;
-          if (!done) {
-            status |= VOF_ST_FALLBACK;
-            prepare64();  // bisection over [lo, hi] on every row
-          }
-        } else {
-          __syncwarp(mask);
-          // FP64 phase on the rows of a window of 2e-3 of the range around the refined point
-          // (a thousand times the FP32 refinement's accuracy); every FP64 point stays inside it
-          double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
-          const double wlo = dmax(c1 - 1e-3 * range, lo), whi = dmin(c1 + 1e-3 * range, hi);
-          prepare_window(wlo, whi);
-          prepared = true;
-          double f1 = eval64(c1);
-          double spread = 1e-6 * range;  // distance between the first two FP64 points
-          if (!done && opt.max_secant > 0) {
-            // second point: one Newton step with the FP32 slope, kept inside the bracket
-            double c0 = fma(-f1, range * (double)(1.0f / slope), c1);
-            if (!inside(c0, dmax(L, wlo), dmin(H, whi)) || c0 == c1) {
-              const double step = 4e-6 * range;
-              c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + dmin(H, whi))) : fmax(c1 - step, 0.5 * (c1 + dmax(L, wlo)));
-            }
-            spread = dmax(spread, fabs(c0 - c1));
-            double f0 = eval64(c0);
-            for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
-              if (__double_as_longlong(f0) == __double_as_longlong(f1)) break;
-              // secant point; the reciprocal of f0 - f1 from an FP32 seed and one FP64 Newton step
-              const double d = f0 - f1;
-              double r = (double)(1.0f / (float)d);
-              r = fma(r, fma(-d, r, 1.0), r);
-              double c2 = fma(-f0, (c0 - c1) * r, c0);
-              const double Lw = dmax(L, wlo), Hw = dmin(H, whi);
-              if (!inside(c2, Lw, Hw)) c2 = 0.5 * (Lw + Hw);
-              const double f2 = eval64(c2);
-              c1 = c0; f1 = f0; c0 = c2; f0 = f2;
-            }
-          }
-          if (!done) {
-            status |= VOF_ST_FALLBACK;
-            prepare64();  // the fallback may leave the window: every row
-            // When the FP64 points all lie on one side of the root, close the bracket next to
-            // them before bisecting: steps away from the nearest point towards the root,
-            // doubling (each an evaluation, counted).
-            const bool open_lo = !(okey(L) > okey(lo)), open_hi = !(okey(H) < okey(hi));
-            if (open_lo != open_hi) {
-              double step = spread;
-              for (int k = 0; k < 40 && !done; ++k) {
-                const double cp = open_lo ? H - step : L + step;
-                if (!inside(cp, L, H)) break;
-                const double fq = eval64(cp);
-                if (positive(fq) == open_lo) break;  // the open side is closed
-                step *= 2.0;
+          } else {
+            c1 = dmin(dmax(c1, L), H);
+            double f1 = evalP(c1);
+            if (!done && opt.max_secant > 0) {
+              // second point: one Newton step with the FP32 slope, kept inside the bracket
+              double c0 = fma(-f1, range * (double)(1.0f / slope), c1);
+              if (!inside(c0, L, H) || c0 == c1) {
+                const double step = 4e-6 * range;
+                c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
+              }
+              double f0 = evalP(c0);
+              for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
+                if (__double_as_longlong(f0) == __double_as_longlong(f1)) break;
+                // secant point; the reciprocal of f0 - f1 from an FP32 seed and one FP64 Newton step
+                const double d = f0 - f1;
+                double r = (double)(1.0f / (float)d);
+                r = fma(r, fma(-d, r, 1.0), r);
+                double c2 = fma(-f0, (c0 - c1) * r, c0);
+                if (!inside(c2, L, H)) c2 = 0.5 * (L + H);
+                const double f2 = evalP(c2);
+                c1 = c0; f1 = f0; c0 = c2; f0 = f2;
               }
             }
           }
+          if (!done) {
+            status |= VOF_ST_FALLBACK;
+            for (int it = 0; it < opt.max_bisect && !done; ++it) {
+              evalP(0.5 * (L + H));
+              if (okey(H) - okey(L) <= 4) break;  // a few representable values left
+            }
+          }
+        } else {
+          status |= VOF_ST_FALLBACK;
+          for (int it = 0; it < opt.max_bisect && !done; ++it) {
+            eval_direct(0.5 * (L + H));
+            if (okey(H) - okey(L) <= 4) break;
+          }
         }
-      }
-      if (!prepared) prepare64();
-      for (int it = 0; it < opt.max_bisect && !done; ++it) {
-        eval64(0.5 * (L + H));
-        // stop when the bracket is down to a few representable values
-        if (okey(H) - okey(L) <= 4) break;
+      } else {
+        prepare64();
+        for (int it = 0; it < opt.max_bisect && !done; ++it) {
+          eval64(0.5 * (L + H));
+          // stop when the bracket is down to a few representable values
+          if (okey(H) - okey(L) <= 4) break;
+        }
       }
       if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
     }
@@ -2030,8 +2081,7 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
   const int max_cv = m->max_cv;
-  const size_t grp_bytes = (size_t)max_ct * sizeof(TetRow) + (size_t)((max_cv + 1) & ~1) * sizeof(float) +
-                           (size_t)((2 * max_ct + 7) & ~7);
+  const size_t grp_bytes = root_group_bytes(max_ct, max_cv, mode);
   while (threads > 32 && threads > G && (size_t)(threads / G) * grp_bytes > 110 * 1024) threads /= 2;
   const size_t smem = (size_t)(threads / G) * grp_bytes;
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
@@ -2070,11 +2120,11 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   Timing& tm = m->timing;
   // selection, band, vertex field and bins: one cooperative launch, as many blocks as are resident
   // phase 3's band cells and vertices per pass
-  const size_t sel_smem = (size_t)(kThreads / 16) * (1 + m->max_cf + m->max_cv) * sizeof(int32_t);
+  const size_t sel_smem = (size_t)(kThreads / kSelLanes) * (1 + m->max_cf + m->max_cv) * sizeof(int32_t);
   if (!m->sel_grid) {
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_select, kThreads, sel_smem);
-    m->sel_grid = m->num_sms * std::max(1, std::min(bps, 4));
+    m->sel_grid = std::min(m->num_sms * std::max(1, std::min(bps, 8)), kMaxSelGrid);
   }
   if (!m->geom_grid) {  // the geometry grid: every resident warp of the device
     int bps = 0;
