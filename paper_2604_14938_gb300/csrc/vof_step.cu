@@ -85,6 +85,7 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
   cn->step += 1;
   cn->reduce_done = 0;
   cn->n_iface = cn->n_band = cn->n_crossing = cn->n_uvert = 0;
+  cn->n_band_a = cn->n_band_b = 0;
   cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
   cn->evals_total = 0;
   cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
@@ -395,6 +396,44 @@ __device__ __forceinline__ double tet_wet_volume(const TetRow& r, uint64_t kc, d
   const double D = k == 1 ? r.d1 : (k == 2 ? r.d2 : (k == 3 ? r.d3 : 0.0));
   const double x = ref - c;
   return fma(fma(fma(D, x, C), x, B), x, A);
+}
+
+// The piece of a tetrahedron that straddles a vertex interval (va, vb] of its cell (kvb =
+// okey(vb)): its wet volume there is one cubic A + B x + C x^2 + D x^3 in x = ref - c (the case
+// of its nk corners at or above vb), added to q0..q3 expanded about cm (x = (ref - cm) - y). Only
+// that case's coefficients are formed, by selecting its difference factors before one division:
+// wet corners lie at or above vb and dry ones at or below va, so every denominator is a product of
+// (wet - dry) differences, all positive.
+__device__ __forceinline__ void tet_piece(double p0, double p1, double p2, double p3, double vt, uint64_t kvb,
+                                          double cm, double& q0, double& q1, double& q2, double& q3) {
+  uint64_t k0 = okey(p0), k1 = okey(p1), k2 = okey(p2), k3 = okey(p3);
+  cswap(k0, p0, k1, p1);
+  cswap(k2, p2, k3, p3);
+  cswap(k0, p0, k2, p2);
+  cswap(k1, p1, k3, p3);
+  cswap(k1, p1, k2, p2);
+  const int nk = (k0 >= kvb) + (k1 >= kvb) + (k2 >= kvb) + (k3 >= kvb);  // 1, 2 or 3
+  const bool one = nk == 1, two = nk == 2;
+  // denominators: nk = 1: d01 d02 d03; nk = 2: d02 d03 d12 d13; nk = 3: d03 d13 d23
+  const double X = (one ? p0 : (two ? p0 : p1)) - (one ? p1 : (two ? p2 : p3));  // d01 | d02 | d13
+  const double Y = (one ? p0 : (two ? p1 : p2)) - (one ? p2 : (two ? p2 : p3));  // d02 | d12 | d23
+  const double Z = (two ? p1 : 1.0) - (two ? p3 : 0.0);                          // 1   | d13 | 1
+  const double d03 = p0 - p3;
+  const double YZ = Y * Z;
+  const double R = vt / ((d03 * X) * YZ);
+  // nk = 2: a = d01, e = d12 (= Y), f = d13 (= Z); vk = vt / (d02 d03) = R e f
+  const double a = p0 - p1;
+  const double vk = R * YZ;
+  const double A = two ? vk * (a * a) : (one ? 0.0 : vt);
+  const double B = two ? 3.0 * (vk * a) : 0.0;
+  const double C = two ? 3.0 * vk : 0.0;
+  const double D = two ? -R * (a + (Y + Z)) : R;
+  const double dl = (one ? p0 : (two ? p1 : p3)) - cm;
+  q0 += fma(fma(fma(D, dl, C), dl, B), dl, A);
+  const double D3 = 3.0 * D;
+  q1 -= fma(fma(D3, dl, 2.0 * C), dl, B);
+  q2 += fma(D3, dl, C);
+  q3 -= D;
 }
 
 template <int G>
@@ -762,21 +801,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
       for (int k = lane; k < n; k += G) {
         const int t = actl[k];
         const uint32_t pk = tpk[t];
-        const TetRow r = tet_prepare(p_apex, dvert[pk & 255], dvert[(pk >> 8) & 255], dvert[(pk >> 16) & 255],
-                                     __ldg(M.tet_vol + t0 + t));
-        // the piece on (va, vb]: its wet corners are those at or above vb
-        const int nk = (okey(r.s0) >= kvb) + (okey(r.s1) >= kvb) + (okey(r.s2) >= kvb) + (okey(r.s3) >= kvb);
-        const double ref = nk == 1 ? r.s0 : (nk == 2 ? r.s1 : r.s3);
-        const double A = nk == 2 ? r.a2 : (nk >= 3 ? r.v : 0.0);
-        const double B = nk == 2 ? r.b2 : 0.0;
-        const double C = nk == 2 ? r.c2 : 0.0;
-        const double D = nk == 1 ? r.d1 : (nk == 2 ? r.d2 : (nk == 3 ? r.d3 : 0.0));
-        // A + B x + C x^2 + D x^3 with x = (ref - cm) - y, expanded in y
-        const double dl = ref - cm;
-        q0 += fma(fma(fma(D, dl, C), dl, B), dl, A);
-        q1 -= fma(fma(3.0 * D, dl, 2.0 * C), dl, B);
-        q2 += fma(3.0 * D, dl, C);
-        q3 -= D;
+        tet_piece(p_apex, dvert[pk & 255], dvert[(pk >> 8) & 255], dvert[(pk >> 16) & 255], __ldg(M.tet_vol + t0 + t),
+                  kvb, cm, q0, q1, q2, q3);
       }
       P0 = group_sum<G>(q0, mask);
       P1 = group_sum<G>(q1, mask);
@@ -1291,24 +1317,42 @@ __device__ double crossing_t(const MeshView& M, const Workspace& W, const double
 // A face is listed once: by its owner when the owner is a band cell, else by its neighbour.
 constexpr int kLsqLanes = 8;
 
+// A group of kLsqLanes lanes per band cell lists its crossing faces and sorts the cell for the
+// least squares: band_a when it has a crossing face, a boundary face or a singular plain G_P (the
+// full stencil), else band_b (the plain stencil's precomputed inverse). Group-aggregated appends.
 __global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
-  const int lane = threadIdx.x % kLsqLanes;
+  const int lane = threadIdx.x % kLsqLanes, grp = (threadIdx.x & 31) / kLsqLanes;
+  const unsigned gbits = ((1u << kLsqLanes) - 1u) << (grp * kLsqLanes);
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
-  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + threadIdx.x / kLsqLanes; j < nb; j += groups) {
-    const int32_t c = W.band_idx[j];
-    const double aP = alpha[c];
-    for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
-      const int32_t f = M.cell_face[k] & 0x7fffffff;
-      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-      if (nbr < 0) continue;
-      const int32_t q = o == c ? nbr : o;
-      if (!crossing_pair(aP, alpha[q])) continue;
-      if (o == c || W.band_stamp[o] != step) {
-        const unsigned long long slot = atomicAdd((unsigned long long*)&W.counters->n_crossing, 1ull);
-        W.xface_list[slot] = f;
+  // warp-uniform trip count: every lane of a warp runs the same iterations (ballots below)
+  const int64_t first = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + (threadIdx.x & ~31) / kLsqLanes;
+  for (int64_t base = first; base < nb; base += groups) {
+    const int64_t j = base + grp;
+    bool full = false;
+    int32_t c = -1;
+    if (j < nb) {
+      c = W.band_idx[j];
+      const double aP = alpha[c];
+      full = lane == 0 && (M.cell_flags[c] != 0);
+      for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
+        const int32_t f = M.cell_face[k] & 0x7fffffff;
+        const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+        if (nbr < 0) continue;
+        const int32_t q = o == c ? nbr : o;
+        if (!crossing_pair(aP, alpha[q])) continue;
+        full = true;
+        if (o == c || W.band_stamp[o] != step) {
+          const unsigned long long slot = atomicAdd((unsigned long long*)&W.counters->n_crossing, 1ull);
+          W.xface_list[slot] = f;
+        }
       }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, full);
+    if (lane == 0 && c >= 0) {
+      if (bal & gbits) W.band_a[atomicAdd((unsigned long long*)&W.counters->n_band_a, 1ull)] = c;
+      else W.band_b[atomicAdd((unsigned long long*)&W.counters->n_band_b, 1ull)] = c;
     }
   }
 }
@@ -1345,48 +1389,65 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
 }
 
 // ---- interface-modified least squares (R7) on band cells -----------------------------------------
-// A thread per band cell over its faces: a crossing face contributes its crossing point x_f
-// (computed first) with T_sat, and every face runs the same FP64 instructions (the point and the
-// value are selected, the crossing test is on alpha's bits). One cell per lane keeps every lane of
-// the FP64 warp instructions busy, the per-cell inverse included (an FP64 warp instruction costs
-// the same with one active lane as with 32); no block barrier.
+// A thread per band cell over its faces (one cell per lane keeps every lane of the FP64 warp
+// instructions busy; an FP64 warp instruction costs the same with one active lane as with 32; no
+// block barrier). The crossing faces' list (k_xmark) sorted the band: cells in band_a have a
+// crossing face (it contributes its crossing point x_f with T_sat; point and value are selected,
+// the crossing test is on alpha's bits), a boundary face or a singular plain G_P, and form and
+// invert G_P; cells in band_b have none of these, so their G_P is the plain stencil's, inverted once
+// per mesh, and only b_P is summed. The threads take band_a first, then band_b.
 __device__ void lsq_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
   const uint32_t step = W.counters->step;
-  const int64_t nb = W.counters->n_band;
+  const int64_t na = W.counters->n_band_a, nb = na + W.counters->n_band_b;
   int nsing = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = W.band_idx[j];
+    const bool full = j < na;
+    const int32_t c = full ? W.band_a[j] : W.band_b[j - na];
     const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
     const double TP = a.T[c], aP = a.alpha[c];
-    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
-    for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
-      const int32_t f = M.cell_face[k] & 0x7fffffff;
-      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-      const int32_t q = o == c ? nbr : o;
-      if (q < 0 && !a.T_bnd) continue;
-      const bool cross = q >= 0 && crossing_pair(aP, a.alpha[q]);
-      const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
-      const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
-      const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
-      const double dT = Tq - TP;
-      g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
-      g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
-      b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
-    }
-    // explicit symmetric inverse (cofactors / det), Appendix B
-    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-    const double det = g00 * c00 + g01 * c01 + g02 * c02;
-    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
     int st = 0;
     Vec3 g = v3(0, 0, 0);
-    if (det > 1e-12 * tr * tr * tr) {
-      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-      const double id = 1.0 / det;
-      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
-             (c02 * b0 + c12 * b1 + c22 * b2) * id);
+    if (full) {
+      double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+      for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
+        const int32_t f = M.cell_face[k] & 0x7fffffff;
+        const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+        const int32_t q = o == c ? nbr : o;
+        if (q < 0 && !a.T_bnd) continue;
+        const bool cross = q >= 0 && crossing_pair(aP, a.alpha[q]);
+        const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
+        const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
+        const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
+        const double dT = Tq - TP;
+        g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
+        g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
+        b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+      }
+      // explicit symmetric inverse (cofactors / det), Appendix B
+      const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+      const double det = g00 * c00 + g01 * c01 + g02 * c02;
+      const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
+      if (det > 1e-12 * tr * tr * tr) {
+        const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+        const double id = 1.0 / det;
+        g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+               (c02 * b0 + c12 * b1 + c22 * b2) * id);
+      } else {
+        st = VOF_ST_SINGULAR_LSQ;
+        ++nsing;
+      }
     } else {
-      st = VOF_ST_SINGULAR_LSQ;
-      ++nsing;
+      double b0 = 0, b1 = 0, b2 = 0;
+      for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
+        const int32_t f = M.cell_face[k] & 0x7fffffff;
+        const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
+        const Vec3 r = v3(M.cell_cen[3 * q], M.cell_cen[3 * q + 1], M.cell_cen[3 * q + 2]) - xP;
+        const double dT = a.T[q] - TP;
+        b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+      }
+      const double* gi = M.lsq_ginv + 6 * c;
+      g = v3(fma(gi[0], b0, fma(gi[1], b1, gi[2] * b2)), fma(gi[1], b0, fma(gi[3], b1, gi[4] * b2)),
+             fma(gi[2], b0, fma(gi[4], b1, gi[5] * b2)));
     }
     W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
     if (W.iface_stamp[c] == step) W.status[c] |= st;
