@@ -326,7 +326,7 @@ vof_status vof_mesh_bins(const vof_mesh* mesh, int64_t* cells5);
 /* ---- learned isovalue guess (the learned part of the path; the paper fixes no such model) ----
  * A 40 -> 64 -> 64 -> 64 -> 1 GELU MLP predicting the normalised isovalue position
  * t = (c - phi_min)/(phi_max - phi_min) of an interface cell. BF16 operands with FP32
- * accumulation (forward on the tensor cores), FP32 master weights and Adam.
+ * accumulation (forward and backward on the tensor cores), FP32 master weights and Adam.
  * Parameters (float32, row-major): W1[64][40], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
  * w4[64], b4. Features (float32 [n][40]): alpha; faces/32; the vertex values normalised to [0,1]
  * over the cell's range, sorted descending, padded to 32 with the smallest; bounding-box extents

@@ -1,8 +1,8 @@
 // Learned isovalue guess: a 40 -> 64 -> 64 -> 64 -> 1 GELU MLP that predicts the normalised
 // isovalue position t = (c - phi_min)/(phi_max - phi_min) of an interface cell from its volume
 // fraction, face count, sorted normalised vertex values and shape. BF16 operands, FP32
-// accumulation: the forward pass runs on the tensor cores (mma.sync m16n8k16 bf16), the backward
-// pass on the CUDA cores in FP32 over the BF16-rounded forward operands; FP32 master weights, Adam.
+// accumulation: the forward and backward passes run on the tensor cores (mma.sync m16n8k16 bf16;
+// the backward products take dZ rounded to BF16); FP32 master weights, Adam.
 //
 // Parameter vector (float32), row-major: W1 [64][40], b1 [64], W2 [64][64], b2 [64], W3 [64][64],
 // b3 [64], w4 [64], b4 [1]  (VOF_MLP_N_PARAMS = 11009).
@@ -414,108 +414,206 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w,
   }
 }
 
-// ---- training: forward (tensor cores) + backward (FP32) for one tile, gradient partials --------
+// ---- training: forward and backward on the tensor cores, gradient partials per CTA ---------------
+// A CTA takes tiles of kRows samples (tiles b, b + gridDim, ...). Forward: warp_forward (four warps,
+// 16 rows each) keeps the pre-activations Z (FP32) and the BF16 hidden layers. Backward, layer by
+// layer (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+//   dZ3 = dy w4 gelu'(Z3);   dW3 += dZ3^T H2;   dH2 = dZ3 W3;   dZ2 = dH2 gelu'(Z2);
+//   dW2 += dZ2^T H1;         dH1 = dZ2 W2;      dZ1 = dH1 gelu'(Z1);   dW1 += dZ1^T X.
+// dZ is rounded to BF16 for the products (kept in [row][unit] and transposed layouts); the bias
+// gradients sum the FP32 dZ. Each warp keeps its 16 x 32 (dW1: 16 x 24) block of every weight
+// gradient in its accumulator registers across the CTA's tiles, and threads 0..64 keep the bias,
+// w4 and b4 sums, so a CTA writes one gradient partial, summed in tile order (deterministic).
+constexpr int LDR = kRows + 8;  // bf16 stride of the transposed tiles [unit][row]
+
 struct TrainSmem {
   Smem f;
-  float Z1[kRows * kH], Z2[kRows * kH], Z3[kRows * kH], H3[kRows * kH];
-  float dA[kRows * kH], dB[kRows * kH];
+  __nv_bfloat16 W2T[kH * LDH], W3T[kH * LDH];  // transposed weights [in][out]
+  float Z1[kRows * kH], Z2[kRows * kH], Z3[kRows * kH];  // pre-activations, then that layer's FP32 dZ
+  float H3[kRows * kH];
+  __nv_bfloat16 dZ[kRows * LDH];   // the current layer's dZ [row][unit], BF16
+  __nv_bfloat16 dZT[kH * LDR];     // its transpose [unit][row]
+  __nv_bfloat16 AT[kH * LDR];      // the layer's input transposed [in][row] (H2, H1 or X)
   float dy[kRows];
 };
 
-// partial gradient of tile `blockIdx.x` (scaled by 1/batch) into part[tile][kNP]
-__global__ void __launch_bounds__(256) k_mlp_train_tile(WeightsBF16* w, const float* X, const float* t, int64_t n,
-                                                       float inv_batch, float* part, float* loss_part) {
+// acc[j] += A[m0 .. m0 + 16)[0 .. K) * B[n0 + 8 j .. n0 + 8 j + 8)[0 .. K)^T for j < NT; A and B
+// row-major BF16 with strides LDA and LDB (the fragment layouts of warp_gemm)
+template <int K, int NT, int LDA, int LDB>
+__device__ __forceinline__ void warp_mma(const __nv_bfloat16* A, const __nv_bfloat16* B, int m0, int n0,
+                                         float (&acc)[NT][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t*>(A + (m0 + g) * LDA + k0 + 2 * q);
+    a[1] = *reinterpret_cast<const uint32_t*>(A + (m0 + g + 8) * LDA + k0 + 2 * q);
+    a[2] = *reinterpret_cast<const uint32_t*>(A + (m0 + g) * LDA + k0 + 8 + 2 * q);
+    a[3] = *reinterpret_cast<const uint32_t*>(A + (m0 + g + 8) * LDA + k0 + 8 + 2 * q);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const __nv_bfloat16* w = B + (n0 + 8 * j + g) * LDB + k0 + 2 * q;
+      mma16816(acc[j], a, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+  }
+}
+
+// dZ of a hidden layer from this warp's block of dH (rows m0.., units n0..n0 + 32): the FP32 value
+// into Zf (in place of the pre-activation), BF16 copies into dZ [row][unit] and dZT [unit][row]
+__device__ __forceinline__ void store_dz(const float (&dh)[4][4], float* Zf, __nv_bfloat16* dZ, __nv_bfloat16* dZT,
+                                         int m0, int n0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = n0 + 8 * j + 2 * q + (i & 1);
+      const float d = dh[j][i] * gelu_grad(Zf[r * kH + c]);
+      Zf[r * kH + c] = d;
+      const __nv_bfloat16 b = __float2bfloat16_rn(d);
+      dZ[r * LDH + c] = b;
+      dZT[c * LDR + r] = b;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mlp_train(WeightsBF16* w, const float* X, const float* t, int64_t n,
+                                                  float inv_batch, float* part, float* loss_part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
-  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+  const int warp = threadIdx.x >> 5, tid = threadIdx.x;
+  const int64_t ntiles = (n + kRows - 1) / kRows;
   stage_weights(s.f, *w);
-  load_x(s.f, X, row0, n);
   cp_async_wait();
   __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  if (warp < kWarps) warp_forward(s.f, warp * 16, s.Z1, s.Z2, s.Z3, s.H3);
-  __syncthreads();
+  for (int i = tid; i < kH * kH; i += blockDim.x) {  // transposed weights, once per CTA
+    const int o = i / kH, k = i % kH;
+    s.W2T[k * LDH + o] = s.f.W2[o * LDH + k];
+    s.W3T[k * LDH + o] = s.f.W3[o * LDH + k];
+  }
+  // this warp's blocks of the weight gradients (rows = units m0.., columns = inputs n0.. / n1..)
+  const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 32, n1 = (warp & 1) * 24;
+  float g3[4][4], g2[4][4], g1[3][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g3[j][i] = g2[j][i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g1[j][i] = 0.f;
+  // thread u < kH: sums of unit u's bias gradients (layers 3, 2, 1) and of w4[u]; thread kH: b4;
+  // thread 0: the loss
+  float sb3 = 0.f, sb2 = 0.f, sb1 = 0.f, sw4 = 0.f, sb4 = 0.f, sloss = 0.f;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kRows;
+    load_x(s.f, X, row0, n);
+    __syncthreads();
+    if (warp < kWarps) warp_forward(s.f, warp * 16, s.Z1, s.Z2, s.Z3, s.H3);
+    __syncthreads();
+    if (tid < kRows) {
+      const int64_t gr = row0 + tid;
+      const float r = gr < n ? s.f.y[tid] - t[gr] : 0.f;  // padded rows carry no gradient
+      s.dy[tid] = 2.f * r * inv_batch;
+      s.f.y[tid] = r * r;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float l = 0.f;
+      for (int r = 0; r < kRows; ++r) l += s.f.y[r];
+      sloss += l;
+    }
+    if (tid < kH) {
+      float a = 0.f;
+      for (int r = 0; r < kRows; ++r) a = fmaf(s.H3[r * kH + tid], s.dy[r], a);
+      sw4 += a;
+    } else if (tid == kH) {
+      float a = 0.f;
+      for (int r = 0; r < kRows; ++r) a += s.dy[r];
+      sb4 += a;
+    }
+    // dZ3 = dy w4 gelu'(Z3); the input of layer 3 (H2) transposed
+    for (int i = tid; i < kRows * kH; i += blockDim.x) {
+      const int r = i / kH, c = i % kH;
+      const float d = s.dy[r] * s.f.w4[c] * gelu_grad(s.Z3[i]);
+      s.Z3[i] = d;
+      const __nv_bfloat16 b = __float2bfloat16_rn(d);
+      s.dZ[r * LDH + c] = b;
+      s.dZT[c * LDR + r] = b;
+      s.AT[c * LDR + r] = s.f.H2[r * LDH + c];
+    }
+    __syncthreads();
+    if (tid < kH) {
+      float a = 0.f;
+      for (int r = 0; r < kRows; ++r) a += s.Z3[r * kH + tid];
+      sb3 += a;
+    }
+    warp_mma<kRows, 4, LDR, LDR>(s.dZT, s.AT, m0, n0, g3);  // dW3 += dZ3^T H2
+    float dh[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dh[j][i] = 0.f;
+    warp_mma<kH, 4, LDH, LDH>(s.dZ, s.W3T, m0, n0, dh);  // dH2 = dZ3 W3 (rows m0.., inputs n0..)
+    __syncthreads();
+    store_dz(dh, s.Z2, s.dZ, s.dZT, m0, n0);  // dZ2 = dH2 gelu'(Z2)
+    for (int i = tid; i < kRows * kH; i += blockDim.x) {
+      const int r = i / kH, c = i % kH;
+      s.AT[c * LDR + r] = s.f.H1[r * LDH + c];
+    }
+    __syncthreads();
+    if (tid < kH) {
+      float a = 0.f;
+      for (int r = 0; r < kRows; ++r) a += s.Z2[r * kH + tid];
+      sb2 += a;
+    }
+    warp_mma<kRows, 4, LDR, LDR>(s.dZT, s.AT, m0, n0, g2);  // dW2 += dZ2^T H1
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dh[j][i] = 0.f;
+    warp_mma<kH, 4, LDH, LDH>(s.dZ, s.W2T, m0, n0, dh);  // dH1 = dZ2 W2
+    __syncthreads();
+    store_dz(dh, s.Z1, s.dZ, s.dZT, m0, n0);  // dZ1 = dH1 gelu'(Z1)
+    for (int i = tid; i < kRows * kInPad; i += blockDim.x) {
+      const int r = i / kInPad, c = i % kInPad;
+      s.AT[c * LDR + r] = s.f.X[r * LDX + c];
+    }
+    __syncthreads();
+    if (tid < kH) {
+      float a = 0.f;
+      for (int r = 0; r < kRows; ++r) a += s.Z1[r * kH + tid];
+      sb1 += a;
+    }
+    warp_mma<kRows, 3, LDR, LDR>(s.dZT, s.AT, m0, n1, g1);  // dW1 += dZ1^T X (inputs padded to 48)
+    __syncthreads();  // the next tile overwrites the tiles read above
+  }
+  // this CTA's partial
   float* P = part + (size_t)blockIdx.x * kNP;
-  // output layer
-  if (threadIdx.x < kRows) {
-    const int64_t gr = row0 + threadIdx.x;
-    const float r = gr < n ? s.f.y[threadIdx.x] - t[gr] : 0.f;
-    s.dy[threadIdx.x] = 2.f * r * inv_batch;
-    s.f.y[threadIdx.x] = r * r;
+  const int lane = tid & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = n0 + 8 * j + 2 * q + (i & 1);
+      P[oW3 + r * kH + c] = g3[j][i];
+      P[oW2 + r * kH + c] = g2[j][i];
+    }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + g + (i >= 2 ? 8 : 0), c = n1 + 8 * j + 2 * q + (i & 1);
+      if (c < kIn) P[oW1 + r * kIn + c] = g1[j][i];
+    }
+  if (tid < kH) {
+    P[ob3 + tid] = sb3;
+    P[ob2 + tid] = sb2;
+    P[ob1 + tid] = sb1;
+    P[ow4 + tid] = sw4;
+  } else if (tid == kH) {
+    P[ob4] = sb4;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float l = 0;
-    for (int r = 0; r < kRows; ++r) l += s.f.y[r];
-    loss_part[blockIdx.x] = l;
-  }
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
-    float gw = 0;
-    for (int r = 0; r < kRows; ++r) gw = fmaf(s.H3[r * kH + c], s.dy[r], gw);
-    P[ow4 + c] = gw;
-  }
-  if (threadIdx.x == 0) {
-    float gb = 0;
-    for (int r = 0; r < kRows; ++r) gb += s.dy[r];
-    P[ob4] = gb;
-  }
-  // dZ3 = dy w4 gelu'(Z3)  -> dA
-  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
-    const int r = i / kH, c = i % kH;
-    s.dA[i] = s.dy[r] * s.f.w4[c] * gelu_grad(s.Z3[i]);
-  }
-  __syncthreads();
-  // layer 3 weights: dW3[n][k] = sum_r dZ3[r][n] H2[r][k]; db3
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    const int nn = i / kH, k = i % kH;
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.H2[r * LDH + k]), acc);
-    P[oW3 + i] = acc;
-  }
-  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc += s.dA[r * kH + nn];
-    P[ob3 + nn] = acc;
-  }
-  // dZ2 = (dZ3 W3) gelu'(Z2) -> dB
-  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
-    const int r = i / kH, k = i % kH;
-    float acc = 0;
-    for (int nn = 0; nn < kH; ++nn) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.W3[nn * LDH + k]), acc);
-    s.dB[i] = acc * gelu_grad(s.Z2[i]);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    const int nn = i / kH, k = i % kH;
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dB[r * kH + nn], __bfloat162float(s.f.H1[r * LDH + k]), acc);
-    P[oW2 + i] = acc;
-  }
-  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc += s.dB[r * kH + nn];
-    P[ob2 + nn] = acc;
-  }
-  __syncthreads();
-  // dZ1 = (dZ2 W2) gelu'(Z1) -> dA
-  for (int i = threadIdx.x; i < kRows * kH; i += blockDim.x) {
-    const int r = i / kH, k = i % kH;
-    float acc = 0;
-    for (int nn = 0; nn < kH; ++nn) acc = fmaf(s.dB[r * kH + nn], __bfloat162float(s.f.W2[nn * LDH + k]), acc);
-    s.dA[i] = acc * gelu_grad(s.Z1[i]);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
-    const int nn = i / kIn, k = i % kIn;
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc = fmaf(s.dA[r * kH + nn], __bfloat162float(s.f.X[r * LDX + k]), acc);
-    P[oW1 + i] = acc;
-  }
-  for (int nn = threadIdx.x; nn < kH; nn += blockDim.x) {
-    float acc = 0;
-    for (int r = 0; r < kRows; ++r) acc += s.dA[r * kH + nn];
-    P[ob1 + nn] = acc;
-  }
+  if (tid == 0) loss_part[blockIdx.x] = sloss;
 }
 
 // BF16 copy of parameter p (index into the vector) written into the kernel layout.
@@ -663,15 +761,23 @@ static vof_status train_impl(vof_mlp* m, const float* d_X, const float* d_t, int
                              float* d_loss, cudaStream_t s) {
   if (!m || !d_X || !d_t || n < 1 || n > kMaxBatch || !(lr >= 0)) { set_error("bad argument"); return VOF_EINVAL; }
   const int ntiles = (int)((n + kRows - 1) / kRows);
-  cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(TrainSmem));
-  k_mlp_train_tile<<<ntiles, 256, sizeof(TrainSmem), s>>>(m->w, d_X, d_t, n, 1.0f / (float)n, m->part, m->loss_part);
+  static int train_grid = 0;  // a CTA per SM at most (one partial each)
+  if (!train_grid) {
+    cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(TrainSmem));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&train_grid, cudaDevAttrMultiProcessorCount, dev);
+    if (train_grid < 1) train_grid = 1;
+  }
+  const int nparts = std::min(ntiles, train_grid);
+  k_mlp_train<<<nparts, 256, sizeof(TrainSmem), s>>>(m->w, d_X, d_t, n, 1.0f / (float)n, m->part, m->loss_part);
   float b1t = 1, b2t = 1;
   if (lr > 0) {
     m->adam_t += 1;
     b1t = (float)std::pow(0.9, (double)m->adam_t);
     b2t = (float)std::pow(0.999, (double)m->adam_t);
   }
-  k_mlp_reduce_adam<<<(kNP + 255) / 256, 256, 0, s>>>(m->part, ntiles, m->loss_part, m->params, m->m1, m->m2, m->w, lr,
+  k_mlp_reduce_adam<<<(kNP + 255) / 256, 256, 0, s>>>(m->part, nparts, m->loss_part, m->params, m->m1, m->m2, m->w, lr,
                                                       b1t, b2t, n, d_grad, d_loss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "mlp training kernels");
