@@ -27,7 +27,6 @@ struct Counters {
   uint32_t step;        // incremented on the device every step (membership stamps)
   uint32_t reduce_done; // blocks finished in the totals reduction
   int64_t n_iface, n_band, n_crossing;
-  int64_t n_band_a, n_band_b;  // band cells with a crossing or boundary face (full least squares) / without
   int64_t n_uvert;  // distinct vertices of interface cells (vertex field values computed)
   int64_t n_degenerate, n_not_converged, n_fallback, n_singular, n_no_side, n_mlp_skipped;
   int64_t evals_total;
@@ -64,8 +63,6 @@ struct MeshView {
   const double* face_area;   // [n][3] outward from owner
   const double* face_cen;    // [n][3]
   const double* face_len;    // [n] |x_neigh - x_owner| (0 on boundary faces)
-  const double* lsq_ginv;    // [n_cells][6] inverse of G_P of the plain face stencil (g00 g01 g02 g11 g12 g22)
-  const uint8_t* cell_flags; // [n_cells] bit 0: a boundary face; bit 1: the plain stencil's G_P is singular
   const double* face_iarea;  // [n] 1 / |face_area|
 };
 
@@ -80,8 +77,6 @@ struct Workspace {
   uint32_t* sel_mask;      // [n_sel_blocks][kSelTile / 32] interface flags of the selection tiles
   int64_t* sel_tot;        // [kMaxSelGrid] interface cells per selection block
   int32_t* band_idx;       // [n_cells] band cells (unordered)
-  int32_t* band_a;         // [n_cells] band cells with a crossing or boundary face, or a singular plain G_P
-  int32_t* band_b;         // [n_cells] the other band cells (plain stencil: the precomputed inverse)
   double* phi_v;           // [n_verts]
   float2* phi_ff;          // [n_verts] phi_v as a (hi, lo) float pair
   double* iso;             // [n_cells]

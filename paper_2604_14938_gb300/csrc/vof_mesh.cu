@@ -134,40 +134,6 @@ __global__ void k_face_static(int64_t nf, const int32_t* own, const int32_t* nei
   iarea[f] = 1.0 / sqrt(ax * ax + ay * ay + az * az);
 }
 
-// Appendix B's least squares without an interface: G_P = sum r r^T over the face neighbours (and
-// the boundary faces' virtual neighbours at the face centroid), inverted once per mesh by the
-// explicit symmetric inverse; flags: a boundary face (bit 0), det G <= 1e-12 (tr G / 3)^3 (bit 1).
-__global__ void k_lsq_static(int64_t nc, const int64_t* cfo, const int32_t* cf, const int32_t* own, const int32_t* nei,
-                             const double* cen, const double* fcen, double* ginv, uint8_t* flags) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  const double xP = cen[3 * c], yP = cen[3 * c + 1], zP = cen[3 * c + 2];
-  double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
-  uint8_t fl = 0;
-  for (int64_t k = cfo[c]; k < cfo[c + 1]; ++k) {
-    const int32_t f = cf[k] & 0x7fffffff;
-    const int32_t q = own[f] == c ? nei[f] : own[f];
-    const double* xs = q >= 0 ? cen + 3 * q : fcen + 3 * f;
-    if (q < 0) fl |= 1;
-    const double rx = xs[0] - xP, ry = xs[1] - yP, rz = xs[2] - zP;
-    g00 = fma(rx, rx, g00); g01 = fma(rx, ry, g01); g02 = fma(rx, rz, g02);
-    g11 = fma(ry, ry, g11); g12 = fma(ry, rz, g12); g22 = fma(rz, rz, g22);
-  }
-  const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-  const double det = g00 * c00 + g01 * c01 + g02 * c02;
-  const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
-  double* gi = ginv + 6 * c;
-  if (det > 1e-12 * tr * tr * tr) {
-    const double id = 1.0 / det;
-    gi[0] = c00 * id; gi[1] = c01 * id; gi[2] = c02 * id;
-    gi[3] = (g00 * g22 - g02 * g02) * id; gi[4] = (g02 * g01 - g00 * g12) * id; gi[5] = (g00 * g11 - g01 * g01) * id;
-  } else {
-    fl |= 2;
-    for (int q = 0; q < 6; ++q) gi[q] = 0.0;
-  }
-  flags[c] = fl;
-}
-
 __global__ void k_idw(int64_t nv, const int64_t* vco, const int32_t* vc, const double* vx, const double* vy,
                       const double* vz, const double* cen, double* w) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -382,12 +348,9 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &d_fa, 3 * nf));
   TRY(dev_alloc(m, &d_fc, 3 * nf));
   TRY(dev_alloc(m, &d_w, vc.size()));
-  double *d_flen, *d_fia, *d_ginv;
-  uint8_t* d_cflag;
+  double *d_flen, *d_fia;
   TRY(dev_alloc(m, &d_flen, nf));
   TRY(dev_alloc(m, &d_fia, nf));
-  TRY(dev_alloc(m, &d_ginv, 6 * (size_t)nc));
-  TRY(dev_alloc(m, &d_cflag, nc));
   TRY(dev_alloc(m, &d_bad, 1));
   cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
   k_face_geom<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_fvo, d_fv, d_vx, d_vy, d_vz, d_fa, d_fc);
@@ -396,7 +359,6 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   k_rel_pos<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cvo, d_cv, d_vx, d_vy, d_vz, d_rel);
   k_idw<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, d_vco, d_vc, d_vx, d_vy, d_vz, d_cen, d_w);
   k_face_static<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(nf, d_own, d_nei, d_cen, d_fa, d_flen, d_fia);
-  k_lsq_static<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, d_cfo, d_cf, d_own, d_nei, d_cen, d_fc, d_ginv, d_cflag);
   int32_t h_bad = 0;
   cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
@@ -409,7 +371,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   V.rel_pos = d_rel;
   V.vert_cell_off = d_vco; V.vert_cell = d_vc; V.vert_w = d_w;
   V.cell_vol = d_vol; V.cell_ivol = d_ivol; V.cell_cen = d_cen; V.face_area = d_fa; V.face_cen = d_fc;
-  V.face_len = d_flen; V.face_iarea = d_fia; V.lsq_ginv = d_ginv; V.cell_flags = d_cflag;
+  V.face_len = d_flen; V.face_iarea = d_fia;
   // ---- workspace
   Workspace& W = m->ws;
   m->n_sel_blocks = (int)((nc + kSelTile - 1) / kSelTile);
@@ -423,8 +385,6 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.sel_tot, kMaxSelGrid));
   TRY(dev_alloc(m, &W.tile_part, 2 * (size_t)((nc + kSrcTile - 1) / kSrcTile)));
   TRY(dev_alloc(m, &W.band_idx, nc));
-  TRY(dev_alloc(m, &W.band_a, nc));
-  TRY(dev_alloc(m, &W.band_b, nc));
   TRY(dev_alloc(m, &W.phi_v, nv));
   TRY(dev_alloc(m, &W.phi_ff, nv));
   TRY(dev_alloc(m, &W.iso, nc));

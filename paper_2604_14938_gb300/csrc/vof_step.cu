@@ -31,6 +31,9 @@ __device__ __forceinline__ uint64_t mag(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }  // x > 0
+__device__ __forceinline__ double flip_if(double x, bool f) {  // -x when f, by the sign bit
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
+}
 __device__ __forceinline__ bool inside(double x, double L, double H) {  // L < x < H
   const uint64_t k = okey(x);
   return k > okey(L) && k < okey(H);
@@ -85,7 +88,6 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
   cn->step += 1;
   cn->reduce_done = 0;
   cn->n_iface = cn->n_band = cn->n_crossing = cn->n_uvert = 0;
-  cn->n_band_a = cn->n_band_b = 0;
   cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
   cn->evals_total = 0;
   cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
@@ -523,10 +525,6 @@ struct ff {
   float hi, lo;
 };
 __device__ __forceinline__ ff ff_make(float2 v) { return {v.x, v.y}; }
-__device__ __forceinline__ ff ff_of(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
 // FP32 -> FP64 by the bits (exact; zero, normal and infinite/NaN values), so that the widening
 // stays off the FP64 unit; subnormals take the conversion instruction
 __device__ __forceinline__ double fl2d(float f) {
@@ -541,6 +539,23 @@ __device__ __forceinline__ double fl2d(float f) {
   return __longlong_as_double((long long)(sgn | (de << 52) | ((uint64_t)mant << 29)));
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return fl2d(a.hi) + fl2d(a.lo); }
+// FP64 -> FP32, round to nearest even, by the bits (the conversion instruction runs on the FP64
+// unit); a value whose float is not normal (zero, subnormal, overflow, infinite, NaN) takes the
+// conversion instruction. A carry out of the mantissa moves to the next binade, as rounding does.
+__device__ __forceinline__ float d2f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e < 1 || e > 254) return __double2float_rn(x);
+  const uint64_t m = b & 0xfffffffffffffull;
+  uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & 0x1fffffffull), half = 0x10000000u;
+  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(((uint32_t)(b >> 32) & 0x80000000u) | r);
+}
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = d2f(x);
+  return {h, d2f(x - fl2d(h))};
+}
 __device__ __forceinline__ ff ff_norm(float s, float e) {  // |s| >= |e|
   const float h = __fadd_rn(s, e);
   return {h, __fsub_rn(e, __fsub_rn(h, s))};
@@ -819,13 +834,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
     int64_t tev = 0;  // tetrahedron evaluations
     double c_best;
     uint64_t kbest = 0;  // |f| at c_best, as a magnitude key
-    if (hi - lo < 1e-14) {
+    // scalar comparisons on order keys and conversions by the bits: an FP64 compare or conversion
+    // holds the FP64 unit like an FMA, for every lane group of the warp
+    const double range = hi - lo;
+    if (__double_as_longlong(range) < __double_as_longlong(1e-14)) {  // range >= 0
       status = VOF_ST_DEGENERATE;
       c_best = lo;
     } else {
       // f(lo) = 1 - alpha (everything wet), f(hi) = -alpha
-      kbest = mag(fmin(1.0 - a, a));
-      c_best = (1.0 - a) <= a ? lo : hi;
+      const double oma = 1.0 - a;
+      kbest = min(mag(oma), mag(a));
+      c_best = okey(oma) <= okey(a) ? lo : hi;
       double L = lo, H = hi;
       bool done = false;
       // f = V_L(c)/V - alpha at a point: best point and bracket updated, convergence test
@@ -870,25 +889,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         // bisection inside the bracket found so far as the counted fallback. The interval-cubic
         // mode runs the same FP32 refinement (from the MLP guess when the mesh has an MLP, else
         // from 1 - alpha) and replaces the FP64 phase.
-        float u0 = use_mlp ? W.mlp_out[i] : 1.0f - (float)a;
+        float u0 = use_mlp ? W.mlp_out[i] : 1.0f - d2f(a);
         if (!(u0 >= 0.0f)) {
           status |= VOF_ST_MLP_SKIPPED;
-          u0 = 1.0f - (float)a;
+          u0 = 1.0f - d2f(a);
         }
-        const double range = hi - lo;
         // Local FP32 coordinate u in [-1, 0] with the minority phase next to u = 0: for
         // alpha <= 1/2, u = (phi - phi_max)/range and the wet volume is matched to t = alpha; for
         // alpha > 1/2, u = (phi_min - phi)/range (the field reflected) and the wet volume of the
         // reflected field, the original dry volume, is matched to t = 1 - alpha. A small volume
         // fraction and a root next to an extreme vertex value then keep their relative precision.
-        const bool refl = a > 0.5;
-        const double org = refl ? lo : hi, dir = refl ? -1.0 : 1.0;
-        const float af = (float)(refl ? 1.0 - a : a);
+        const bool refl = okey(a) > kKeyHalf;  // alpha > 1/2
+        const double org = refl ? lo : hi;
+        const float af = d2f(refl ? oma : a);
         float ubest, slope;
         {
           TetRow32* rows32 = reinterpret_cast<TetRow32*>(rows);
           // u from the vertex values' float pairs (FP32 work only): (phi - org) * dir / range
-          const float r32 = __frcp_rn((float)range);
+          const float r32 = __frcp_rn(d2f(range));
           const float su = refl ? -r32 : r32;
           const ff of = ff_of(org);
           for (int j = lane; j < nv; j += G) {
@@ -949,7 +967,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         // fallback); if no interval brackets the target, in bisection over [phi_min, phi_max]
         // with every tetrahedron evaluated directly.
         __syncwarp(mask);
-        double c1 = dmin(dmax(fma(dir * (double)ubest, range, org), lo), hi);
+        double c1 = dmin(dmax(fma(flip_if(fl2d(ubest), refl), range, org), lo), hi);
         if (!(okey(c1) < okey(hi))) c1 = okey_inv(okey(hi) - 1);  // an interval above c1 exists
         // largest vertex value <= c and smallest above it, by integer keys
         auto vertex_interval = [&](double c, double& va, double& vb) {
@@ -972,9 +990,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
           const double ya = va - cm, yb = vb - cm;
           const double ga = fma(fma(fma(P3, ya, P2), ya, P1), ya, P0) - tgt;
           const double gb = fma(fma(fma(P3, yb, P2), yb, P1), yb, P0) - tgt;
-          if (gb > 0.0 && okey(vb) < okey(hi)) {  // the root lies above vb
+          if (positive(gb) && okey(vb) < okey(hi)) {  // the root lies above vb
             vertex_interval(vb, va, vb);
-          } else if (ga < 0.0 && okey(va) > okey(lo)) {  // below va
+          } else if (okey(ga) < okey(0.0) && okey(va) > okey(lo)) {  // below va
             vertex_interval(okey_inv(okey(va) - 1), va, vb);
           } else {
             bracketed = true;
@@ -996,17 +1014,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
             for (int it = 0; it < 12 && !done; ++it) {
               const double g = fma(fma(fma(P3, y, P2), y, P1), y, P0) - tgt;
               record(cm + y, g * invV);
-              if (g == 0.0 || done) break;
-              if (g > 0.0) ya = y; else yb = y;
+              if (mag(g) == 0ull || done) break;
+              if (positive(g)) ya = y; else yb = y;
               const double dp = fma(fma(3.0 * P3, y, 2.0 * P2), y, P1);  // dg/dy <= 0
               double yn = 0.5 * (ya + yb);
-              if (dp < 0.0) {
-                double r = (double)(1.0f / (float)dp);
+              if (okey(dp) < okey(0.0)) {
+                double r = fl2d(1.0f / d2f(dp));
                 r = fma(r, fma(-dp, r, 1.0), r);
                 const double yt = fma(-g, r, y);
                 if (inside(yt, ya, yb)) yn = yt;
               }
-              if (yn == y || !inside(yn, ya, yb)) break;
+              if (okey(yn) == okey(y) || !inside(yn, ya, yb)) break;
               y = yn;
             }
           } else {
@@ -1014,8 +1032,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
             double f1 = evalP(c1);
             if (!done && opt.max_secant > 0) {
               // second point: one Newton step with the FP32 slope, kept inside the bracket
-              double c0 = fma(-f1, range * (double)(1.0f / slope), c1);
-              if (!inside(c0, L, H) || c0 == c1) {
+              double c0 = fma(-f1, range * fl2d(1.0f / slope), c1);
+              if (!inside(c0, L, H) || __double_as_longlong(c0) == __double_as_longlong(c1)) {
                 const double step = 4e-6 * range;
                 c0 = positive(f1) ? fmin(c1 + step, 0.5 * (c1 + H)) : fmax(c1 - step, 0.5 * (c1 + L));
               }
@@ -1024,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
                 if (__double_as_longlong(f0) == __double_as_longlong(f1)) break;
                 // secant point; the reciprocal of f0 - f1 from an FP32 seed and one FP64 Newton step
                 const double d = f0 - f1;
-                double r = (double)(1.0f / (float)d);
+                double r = fl2d(1.0f / d2f(d));
                 r = fma(r, fma(-d, r, 1.0), r);
                 double c2 = fma(-f0, (c0 - c1) * r, c0);
                 if (!inside(c2, L, H)) c2 = 0.5 * (L + H);
@@ -1317,42 +1335,47 @@ __device__ double crossing_t(const MeshView& M, const Workspace& W, const double
 // A face is listed once: by its owner when the owner is a band cell, else by its neighbour.
 constexpr int kLsqLanes = 8;
 
-// A group of kLsqLanes lanes per band cell lists its crossing faces and sorts the cell for the
-// least squares: band_a when it has a crossing face, a boundary face or a singular plain G_P (the
-// full stencil), else band_b (the plain stencil's precomputed inverse). Group-aggregated appends.
+// A group of kLsqLanes lanes per band cell lists its crossing faces.
 __global__ void k_xmark(MeshView M, const double* alpha, Workspace W) {
   const uint32_t step = W.counters->step;
   const int64_t nb = W.counters->n_band;
   const int lane = threadIdx.x % kLsqLanes, grp = (threadIdx.x & 31) / kLsqLanes;
-  const unsigned gbits = ((1u << kLsqLanes) - 1u) << (grp * kLsqLanes);
+  const int wl = threadIdx.x & 31;
+  const unsigned below = (1u << wl) - 1u;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLsqLanes);
-  // warp-uniform trip count: every lane of a warp runs the same iterations (ballots below)
+  // warp-uniform trip counts (ballots below); appends aggregated per warp, one atomic per pass,
+  // since the list's counter is a single address that every warp of the grid updates
   const int64_t first = blockIdx.x * (int64_t)(blockDim.x / kLsqLanes) + (threadIdx.x & ~31) / kLsqLanes;
   for (int64_t base = first; base < nb; base += groups) {
     const int64_t j = base + grp;
-    bool full = false;
     int32_t c = -1;
+    int64_t f0 = 0, nf = 0;
+    double aP = 0;
     if (j < nb) {
       c = W.band_idx[j];
-      const double aP = alpha[c];
-      full = lane == 0 && (M.cell_flags[c] != 0);
-      for (int64_t k = M.cell_face_off[c] + lane; k < M.cell_face_off[c + 1]; k += kLsqLanes) {
-        const int32_t f = M.cell_face[k] & 0x7fffffff;
+      aP = alpha[c];
+      f0 = M.cell_face_off[c];
+      nf = M.cell_face_off[c + 1] - f0;
+    }
+    const int maxf = __reduce_max_sync(0xffffffffu, (unsigned)nf);
+    for (int s0 = 0; s0 < maxf; s0 += kLsqLanes) {
+      const int k = s0 + lane;
+      bool take = false;
+      int32_t f = 0;
+      if (k < nf) {
+        f = M.cell_face[f0 + k] & 0x7fffffff;
         const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-        if (nbr < 0) continue;
-        const int32_t q = o == c ? nbr : o;
-        if (!crossing_pair(aP, alpha[q])) continue;
-        full = true;
-        if (o == c || W.band_stamp[o] != step) {
-          const unsigned long long slot = atomicAdd((unsigned long long*)&W.counters->n_crossing, 1ull);
-          W.xface_list[slot] = f;
+        if (nbr >= 0) {
+          const int32_t q = o == c ? nbr : o;
+          if (crossing_pair(aP, alpha[q]))
+            take = o == c || W.band_stamp[o] != step;  // listed once: by the owner if it is a band cell
         }
       }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, full);
-    if (lane == 0 && c >= 0) {
-      if (bal & gbits) W.band_a[atomicAdd((unsigned long long*)&W.counters->n_band_a, 1ull)] = c;
-      else W.band_b[atomicAdd((unsigned long long*)&W.counters->n_band_b, 1ull)] = c;
+      const unsigned tb = __ballot_sync(0xffffffffu, take);
+      unsigned long long fb = 0;
+      if (wl == 0 && tb) fb = atomicAdd((unsigned long long*)&W.counters->n_crossing, (unsigned long long)__popc(tb));
+      fb = __shfl_sync(0xffffffffu, fb, 0);
+      if (take) W.xface_list[fb + __popc(tb & below)] = f;
     }
   }
 }
@@ -1389,65 +1412,48 @@ __device__ void xface_phase(const MeshView& M, const double* alpha, int xf_mode,
 }
 
 // ---- interface-modified least squares (R7) on band cells -----------------------------------------
-// A thread per band cell over its faces (one cell per lane keeps every lane of the FP64 warp
-// instructions busy; an FP64 warp instruction costs the same with one active lane as with 32; no
-// block barrier). The crossing faces' list (k_xmark) sorted the band: cells in band_a have a
-// crossing face (it contributes its crossing point x_f with T_sat; point and value are selected,
-// the crossing test is on alpha's bits), a boundary face or a singular plain G_P, and form and
-// invert G_P; cells in band_b have none of these, so their G_P is the plain stencil's, inverted once
-// per mesh, and only b_P is summed. The threads take band_a first, then band_b.
+// A thread per band cell over its faces: a crossing face contributes its crossing point x_f
+// (computed first) with T_sat, and every face runs the same FP64 instructions (the point and the
+// value are selected, the crossing test is on alpha's bits). One cell per lane keeps every lane of
+// the FP64 warp instructions busy, the per-cell inverse included (an FP64 warp instruction costs
+// the same with one active lane as with 32); no block barrier.
 __device__ void lsq_phase(const MeshView& M, const StepArgs& a, Workspace& W) {
   const uint32_t step = W.counters->step;
-  const int64_t na = W.counters->n_band_a, nb = na + W.counters->n_band_b;
+  const int64_t nb = W.counters->n_band;
   int nsing = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
-    const bool full = j < na;
-    const int32_t c = full ? W.band_a[j] : W.band_b[j - na];
+    const int32_t c = W.band_idx[j];
     const Vec3 xP = v3(M.cell_cen[3 * c], M.cell_cen[3 * c + 1], M.cell_cen[3 * c + 2]);
     const double TP = a.T[c], aP = a.alpha[c];
+    double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
+      const int32_t f = M.cell_face[k] & 0x7fffffff;
+      const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
+      const int32_t q = o == c ? nbr : o;
+      if (q < 0 && !a.T_bnd) continue;
+      const bool cross = q >= 0 && crossing_pair(aP, a.alpha[q]);
+      const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
+      const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
+      const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
+      const double dT = Tq - TP;
+      g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
+      g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
+      b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
+    }
+    // explicit symmetric inverse (cofactors / det), Appendix B
+    const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
+    const double det = g00 * c00 + g01 * c01 + g02 * c02;
+    const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
     int st = 0;
     Vec3 g = v3(0, 0, 0);
-    if (full) {
-      double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, b0 = 0, b1 = 0, b2 = 0;
-      for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
-        const int32_t f = M.cell_face[k] & 0x7fffffff;
-        const int32_t o = M.face_owner[f], nbr = M.face_neigh[f];
-        const int32_t q = o == c ? nbr : o;
-        if (q < 0 && !a.T_bnd) continue;
-        const bool cross = q >= 0 && crossing_pair(aP, a.alpha[q]);
-        const double* xs = cross ? W.x_f + 3 * f : (q >= 0 ? M.cell_cen + 3 * q : M.face_cen + 3 * f);
-        const double Tq = cross ? a.props.T_sat : (q >= 0 ? a.T[q] : a.T_bnd[f]);
-        const Vec3 r = v3(xs[0], xs[1], xs[2]) - xP;
-        const double dT = Tq - TP;
-        g00 = fma(r.x, r.x, g00); g01 = fma(r.x, r.y, g01); g02 = fma(r.x, r.z, g02);
-        g11 = fma(r.y, r.y, g11); g12 = fma(r.y, r.z, g12); g22 = fma(r.z, r.z, g22);
-        b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
-      }
-      // explicit symmetric inverse (cofactors / det), Appendix B
-      const double c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-      const double det = g00 * c00 + g01 * c01 + g02 * c02;
-      const double tr = (g00 + g11 + g22) * (1.0 / 3.0);
-      if (det > 1e-12 * tr * tr * tr) {
-        const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-        const double id = 1.0 / det;
-        g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
-               (c02 * b0 + c12 * b1 + c22 * b2) * id);
-      } else {
-        st = VOF_ST_SINGULAR_LSQ;
-        ++nsing;
-      }
+    if (det > 1e-12 * tr * tr * tr) {
+      const double c11 = g00 * g22 - g02 * g02, c12 = g02 * g01 - g00 * g12, c22 = g00 * g11 - g01 * g01;
+      const double id = 1.0 / det;
+      g = v3((c00 * b0 + c01 * b1 + c02 * b2) * id, (c01 * b0 + c11 * b1 + c12 * b2) * id,
+             (c02 * b0 + c12 * b1 + c22 * b2) * id);
     } else {
-      double b0 = 0, b1 = 0, b2 = 0;
-      for (int64_t k = M.cell_face_off[c]; k < M.cell_face_off[c + 1]; ++k) {
-        const int32_t f = M.cell_face[k] & 0x7fffffff;
-        const int32_t q = M.face_owner[f] == c ? M.face_neigh[f] : M.face_owner[f];
-        const Vec3 r = v3(M.cell_cen[3 * q], M.cell_cen[3 * q + 1], M.cell_cen[3 * q + 2]) - xP;
-        const double dT = a.T[q] - TP;
-        b0 = fma(r.x, dT, b0); b1 = fma(r.y, dT, b1); b2 = fma(r.z, dT, b2);
-      }
-      const double* gi = M.lsq_ginv + 6 * c;
-      g = v3(fma(gi[0], b0, fma(gi[1], b1, gi[2] * b2)), fma(gi[1], b0, fma(gi[3], b1, gi[4] * b2)),
-             fma(gi[2], b0, fma(gi[4], b1, gi[5] * b2)));
+      st = VOF_ST_SINGULAR_LSQ;
+      ++nsing;
     }
     W.grad[3 * c] = g.x; W.grad[3 * c + 1] = g.y; W.grad[3 * c + 2] = g.z;
     if (W.iface_stamp[c] == step) W.status[c] |= st;
@@ -1494,9 +1500,6 @@ __device__ double block_tree(const double* x, int64_t n, int64_t base, double* s
   return r;
 }
 
-__device__ __forceinline__ double flip_if(double x, bool f) {  // -x when f, by the sign bit
-  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ ((unsigned long long)f << 63)));
-}
 
 // Sum of the aligned leaves [tile * kThreads, (tile + 1) * kThreads) in thread order: each warp's
 // 32 leaves by shuffles (lane t + 2^k joins lane t), then warp 0 pairs the warp sums. Valid in
