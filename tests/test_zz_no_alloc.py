@@ -39,6 +39,8 @@ def _step_products(name):
 
 
 def test_static_totals_match_step_totals_twice():
+    """Both entry points sum the same pairwise tree (zero-padded to a power of two), so the totals
+    agree bit for bit; two calls in a row with different sizes."""
     vof, L = _lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     out = torch.empty(2, dtype=torch.float64, device="cuda")
@@ -48,7 +50,29 @@ def test_static_totals_match_step_totals_twice():
         st = L.vof_totals_static(mv.data_ptr(), qv.data_ptr(), mv.numel(), out.data_ptr(), stream)
         assert st == 0, L.vof_last_error()
         torch.cuda.synchronize()
-        np.testing.assert_allclose(out.cpu().numpy(), tot.cpu().numpy(), rtol=1e-8)
+        assert np.array_equal(out.cpu().numpy(), tot.cpu().numpy())
+
+
+@pytest.mark.parametrize("n", [0, 1, 2049, 3_141_593, 4_194_304])
+def test_static_totals_sizes_against_the_tree(n):
+    """Seeded values at the edges of the size range (empty, one value, one past a chunk, many
+    chunks over the grid-stride loop, the maximum) against the pairwise tree summed on the host
+    (the oracle's), bit for bit, on two calls in a row."""
+    import oracle
+    vof, L = _lib()
+    rng = np.random.default_rng(n)
+    a = rng.normal(size=n) * np.exp(rng.uniform(-20, 20, size=n))
+    b = rng.uniform(-1, 1, size=n)
+    da = torch.as_tensor(a, device="cuda") if n else torch.zeros(1, dtype=torch.float64, device="cuda")
+    db = torch.as_tensor(b, device="cuda") if n else torch.zeros(1, dtype=torch.float64, device="cuda")
+    want = np.array([oracle.pairwise_sum(a), oracle.pairwise_sum(b)])
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        assert L.vof_totals_static(da.data_ptr(), db.data_ptr(), n, out.data_ptr(), stream) == 0, L.vof_last_error()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want)
 
 
 def test_static_totals_reject_oversize():
