@@ -45,9 +45,23 @@ struct WeightsBF16 {
   float b1[kH], b2[kH], b3[kH], w4[kH], b4;  // w4 holds bf16-rounded values
 };
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// Standard normal CDF Phi(x) = (1 + erf(x / sqrt 2)) / 2, erf by Abramowitz and Stegun 7.1.26
+// (absolute error below 1.5e-7, far under the BF16 rounding that follows every hidden layer): with
+// u = |x| / sqrt 2 and t = 1 / (1 + p u), 1 - erf(u) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-u^2).
+// The tail (1 - erf(u)) / 2 is formed directly, so neither sign cancels; about 12 instructions.
+__device__ __forceinline__ float phi_cdf(float x) {
+  const float u = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
+  float p = fmaf(t, 1.061405429f, -1.453152027f);
+  p = fmaf(t, p, 1.421413741f);
+  p = fmaf(t, p, -0.284496736f);
+  p = fmaf(t, p, 0.254829592f);
+  const float tail = 0.5f * t * p * __expf(-u * u);
+  return x >= 0.f ? 1.0f - tail : tail;
+}
+__device__ __forceinline__ float gelu(float x) { return x * phi_cdf(x); }
 __device__ __forceinline__ float gelu_grad(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+  return phi_cdf(x) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -108,6 +122,16 @@ struct Smem {
   float y[kRows];
 };
 
+// Inference: the hidden layers stay in registers, so only the input tile and the weights are staged.
+struct FwdSmem {
+  __nv_bfloat16 X[kRows * LDX];
+  __nv_bfloat16 W1[kH * LDX];
+  __nv_bfloat16 W2[kH * LDH];
+  __nv_bfloat16 W3[kH * LDH];
+  float b1[kH], b2[kH], b3[kH], w4[kH];
+  float b4;
+};
+
 // 16-byte asynchronous copy global -> shared (no register round trip; completes at cp_async_wait)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -119,13 +143,14 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 // cp_async_wait() and a barrier. 16-byte chunks: 6 per W1 row (48 bf16), 8 per W2 / W3 row
 // (64 bf16); row strides of 56 and 72 bf16 keep every chunk 16-byte aligned, and b1, b2, b3, w4
 // are contiguous in both layouts.
-__device__ void stage_weights(Smem& s, const WeightsBF16& w) {
+template <class S>
+__device__ void stage_weights(S& s, const WeightsBF16& w) {
   for (int i = threadIdx.x; i < kH * 6; i += blockDim.x) cp_async16(s.W1 + (i / 6) * LDX + (i % 6) * 8, &w.W1[i / 6][(i % 6) * 8]);
   for (int i = threadIdx.x; i < kH * 8; i += blockDim.x) {
     cp_async16(s.W2 + (i / 8) * LDH + (i % 8) * 8, &w.W2[i / 8][(i % 8) * 8]);
     cp_async16(s.W3 + (i / 8) * LDH + (i % 8) * 8, &w.W3[i / 8][(i % 8) * 8]);
   }
-  static_assert(offsetof(Smem, w4) == offsetof(Smem, b1) + 3 * kH * sizeof(float), "biases contiguous");
+  static_assert(offsetof(S, w4) == offsetof(S, b1) + 3 * kH * sizeof(float), "biases contiguous");
   static_assert(offsetof(WeightsBF16, w4) == offsetof(WeightsBF16, b1) + 3 * kH * sizeof(float), "biases contiguous");
   for (int i = threadIdx.x; i < kH; i += blockDim.x) cp_async16(s.b1 + 4 * i, w.b1 + 4 * i);
   if (threadIdx.x == 0) s.b4 = w.b4;
@@ -183,10 +208,76 @@ __device__ void warp_forward(Smem& s, int m0, float* Z1, float* Z2, float* Z3, f
   __syncwarp();
 }
 
+// GELU of a layer's accumulators plus bias, rounded to BF16 and packed as the next layer's A
+// fragments: the C fragments of 8-column tiles 2j and 2j+1 (c0c1 row g, c2c3 row g+8, columns
+// 2q, 2q+1) are the A fragment of 16-column k-step j (a0a1, a2a3 from tile 2j; a4a5, a6a7 from
+// tile 2j+1), the lower column in the lower half of each register.
+__device__ __forceinline__ void gelu_to_a(const float (&acc)[8][4], const float* b, uint32_t (&a)[4][4]) {
+  const int q = threadIdx.x & 3;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int nt = 2 * j + h;
+      const float2 bb = *reinterpret_cast<const float2*>(b + nt * 8 + 2 * q);
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(gelu(acc[nt][0] + bb.x), gelu(acc[nt][1] + bb.y));
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(gelu(acc[nt][2] + bb.x), gelu(acc[nt][3] + bb.y));
+      a[j][2 * h] = *reinterpret_cast<const uint32_t*>(&lo);
+      a[j][2 * h + 1] = *reinterpret_cast<const uint32_t*>(&hi);
+    }
+}
+
+// acc = (16 x 64 hidden tile in A fragments) times W[0..64)[0..64)^T, same k order as warp_gemm
+__device__ __forceinline__ void warp_gemm_regs(const uint32_t (&a)[4][4], const __nv_bfloat16* W, float (&acc)[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* w = W + (nt * 8 + g) * LDH + 16 * j + 2 * q;
+      mma16816(acc[nt], a[j], *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+    }
+}
+
+// Inference forward of the warp's 16 rows (input tile rows m0..m0+15 of s.X) with the hidden
+// layers in registers; the same roundings and summation order as warp_forward. y0 and y1 are the
+// outputs of rows m0 + g and m0 + g + 8 (g = lane / 4), in every lane of the quad.
+template <class S>
+__device__ __forceinline__ void warp_forward_regs(const S& s, int m0, float& y0, float& y1) {
+  const int q = threadIdx.x & 3;
+  float acc[8][4];
+  uint32_t a[4][4];
+  warp_gemm<kInPad, LDX, LDX>(s.X, s.W1, m0, acc);
+  gelu_to_a(acc, s.b1, a);
+  warp_gemm_regs(a, s.W2, acc);
+  gelu_to_a(acc, s.b2, a);
+  warp_gemm_regs(a, s.W3, acc);
+  float part[2] = {0.f, 0.f};
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float2 bb = *reinterpret_cast<const float2*>(s.b3 + nt * 8 + 2 * q);
+    const float2 ww = *reinterpret_cast<const float2*>(s.w4 + nt * 8 + 2 * q);
+    part[0] = fmaf(gelu(acc[nt][0] + bb.x), ww.x, part[0]);
+    part[0] = fmaf(gelu(acc[nt][1] + bb.y), ww.y, part[0]);
+    part[1] = fmaf(gelu(acc[nt][2] + bb.x), ww.x, part[1]);
+    part[1] = fmaf(gelu(acc[nt][3] + bb.y), ww.y, part[1]);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 1);
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 2);
+  }
+  y0 = part[0] + s.b4;
+  y1 = part[1] + s.b4;
+}
+
 // Loads kRows feature rows (float32 [n][40], or zeros past n) into the bf16 X tile: four values
 // per load when X is 16-byte aligned (rows are 160 bytes), all of a thread's loads issued before
 // its stores.
-__device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n, int rows = kRows) {
+template <class S>
+__device__ void load_x(S& s, const float* X, int64_t row0, int64_t n, int rows = kRows) {
   if ((reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
     constexpr int C4 = kInPad / 4, U = 8;
     for (int i0 = threadIdx.x; i0 < rows * C4; i0 += U * blockDim.x) {
@@ -219,17 +310,22 @@ __device__ void load_x(Smem& s, const float* X, int64_t row0, int64_t n, int row
 
 __global__ void __launch_bounds__(kRows * 2) k_mlp_forward(WeightsBF16* w, const float* X, int64_t n, float* y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  FwdSmem& s = *reinterpret_cast<FwdSmem*>(smem_raw);
   stage_weights(s, *w);
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < n; row0 += (int64_t)gridDim.x * kRows) {
     load_x(s, X, row0, n);
     cp_async_wait();
     __syncthreads();
-    if (warp < kWarps) warp_forward(s, warp * 16, nullptr, nullptr, nullptr, nullptr);
-    __syncthreads();
-    for (int r = threadIdx.x; r < kRows; r += blockDim.x)
-      if (row0 + r < n) y[row0 + r] = s.y[r];
+    if (warp < kWarps) {
+      float y0, y1;
+      warp_forward_regs(s, warp * 16, y0, y1);
+      const int64_t r0 = row0 + warp * 16 + (lane >> 2);
+      if ((lane & 3) == 0) {
+        if (r0 < n) y[r0] = y0;
+        if (r0 + 8 < n) y[r0 + 8] = y1;
+      }
+    }
     __syncthreads();
   }
 }
@@ -281,90 +377,97 @@ __global__ void k_mlp_static(MeshView M, float* S) {
   }
 }
 
-// Per step: a warp takes a batch of 32 interface cells. Lane j reads cell j's alpha (one FP32
-// conversion for the batch: conversions run on the FP64 unit) and its static features; then the
-// warp takes the cells one by one, lane j holding vertex j (at most 32): the range comes from the
-// order keys of the FP64 vertex values (integer min / max), the normalised values from the values'
-// (hi, lo) float pairs in FP32 (no FP64 instruction), sorted descending by a bitonic network over
-// the warp. A cell whose range is below 1e-14 (as a float pair difference) gets no features.
-__global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, const float* S, float* X, int32_t* ok) {
-  const int64_t n = W.counters->n_iface;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t b0 = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; b0 < n; b0 += warps * 32) {
-    const int64_t ib = b0 + lane;
-    const int32_t cb = ib < n ? W.iface_idx[ib] : 0;
-    const float ab = ib < n ? (float)alpha[cb] : 0.f;
-    // lane j's cell's vertex range, so that the loop below reads it by shuffles
-    const int64_t vob = M.cell_vert_off[cb];
-    const int nvb = (int)(M.cell_vert_off[cb + 1] - vob);
-    const int nb = n - b0 < 32 ? (int)(n - b0) : 32;
-    // the vertices of cell j + 1 are read while cell j is processed (one cell ahead)
-    auto vertex_of = [&](int j) -> int32_t {
-      const int64_t v0 = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)vob, j);
-      const int nv = __shfl_sync(0xffffffffu, nvb, j);
-      return M.cell_vert[v0 + (lane < nv && lane < 32 ? lane : 0)];
-    };
-    int32_t vn = vertex_of(0);
-    double pn = W.phi_v[vn];
-    float2 fn = W.phi_ff[vn];
-    int okb = 0;
-    for (int j = 0; j < nb; ++j) {
-      const int nv = __shfl_sync(0xffffffffu, nvb, j);
-      const double pv = pn;
-      const float2 pf = fn;
-      if (j + 1 < nb) {
-        vn = vertex_of(j + 1);
-        pn = W.phi_v[vn];
-        fn = W.phi_ff[vn];
-      }
-      if (nv > 32) continue;
-      const bool has = lane < nv;
-      const uint64_t kp = okey(pv);
-      // extreme vertices by integer min / max of the order keys
-      uint64_t klo = kp, khi = kp;
+// Per step: a thread per interface cell. Its vertex values' (hi, lo) float pairs (at most 32) are
+// held in registers; the range comes from their lexicographic minimum and maximum (the pair of a
+// vertex value is monotone in the value, so these are the pairs of the extreme vertices), the
+// normalised values are formed in FP32 (no FP64 instruction but alpha's conversion) and sorted
+// descending by a bitonic network over the registers: 16 inputs when no cell of the warp has more
+// than 16 vertices, else 32. Missing entries take -1 and sort last; the output pads with the
+// smallest value. A cell whose range is below 1e-14 (as a float pair difference) gets no features.
+template <int NV>
+__device__ __forceinline__ void bitonic_desc(float (&u)[NV]) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        klo = min(klo, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)klo, o));
-        khi = max(khi, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)khi, o));
-      }
-      const int slo = __ffs(__ballot_sync(0xffffffffu, kp == klo)) - 1;
-      const int shi = __ffs(__ballot_sync(0xffffffffu, kp == khi)) - 1;
-      const ff lo = {__shfl_sync(0xffffffffu, pf.x, slo), __shfl_sync(0xffffffffu, pf.y, slo)};
-      const ff hi = {__shfl_sync(0xffffffffu, pf.x, shi), __shfl_sync(0xffffffffu, pf.y, shi)};
-      const ff rg = ff_add(hi, ff{-lo.hi, -lo.lo});
-      const float range = rg.hi + rg.lo;
-      if (!(range >= 1e-14f)) continue;
-      const float irange = 1.0f / range;
-      float u = has ? ((pf.x - lo.hi) + (pf.y - lo.lo)) * irange : -1.0f;  // missing lanes sort last
-      // bitonic sort, descending
+  for (int k = 2; k <= NV; k <<= 1)
 #pragma unroll
-      for (int k = 2; k <= 32; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1)
 #pragma unroll
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-          const float other = __shfl_xor_sync(0xffffffffu, u, jj);
-          const bool up = ((lane & k) == 0);  // this block of the network sorts descending
-          const bool lower = ((lane & jj) == 0);
-          u = (up == lower) ? fmaxf(u, other) : fminf(u, other);
+      for (int i = 0; i < NV; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const float a = u[i], b = u[l];
+          const bool desc = (i & k) == 0;  // this block of the network sorts descending
+          u[i] = desc ? fmaxf(a, b) : fminf(a, b);
+          u[l] = desc ? fminf(a, b) : fmaxf(a, b);
         }
       }
-      const float smallest = __shfl_sync(0xffffffffu, u, nv - 1);
-      X[(b0 + j) * kIn + 2 + lane] = lane < nv ? u : smallest;
-      if (lane == j) okb = 1;
+}
+
+template <int NV>
+__device__ __forceinline__ void cell_features(const MeshView& M, const Workspace& W, const float* S, int64_t v0,
+                                              int m, int32_t c, float ab, bool live, float* x, int32_t* okp) {
+  int32_t vi[NV];
+  float2 p[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) vi[k] = k < m ? M.cell_vert[v0 + k] : -1;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) p[k] = vi[k] >= 0 ? W.phi_ff[vi[k]] : make_float2(0.f, 0.f);
+  float2 mn = p[0], mx = p[0];
+#pragma unroll
+  for (int k = 1; k < NV; ++k)
+    if (k < m) {
+      if (p[k].x < mn.x || (p[k].x == mn.x && p[k].y < mn.y)) mn = p[k];
+      if (p[k].x > mx.x || (p[k].x == mx.x && p[k].y > mx.y)) mx = p[k];
     }
-    // alpha, faces / 32 and the shape features, a cell per lane
-    if (ib < n) {
-      float* x = X + ib * kIn;
-      if (okb) {
-        const float4 s0 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)cb);
-        const float4 s1 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)cb + 4);
-        x[0] = ab;
-        x[1] = s0.x;
-        x[34] = s0.y; x[35] = s0.z; x[36] = s0.w;
-        x[37] = s1.x; x[38] = s1.y; x[39] = s1.z;
-      }
-      ok[ib] = okb;
-    }
+  const ff rg = ff_add(ff{mx.x, mx.y}, ff{-mn.x, -mn.y});
+  const float range = rg.hi + rg.lo;
+  const bool good = m > 0 && range >= 1e-14f;
+  const float irange = 1.0f / range;
+  float u[NV];
+  float smallest = 3.4e38f;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    u[k] = k < m ? ((p[k].x - mn.x) + (p[k].y - mn.y)) * irange : -1.0f;
+    if (k < m) smallest = fminf(smallest, u[k]);
+  }
+  bitonic_desc<NV>(u);
+  if (!live) return;
+  *okp = good ? 1 : 0;
+  if (!good) return;
+  float v[kIn];
+  const float4 s0 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)c);
+  const float4 s1 = *reinterpret_cast<const float4*>(S + 8 * (int64_t)c + 4);
+  v[0] = ab;
+  v[1] = s0.x;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[2 + k] = (k < NV && k < m) ? u[k < NV ? k : 0] : smallest;
+  v[34] = s0.y; v[35] = s0.z; v[36] = s0.w;
+  v[37] = s1.x; v[38] = s1.y; v[39] = s1.z;
+  if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+#pragma unroll
+    for (int k = 0; k < kIn; k += 4) *reinterpret_cast<float4*>(x + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) x[k] = v[k];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_features(MeshView M, const double* alpha, Workspace W, const float* S,
+                                                      float* X, int32_t* ok) {
+  const int64_t n = W.counters->n_iface;
+  const int lane = threadIdx.x & 31;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += nthr) {
+    const int64_t i = b + lane;
+    const bool live = i < n;
+    const int32_t c = live ? W.iface_idx[i] : 0;
+    const int64_t v0 = M.cell_vert_off[c];
+    const int nv = (int)(M.cell_vert_off[c + 1] - v0);
+    const int m = live && nv <= 32 ? nv : 0;
+    const float ab = live ? (float)alpha[c] : 0.f;
+    if (__any_sync(0xffffffffu, m > 16))
+      cell_features<32>(M, W, S, v0, m, c, ab, live, X + i * kIn, ok + i);
+    else
+      cell_features<16>(M, W, S, v0, m, c, ab, live, X + i * kIn, ok + i);
   }
 }
 
@@ -376,7 +479,7 @@ __global__ void k_mlp_features(MeshView M, const double* alpha, Workspace W, con
 __global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w, const float* X, const int32_t* ok,
                                                                  Workspace W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  FwdSmem& s = *reinterpret_cast<FwdSmem*>(smem_raw);
   const int64_t n = W.counters->n_iface;
   const int64_t ntile = (n + 15) / 16;
   if ((int64_t)blockIdx.x * kWarps >= ntile) return;
@@ -405,12 +508,14 @@ __global__ void __launch_bounds__(kRows * 2) k_mlp_forward_iface(WeightsBF16* w,
       d[1] = __floats2bfloat162_rn(v[u].z, v[u].w);
     }
     __syncwarp();
-    warp_forward(s, m0, nullptr, nullptr, nullptr, nullptr);  // ends with a warp barrier after s.y
-    if (lane < 16) {
-      const int64_t i = row0 + lane;
-      if (i < n) W.mlp_out[i] = ok[i] ? fminf(fmaxf(s.y[m0 + lane], 0.f), 1.f) : -1.f;
+    float y0, y1;
+    warp_forward_regs(s, m0, y0, y1);
+    if ((lane & 3) == 0) {
+      const int64_t i0 = row0 + (lane >> 2), i1 = i0 + 8;
+      if (i0 < n) W.mlp_out[i0] = ok[i0] ? fminf(fmaxf(y0, 0.f), 1.f) : -1.f;
+      if (i1 < n) W.mlp_out[i1] = ok[i1] ? fminf(fmaxf(y1, 0.f), 1.f) : -1.f;
     }
-    __syncwarp();
+    __syncwarp();  // the tile's X rows are read before the next tile overwrites them
   }
 }
 
@@ -680,9 +785,9 @@ cudaError_t launch_mlp_guess(vof_mesh* m, cudaStream_t s) {
   float* X = m->ws.mlp_x;
   int32_t* ok = m->ws.mlp_ok;
   m->timing.start(KC_MLP_FEATURES, s);
-  k_mlp_features<<<m->num_sms * 8, 256, 0, s>>>(m->view, m->ws.alpha_in, m->ws, m->ws.mlp_static, X, ok);
+  k_mlp_features<<<m->num_sms * 8, 128, 0, s>>>(m->view, m->ws.alpha_in, m->ws, m->ws.mlp_static, X, ok);
   m->timing.stop(s);
-  const size_t fwd_smem = sizeof(Smem);
+  const size_t fwd_smem = sizeof(FwdSmem);
   static int fwd_bps = 0;  // resident blocks per SM of the forward pass
   if (!fwd_bps) {
     cudaFuncSetAttribute(k_mlp_forward_iface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem);
@@ -749,9 +854,9 @@ vof_status vof_mlp_forward(vof_mlp* m, const float* d_X, int64_t n, float* d_y, 
   if (!m || (n > 0 && (!d_X || !d_y)) || n < 0) { set_error("bad argument"); return VOF_EINVAL; }
   if (n == 0) return VOF_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(Smem));
+  cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(FwdSmem));
   const int grid = (int)std::min<int64_t>((n + kRows - 1) / kRows, 1024);
-  k_mlp_forward<<<grid, kRows * 2, sizeof(Smem), s>>>(m->w, d_X, n, d_y);
+  k_mlp_forward<<<grid, kRows * 2, sizeof(FwdSmem), s>>>(m->w, d_X, n, d_y);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_forward");
   return VOF_OK;
@@ -837,7 +942,7 @@ vof_status vof_mlp_features(vof_mesh* m, const double* d_alpha, float* d_X, int3
     m->allocs.push_back(m->ws.mlp_static);
     k_mlp_static<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, m->ws.mlp_static);
   }
-  k_mlp_features<<<m->num_sms * 8, 256, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, m->ws.mlp_static, d_X,
+  k_mlp_features<<<m->num_sms * 8, 128, 0, (cudaStream_t)stream>>>(m->view, d_alpha, m->ws, m->ws.mlp_static, d_X,
                                                                   d_ok);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "vof_mlp_features");

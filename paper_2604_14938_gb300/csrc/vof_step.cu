@@ -1841,6 +1841,12 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
   return v;
 }
 
+// Arrival with release semantics at GPU scope: the block's iterates (ordered before this thread by
+// the block barrier) are visible to any thread whose acquire load sees the sum.
+__device__ __forceinline__ void red_release_add_gpu(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double* alpha, double eps, int max_iter,
                                                         double tol, int poll_limit, Workspace W) {
   cg::grid_group grid = cg::this_grid();
@@ -1918,14 +1924,12 @@ __global__ void __launch_bounds__(kExThreads) k_extrap(MeshView M, const double*
 #pragma unroll
       for (int j = 0; j < 6; ++j)
         if ((v >> j) & 1u) add += 1ull << (16 + 8 * j);
-      __threadfence();  // this block's iterates before its arrival
-      atomicAdd(W.ex_itmax + k, add);
+      red_release_add_gpu(W.ex_itmax + k, add);
       unsigned long long cur = 0;
       long long spins = 0;
-      do {
+      do {  // the acquire load orders this block's next reads (through the block barrier) after it
         cur = ld_acquire_gpu(W.ex_itmax + k);
       } while ((cur & 0xffffull) < gridDim.x && ++spins < poll_limit);
-      __threadfence();  // the other blocks' iterates after their arrivals
       unsigned dec = 0;
       if ((cur & 0xffffull) < gridDim.x) {
         dec = 0x80000000u;  // gave up waiting
