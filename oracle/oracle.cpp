@@ -626,7 +626,9 @@ double crossing_t(const OrcMesh& m, int64_t f, const double* alpha, const double
     if (den == 0) continue;
     const double t = dot(nn, sub(xg, xo)) / den;
     if (!(t >= 0 && t <= 1)) continue;
-    const double d = norm(sub(add(xo, mul(sub(xn, xo), t)), xfc));
+    // nearest by squared distance: the same order as the distance, without a square root
+    const V3 r = sub(add(xo, mul(sub(xn, xo), t)), xfc);
+    const double d = dot(r, r);
     if (*src < 0 || d < best_d) { best_t = t; best_d = d; *src = c; }
   }
   return *src >= 0 ? best_t : t_lin;
