@@ -192,6 +192,7 @@ struct vof_mesh {
   int num_sms = 0;
   int sel_grid = 0;   // blocks of the cooperative selection launch (all resident)
   int geom_grid = 0;  // blocks of the interface-geometry launch
+  int geom_bmax = 0;  // interface cells per warp batch of the geometry
   int ex_grid = 0;    // blocks of the cooperative extrapolation launch
   int32_t* bnd_faces = nullptr;  // device list of the boundary faces (face_neigh < 0)
   int64_t n_bnd = 0;

@@ -45,21 +45,36 @@ struct WeightsBF16 {
   float b1[kH], b2[kH], b3[kH], w4[kH], b4;  // w4 holds bf16-rounded values
 };
 
-// Standard normal CDF Phi(x) = (1 + erf(x / sqrt 2)) / 2, erf by Abramowitz and Stegun 7.1.26
-// (absolute error below 1.5e-7, far under the BF16 rounding that follows every hidden layer): with
-// u = |x| / sqrt 2 and t = 1 / (1 + p u), 1 - erf(u) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-u^2).
-// The tail (1 - erf(u)) / 2 is formed directly, so neither sign cancels; about 12 instructions.
+// Standard normal CDF Phi(x) = (1 + erf(x / sqrt 2)) / 2, erf by Abramowitz and Stegun 7.1.25
+// (absolute error below 2.5e-5, under a hundredth of the BF16 rounding that follows every hidden
+// layer): with u = |x| / sqrt 2 and t = 1 / (1 + p u), 1 - erf(u) = t (a1 + t (a2 + t a3)) e^(-u^2).
+// The tail (1 - erf(u)) / 2 is formed directly, so neither sign cancels. Here p u = (p / sqrt 2)|x|,
+// the halves are folded into the coefficients, and e^(-u^2) = 2^(-(x s)^2) with s^2 = log2(e) / 2,
+// so that the reciprocal and the exponential are one approximate hardware instruction each.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float phi_tail(float x) {  // (1 - erf(|x| / sqrt 2)) / 2
+  const float t = rcp_approx(fmaf(0.33267253f, fabsf(x), 1.0f));          // p / sqrt 2, p = 0.47047
+  const float poly = fmaf(fmaf(t, 0.3739278f, -0.0479399f), t, 0.1740121f);  // a3 / 2, a2 / 2, a1 / 2
+  const float w = x * 0.84932180f;                                          // s = sqrt(log2(e) / 2)
+  return t * poly * ex2_approx(-(w * w));
+}
 __device__ __forceinline__ float phi_cdf(float x) {
-  const float u = fabsf(x) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
-  float p = fmaf(t, 1.061405429f, -1.453152027f);
-  p = fmaf(t, p, 1.421413741f);
-  p = fmaf(t, p, -0.284496736f);
-  p = fmaf(t, p, 0.254829592f);
-  const float tail = 0.5f * t * p * __expf(-u * u);
+  const float tail = phi_tail(x);
   return x >= 0.f ? 1.0f - tail : tail;
 }
-__device__ __forceinline__ float gelu(float x) { return x * phi_cdf(x); }
+__device__ __forceinline__ float gelu(float x) {
+  const float xt = x * phi_tail(x);
+  return x >= 0.f ? x - xt : xt;
+}
 __device__ __forceinline__ float gelu_grad(float x) {
   return phi_cdf(x) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }

@@ -1127,15 +1127,18 @@ __global__ void k_fixed_iso(MeshView M, Workspace W, double alpha_iso) {
 
 // Interface geometry (paper Sec. 2.1: area, unit normal and centroid of the cut polygons) at the
 // isovalues of the root search, kept apart from it: the root search's per-cell chain is FP64
-// latency, while here every cell is in flight at once. A warp takes kGeomCells consecutive
-// interface cells and lists their cut tetrahedra together (tetrahedron order within a cell), so
-// that the sections (FP32 pair arithmetic) keep most lanes busy; each lane adds its sections into
-// its own partial sums per cell in shared memory, and kGeomRed lanes per cell then add the 32
-// partials in a fixed order: the result does not depend on timing.
-constexpr int kGeomCells = 2;  // at most 4 (two bits of a list entry)
-constexpr int kGeomRed = 32 / kGeomCells;
-constexpr int kGeomThreads = 128;  // small blocks: five per SM keep every warp resident at 96 registers
+// latency, while here every cell is in flight at once. A warp takes a batch of B consecutive
+// interface cells (B up to kGeomBatch, fewer when the step has too few interface cells to give
+// every resident warp a full batch). The per-cell set-up (isovalue as a pair, apex value minus it)
+// and the final FP64 outputs run a cell per lane, so that their FP64 instructions serve B cells at
+// once. In between, the batch's tetrahedra are tested 32 at a time and the cut ones listed in cell
+// order; the sections (FP32 pair arithmetic) then take that list 32 at a time, so that every lane
+// is busy whatever the cells' cut counts, and a segmented warp scan by cell adds each round's
+// sections into the cells' sums in shared memory. The summation order is fixed by the batch, so the
+// result does not depend on timing.
+constexpr int kGeomThreads = 128;
 constexpr int kGeomWarps = kGeomThreads / 32;
+constexpr int kGeomBatch = 32;  // at most 32: a cell slot is five bits of a list entry
 
 struct GeomSlot {
   int64_t v0, t0;  // first vertex / tetrahedron entry of the cell
@@ -1145,39 +1148,34 @@ struct GeomSlot {
   int32_t nt;      // tetrahedra (0 for a degenerate cell)
 };
 
-constexpr int kGeomBatch = 32;  // interface cells whose per-cell set-up and outputs a warp does lane per cell
-
-size_t geom_smem_bytes(int max_ct) {
-  return (size_t)kGeomWarps * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomBatch * sizeof(GeomSlot) +
-                               (size_t)kGeomBatch * 7 * sizeof(float2) + (size_t)kGeomCells * max_ct * sizeof(uint32_t));
+// Shared memory of one warp: the batch's slots, its cells' sums (7 pairs each), the prefix of the
+// tetrahedron counts, and the cut list (at most bmax cells x max_ct tetrahedra).
+__host__ __device__ inline size_t geom_warp_bytes(int max_ct, int bmax) {
+  return (size_t)kGeomBatch * sizeof(GeomSlot) + (size_t)kGeomBatch * 7 * sizeof(float2) +
+         (size_t)(kGeomBatch + 4) * sizeof(int32_t) + (((size_t)bmax * max_ct * sizeof(uint32_t) + 15) & ~(size_t)15);
 }
+size_t geom_smem_bytes(int max_ct, int bmax) { return (size_t)kGeomWarps * geom_warp_bytes(max_ct, bmax); }
 
-// A warp takes a batch of B consecutive interface cells (B up to kGeomBatch, fewer when the step has
-// too few interface cells to give every resident warp a full batch): the per-cell set-up (isovalue
-// as a pair, apex value minus it) and the final FP64 outputs run a cell per lane, so that their
-// FP64 instructions serve B cells at once; the sections in between take kGeomCells cells at a time.
-__global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace W, int max_ct) {
+__global__ void __launch_bounds__(kGeomThreads, 4) k_geom(MeshView M, Workspace W, int max_ct, int bmax) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
-  unsigned char* wbase = smem + (size_t)warp * (kGeomCells * 7 * 32 * sizeof(float2) + kGeomBatch * sizeof(GeomSlot) +
-                                                (size_t)kGeomBatch * 7 * sizeof(float2) +
-                                                (size_t)kGeomCells * max_ct * sizeof(uint32_t));
-  float2* part = reinterpret_cast<float2*>(wbase);                                  // [cell][k][lane]
-  GeomSlot* bslot = reinterpret_cast<GeomSlot*>(part + kGeomCells * 7 * 32);        // [batch cell]
-  float2* res = reinterpret_cast<float2*>(bslot + kGeomBatch);                      // [batch cell][7]
-  uint32_t* lst = reinterpret_cast<uint32_t*>(res + kGeomBatch * 7);                // [kGeomCells * max_ct]
+  unsigned char* wbase = smem + (size_t)warp * geom_warp_bytes(max_ct, bmax);
+  GeomSlot* bslot = reinterpret_cast<GeomSlot*>(wbase);                 // [batch cell]
+  float2* res = reinterpret_cast<float2*>(bslot + kGeomBatch);          // [batch cell][7]
+  int32_t* off = reinterpret_cast<int32_t*>(res + kGeomBatch * 7);      // [batch cell + 1]
+  uint32_t* lst = reinterpret_cast<uint32_t*>(off + kGeomBatch + 4);    // cut list: t << 9 | slot << 4 | mask
   const int64_t n = W.counters->n_iface;
   const int64_t nwarps = (int64_t)gridDim.x * kGeomWarps;
   const int64_t per_warp = n / (nwarps > 0 ? nwarps : 1);
-  int B = per_warp >= kGeomBatch ? kGeomBatch : (per_warp <= kGeomCells ? kGeomCells : (int)per_warp);
-  B -= B % kGeomCells;
+  const int B = per_warp >= bmax ? bmax : (per_warp < 1 ? 1 : (int)per_warp);
   int64_t sect = 0;
   for (int64_t b0 = ((int64_t)blockIdx.x * kGeomWarps + warp) * B; b0 < n; b0 += nwarps * B) {
     // set-up of the batch's cells, a cell per lane
-    if (lane < B) {
+    int nt_l = 0;
+    {
       GeomSlot g = {0, 0, 0.0, make_float2(0.f, 0.f), make_float2(0.f, 0.f), -1, 0};
-      if (b0 + lane < n) {
+      if (lane < B && b0 + lane < n) {
         g.cell = W.iface_idx[b0 + lane];
         g.v0 = M.cell_vert_off[g.cell];
         if (!(W.status[g.cell] & VOF_ST_DEGENERATE)) {
@@ -1191,49 +1189,59 @@ __global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace 
         }
       }
       bslot[lane] = g;
+      nt_l = g.nt;
+    }
+    int incl = nt_l;  // inclusive prefix of the tetrahedron counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
+    }
+    off[lane + 1] = incl;
+    if (lane == 0) off[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) res[lane * 7 + k] = make_float2(0.f, 0.f);
+    const int total = __shfl_sync(full, incl, 31);
+    __syncwarp();
+    // the cut tetrahedra of the batch, in cell order, by integer order keys
+    int n_cut = 0;
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      const int q = r0 + lane;
+      bool cut = false;
+      uint32_t ent = 0;
+      if (q < total) {
+        int sl = 0;  // the cell: the largest slot whose first position is at or below q
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+          if (sl + st < B && off[sl + st] <= q) sl += st;
+        const GeomSlot& g = bslot[sl];
+        const int t = q - off[sl];
+        const uint64_t kc = okey(g.c);
+        const int32_t* cv = M.cell_vert + g.v0;
+        const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
+        const unsigned m = (unsigned)(okey(W.phi_v[cv[0]]) >= kc) | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
+                           ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
+                           ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
+        cut = m != 0u && m != 15u;
+        ent = ((uint32_t)t << 9) | ((uint32_t)sl << 4) | m;
+      }
+      const unsigned bal = __ballot_sync(full, cut);
+      if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = ent;
+      n_cut += __popc(bal);
     }
     __syncwarp();
-    for (int p0 = 0; p0 < B; p0 += kGeomCells) {
-      const GeomSlot* slot = bslot + p0;
+    // sections, 32 at a time; a segmented scan by cell, then the last lane of each cell's run adds
+    // the run's sum into the cell's sums
+    for (int r0 = 0; r0 < n_cut; r0 += 32) {
+      const int jj = r0 + lane;
+      int key = 64 + lane;  // past the list: a run of its own
+      ff v[7];
 #pragma unroll
-      for (int k = 0; k < kGeomCells * 7; ++k) part[k * 32 + lane] = make_float2(0.f, 0.f);
-      __syncwarp();
-      int off[kGeomCells + 1];
-      off[0] = 0;
-#pragma unroll
-      for (int q = 0; q < kGeomCells; ++q) off[q + 1] = off[q] + slot[q].nt;
-      // the cut tetrahedra of the pair's cells, by integer order keys
-      int n_cut = 0;
-      for (int r0 = 0; r0 < off[kGeomCells]; r0 += 32) {
-        const int q = r0 + lane;
-        bool cut = false;
-        uint32_t ent = 0;
-        if (q < off[kGeomCells]) {
-          int sl = 0, base = 0;
-#pragma unroll
-          for (int k = 1; k < kGeomCells; ++k)
-            if (q >= off[k]) { sl = k; base = off[k]; }
-          const GeomSlot& g = slot[sl];
-          const int t = q - base;
-          const uint64_t kc = okey(g.c);
-          const int32_t* cv = M.cell_vert + g.v0;
-          const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
-          const unsigned m = (unsigned)(okey(W.phi_v[cv[0]]) >= kc) | ((unsigned)(okey(W.phi_v[cv[pk & 255]]) >= kc) << 1) |
-                             ((unsigned)(okey(W.phi_v[cv[(pk >> 8) & 255]]) >= kc) << 2) |
-                             ((unsigned)(okey(W.phi_v[cv[(pk >> 16) & 255]]) >= kc) << 3);
-          cut = m != 0u && m != 15u;
-          ent = ((uint32_t)t << 6) | ((uint32_t)sl << 4) | m;
-        }
-        const unsigned bal = __ballot_sync(full, cut);
-        if (cut) lst[n_cut + __popc(bal & ((1u << lane) - 1u))] = ent;
-        n_cut += __popc(bal);
-      }
-      __syncwarp();
-      // sections, each added to this lane's partials of its cell
-      for (int jj = lane; jj < n_cut; jj += 32) {
+      for (int k = 0; k < 7; ++k) v[k] = ff{0.f, 0.f};
+      if (jj < n_cut) {
         const uint32_t e = lst[jj];
-        const int sl = (int)((e >> 4) & 3u), t = (int)(e >> 6);
-        const GeomSlot& g = slot[sl];
+        const int sl = (int)((e >> 4) & 31u), t = (int)(e >> 9);
+        const GeomSlot& g = bslot[sl];
         const int32_t* cv = M.cell_vert + g.v0;
         const uint32_t pk = __ldg(M.cell_tet + g.t0 + t);
         const int l1 = pk & 255, l2 = (pk >> 8) & 255, l3 = (pk >> 16) & 255;
@@ -1244,37 +1252,30 @@ __global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace 
         tet_section_ff(ff3_load(rp + 3 * l1), ff3_load(rp + 3 * l2), ff3_load(rp + 3 * l3), ff_make(g.w0),
                        ff_sub(ff_make(W.phi_ff[cv[l1]]), cf), ff_sub(ff_make(W.phi_ff[cv[l2]]), cf),
                        ff_sub(ff_make(W.phi_ff[cv[l3]]), cf), e & 15u, tA, ta, tm);
-        const ff add[7] = {tA.x, tA.y, tA.z, ta, tm.x, tm.y, tm.z};
-        float2* pc = part + (size_t)sl * 7 * 32 + lane;
+        v[0] = tA.x; v[1] = tA.y; v[2] = tA.z; v[3] = ta; v[4] = tm.x; v[5] = tm.y; v[6] = tm.z;
+        key = sl;
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int kp = __shfl_up_sync(full, key, o);
+        const bool take = lane >= o && kp == key;  // keys ascend, so the whole span is this cell's
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-          const ff r = ff_add(ff_make(pc[k * 32]), add[k]);
-          pc[k * 32] = make_float2(r.hi, r.lo);
+          const ff u = {__shfl_up_sync(full, v[k].hi, o), __shfl_up_sync(full, v[k].lo, o)};
+          if (take) v[k] = ff_add(v[k], u);
         }
       }
-      sect += n_cut;
-      __syncwarp();
-      // per cell: kGeomRed lanes add the 32 partials (lane l takes l, l + kGeomRed, ...), then a tree
-      const int sl = lane / kGeomRed, l = lane % kGeomRed;
-      ff v[7];
+      const int kn = __shfl_down_sync(full, key, 1);
+      if (jj < n_cut && (lane == 31 || kn != key)) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const float2* pc = part + ((size_t)sl * 7 + k) * 32;
-        ff acc = ff_make(pc[l]);
-#pragma unroll
-        for (int j = 1; j < 32 / kGeomRed; ++j) acc = ff_add(acc, ff_make(pc[l + j * kGeomRed]));
-        v[k] = acc;
-      }
-#pragma unroll
-      for (int o = kGeomRed / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 7; ++k) v[k] = ff_add(v[k], ff{__shfl_xor_sync(full, v[k].hi, o), __shfl_xor_sync(full, v[k].lo, o)});
-      if (l == 0) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) res[(p0 + sl) * 7 + k] = make_float2(v[k].hi, v[k].lo);
+        for (int k = 0; k < 7; ++k) {
+          const ff r = ff_add(ff_make(res[key * 7 + k]), v[k]);
+          res[key * 7 + k] = make_float2(r.hi, r.lo);
+        }
       }
       __syncwarp();
     }
+    sect += n_cut;
     // outputs, a cell per lane
     if (lane < B && bslot[lane].cell >= 0) {
       const GeomSlot& g = bslot[lane];
@@ -1322,11 +1323,15 @@ __device__ double crossing_t(const MeshView& M, const Workspace& W, const double
     const Vec3 nn = v3(W.n_int[3 * c], W.n_int[3 * c + 1], W.n_int[3 * c + 2]);
     const Vec3 xg = v3(W.x_gamma[3 * c], W.x_gamma[3 * c + 1], W.x_gamma[3 * c + 2]);
     const double den = dot(nn, dn);
-    if (den == 0) continue;
+    if (mag(den) == 0ull) continue;
     const double t = dot(nn, xg - xo) / den;
-    if (!(t >= 0 && t <= 1)) continue;
-    const double d = norm(xo + dn * t - xfc);
-    if (*src < 0 || d < best_d) { best_t = t; best_d = d; *src = c; }
+    // 0 <= t <= 1 and the nearer plane (squared distance) by order keys: FP64 compares cost an
+    // FP64 issue slot each; NaN fails both tests as it does in floating point
+    const uint64_t kt = okey(t);
+    if (!(kt >= okey(0.0) && kt <= okey(1.0))) continue;
+    const Vec3 r = xo + dn * t - xfc;
+    const double d = dot(r, r);
+    if (*src < 0 || okey(d) < okey(best_d)) { best_t = t; best_d = d; *src = c; }
   }
   return *src >= 0 ? best_t : (alpha[o] - 0.5) / (alpha[o] - alpha[n]);
 }
@@ -2195,9 +2200,17 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     m->sel_grid = std::min(m->num_sms * std::max(1, std::min(bps, 8)), kMaxSelGrid);
   }
   if (!m->geom_grid) {  // the geometry grid: every resident warp of the device
+    // cells per batch: the cut list of a full batch within a quarter of an SM's shared memory
+    int bmax = kGeomBatch;
+    while (bmax > 1 && geom_smem_bytes(m->max_ct, bmax) > (56u << 10)) --bmax;
+    if (geom_smem_bytes(m->max_ct, bmax) > (227u << 10)) {
+      set_error("interface geometry: a cell has too many tetrahedra for the cut list in shared memory");
+      return VOF_EINVAL;
+    }
     int bps = 0;
-    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem_bytes(m->max_ct));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_geom, kGeomThreads, geom_smem_bytes(m->max_ct));
+    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem_bytes(m->max_ct, bmax));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_geom, kGeomThreads, geom_smem_bytes(m->max_ct, bmax));
+    m->geom_bmax = bmax;
     m->geom_grid = m->num_sms * std::max(1, bps);
   }
   {
@@ -2211,20 +2224,24 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     tm.stop(s);
     if (el != cudaSuccess) return cuda_fail(el, "selection kernel (cooperative launch)");
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "selection kernels");
+  if (learned) {
+    e = launch_mlp_guess(m, s);  // times its two kernels itself
+    if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
+  }
   if (early_xmark) {
-    // crossing faces next to the band: needed only by the least squares
+    // crossing faces next to the band, needed only by the least squares: a side branch next to
+    // the root search (latency-bound), forked after the network's kernels (issue-bound), which
+    // would otherwise share the SMs with it
     cudaEventRecord(m->ev_xfork, s);
     cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
     tm.start(KC_XMARK, m->xm_stream);
     k_xmark<<<m->num_sms * 4, kThreads, 0, m->xm_stream>>>(M, d_alpha, W);
     tm.stop(m->xm_stream);
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "selection kernels");
-  if (learned) {
-    e = launch_mlp_guess(m, s);  // times its two kernels itself
-    if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "crossing-face kernel");
   }
   // one branch per non-empty bin (root search); the branches join on s, then the geometry
   if (opt.root_mode == VOF_ROOT_FIXED) {
@@ -2247,7 +2264,7 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   }
   if (e != cudaSuccess) return cuda_fail(e, "root search kernels");
   tm.start(KC_GEOM, s);
-  k_geom<<<m->geom_grid, kGeomThreads, geom_smem_bytes(m->max_ct), s>>>(M, W, m->max_ct);
+  k_geom<<<m->geom_grid, kGeomThreads, geom_smem_bytes(m->max_ct, m->geom_bmax), s>>>(M, W, m->max_ct, m->geom_bmax);
   tm.stop(s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "interface geometry kernel");
