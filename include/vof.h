@@ -164,6 +164,14 @@ typedef struct {
    * ends the solve: every solve reports -1 iterations and the step's per-side gradients and
    * sources are invalid; the kernel returns normally and the next step is unaffected. */
   int extrap_poll_limit;
+  /* Lanes per cell 1 (group_size, or the autotuner's choice) with VOF_ROOT_LEARNED or
+   * VOF_ROOT_CUBIC, on cells of at most 24 tetrahedra, runs the thread-per-cell root search: its
+   * root phase is in FP32-pair arithmetic (about 48 significant bits), with values normalised by
+   * the cell's vertex range. A cell whose vertex interval around the root is narrower than
+   * root_narrow times that range, or whose target no interval brackets, is handed to the FP64
+   * lane-group path, which solves it from the start (default 2^-20, the narrowest interval the
+   * pairs take; range 2^-20 .. 2; 2 hands every cell over). */
+  double root_narrow;
 } vof_options;
 
 /* Fills *o with the defaults above. */

@@ -57,7 +57,7 @@ class Options(ctypes.Structure):
                 ("vertex_mode", ctypes.c_int), ("group_size", ctypes.c_int), ("htc", ctypes.c_int),
                 ("alpha_iso", ctypes.c_double), ("extrap", ctypes.c_int), ("extrap_max_iter", ctypes.c_int),
                 ("extrap_tol", ctypes.c_double), ("lsq_variant", ctypes.c_int), ("guess", ctypes.c_int),
-                ("extrap_poll_limit", ctypes.c_int)]
+                ("extrap_poll_limit", ctypes.c_int), ("root_narrow", ctypes.c_double)]
 
 
 class Counts(ctypes.Structure):

@@ -36,6 +36,8 @@ struct Counters {
   int64_t evals32_total;  // FP32 evaluations of the learned path's refinement
   int64_t bin_count[5];   // interface cells per tetrahedron-count bin
   int64_t bin_next[5];    // next bin-list position to take (cells fetched dynamically by the root search)
+  int64_t slow_count[5];  // cells the thread-per-cell root search hands to the lane-group kernel, per bin
+  int64_t slow_next[5];   // next slow-list position to take
   int64_t extrap_iters[6];  // iterations of the pseudo-time solves (liquid x, y, z, vapour x, y, z)
 };
 
@@ -103,6 +105,7 @@ struct Workspace {
   double* tile_part;       // [2][ceil(n_cells / kSrcTile)]: totals of aligned tiles of the interface list
   float* mlp_out;          // [n_cells] learned guesses (normalised position in the range)
   int32_t* bin_list;       // [kBins][n_cells] interface-list positions per bin
+  int32_t* slow_list;      // [kBins][n_cells] bin-list entries left to the lane-group root search
   const double* alpha_in;  // alpha of the current step
   float* mlp_x;            // [n_cells][40] features of interface cells (allocated with an MLP)
   int32_t* mlp_ok;         // [n_cells] 1 where the cell has features

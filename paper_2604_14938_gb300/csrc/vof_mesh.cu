@@ -425,6 +425,7 @@ vof_status create(const vof_mesh_desc* d, cudaStream_t s, vof_mesh* m) {
   TRY(dev_alloc(m, &W.io_totals, 2));
   TRY(dev_alloc(m, &W.mlp_out, nc));
   TRY(dev_alloc(m, &W.bin_list, (size_t)kBins * nc));
+  TRY(dev_alloc(m, &W.slow_list, (size_t)kBins * nc));
   TRY(dev_alloc(m, &W.iface_slot, nc));
   TRY(dev_alloc(m, &W.ex_x, 8 * (size_t)nc));
   TRY(dev_alloc(m, &W.ex_k, 5 * (size_t)nc));
@@ -511,6 +512,7 @@ void vof_default_options(vof_options* o) {
   o->lsq_variant = 0;
   o->guess = 0;
   o->extrap_poll_limit = 1 << 22;
+  o->root_narrow = 0x1p-20;
 }
 
 vof_status vof_mesh_create(const vof_mesh_desc* desc, void* stream, vof_mesh** out) {
@@ -564,6 +566,7 @@ static vof_status check_opt(const vof_options* o) {
       o->extrap_max_iter < 1 || o->extrap_max_iter > kExMaxIter || !(o->extrap_tol > 0) ||
       !std::isfinite(o->extrap_tol) || o->lsq_variant < 0 || o->lsq_variant > 15 || o->guess < 0 || o->guess > 1 ||
       o->extrap_poll_limit < 1 || o->extrap_poll_limit > (1 << 30) ||
+      !(o->root_narrow >= 0x1p-20 && o->root_narrow <= 2.0) ||
       o->xf_mode < 0 || o->xf_mode > 2 || o->vertex_mode < 0 || o->vertex_mode > 1 ||
       !(o->group_size == 0 || o->group_size == 1 || o->group_size == 2 || o->group_size == 4 || o->group_size == 8 ||
         o->group_size == 16 || o->group_size == 32)) {

@@ -91,7 +91,7 @@ __device__ __forceinline__ void begin_step(Counters* cn) {
   cn->n_degenerate = cn->n_not_converged = cn->n_fallback = cn->n_singular = cn->n_no_side = cn->n_mlp_skipped = 0;
   cn->evals_total = 0;
   cn->tet_evals = cn->tets_prepared = cn->tets_sectioned = cn->evals32_total = 0;
-  for (int b = 0; b < kBins; ++b) cn->bin_count[b] = cn->bin_next[b] = 0;
+  for (int b = 0; b < kBins; ++b) cn->bin_count[b] = cn->bin_next[b] = cn->slow_count[b] = cn->slow_next[b] = 0;
   for (int k = 0; k < 6; ++k) cn->extrap_iters[k] = 0;
 }
 
@@ -611,6 +611,76 @@ __device__ __forceinline__ ff3 ff3_pick(int i, ff3 a, ff3 b, ff3 c, ff3 d) {
   return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
 __device__ __forceinline__ ff ff_pick(int i, ff a, ff b, ff c, ff d) { return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d)); }
+// Order of normalised pairs (|lo| <= ulp(hi) / 2, and hi = 0 only for the zero pair): by hi, then
+// lo. Every test is false when a NaN is involved.
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool ff_eq(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool ff_inside(ff y, ff L, ff H) { return ff_lt(L, y) && ff_lt(y, H); }  // L < y < H
+__device__ __forceinline__ ff ff_min(ff a, ff b) { return ff_lt(b, a) ? b : a; }
+__device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
+__device__ __forceinline__ ff ff_mid(ff a, ff b) { return ff_scale(ff_add(a, b), 0.5f); }
+// q0 + q1 y + q2 y^2 + q3 y^3 (Horner)
+__device__ __forceinline__ ff ff_cubic(ff q0, ff q1, ff q2, ff q3, ff y) {
+  return ff_add(ff_mul(ff_add(ff_mul(ff_add(ff_mul(q3, y), q2), y), q1), y), q0);
+}
+template <int G>
+__device__ __forceinline__ ff group_sum_ff(ff v, unsigned mask) {
+  // the pair sum is commutative bit for bit (the two-sum error is exact), so every lane of the
+  // butterfly ends with the same pair
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = ff_add(v, ff{__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o)});
+  return v;
+}
+
+__device__ __forceinline__ void cswap_ff(uint64_t& ka, ff& va, uint64_t& kb, ff& vb) {
+  // descending order by key
+  const bool sw = ka < kb;
+  const uint64_t tk = sw ? kb : ka;
+  kb = sw ? ka : kb;
+  ka = tk;
+  const ff tv = sw ? vb : va;
+  vb = sw ? va : vb;
+  va = tv;
+}
+
+// tet_piece in pair arithmetic on normalised values: corner values p relative to the interval's
+// midpoint cm and divided by the cell's range (so that the differences are O(1)), their FP64 order
+// keys k, the volume fraction vt = V_t / V. The piece's cubic in y = (c - cm) / range is added to
+// q0..q3, in units of the cell volume. The caller takes this path only when the interval is wider
+// than 2^-20 of the range: every denominator is then a product of (wet - dry) differences of at
+// least 2^-20 each, so nothing leaves the FP32 exponent range or loses the pairs' 48 bits.
+__device__ __forceinline__ void tet_piece_ff(ff p0, ff p1, ff p2, ff p3, uint64_t k0, uint64_t k1, uint64_t k2,
+                                             uint64_t k3, ff vt, uint64_t kvb, ff& q0, ff& q1, ff& q2, ff& q3) {
+  cswap_ff(k0, p0, k1, p1);
+  cswap_ff(k2, p2, k3, p3);
+  cswap_ff(k0, p0, k2, p2);
+  cswap_ff(k1, p1, k3, p3);
+  cswap_ff(k1, p1, k2, p2);
+  const int nk = (k0 >= kvb) + (k1 >= kvb) + (k2 >= kvb) + (k3 >= kvb);  // 1, 2 or 3
+  const bool one = nk == 1, two = nk == 2;
+  const ff zero = {0.f, 0.f};
+  // denominators: nk = 1: d01 d02 d03; nk = 2: d02 d03 d12 d13; nk = 3: d03 d13 d23
+  const ff X = ff_sub(one ? p0 : (two ? p0 : p1), one ? p1 : (two ? p2 : p3));  // d01 | d02 | d13
+  const ff Y = ff_sub(one ? p0 : (two ? p1 : p2), one ? p2 : (two ? p2 : p3));  // d02 | d12 | d23
+  const ff Z = two ? ff_sub(p1, p3) : ff{1.f, 0.f};                             // 1   | d13 | 1
+  const ff d03 = ff_sub(p0, p3);
+  const ff YZ = ff_mul(Y, Z);
+  const ff R = ff_mul(vt, ff_rcp(ff_mul(ff_mul(d03, X), YZ)));
+  // nk = 2: a = d01, e = d12 (= Y), f = d13 (= Z); vk = vt / (d02 d03) = R e f
+  const ff a = ff_sub(p0, p1);
+  const ff vk = ff_mul(R, YZ);
+  const ff A = two ? ff_mul(vk, ff_mul(a, a)) : (one ? zero : vt);
+  const ff B = two ? ff_scale(ff_mul(vk, a), 3.f) : zero;
+  const ff C = two ? ff_scale(vk, 3.f) : zero;
+  const ff D = two ? ff_neg(ff_mul(R, ff_add(a, ff_add(Y, Z)))) : R;
+  const ff dl = one ? p0 : (two ? p1 : p3);  // ref - cm, normalised
+  q0 = ff_add(q0, ff_cubic(A, B, C, D, dl));
+  const ff D3 = ff_scale(D, 3.f);
+  q1 = ff_sub(q1, ff_add(ff_mul(ff_add(ff_mul(D3, dl), ff_scale(C, 2.f)), dl), B));
+  q2 = ff_add(q2, ff_add(ff_mul(D3, dl), C));
+  q3 = ff_sub(q3, D);
+}
+
 
 // The section of tet_section in pair arithmetic, with positions relative to the cell's apex (P0 is
 // the origin) and w_i = phi_i - c: the same quadrilateral of cut points, vector area (wet -> dry),
@@ -719,7 +789,7 @@ __host__ __device__ inline size_t root_group_bytes(int max_ct, int max_cv, int m
 
 template <int G>
 __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* alpha, vof_options opt, Workspace W,
-                                                   int max_ct, int max_cv, int mode, int use_mlp, int bin) {
+                                                   int max_ct, int max_cv, int mode, int use_mlp, int bin, int slow) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gib = threadIdx.x / G;  // group in block
   const int lane = threadIdx.x % G;
@@ -738,14 +808,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
   float* uvert = reinterpret_cast<float*>(gbase + rw_bytes + dv_bytes);
   uint32_t* tpk = reinterpret_cast<uint32_t*>(gbase + rw_bytes + dv_bytes + uv_bytes);
   uint16_t* actl = reinterpret_cast<uint16_t*>(gbase + rw_bytes + dv_bytes + uv_bytes + pk_bytes);
-  const int64_t n_bin = W.counters->bin_count[bin];
-  const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
+  // the bin's list, or (slow) the cells of the bin that the thread-per-cell kernel handed over
+  const int64_t n_bin = slow ? W.counters->slow_count[bin] : W.counters->bin_count[bin];
+  const int32_t* list = (slow ? W.slow_list : W.bin_list) + (size_t)bin * M.n_cells;
+  unsigned long long* next = (unsigned long long*)(slow ? &W.counters->slow_next[bin] : &W.counters->bin_next[bin]);
   int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
   // each group takes the next cell of the bin when it is done with the last one: the learned
   // path's fallback cells cost ten times a typical cell, so a static split leaves SMs idle
   for (;;) {
     int64_t j = 0;
-    if (lane == 0) j = (int64_t)atomicAdd((unsigned long long*)&W.counters->bin_next[bin], 1ull);
+    if (lane == 0) j = (int64_t)atomicAdd(next, 1ull);
     j = __shfl_sync(mask, j, 0, G);
     if (j >= n_bin) break;
     const int64_t i = list[j];  // position in the interface list
@@ -961,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         // interval's ends the neighbouring interval is taken instead (another pass). On [va, vb]
         // every FP64 evaluation of V_L is P, exactly.
         //  - Learned: an evaluation at the refined point, one at a Newton point with the FP32
-        //    slope, at most max_secant secant steps (the benchmark spec's guess + secant steps).
+        //    slope, at most max_secant secant steps (the guess + secant steps of the learned path).
         //  - Interval cubic (the next row N1 of the scope): safeguarded Newton steps on P.
         // A miss of the tolerance ends in bisection on P inside the bracket (the counted
         // fallback); if no interval brackets the target, in bisection over [phi_min, phi_max]
@@ -1099,11 +1171,317 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
   }
 }
 
-// Interface geometry (paper Sec. 2.1: area, unit normal and centroid of the cut polygons) at the
-// isovalues of the root search: a warp per interface cell, in interface-list order, each lane
-// sectioning its share of the cell's cut tetrahedra in FP32 pair arithmetic. Kept apart from the
-// root search, whose per-cell chain is FP64 latency: here every cell is in flight at once and the
-// chain is one or two sections and the pair sums.
+// ---- root search with a thread per cell (cells of at most kCellMaxTets tetrahedra) ------------------
+// The learned and interval-cubic modes for small cells (tetrahedra, prisms, hexahedra, the pipe's
+// extruded polygons): every lane of a warp owns one cell and runs the same steps, so the warp's
+// instructions serve 32 cells and no lane group drifts out of step with the others. Nothing per
+// tetrahedron is kept in shared memory: each FP32 evaluation forms the wet fraction of a
+// tetrahedron from its corner values in one pass (tet_wet32), and the root phase runs on the FP32
+// pipe in pair arithmetic (tet_piece_ff), since on this part an FP64 warp instruction costs 64
+// issue slots of its sub-partition. Per thread, shared memory holds the cell's FP64 vertex values
+// (order keys of the interval pass) and one float2 per vertex: the normalised FP32 values of the
+// refinement, then the normalised pairs of the root phase; both arrays are strided by the block
+// size, so a lane's element k sits in the lane's own bank whatever k is. A cell whose vertex
+// interval is narrower than options.root_narrow (default 2^-20) of its range, or whose target no
+// interval brackets, is handed to the lane-group kernel (its slow list), which runs the FP64 path
+// on it from the start.
+constexpr int kCellThreads = 128;
+constexpr int kCellMaxTets = 24;  // the tetrahedra of a straddling set fit a 32-bit mask
+
+// Wet fraction of a tetrahedron at level u (FP32, for the refinement): corner values p, volume
+// fraction vf; the closed form of its number of wet corners (the header's formulas) with one
+// division, the same instructions on every lane.
+__device__ __forceinline__ float tet_wet32(float p0, float p1, float p2, float p3, float vf, float u) {
+  float s0 = fmaxf(p0, p1), s1 = fminf(p0, p1), s2 = fmaxf(p2, p3), s3 = fminf(p2, p3), t;
+  t = fmaxf(s0, s2); s2 = fminf(s0, s2); s0 = t;
+  t = fmaxf(s1, s3); s3 = fminf(s1, s3); s1 = t;
+  t = fmaxf(s1, s2); s2 = fminf(s1, s2); s1 = t;
+  const int k = (s0 >= u) + (s1 >= u) + (s2 >= u) + (s3 >= u);
+  const float d02 = s0 - s2, d03 = s0 - s3, d13 = s1 - s3;
+  const float wa = s0 - u, wb = s1 - u, uc = u - s2, ud = u - s3;
+  float num, den;
+  if (k == 1) {
+    num = wa * wa * wa;
+    den = (s0 - s1) * d02 * d03;
+  } else if (k == 2) {
+    const float ab = wa * wb;
+    num = ab * ab + (uc + ud) * ab * (wa + wb) + uc * ud * (wa * wa + ab + wb * wb);
+    den = d02 * d03 * (s1 - s2) * d13;
+  } else if (k == 3) {
+    den = d03 * d13 * (s2 - s3);
+    num = den - ud * ud * ud;
+  } else {
+    num = k == 4 ? 1.f : 0.f;
+    den = 1.f;
+  }
+  return vf * __fdividef(num, den);
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const double* alpha, vof_options opt,
+                                                            Workspace W, int nvmax, int mode, int use_mlp, int bin) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  double* dv = reinterpret_cast<double*>(smem) + threadIdx.x;                 // [k * T]
+  float2* sv = reinterpret_cast<float2*>(smem + (size_t)nvmax * T * sizeof(double)) + threadIdx.x;  // [k * T]
+  const int64_t n_bin = W.counters->bin_count[bin];
+  const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
+  const uint64_t ktol = mag(opt.tol_alpha);
+  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
+  for (int64_t j = (int64_t)blockIdx.x * T + threadIdx.x; j < n_bin; j += (int64_t)gridDim.x * T) {
+    const int64_t i = list[j];
+    const int32_t cell = W.iface_idx[i];
+    const int64_t v0 = M.cell_vert_off[cell], t0 = M.cell_tet_off[cell];
+    const int nv = (int)(M.cell_vert_off[cell + 1] - v0), nt = (int)(M.cell_tet_off[cell + 1] - t0);
+    const int32_t* cv = M.cell_vert + v0;
+    const uint32_t* ctp = M.cell_tet + t0;
+    uint64_t klo = ~0ull, khi = 0ull;
+    for (int k = 0; k < nv; ++k) {
+      const double p = W.phi_v[cv[k]];
+      dv[k * T] = p;
+      const uint64_t kk = okey(p);
+      klo = min(klo, kk);
+      khi = max(khi, kk);
+    }
+    const double lo = okey_inv(klo), hi = okey_inv(khi);
+    const double a = alpha[cell];
+    int status = 0, evals = 0, evals32 = 0, n_prep = 0;
+    int64_t tev = 0;
+    double c_best;
+    uint64_t kbest = 0;
+    bool slow = false;
+    const double range = hi - lo;
+    if (__double_as_longlong(range) < __double_as_longlong(1e-14)) {
+      status = VOF_ST_DEGENERATE;
+      c_best = lo;
+    } else {
+      const double oma = 1.0 - a;
+      kbest = min(mag(oma), mag(a));
+      c_best = okey(oma) <= okey(a) ? lo : hi;
+      // FP32 refinement, as in k_root: the guess u0, the local coordinate with the minority phase
+      // next to u = 0, regula falsi (Illinois) on the FP32 wet fractions
+      float u0 = use_mlp ? W.mlp_out[i] : 1.0f - d2f(a);
+      if (!(u0 >= 0.0f)) {
+        status |= VOF_ST_MLP_SKIPPED;
+        u0 = 1.0f - d2f(a);
+      }
+      const bool refl = okey(a) > kKeyHalf;
+      const double org = refl ? lo : hi;
+      const float af = d2f(refl ? oma : a);
+      {
+        const float r32 = __frcp_rn(d2f(range));
+        const float su = refl ? -r32 : r32;
+        const ff of = ff_of(org);
+        for (int k = 0; k < nv; ++k) {
+          const float2 pv = W.phi_ff[cv[k]];
+          sv[k * T].x = __fmul_rn(__fadd_rn(__fsub_rn(pv.x, of.hi), __fsub_rn(pv.y, of.lo)), su);
+        }
+      }
+      auto V32 = [&](float u) -> float {
+        const float pa = sv[0].x;
+        float v = 0.f;
+        for (int t = 0; t < nt; ++t) {
+          const uint32_t pk = __ldg(ctp + t);
+          v += tet_wet32(pa, sv[(pk & 255) * T].x, sv[((pk >> 8) & 255) * T].x, sv[((pk >> 16) & 255) * T].x,
+                         __ldg(M.tet_vfrac + t0 + t), u);
+        }
+        return v;
+      };
+      float ua = -1.f, fa = 1.f - af, ub = 0.f, fb = -af;
+      float uc = fminf(fmaxf(refl ? -u0 : u0 - 1.f, -1.f), 0.f);
+      float fc = V32(uc) - af;
+      ++evals32;
+      float up = uc, fp = fc;
+      int side = 0;
+      for (int it = 0; it < 16; ++it) {
+        if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
+        if (fabsf(fc) <= 1e-6f * af || ub - ua <= 1e-6f * fmaxf(fabsf(ua), fabsf(ub))) break;
+        float un;
+        if (it == 0) {
+          const float step = 0.02f;
+          un = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
+        } else {
+          un = ua + (ub - ua) * (fa / (fa - fb));
+          if (!(un > ua && un < ub)) un = 0.5f * (ua + ub);
+        }
+        up = uc;
+        fp = fc;
+        uc = un;
+        fc = V32(uc) - af;
+        ++evals32;
+        const int s2 = fc > 0.f ? 1 : -1;
+        if (s2 == side) {
+          if (s2 > 0) fb *= 0.5f; else fa *= 0.5f;
+        }
+        side = s2;
+      }
+      float slope = (uc != up) ? (fc - fp) / (uc - up) : 0.f;
+      if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
+      // root phase in pairs: the refined point picks the vertex interval, one pass sums the
+      // interval's cubic Q(y) = V_L/V - alpha, y = (c - cm) / range
+      double c1 = dmin(dmax(fma(flip_if(fl2d(uc), refl), range, org), lo), hi);
+      if (!(okey(c1) < okey(hi))) c1 = okey_inv(okey(hi) - 1);
+      auto vertex_interval = [&](double c, double& va, double& vb) {
+        const uint64_t kc = okey(c);
+        uint64_t ka = 0ull, kb = ~0ull;
+        for (int k = 0; k < nv; ++k) {
+          const uint64_t kk = okey(dv[k * T]);
+          if (kk <= kc) ka = max(ka, kk); else kb = min(kb, kk);
+        }
+        va = okey_inv(ka);
+        vb = okey_inv(kb);
+      };
+      double va, vb, cm = 0;
+      vertex_interval(c1, va, vb);
+      const ff ir = ff_rcp(ff_of(range)), ivV = ff_of(M.cell_ivol[cell]), a_ff = ff_of(a);
+      const uint64_t kwide = okey(range * opt.root_narrow);
+      const uint64_t kap = okey(dv[0]);
+      ff Q0 = {0.f, 0.f}, Q1 = Q0, Q2 = Q0, Q3 = Q0, yA = Q0, yB = Q0;
+      bool bracketed = false;
+      for (int mv = 0; mv < 8; ++mv) {
+        if (okey(vb - va) < kwide) break;  // narrower than root_narrow x range: the slow path
+        const uint64_t kva = okey(va), kvb = okey(vb);
+        cm = 0.5 * (va + vb);
+        for (int k = 0; k < nv; ++k) {
+          const ff r = ff_mul(ff_of(dv[k * T] - cm), ir);
+          sv[k * T] = make_float2(r.hi, r.lo);
+        }
+        // wet tetrahedra summed, straddling ones marked (keys only)
+        double ws = 0;
+        uint32_t smask = 0;
+        for (int t = 0; t < nt; ++t) {
+          const uint32_t pk = __ldg(ctp + t);
+          const uint64_t k1 = okey(dv[(pk & 255) * T]), k2 = okey(dv[((pk >> 8) & 255) * T]),
+                         k3 = okey(dv[((pk >> 16) & 255) * T]);
+          const uint64_t kmin = min(min(kap, k1), min(k2, k3)), kmax = max(max(kap, k1), max(k2, k3));
+          if (kmin >= kvb) ws += __ldg(M.tet_vol + t0 + t);
+          else if (kmax > kva) smask |= 1u << t;
+        }
+        ff q0 = ff_mul(ff_of(ws), ivV), q1 = {0.f, 0.f}, q2 = q1, q3 = q1;
+        const ff r0 = ff_make(sv[0]);
+        const int npc = __popc(smask);
+        while (smask) {
+          const int t = __ffs(smask) - 1;
+          smask &= smask - 1u;
+          const uint32_t pk = __ldg(ctp + t);
+          const int i1 = pk & 255, i2 = (pk >> 8) & 255, i3 = (pk >> 16) & 255;
+          tet_piece_ff(r0, ff_make(sv[i1 * T]), ff_make(sv[i2 * T]), ff_make(sv[i3 * T]), kap, okey(dv[i1 * T]),
+                       okey(dv[i2 * T]), okey(dv[i3 * T]), ff_mul(ff_of(__ldg(M.tet_vol + t0 + t)), ivV), kvb, q0,
+                       q1, q2, q3);
+        }
+        Q0 = ff_sub(q0, a_ff);
+        Q1 = q1;
+        Q2 = q2;
+        Q3 = q3;
+        n_prep += npc;
+        tev += npc;
+        ++evals;
+        yA = ff_mul(ff_of(va - cm), ir);
+        yB = ff_mul(ff_of(vb - cm), ir);
+        const bool above = ff_cubic(Q0, Q1, Q2, Q3, yB).hi > 0.f, below = ff_cubic(Q0, Q1, Q2, Q3, yA).hi < 0.f;
+        if (above && okey(vb) < okey(hi)) {
+          vertex_interval(vb, va, vb);
+        } else if (below && okey(va) > okey(lo)) {
+          vertex_interval(okey_inv(okey(va) - 1), va, vb);
+        } else {
+          bracketed = true;
+          break;
+        }
+      }
+      if (!bracketed) {
+        slow = true;
+      } else {
+        bool done = false;
+        ff yL = yA, yH = yB, ybest = yA;
+        bool have_best = false;
+        auto evalQ = [&](ff y) -> ff {
+          const ff f = ff_cubic(Q0, Q1, Q2, Q3, y);
+          const uint64_t kf = mag(fl2d(f.hi));
+          if (kf < kbest) { kbest = kf; ybest = y; have_best = true; }
+          if (f.hi > 0.f) yL = ff_max(yL, y); else yH = ff_min(yH, y);
+          if (kf <= ktol) done = true;
+          return f;
+        };
+        ff y1 = ff_min(ff_max(ff_mul(ff_of(c1 - cm), ir), yL), yH);
+        if (mode == VOF_ROOT_CUBIC) {
+          // safeguarded Newton steps on the cubic, bisection when a step leaves the bracket
+          ff ya = yL, yb = yH, y = y1;
+          for (int it = 0; it < 12 && !done; ++it) {
+            const ff g = evalQ(y);
+            if (g.hi == 0.f || done) break;
+            if (g.hi > 0.f) ya = y; else yb = y;
+            const ff dp = ff_add(ff_mul(ff_add(ff_mul(ff_scale(Q3, 3.f), y), ff_scale(Q2, 2.f)), y), Q1);  // <= 0
+            ff yn = ff_mid(ya, yb);
+            if (dp.hi < 0.f) {
+              const ff yt = ff_sub(y, ff_mul(g, ff_rcp(dp)));
+              if (ff_inside(yt, ya, yb)) yn = yt;
+            }
+            if (ff_eq(yn, y) || !ff_inside(yn, ya, yb)) break;
+            y = yn;
+          }
+        } else {
+          // learned: the refined point, a Newton point with the FP32 slope (df/dy), at most
+          // max_secant secant steps
+          ff f1 = evalQ(y1);
+          if (!done && opt.max_secant > 0) {
+            ff y0 = ff_sub(y1, ff_scale(f1, 1.0f / slope));
+            if (!ff_inside(y0, yL, yH) || ff_eq(y0, y1)) {
+              const ff st = {4e-6f, 0.f};
+              y0 = f1.hi > 0.f ? ff_min(ff_add(y1, st), ff_mid(y1, yH)) : ff_max(ff_sub(y1, st), ff_mid(y1, yL));
+            }
+            ff f0 = evalQ(y0);
+            for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
+              if (ff_eq(f0, f1)) break;
+              ff y2 = ff_sub(y0, ff_mul(ff_mul(f0, ff_sub(y0, y1)), ff_rcp(ff_sub(f0, f1))));
+              if (!ff_inside(y2, yL, yH)) y2 = ff_mid(yL, yH);
+              const ff f2 = evalQ(y2);
+              y1 = y0; f1 = f0; y0 = y2; f0 = f2;
+            }
+          }
+        }
+        if (!done) {  // the counted fallback: bisection on the cubic inside the bracket
+          status |= VOF_ST_FALLBACK;
+          for (int it = 0; it < opt.max_bisect && !done; ++it) {
+            evalQ(ff_mid(yL, yH));
+            if (!(ff_sub(yH, yL).hi > 0x1p-44f)) break;  // the pairs' resolution of the interval
+          }
+        }
+        if (have_best) c_best = dmin(dmax(fma(ff_to_double(ybest), range, cm), va), vb);
+        if (kbest > ktol) status |= VOF_ST_NOT_CONVERGED;
+      }
+    }
+    if (slow) {
+      // the lane-group kernel takes the cell from the start (FP64 root phase)
+      const unsigned long long s = atomicAdd((unsigned long long*)&W.counters->slow_count[bin], 1ull);
+      W.slow_list[(size_t)bin * M.n_cells + s] = (int32_t)i;
+    } else {
+      W.iso[cell] = c_best;
+      W.status[cell] = status;
+      W.evals[cell] = evals;
+      evals_acc += evals;
+      ev32_acc += evals32;
+      tetev_acc += tev;
+      prep_acc += n_prep;
+      if (status & VOF_ST_DEGENERATE) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
+      if (status & VOF_ST_NOT_CONVERGED) atomicAdd((unsigned long long*)&W.counters->n_not_converged, 1ull);
+      if (status & VOF_ST_FALLBACK) atomicAdd((unsigned long long*)&W.counters->n_fallback, 1ull);
+      if (status & VOF_ST_MLP_SKIPPED) atomicAdd((unsigned long long*)&W.counters->n_mlp_skipped, 1ull);
+    }
+  }
+  // counters: warp sums, one atomic each per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    evals_acc += __shfl_xor_sync(0xffffffffu, evals_acc, o);
+    tetev_acc += __shfl_xor_sync(0xffffffffu, tetev_acc, o);
+    prep_acc += __shfl_xor_sync(0xffffffffu, prep_acc, o);
+    ev32_acc += __shfl_xor_sync(0xffffffffu, ev32_acc, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (evals_acc || ev32_acc)) {
+    atomicAdd((unsigned long long*)&W.counters->evals_total, (unsigned long long)evals_acc);
+    atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
+    atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
+    atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
+  }
+}
+
 // Fixed isovalue (VOF_ROOT_FIXED, Sec. 2.1's prescribed alpha_iso): no root search; one thread per
 // interface cell checks the cell's vertex range (degenerate as in the root search) and sets c.
 __global__ void k_fixed_iso(MeshView M, Workspace W, double alpha_iso) {
@@ -2149,7 +2527,7 @@ int pick_group(const vof_mesh* m, const vof_options& o, int bin) {
 
 template <int G>
 cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
-                          int use_mlp, int bin) {
+                          int use_mlp, int bin, int slow = 0) {
   const int max_ct = m->bin_max_ct[bin];
   // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
   int threads = kThreads;
@@ -2167,9 +2545,32 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_root<G>, threads, smem);
   if (bps < 1) bps = 1;
   const int64_t need = (m->bin_cells[bin] + (threads / G) - 1) / (threads / G);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
-  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, mode, use_mlp, bin);
+  // the slow list is short (usually empty): one block per SM at most
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * (slow ? 1 : bps)));
+  k_root<G><<<grid, threads, smem, s>>>(m->view, alpha, opt, m->ws, max_ct, max_cv, mode, use_mlp, bin, slow);
   return cudaGetLastError();
+}
+
+// Thread-per-cell root search of a bin whose cells have at most kCellMaxTets tetrahedra, then the
+// lane-group kernel on the cells it handed over.
+cudaError_t launch_root_cell(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
+                             int use_mlp, int bin) {
+  const int nvmax = std::min(m->bin_max_ct[bin] + 3, m->max_cv);
+  const size_t smem = (size_t)nvmax * kCellThreads * (sizeof(double) + sizeof(float2));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_root_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_root_cell, kCellThreads, smem);
+  if (bps < 1) bps = 1;
+  const int64_t need = (m->bin_cells[bin] + kCellThreads - 1) / kCellThreads;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
+  k_root_cell<<<grid, kCellThreads, smem, s>>>(m->view, alpha, opt, m->ws, nvmax, mode, use_mlp, bin);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_root_g<4>(m, alpha, opt, s, mode, use_mlp, bin, 1);
 }
 
 }  // namespace
@@ -2273,6 +2674,9 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
 
 cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                             int use_mlp, int bin, int G) {
+  // one lane per cell of a small-cell bin: the thread-per-cell kernel (learned and cubic modes)
+  if (G == 1 && mode != VOF_ROOT_BISECT && m->bin_max_ct[bin] <= kCellMaxTets)
+    return launch_root_cell(m, alpha, opt, s, mode, use_mlp, bin);
   switch (G) {
     case 1: return launch_root_g<1>(m, alpha, opt, s, mode, use_mlp, bin);
     case 2: return launch_root_g<2>(m, alpha, opt, s, mode, use_mlp, bin);
