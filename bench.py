@@ -38,11 +38,11 @@ UNIT = "interface cells/s"
 FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 152 SMs x 2070 MHz x 2 FP64 FMA (4 flops) per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 RESIDENT_STEPS = 100  # device-resident input pairs of the moving-film workload (default)
-# The survey's per-unit figure, kept as a secondary basis: about 2 kFLOP per FP64 cut-volume
+# A clipping-based estimate, kept as a secondary basis: about 2 kFLOP per FP64 cut-volume
 # evaluation of a Voronoi cell of about 14 faces (36 straddle tests, ~15 cut points, ~90 fan
-# tetrahedra at ~20 flops). The roofline's own basis is the FP64 work the kernel counts on the
-# device (prepared rows, three-FMA evaluations of the straddling rows).
-SURVEY_FLOPS_PER_EVAL = 2000
+# tetrahedra at ~20 flops). The roofline's own basis is the FP64-equivalent work the kernel counts
+# on the device (pieces prepared and expanded, per-pass scaling).
+CLIP_FLOPS_PER_EVAL = 2000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per root-search launch, from ncu
 # captures of the workload (and layers), path and lanes per cell given; null for anything else
 ROOT_TRAFFIC: dict = {}
@@ -435,13 +435,18 @@ def main():
     nst = max(kt["select"][1], 1)
     root_ms, root_launches = kt["root"]
     counted = M.root_flops(ks)
-    survey = SURVEY_FLOPS_PER_EVAL * ks["evals_total"]
+    clip = CLIP_FLOPS_PER_EVAL * ks["evals_total"]
     peak = info["fp64"]["tflops"]
     achieved = counted / (root_ms / 1e3) / 1e12 if root_ms and counted else None
-    survey_tf = survey / (root_ms / 1e3) / 1e12 if root_ms and survey else None
+    clip_tf = clip / (root_ms / 1e3) / 1e12 if root_ms and clip else None
     ktot = sum(v[0] for v in kt.values())
     share = {k: round(v[0] / max(ktot, 1e-30), 4) for k, v in kt.items() if v[1]}
-    nbins = sum(1 for c in M.bin_cells if c)  # the root search launches once per non-empty bin
+    # the root search launches once per non-empty bin; a bin of at most 24 tetrahedra per cell
+    # with one lane per cell (learned or cubic mode) launches the thread-per-cell kernel and then
+    # the lane-group kernel on the cells it handed over
+    cell_kernel = PATHS[best][0] != 0
+    nbins = sum((2 if (cell_kernel and b <= 2 and info["tuned"][best][b] == 1) else 1)
+                for b, c in enumerate(M.bin_cells) if c)
     mlp_used = best in ("learned", "learned_extrap")
     # selection, crossing list, crossing points, least squares, source, geometry; root search per
     # bin; MLP features and forward; the pseudo-time extrapolation; batch totals
@@ -473,16 +478,18 @@ def main():
                      "flops_per_launch": counted / max(root_launches, 1),
                      "flops_per_iface_cell": counted / max(ks["n_iface"], 1),
                      "launches": root_launches, "ms_per_launch": root_ms / max(root_launches, 1),
-                     "flops_basis": "FP64 work counted on the device: 8 flops per tetrahedron row evaluation, 24 per "
-                                    "row prepared, 2 per evaluation (summed over the eager timing pass)",
+                     "flops_basis": "FP64-equivalent work counted on the device: 8 flops per tetrahedron row "
+                                    "evaluation or piece expanded, 24 per row or piece prepared, 2 per pass (summed "
+                                    "over the eager timing pass); the thread-per-cell kernel does this work in "
+                                    "FP32-pair arithmetic, and its FP32 refinement is not counted",
                      "peak_source": (f"FP64 FMA-chain probe in this run (vof_probe_fp64_fma: 8 independent chains per "
                                      f"thread, every SM at full occupancy, best of 3): {peak:.4f} TFLOP/s of measured; "
                                      f"nominal 152 SMs x 2070 MHz x 4 flop/clk = {FP64_NOMINAL_TFLOPS:.4f}"),
-                     "survey_basis": {"flops_per_eval": SURVEY_FLOPS_PER_EVAL, "achieved": survey_tf,
-                                      "frac": survey_tf / peak if survey_tf else None,
-                                      "note": "the survey's 2 kFLOP per FP64 cut-volume evaluation of a ~14-face cell "
-                                              "x the evaluations made; it credits the windowed rows' saving, so it "
-                                              "can exceed the peak on small cells"}},
+                     "clip_estimate": {"flops_per_eval": CLIP_FLOPS_PER_EVAL, "achieved": clip_tf,
+                                       "frac": clip_tf / peak if clip_tf else None,
+                                       "note": "a clipping-based 2 kFLOP per FP64 cut-volume evaluation of a ~14-face "
+                                               "cell x the evaluations made; it credits the interval pass's saving, "
+                                               "so it can exceed the peak on small cells"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": info["h2d"],
                 "d2h_bytes_per_step": info["d2h"]},
         "gpu_launches": args.steps * per_step,

@@ -74,7 +74,11 @@ typedef enum {
 #define VOF_ROOT_BISECT 0  /* plain FP64 bisection on [phi_min, phi_max] */
 /* Learned: BF16 MLP guess refined on the FP32 pipe, then FP64: the cubic V_L of the vertex interval
  * that holds the refined point (one pass over the cell's tetrahedra), an evaluation at the refined
- * point, one at a Newton point, <= max_secant secant steps, bracketed bisection as the fallback. */
+ * point, one at a Newton point, <= max_secant secant steps, bracketed bisection as the fallback.
+ * Cells of at most 24 tetrahedra with one lane per cell (group_size 1, or the autotuner's choice)
+ * take the thread-per-cell path instead (see root_narrow): the FP32 refinement stops once its
+ * bracket holds no vertex value, the interval's cubic is summed in FP32 pairs, and safeguarded
+ * Newton steps on it (up to 12) replace the Newton point and the secant steps. */
 #define VOF_ROOT_LEARNED 1
 /* Interval cubic: V_L(c) is one cubic between consecutive vertex values of a cell (Sec. 2.1 with
  * the cell split into tetrahedra of its own vertices); an FP32 refinement (from the MLP guess when
@@ -115,7 +119,7 @@ typedef struct {
   double tol_alpha;  /* root accepted when |V_L(c)/V - alpha| <= tol_alpha (default 1e-12) */
   int max_bisect;    /* bisection iteration cap (default 100) */
   int root_mode;     /* VOF_ROOT_BISECT, VOF_ROOT_LEARNED, VOF_ROOT_CUBIC or VOF_ROOT_FIXED */
-  int max_secant;    /* secant steps after the learned guess (default 2) */
+  int max_secant;    /* secant steps after the learned guess (default 2; the lane-group path) */
   int xf_mode;       /* VOF_XF_* (default VOF_XF_RECON) */
   int vertex_mode;   /* 0 inverse distance to cell centroids (default), 1 plain average */
   int group_size;    /* lanes per cell in the root search: 0 = auto, else 1, 2, 4, 8, 16 or 32 */

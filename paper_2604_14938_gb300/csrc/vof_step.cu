@@ -1174,23 +1174,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
 // ---- root search with a thread per cell (cells of at most kCellMaxTets tetrahedra) ------------------
 // The learned and interval-cubic modes for small cells (tetrahedra, prisms, hexahedra, the pipe's
 // extruded polygons): every lane of a warp owns one cell and runs the same steps, so the warp's
-// instructions serve 32 cells and no lane group drifts out of step with the others. Nothing per
-// tetrahedron is kept in shared memory: each FP32 evaluation forms the wet fraction of a
-// tetrahedron from its corner values in one pass (tet_wet32), and the root phase runs on the FP32
-// pipe in pair arithmetic (tet_piece_ff), since on this part an FP64 warp instruction costs 64
-// issue slots of its sub-partition. Per thread, shared memory holds the cell's FP64 vertex values
-// (order keys of the interval pass) and one float2 per vertex: the normalised FP32 values of the
-// refinement, then the normalised pairs of the root phase; both arrays are strided by the block
-// size, so a lane's element k sits in the lane's own bank whatever k is. A cell whose vertex
-// interval is narrower than options.root_narrow (default 2^-20) of its range, or whose target no
-// interval brackets, is handed to the lane-group kernel (its slow list), which runs the FP64 path
-// on it from the start.
+// instructions serve 32 cells and no lane group drifts out of step with the others.
+//  - FP32 refinement from the start value (the MLP guess, or 1 - alpha), regula falsi with the
+//    Illinois modification on FP32 wet fractions formed from the tetrahedra's corner values in one
+//    pass each (tet_wet32: nothing per tetrahedron is kept in shared memory). It stops as soon as
+//    its bracket holds no vertex value, i.e. once it has found the vertex interval of the root.
+//  - One pass over the tetrahedra for that interval sums the interval's cubic in FP32-pair
+//    arithmetic (tet_piece_roles_ff) on values normalised by the cell's range (on this part an
+//    FP64 warp instruction costs 64 issue slots of its sub-partition). The vertices' wet/dry roles
+//    over the interval come from their FP64 order keys, as a bit mask.
+//  - Safeguarded Newton steps on the exact cubic (both modes), bisection on it as the counted
+//    fallback.
+// Per thread, shared memory holds one float2 per vertex (the normalised FP32 values of the
+// refinement, then the normalised pairs of the root phase), strided by the block size so that a
+// lane's element k sits in the lane's own bank whatever k is. A cell whose vertex interval is
+// narrower than options.root_narrow (default 2^-20) of its range, or whose target no interval
+// brackets, is handed to the lane-group kernel (its slow list), which runs the FP64 path on it
+// from the start.
 constexpr int kCellThreads = 128;
 constexpr int kCellMaxTets = 24;  // the tetrahedra of a straddling set fit a 32-bit mask
 
 // Wet fraction of a tetrahedron at level u (FP32, for the refinement): corner values p, volume
 // fraction vf; the closed form of its number of wet corners (the header's formulas) with one
-// division, the same instructions on every lane.
+// division, selected rather than branched so that every lane runs the same instructions.
 __device__ __forceinline__ float tet_wet32(float p0, float p1, float p2, float p3, float vf, float u) {
   float s0 = fmaxf(p0, p1), s1 = fminf(p0, p1), s2 = fmaxf(p2, p3), s3 = fminf(p2, p3), t;
   t = fmaxf(s0, s2); s2 = fminf(s0, s2); s0 = t;
@@ -1198,35 +1204,71 @@ __device__ __forceinline__ float tet_wet32(float p0, float p1, float p2, float p
   t = fmaxf(s1, s2); s2 = fminf(s1, s2); s1 = t;
   const int k = (s0 >= u) + (s1 >= u) + (s2 >= u) + (s3 >= u);
   const float d02 = s0 - s2, d03 = s0 - s3, d13 = s1 - s3;
-  const float wa = s0 - u, wb = s1 - u, uc = u - s2, ud = u - s3;
-  float num, den;
-  if (k == 1) {
-    num = wa * wa * wa;
-    den = (s0 - s1) * d02 * d03;
-  } else if (k == 2) {
-    const float ab = wa * wb;
-    num = ab * ab + (uc + ud) * ab * (wa + wb) + uc * ud * (wa * wa + ab + wb * wb);
-    den = d02 * d03 * (s1 - s2) * d13;
-  } else if (k == 3) {
-    den = d03 * d13 * (s2 - s3);
-    num = den - ud * ud * ud;
-  } else {
-    num = k == 4 ? 1.f : 0.f;
-    den = 1.f;
-  }
+  const float wa = s0 - u, wb = s1 - u, uc = u - s2, ud = u - s3, ab = wa * wb;
+  const float n1 = wa * wa * wa, e1 = (s0 - s1) * d02 * d03;
+  const float n2 = ab * ab + (uc + ud) * ab * (wa + wb) + uc * ud * (wa * wa + ab + wb * wb);
+  const float e2 = d02 * d03 * (s1 - s2) * d13;
+  const float e3 = d03 * d13 * (s2 - s3), n3 = e3 - ud * ud * ud;
+  const float num = k == 1 ? n1 : (k == 2 ? n2 : (k == 3 ? n3 : (k == 4 ? 1.f : 0.f)));
+  const float den = k == 1 ? e1 : (k == 2 ? e2 : (k == 3 ? e3 : 1.f));
   return vf * __fdividef(num, den);
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const double* alpha, vof_options opt,
-                                                            Workspace W, int nvmax, int mode, int use_mlp, int bin) {
+// tet_piece_ff with the corners' roles over the interval given as a 4-bit mask of wet corners
+// (1 to 3 bits set) instead of a sort: the wet corners become s0.., the dry ones ..s3. The piece's
+// closed forms depend on the order only through these roles (they are symmetric within the wet
+// and within the dry corners); the two wet corners of the two-wet case are put in descending
+// order, as the FP64 path has them.
+__device__ __forceinline__ void tet_piece_roles_ff(ff p0, ff p1, ff p2, ff p3, unsigned m, ff vt, ff& q0, ff& q1,
+                                                   ff& q2, ff& q3) {
+  const int nk = __popc(m);
+  const unsigned dm = ~m & 15u;
+  // position of corner c: wet corners first, in index order, then the dry ones
+  auto pos = [&](int c) -> int {
+    const unsigned below = (1u << c) - 1u;
+    return ((m >> c) & 1u) ? __popc(m & below) : nk + __popc(dm & below);
+  };
+  const int o0 = pos(0), o1 = pos(1), o2 = pos(2), o3 = pos(3);
+  auto at = [&](int j) -> ff { return o0 == j ? p0 : (o1 == j ? p1 : (o2 == j ? p2 : p3)); };
+  ff s0 = at(0), s1 = at(1);
+  const ff s2 = at(2), s3 = at(3);
+  const bool one = nk == 1, two = nk == 2;
+  if (two && ff_lt(s0, s1)) {
+    const ff t = s0;
+    s0 = s1;
+    s1 = t;
+  }
+  const ff zero = {0.f, 0.f};
+  // denominators: nk = 1: d01 d02 d03; nk = 2: d02 d03 d12 d13; nk = 3: d03 d13 d23
+  const ff X = ff_sub(one ? s0 : (two ? s0 : s1), one ? s1 : (two ? s2 : s3));  // d01 | d02 | d13
+  const ff Y = ff_sub(one ? s0 : (two ? s1 : s2), one ? s2 : (two ? s2 : s3));  // d02 | d12 | d23
+  const ff Z = two ? ff_sub(s1, s3) : ff{1.f, 0.f};                             // 1   | d13 | 1
+  const ff d03 = ff_sub(s0, s3);
+  const ff YZ = ff_mul(Y, Z);
+  const ff R = ff_mul(vt, ff_rcp(ff_mul(ff_mul(d03, X), YZ)));
+  const ff a = ff_sub(s0, s1);
+  const ff vk = ff_mul(R, YZ);
+  const ff A = two ? ff_mul(vk, ff_mul(a, a)) : (one ? zero : vt);
+  const ff B = two ? ff_scale(ff_mul(vk, a), 3.f) : zero;
+  const ff C = two ? ff_scale(vk, 3.f) : zero;
+  const ff D = two ? ff_neg(ff_mul(R, ff_add(a, ff_add(Y, Z)))) : R;
+  const ff dl = one ? s0 : (two ? s1 : s3);  // ref - cm, normalised
+  q0 = ff_add(q0, ff_cubic(A, B, C, D, dl));
+  const ff D3 = ff_scale(D, 3.f);
+  q1 = ff_sub(q1, ff_add(ff_mul(ff_add(ff_mul(D3, dl), ff_scale(C, 2.f)), dl), B));
+  q2 = ff_add(q2, ff_add(ff_mul(D3, dl), C));
+  q3 = ff_sub(q3, D);
+}
+
+__global__ void __launch_bounds__(kCellThreads, 5) k_root_cell(MeshView M, const double* alpha, vof_options opt,
+                                                            Workspace W, int mode, int use_mlp, int bin) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
-  double* dv = reinterpret_cast<double*>(smem) + threadIdx.x;                 // [k * T]
-  float2* sv = reinterpret_cast<float2*>(smem + (size_t)nvmax * T * sizeof(double)) + threadIdx.x;  // [k * T]
+  float2* sv = reinterpret_cast<float2*>(smem) + threadIdx.x;  // [k * T]
   const int64_t n_bin = W.counters->bin_count[bin];
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
   const uint64_t ktol = mag(opt.tol_alpha);
-  int64_t evals_acc = 0, tetev_acc = 0, prep_acc = 0, ev32_acc = 0;
+  int64_t evals_acc = 0, tetev_acc = 0, ev32_acc = 0;
   for (int64_t j = (int64_t)blockIdx.x * T + threadIdx.x; j < n_bin; j += (int64_t)gridDim.x * T) {
     const int64_t i = list[j];
     const int32_t cell = W.iface_idx[i];
@@ -1236,15 +1278,13 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
     const uint32_t* ctp = M.cell_tet + t0;
     uint64_t klo = ~0ull, khi = 0ull;
     for (int k = 0; k < nv; ++k) {
-      const double p = W.phi_v[cv[k]];
-      dv[k * T] = p;
-      const uint64_t kk = okey(p);
+      const uint64_t kk = okey(W.phi_v[cv[k]]);
       klo = min(klo, kk);
       khi = max(khi, kk);
     }
     const double lo = okey_inv(klo), hi = okey_inv(khi);
     const double a = alpha[cell];
-    int status = 0, evals = 0, evals32 = 0, n_prep = 0;
+    int status = 0, evals = 0, evals32 = 0;
     int64_t tev = 0;
     double c_best;
     uint64_t kbest = 0;
@@ -1257,8 +1297,8 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
       const double oma = 1.0 - a;
       kbest = min(mag(oma), mag(a));
       c_best = okey(oma) <= okey(a) ? lo : hi;
-      // FP32 refinement, as in k_root: the guess u0, the local coordinate with the minority phase
-      // next to u = 0, regula falsi (Illinois) on the FP32 wet fractions
+      // FP32 refinement, as in k_root: the start value u0, the local coordinate with the minority
+      // phase next to u = 0, regula falsi (Illinois) on the FP32 wet fractions
       float u0 = use_mlp ? W.mlp_out[i] : 1.0f - d2f(a);
       if (!(u0 >= 0.0f)) {
         status |= VOF_ST_MLP_SKIPPED;
@@ -1286,25 +1326,33 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
         }
         return v;
       };
+      // a vertex value strictly inside (ua, ub)
+      auto vertex_inside = [&](float ua, float ub) -> bool {
+        bool in = false;
+        for (int k = 0; k < nv; ++k) {
+          const float x = sv[k * T].x;
+          in |= x > ua && x < ub;
+        }
+        return in;
+      };
       float ua = -1.f, fa = 1.f - af, ub = 0.f, fb = -af;
       float uc = fminf(fmaxf(refl ? -u0 : u0 - 1.f, -1.f), 0.f);
       float fc = V32(uc) - af;
       ++evals32;
-      float up = uc, fp = fc;
       int side = 0;
       for (int it = 0; it < 16; ++it) {
         if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
         if (fabsf(fc) <= 1e-6f * af || ub - ua <= 1e-6f * fmaxf(fabsf(ua), fabsf(ub))) break;
-        float un;
-        if (it == 0) {
-          const float step = 0.02f;
-          un = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
-        } else {
-          un = ua + (ub - ua) * (fa / (fa - fb));
-          if (!(un > ua && un < ub)) un = 0.5f * (ua + ub);
+        float un = ua + (ub - ua) * (fa / (fa - fb));
+        if (!(un > ua && un < ub)) un = 0.5f * (ua + ub);
+        if (it > 0 && !vertex_inside(ua, ub)) {  // the bracket lies in one vertex interval
+          uc = un;
+          break;
         }
-        up = uc;
-        fp = fc;
+        if (it == 0) {
+          const float step = 0.02f;  // probe next to the start, towards the root
+          un = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
+        }
         uc = un;
         fc = V32(uc) - af;
         ++evals32;
@@ -1314,8 +1362,6 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
         }
         side = s2;
       }
-      float slope = (uc != up) ? (fc - fp) / (uc - up) : 0.f;
-      if (!(slope < 0.f)) slope = (fb - fa) / (ub - ua);
       // root phase in pairs: the refined point picks the vertex interval, one pass sums the
       // interval's cubic Q(y) = V_L/V - alpha, y = (c - cm) / range
       double c1 = dmin(dmax(fma(flip_if(fl2d(uc), refl), range, org), lo), hi);
@@ -1324,7 +1370,7 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
         const uint64_t kc = okey(c);
         uint64_t ka = 0ull, kb = ~0ull;
         for (int k = 0; k < nv; ++k) {
-          const uint64_t kk = okey(dv[k * T]);
+          const uint64_t kk = okey(W.phi_v[cv[k]]);
           if (kk <= kc) ka = max(ka, kk); else kb = min(kb, kk);
         }
         va = okey_inv(ka);
@@ -1334,45 +1380,41 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
       vertex_interval(c1, va, vb);
       const ff ir = ff_rcp(ff_of(range)), ivV = ff_of(M.cell_ivol[cell]), a_ff = ff_of(a);
       const uint64_t kwide = okey(range * opt.root_narrow);
-      const uint64_t kap = okey(dv[0]);
       ff Q0 = {0.f, 0.f}, Q1 = Q0, Q2 = Q0, Q3 = Q0, yA = Q0, yB = Q0;
       bool bracketed = false;
       for (int mv = 0; mv < 8; ++mv) {
         if (okey(vb - va) < kwide) break;  // narrower than root_narrow x range: the slow path
-        const uint64_t kva = okey(va), kvb = okey(vb);
+        const uint64_t kvb = okey(vb);
         cm = 0.5 * (va + vb);
+        // roles over [va, vb] (no vertex value lies strictly inside): wet at or above vb, else dry;
+        // the values relative to cm, normalised, as pairs
+        uint32_t wet = 0;
         for (int k = 0; k < nv; ++k) {
-          const ff r = ff_mul(ff_of(dv[k * T] - cm), ir);
+          const double p = W.phi_v[cv[k]];
+          wet |= (uint32_t)(okey(p) >= kvb) << k;
+          const ff r = ff_mul(ff_of(p - cm), ir);
           sv[k * T] = make_float2(r.hi, r.lo);
         }
-        // wet tetrahedra summed, straddling ones marked (keys only)
         double ws = 0;
-        uint32_t smask = 0;
+        ff q0 = {0.f, 0.f}, q1 = q0, q2 = q0, q3 = q0;
+        const ff r0 = ff_make(sv[0]);
+        int npc = 0;
         for (int t = 0; t < nt; ++t) {
           const uint32_t pk = __ldg(ctp + t);
-          const uint64_t k1 = okey(dv[(pk & 255) * T]), k2 = okey(dv[((pk >> 8) & 255) * T]),
-                         k3 = okey(dv[((pk >> 16) & 255) * T]);
-          const uint64_t kmin = min(min(kap, k1), min(k2, k3)), kmax = max(max(kap, k1), max(k2, k3));
-          if (kmin >= kvb) ws += __ldg(M.tet_vol + t0 + t);
-          else if (kmax > kva) smask |= 1u << t;
-        }
-        ff q0 = ff_mul(ff_of(ws), ivV), q1 = {0.f, 0.f}, q2 = q1, q3 = q1;
-        const ff r0 = ff_make(sv[0]);
-        const int npc = __popc(smask);
-        while (smask) {
-          const int t = __ffs(smask) - 1;
-          smask &= smask - 1u;
-          const uint32_t pk = __ldg(ctp + t);
           const int i1 = pk & 255, i2 = (pk >> 8) & 255, i3 = (pk >> 16) & 255;
-          tet_piece_ff(r0, ff_make(sv[i1 * T]), ff_make(sv[i2 * T]), ff_make(sv[i3 * T]), kap, okey(dv[i1 * T]),
-                       okey(dv[i2 * T]), okey(dv[i3 * T]), ff_mul(ff_of(__ldg(M.tet_vol + t0 + t)), ivV), kvb, q0,
-                       q1, q2, q3);
+          const unsigned m4 = (wet & 1u) | ((wet >> i1) & 1u) << 1 | ((wet >> i2) & 1u) << 2 | ((wet >> i3) & 1u) << 3;
+          if (m4 == 15u) {
+            ws += __ldg(M.tet_vol + t0 + t);
+          } else if (m4) {
+            tet_piece_roles_ff(r0, ff_make(sv[i1 * T]), ff_make(sv[i2 * T]), ff_make(sv[i3 * T]), m4,
+                               ff_mul(ff_of(__ldg(M.tet_vol + t0 + t)), ivV), q0, q1, q2, q3);
+            ++npc;
+          }
         }
-        Q0 = ff_sub(q0, a_ff);
+        Q0 = ff_sub(ff_add(q0, ff_mul(ff_of(ws), ivV)), a_ff);
         Q1 = q1;
         Q2 = q2;
         Q3 = q3;
-        n_prep += npc;
         tev += npc;
         ++evals;
         yA = ff_mul(ff_of(va - cm), ir);
@@ -1390,6 +1432,7 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
       if (!bracketed) {
         slow = true;
       } else {
+        // safeguarded Newton steps on the exact cubic, bisection when a step leaves the bracket
         bool done = false;
         ff yL = yA, yH = yB, ybest = yA;
         bool have_best = false;
@@ -1401,42 +1444,18 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
           if (kf <= ktol) done = true;
           return f;
         };
-        ff y1 = ff_min(ff_max(ff_mul(ff_of(c1 - cm), ir), yL), yH);
-        if (mode == VOF_ROOT_CUBIC) {
-          // safeguarded Newton steps on the cubic, bisection when a step leaves the bracket
-          ff ya = yL, yb = yH, y = y1;
-          for (int it = 0; it < 12 && !done; ++it) {
-            const ff g = evalQ(y);
-            if (g.hi == 0.f || done) break;
-            if (g.hi > 0.f) ya = y; else yb = y;
-            const ff dp = ff_add(ff_mul(ff_add(ff_mul(ff_scale(Q3, 3.f), y), ff_scale(Q2, 2.f)), y), Q1);  // <= 0
-            ff yn = ff_mid(ya, yb);
-            if (dp.hi < 0.f) {
-              const ff yt = ff_sub(y, ff_mul(g, ff_rcp(dp)));
-              if (ff_inside(yt, ya, yb)) yn = yt;
-            }
-            if (ff_eq(yn, y) || !ff_inside(yn, ya, yb)) break;
-            y = yn;
+        ff y = ff_min(ff_max(ff_mul(ff_of(c1 - cm), ir), yL), yH);
+        for (int it = 0; it < 12 && !done; ++it) {
+          const ff g = evalQ(y);
+          if (g.hi == 0.f || done) break;
+          const ff dp = ff_add(ff_mul(ff_add(ff_mul(ff_scale(Q3, 3.f), y), ff_scale(Q2, 2.f)), y), Q1);  // <= 0
+          ff yn = ff_mid(yL, yH);
+          if (dp.hi < 0.f) {
+            const ff yt = ff_sub(y, ff_mul(g, ff_rcp(dp)));
+            if (ff_inside(yt, yL, yH)) yn = yt;
           }
-        } else {
-          // learned: the refined point, a Newton point with the FP32 slope (df/dy), at most
-          // max_secant secant steps
-          ff f1 = evalQ(y1);
-          if (!done && opt.max_secant > 0) {
-            ff y0 = ff_sub(y1, ff_scale(f1, 1.0f / slope));
-            if (!ff_inside(y0, yL, yH) || ff_eq(y0, y1)) {
-              const ff st = {4e-6f, 0.f};
-              y0 = f1.hi > 0.f ? ff_min(ff_add(y1, st), ff_mid(y1, yH)) : ff_max(ff_sub(y1, st), ff_mid(y1, yL));
-            }
-            ff f0 = evalQ(y0);
-            for (int sct = 0; sct < opt.max_secant && !done; ++sct) {
-              if (ff_eq(f0, f1)) break;
-              ff y2 = ff_sub(y0, ff_mul(ff_mul(f0, ff_sub(y0, y1)), ff_rcp(ff_sub(f0, f1))));
-              if (!ff_inside(y2, yL, yH)) y2 = ff_mid(yL, yH);
-              const ff f2 = evalQ(y2);
-              y1 = y0; f1 = f0; y0 = y2; f0 = f2;
-            }
-          }
+          if (ff_eq(yn, y) || !ff_inside(yn, yL, yH)) break;
+          y = yn;
         }
         if (!done) {  // the counted fallback: bisection on the cubic inside the bracket
           status |= VOF_ST_FALLBACK;
@@ -1460,24 +1479,22 @@ __global__ void __launch_bounds__(kCellThreads) k_root_cell(MeshView M, const do
       evals_acc += evals;
       ev32_acc += evals32;
       tetev_acc += tev;
-      prep_acc += n_prep;
       if (status & VOF_ST_DEGENERATE) atomicAdd((unsigned long long*)&W.counters->n_degenerate, 1ull);
       if (status & VOF_ST_NOT_CONVERGED) atomicAdd((unsigned long long*)&W.counters->n_not_converged, 1ull);
       if (status & VOF_ST_FALLBACK) atomicAdd((unsigned long long*)&W.counters->n_fallback, 1ull);
       if (status & VOF_ST_MLP_SKIPPED) atomicAdd((unsigned long long*)&W.counters->n_mlp_skipped, 1ull);
     }
   }
-  // counters: warp sums, one atomic each per warp
+  // counters: warp sums, one atomic each per warp (pieces prepared = pieces evaluated here)
   for (int o = 16; o > 0; o >>= 1) {
     evals_acc += __shfl_xor_sync(0xffffffffu, evals_acc, o);
     tetev_acc += __shfl_xor_sync(0xffffffffu, tetev_acc, o);
-    prep_acc += __shfl_xor_sync(0xffffffffu, prep_acc, o);
     ev32_acc += __shfl_xor_sync(0xffffffffu, ev32_acc, o);
   }
   if ((threadIdx.x & 31) == 0 && (evals_acc || ev32_acc)) {
     atomicAdd((unsigned long long*)&W.counters->evals_total, (unsigned long long)evals_acc);
     atomicAdd((unsigned long long*)&W.counters->tet_evals, (unsigned long long)tetev_acc);
-    atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)prep_acc);
+    atomicAdd((unsigned long long*)&W.counters->tets_prepared, (unsigned long long)tetev_acc);
     atomicAdd((unsigned long long*)&W.counters->evals32_total, (unsigned long long)ev32_acc);
   }
 }
@@ -2555,8 +2572,8 @@ cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& o
 // lane-group kernel on the cells it handed over.
 cudaError_t launch_root_cell(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                              int use_mlp, int bin) {
-  const int nvmax = std::min(m->bin_max_ct[bin] + 3, m->max_cv);
-  const size_t smem = (size_t)nvmax * kCellThreads * (sizeof(double) + sizeof(float2));
+  const int nvmax = std::min(m->bin_max_ct[bin] + 3, m->max_cv);  // nt tetrahedra: at most nt + 3 vertices
+  const size_t smem = (size_t)nvmax * kCellThreads * sizeof(float2);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_root_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -2567,7 +2584,7 @@ cudaError_t launch_root_cell(vof_mesh* m, const double* alpha, const vof_options
   if (bps < 1) bps = 1;
   const int64_t need = (m->bin_cells[bin] + kCellThreads - 1) / kCellThreads;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * bps));
-  k_root_cell<<<grid, kCellThreads, smem, s>>>(m->view, alpha, opt, m->ws, nvmax, mode, use_mlp, bin);
+  k_root_cell<<<grid, kCellThreads, smem, s>>>(m->view, alpha, opt, m->ws, mode, use_mlp, bin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_root_g<4>(m, alpha, opt, s, mode, use_mlp, bin, 1);
