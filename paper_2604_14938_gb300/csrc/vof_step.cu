@@ -1395,21 +1395,28 @@ __global__ void __launch_bounds__(kCellThreads, 5) k_root_cell(MeshView M, const
           const ff r = ff_mul(ff_of(p - cm), ir);
           sv[k * T] = make_float2(r.hi, r.lo);
         }
+        // wet tetrahedra summed, straddling ones marked; then the pieces over the marks, so that
+        // a lane runs the piece only as often as it has straddling tetrahedra
         double ws = 0;
+        uint32_t smask = 0;
+        for (int t = 0; t < nt; ++t) {
+          const uint32_t pk = __ldg(ctp + t);
+          const unsigned m4 = (wet & 1u) | ((wet >> (pk & 255)) & 1u) << 1 | ((wet >> ((pk >> 8) & 255)) & 1u) << 2 |
+                              ((wet >> ((pk >> 16) & 255)) & 1u) << 3;
+          if (m4 == 15u) ws += __ldg(M.tet_vol + t0 + t);
+          else if (m4) smask |= 1u << t;
+        }
         ff q0 = {0.f, 0.f}, q1 = q0, q2 = q0, q3 = q0;
         const ff r0 = ff_make(sv[0]);
-        int npc = 0;
-        for (int t = 0; t < nt; ++t) {
+        const int npc = __popc(smask);
+        while (smask) {
+          const int t = __ffs(smask) - 1;
+          smask &= smask - 1u;
           const uint32_t pk = __ldg(ctp + t);
           const int i1 = pk & 255, i2 = (pk >> 8) & 255, i3 = (pk >> 16) & 255;
           const unsigned m4 = (wet & 1u) | ((wet >> i1) & 1u) << 1 | ((wet >> i2) & 1u) << 2 | ((wet >> i3) & 1u) << 3;
-          if (m4 == 15u) {
-            ws += __ldg(M.tet_vol + t0 + t);
-          } else if (m4) {
-            tet_piece_roles_ff(r0, ff_make(sv[i1 * T]), ff_make(sv[i2 * T]), ff_make(sv[i3 * T]), m4,
-                               ff_mul(ff_of(__ldg(M.tet_vol + t0 + t)), ivV), q0, q1, q2, q3);
-            ++npc;
-          }
+          tet_piece_roles_ff(r0, ff_make(sv[i1 * T]), ff_make(sv[i2 * T]), ff_make(sv[i3 * T]), m4,
+                             ff_mul(ff_of(__ldg(M.tet_vol + t0 + t)), ivV), q0, q1, q2, q3);
         }
         Q0 = ff_sub(ff_add(q0, ff_mul(ff_of(ws), ivV)), a_ff);
         Q1 = q1;
@@ -1551,7 +1558,7 @@ __host__ __device__ inline size_t geom_warp_bytes(int max_ct, int bmax) {
 }
 size_t geom_smem_bytes(int max_ct, int bmax) { return (size_t)kGeomWarps * geom_warp_bytes(max_ct, bmax); }
 
-__global__ void __launch_bounds__(kGeomThreads, 4) k_geom(MeshView M, Workspace W, int max_ct, int bmax) {
+__global__ void __launch_bounds__(kGeomThreads, 5) k_geom(MeshView M, Workspace W, int max_ct, int bmax) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
