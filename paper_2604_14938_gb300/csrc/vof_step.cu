@@ -81,7 +81,6 @@ __device__ __forceinline__ Vec3 operator-(Vec3 a, Vec3 b) { return {a.x - b.x, a
 __device__ __forceinline__ Vec3 operator+(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ Vec3 operator*(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
 __device__ __forceinline__ double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ double norm(Vec3 a) { return sqrt(dot(a, a)); }
 
 // First work of a step: step stamp, counters reset (run by one thread of the first kernel).
 __device__ __forceinline__ void begin_step(Counters* cn) {
@@ -632,56 +631,6 @@ __device__ __forceinline__ ff group_sum_ff(ff v, unsigned mask) {
   return v;
 }
 
-__device__ __forceinline__ void cswap_ff(uint64_t& ka, ff& va, uint64_t& kb, ff& vb) {
-  // descending order by key
-  const bool sw = ka < kb;
-  const uint64_t tk = sw ? kb : ka;
-  kb = sw ? ka : kb;
-  ka = tk;
-  const ff tv = sw ? vb : va;
-  vb = sw ? va : vb;
-  va = tv;
-}
-
-// tet_piece in pair arithmetic on normalised values: corner values p relative to the interval's
-// midpoint cm and divided by the cell's range (so that the differences are O(1)), their FP64 order
-// keys k, the volume fraction vt = V_t / V. The piece's cubic in y = (c - cm) / range is added to
-// q0..q3, in units of the cell volume. The caller takes this path only when the interval is wider
-// than 2^-20 of the range: every denominator is then a product of (wet - dry) differences of at
-// least 2^-20 each, so nothing leaves the FP32 exponent range or loses the pairs' 48 bits.
-__device__ __forceinline__ void tet_piece_ff(ff p0, ff p1, ff p2, ff p3, uint64_t k0, uint64_t k1, uint64_t k2,
-                                             uint64_t k3, ff vt, uint64_t kvb, ff& q0, ff& q1, ff& q2, ff& q3) {
-  cswap_ff(k0, p0, k1, p1);
-  cswap_ff(k2, p2, k3, p3);
-  cswap_ff(k0, p0, k2, p2);
-  cswap_ff(k1, p1, k3, p3);
-  cswap_ff(k1, p1, k2, p2);
-  const int nk = (k0 >= kvb) + (k1 >= kvb) + (k2 >= kvb) + (k3 >= kvb);  // 1, 2 or 3
-  const bool one = nk == 1, two = nk == 2;
-  const ff zero = {0.f, 0.f};
-  // denominators: nk = 1: d01 d02 d03; nk = 2: d02 d03 d12 d13; nk = 3: d03 d13 d23
-  const ff X = ff_sub(one ? p0 : (two ? p0 : p1), one ? p1 : (two ? p2 : p3));  // d01 | d02 | d13
-  const ff Y = ff_sub(one ? p0 : (two ? p1 : p2), one ? p2 : (two ? p2 : p3));  // d02 | d12 | d23
-  const ff Z = two ? ff_sub(p1, p3) : ff{1.f, 0.f};                             // 1   | d13 | 1
-  const ff d03 = ff_sub(p0, p3);
-  const ff YZ = ff_mul(Y, Z);
-  const ff R = ff_mul(vt, ff_rcp(ff_mul(ff_mul(d03, X), YZ)));
-  // nk = 2: a = d01, e = d12 (= Y), f = d13 (= Z); vk = vt / (d02 d03) = R e f
-  const ff a = ff_sub(p0, p1);
-  const ff vk = ff_mul(R, YZ);
-  const ff A = two ? ff_mul(vk, ff_mul(a, a)) : (one ? zero : vt);
-  const ff B = two ? ff_scale(ff_mul(vk, a), 3.f) : zero;
-  const ff C = two ? ff_scale(vk, 3.f) : zero;
-  const ff D = two ? ff_neg(ff_mul(R, ff_add(a, ff_add(Y, Z)))) : R;
-  const ff dl = one ? p0 : (two ? p1 : p3);  // ref - cm, normalised
-  q0 = ff_add(q0, ff_cubic(A, B, C, D, dl));
-  const ff D3 = ff_scale(D, 3.f);
-  q1 = ff_sub(q1, ff_add(ff_mul(ff_add(ff_mul(D3, dl), ff_scale(C, 2.f)), dl), B));
-  q2 = ff_add(q2, ff_add(ff_mul(D3, dl), C));
-  q3 = ff_sub(q3, D);
-}
-
-
 // The section of tet_section in pair arithmetic, with positions relative to the cell's apex (P0 is
 // the origin) and w_i = phi_i - c: the same quadrilateral of cut points, vector area (wet -> dry),
 // area and area moment (about the apex).
@@ -1214,11 +1163,17 @@ __device__ __forceinline__ float tet_wet32(float p0, float p1, float p2, float p
   return vf * __fdividef(num, den);
 }
 
-// tet_piece_ff with the corners' roles over the interval given as a 4-bit mask of wet corners
+// tet_piece in pair arithmetic on normalised values: corner values p relative to the interval's
+// midpoint cm and divided by the cell's range (so that the differences are O(1)), the volume
+// fraction vt = V_t / V, and the corners' roles over the interval as a 4-bit mask of wet corners
 // (1 to 3 bits set) instead of a sort: the wet corners become s0.., the dry ones ..s3. The piece's
 // closed forms depend on the order only through these roles (they are symmetric within the wet
 // and within the dry corners); the two wet corners of the two-wet case are put in descending
-// order, as the FP64 path has them.
+// order, as the FP64 path has them. The piece's cubic in y = (c - cm) / range is added to q0..q3,
+// in units of the cell volume. The caller takes this path only for an interval wider than
+// root_narrow (at least 2^-20) of the range: every denominator is then a product of
+// (wet - dry) differences of at least 2^-20 each, so nothing leaves the FP32 exponent range or
+// loses the pairs' 48 bits.
 __device__ __forceinline__ void tet_piece_roles_ff(ff p0, ff p1, ff p2, ff p3, unsigned m, ff vt, ff& q0, ff& q1,
                                                    ff& q2, ff& q3) {
   const int nk = __popc(m);
@@ -1326,42 +1281,37 @@ __global__ void __launch_bounds__(kCellThreads, 5) k_root_cell(MeshView M, const
         }
         return v;
       };
-      // a vertex value strictly inside (ua, ub)
-      auto vertex_inside = [&](float ua, float ub) -> bool {
-        bool in = false;
+      // Bracketing by vertex values: the start u_s lies in the vertex interval [va, vb] of its
+      // neighbouring vertex values; the wet fraction at va and vb (where they are not the bracket's
+      // ends already) tells whether the root lies in it, below or above. Otherwise the next
+      // probe is the regula falsi point of the narrowed bracket. It ends when no vertex value
+      // lies strictly inside the bracket: the bracket is the root's vertex interval, found with
+      // one or two evaluations when the start falls in it.
+      float ua = -1.f, fa = 1.f - af, ub = 0.f, fb = -af;  // f(ua) > 0 > f(ub)
+      float p = fminf(fmaxf(refl ? -u0 : u0 - 1.f, -1.f), 0.f);
+      for (int it = 0; it < 16; ++it) {
+        float va = ua, vb = ub;  // the vertex values next to p inside the bracket
         for (int k = 0; k < nv; ++k) {
           const float x = sv[k * T].x;
-          in |= x > ua && x < ub;
+          if (x <= p) va = fmaxf(va, x); else vb = fminf(vb, x);
         }
-        return in;
-      };
-      float ua = -1.f, fa = 1.f - af, ub = 0.f, fb = -af;
-      float uc = fminf(fmaxf(refl ? -u0 : u0 - 1.f, -1.f), 0.f);
-      float fc = V32(uc) - af;
-      ++evals32;
-      int side = 0;
-      for (int it = 0; it < 16; ++it) {
-        if (fc > 0.f) { ua = uc; fa = fc; } else { ub = uc; fb = fc; }
-        if (fabsf(fc) <= 1e-6f * af || ub - ua <= 1e-6f * fmaxf(fabsf(ua), fabsf(ub))) break;
-        float un = ua + (ub - ua) * (fa / (fa - fb));
-        if (!(un > ua && un < ub)) un = 0.5f * (ua + ub);
-        if (it > 0 && !vertex_inside(ua, ub)) {  // the bracket lies in one vertex interval
-          uc = un;
-          break;
+        if (va == ua && vb == ub) break;
+        if (va > ua) {
+          const float f = V32(va) - af;
+          ++evals32;
+          if (f > 0.f) { ua = va; fa = f; } else { ub = va; fb = f; }
         }
-        if (it == 0) {
-          const float step = 0.02f;  // probe next to the start, towards the root
-          un = fc > 0.f ? fminf(uc + step, 0.5f * (uc + ub)) : fmaxf(uc - step, 0.5f * (ua + uc));
+        if (vb < ub) {  // the root is at or above va here
+          const float f = V32(vb) - af;
+          ++evals32;
+          if (f > 0.f) { ua = vb; fa = f; } else { ub = vb; fb = f; }
         }
-        uc = un;
-        fc = V32(uc) - af;
-        ++evals32;
-        const int s2 = fc > 0.f ? 1 : -1;
-        if (s2 == side) {
-          if (s2 > 0) fb *= 0.5f; else fa *= 0.5f;
-        }
-        side = s2;
+        p = ua + (ub - ua) * (fa / (fa - fb));
+        if (!(p > ua && p < ub)) p = 0.5f * (ua + ub);
       }
+      // the root phase starts at the regula falsi point of the bracket
+      float uc = ua + (ub - ua) * (fa / (fa - fb));
+      if (!(uc >= ua && uc <= ub)) uc = 0.5f * (ua + ub);
       // root phase in pairs: the refined point picks the vertex interval, one pass sums the
       // interval's cubic Q(y) = V_L/V - alpha, y = (c - cm) / range
       double c1 = dmin(dmax(fma(flip_if(fl2d(uc), refl), range, org), lo), hi);
