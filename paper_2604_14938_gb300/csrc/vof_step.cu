@@ -2601,14 +2601,9 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "selection kernels");
-  if (learned) {
-    e = launch_mlp_guess(m, s);  // times its two kernels itself
-    if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
-  }
   if (early_xmark) {
     // crossing faces next to the band, needed only by the least squares: a side branch next to
-    // the root search (latency-bound), forked after the network's kernels (issue-bound), which
-    // would otherwise share the SMs with it
+    // the network's kernels and the root search
     cudaEventRecord(m->ev_xfork, s);
     cudaStreamWaitEvent(m->xm_stream, m->ev_xfork, 0);
     tm.start(KC_XMARK, m->xm_stream);
@@ -2617,6 +2612,10 @@ vof_status launch_reconstruct(vof_mesh* m, const double* d_alpha, const vof_opti
     cudaEventRecord(m->ev_xjoin, m->xm_stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "crossing-face kernel");
+  }
+  if (learned) {
+    e = launch_mlp_guess(m, s);  // times its two kernels itself
+    if (e != cudaSuccess) return cuda_fail(e, "mlp guess");
   }
   // one branch per non-empty bin (root search); the branches join on s, then the geometry
   if (opt.root_mode == VOF_ROOT_FIXED) {
