@@ -1224,7 +1224,39 @@ __global__ void __launch_bounds__(kCellThreads, 5) k_root_cell(MeshView M, const
   const int32_t* list = W.bin_list + (size_t)bin * M.n_cells;
   const uint64_t ktol = mag(opt.tol_alpha);
   int64_t evals_acc = 0, tetev_acc = 0, ev32_acc = 0;
-  for (int64_t j = (int64_t)blockIdx.x * T + threadIdx.x; j < n_bin; j += (int64_t)gridDim.x * T) {
+  // The block takes kCellThreads entries of the bin at a time and sorts them by tetrahedron count
+  // (bitonic network in shared memory), so that the lanes of a warp get cells of similar size: a
+  // warp runs as long as its largest cell.
+  __shared__ uint32_t skey[kCellThreads];
+  for (int64_t base = (int64_t)blockIdx.x * kCellThreads; base < n_bin; base += (int64_t)gridDim.x * kCellThreads) {
+    {
+      const int64_t jj = base + threadIdx.x;
+      uint32_t key = 0xffffffffu;
+      if (jj < n_bin) {
+        const int32_t cc = W.iface_idx[list[jj]];
+        key = ((uint32_t)(M.cell_tet_off[cc + 1] - M.cell_tet_off[cc]) << 8) | threadIdx.x;
+      }
+      skey[threadIdx.x] = key;
+      __syncthreads();
+#pragma unroll
+      for (int k = 2; k <= kCellThreads; k <<= 1)
+#pragma unroll
+        for (int h = k >> 1; h > 0; h >>= 1) {
+          const int t = threadIdx.x, l = t ^ h;
+          if (l > t) {
+            const uint32_t x = skey[t], y = skey[l];
+            if ((x > y) == ((t & k) == 0)) {
+              skey[t] = y;
+              skey[l] = x;
+            }
+          }
+          __syncthreads();
+        }
+    }
+    const uint32_t mine = skey[threadIdx.x];
+    __syncthreads();  // every thread has its entry before the next chunk's keys are written
+    if (mine == 0xffffffffu) continue;
+    const int64_t j = base + (mine & 255u);
     const int64_t i = list[j];
     const int32_t cell = W.iface_idx[i];
     const int64_t v0 = M.cell_vert_off[cell], t0 = M.cell_tet_off[cell];
