@@ -233,7 +233,9 @@ vof_status vof_step_graph(vof_mesh* mesh, const double* d_alpha, const double* d
  * G = 1, 2, 4, 8, 16, 32, the other bins at their current choice, and keeps the fastest;
  * synchronises; h_G_out [5] (may be NULL) gets the choice (0 for bins without interface cells).
  * The choice applies when opt->group_size is 0.
- * vof_set_group_sizes sets it directly (0 = the built-in default for that bin). */
+ * vof_set_group_sizes sets it directly (0 = the built-in default for that bin). A choice whose lane
+ * groups do not fit in a block's shared memory in the step's root mode (plain bisection keeps FP64
+ * rows, twice the other modes' bytes) runs with the next larger lane count that fits. */
 vof_status vof_autotune(vof_mesh* mesh, const double* d_alpha, const vof_options* opt, int reps, int* h_G_out,
                         void* stream);
 vof_status vof_set_group_sizes(vof_mesh* mesh, const int* h_G);

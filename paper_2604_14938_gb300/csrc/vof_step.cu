@@ -2537,16 +2537,28 @@ int pick_group(const vof_mesh* m, const vof_options& o, int bin) {
   return g;
 }
 
+// Block size of a bin's lane-group root search: up to kThreads threads, halved while the groups'
+// rows exceed ~110 KB of shared memory; the shape fits when the block's groups stay within 220 KB.
+int root_threads(const vof_mesh* m, int mode, int bin, int G, size_t* smem) {
+  const size_t grp_bytes = root_group_bytes(m->bin_max_ct[bin], m->max_cv, mode);
+  int threads = kThreads;
+  while (threads > 32 && threads > G && (size_t)(threads / G) * grp_bytes > 110 * 1024) threads /= 2;
+  *smem = (size_t)(threads / G) * grp_bytes;
+  return threads;
+}
+bool root_group_fits(const vof_mesh* m, int mode, int bin, int G) {
+  size_t smem = 0;
+  root_threads(m, mode, bin, G, &smem);
+  return smem <= 220 * 1024;
+}
+
 template <int G>
 cudaError_t launch_root_g(vof_mesh* m, const double* alpha, const vof_options& opt, cudaStream_t s, int mode,
                           int use_mlp, int bin, int slow = 0) {
   const int max_ct = m->bin_max_ct[bin];
-  // block of up to kThreads threads whose cell rows fit in ~110 KB of shared memory
-  int threads = kThreads;
   const int max_cv = m->max_cv;
-  const size_t grp_bytes = root_group_bytes(max_ct, max_cv, mode);
-  while (threads > 32 && threads > G && (size_t)(threads / G) * grp_bytes > 110 * 1024) threads /= 2;
-  const size_t smem = (size_t)(threads / G) * grp_bytes;
+  size_t smem = 0;
+  const int threads = root_threads(m, mode, bin, G, &smem);
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
@@ -2688,6 +2700,10 @@ cudaError_t launch_root_bin(vof_mesh* m, const double* alpha, const vof_options&
   // one lane per cell of a small-cell bin: the thread-per-cell kernel (learned and cubic modes)
   if (G == 1 && mode != VOF_ROOT_BISECT && m->bin_max_ct[bin] <= kCellMaxTets)
     return launch_root_cell(m, alpha, opt, s, mode, use_mlp, bin);
+  // A lanes-per-cell choice whose groups do not fit in shared memory in this mode (plain bisection
+  // keeps FP64 rows, twice the bytes of the other modes' FP32 rows: a choice tuned for one mode may
+  // not fit another) takes the next larger one that fits; 32 lanes always fit.
+  while (G < 32 && !root_group_fits(m, mode, bin, G)) G *= 2;
   switch (G) {
     case 1: return launch_root_g<1>(m, alpha, opt, s, mode, use_mlp, bin);
     case 2: return launch_root_g<2>(m, alpha, opt, s, mode, use_mlp, bin);

@@ -34,14 +34,16 @@ def _dev(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def _run(M, a, T, Tb, n_cells, mode, graph, batch=None, **kw):
-    """Autotune for `mode`, then one step as the benchmark takes it; numpy outputs."""
+def _run(M, a, T, Tb, n_cells, mode, graph, batch=None, tune=True, **kw):
+    """Autotune for `mode` (unless tune is False), then one step as the benchmark takes it; numpy
+    outputs."""
     opt = vof.default_options(root_mode=mode, **kw)
     s = torch.cuda.Stream()  # graph capture needs a stream of its own
     with torch.cuda.stream(s):
         ta, tT = _dev(a), _dev(T)
         tTb = None if Tb is None else _dev(Tb)
-        M.autotune(ta, opt, reps=3, stream=s)
+        if tune:
+            M.autotune(ta, opt, reps=3, stream=s)
         mdot = torch.empty(n_cells, dtype=torch.float64, device="cuda")
         Q = torch.empty_like(mdot)
         tot = torch.empty(2, dtype=torch.float64, device="cuda")
@@ -170,6 +172,26 @@ def test_full_size_other_root_modes(full, mode):
         assert per_cell(g) * 5 < per_cell(gb), (per_cell(g), per_cell(gb))
     else:
         assert per_cell(gb) <= 1.5, per_cell(gb)
+
+
+@pytest.mark.parametrize("G", [1, 2])
+def test_full_size_lanes_that_do_not_fit_the_mode(full, G):
+    """Lanes per cell chosen for one root mode can be too few for another: plain bisection keeps FP64
+    rows, twice the shared memory of the learned path's FP32 rows, and the 2M case's largest cells
+    (the 65-192 tetrahedra bin) do not fit one or two lanes per cell in a block. The step then
+    takes the next lane count that fits, instead of failing the launch, and meets the bar."""
+    name, m, a, T, Tb, g, M = full
+    if name != "voronoi2m":
+        pytest.skip("the 2M case holds the largest cells")
+    M.set_group_sizes([G] * 5)
+    gb = _run(M, a, T, Tb, m.n_cells, vof.ROOT_BISECT, graph=False, tune=False)
+    O = oracle.Oracle(m)
+    V = O.geometry()["cell_vol"]
+    I = gb["iface_idx"]
+    assert len(I) == len(g["iface_idx"])
+    for c in sample_cells(m, a, I, np.random.default_rng(17)):
+        assert abs(O.liquid_volume(int(c), gb["phi_v"], gb["iso"][c])["VL"] / V[c] - a[c]) <= 1e-10
+    assert gb["counts"]["n_not_converged"] == 0
 
 
 def test_full_size_extrapolation(full):
