@@ -17,12 +17,12 @@
 //       sorted vertex values, then the cubic V_L has between two of them, solved on its own)
 //   R4  crossing point x_f on faces with (alpha_P - 1/2)(alpha_Q - 1/2) < 0
 //   R5  per-side gradients: own phase from the modified LSQ gradient, other phase from one upwind
-//       sweep over the neighbours on that side; or (the next row N2 of the scope) from the full
+//       sweep over the neighbours on that side; or from the full
 //       pseudo-time solve of Eq. (extrapolation), first-order upwind, per side and component
 //   R6  q_l, q_v, mdot, Q_phase
 //   R7  interface-modified least squares gradient (Appendix B), explicit symmetric inverse
 //   R8  totals by a fixed pairwise tree
-//   S   stencil variants of R7 for the stencil-anisotropy study (the next row N4 of the scope):
+//   S   stencil variants of R7 for the stencil-anisotropy study:
 //       standard (unmodified) stencil, inverse-distance weights, vertex neighbours; cond(G_P)
 //
 // Pinned only in special cases (invariants otherwise): R1 (the plain mean on a uniform hex mesh),
@@ -52,7 +52,7 @@ struct OrcProps {
   double k_l, k_v, h_lv, T_sat;
 };
 
-// Options of the pseudo-time extrapolation (N2); iters[] returns the iterations each of the six
+// Options of the pseudo-time extrapolation; iters[] returns the iterations each of the six
 // solves took (liquid side x, y, z, then vapour side x, y, z).
 struct OrcExtrap {
   int max_iter;
@@ -309,7 +309,7 @@ RootResult bisect(const OrcMesh& m, int64_t cell, const double* phi, double alph
   return r;
 }
 
-// R3, interval cubic (the NEXT row N1 of the hot-path scope): between two consecutive distinct
+// R3, interval cubic (an alternative to bisection): between two consecutive distinct
 // vertex values of the cell no tetrahedron changes its number of wet corners, so V_L(c) is one
 // cubic polynomial there (R2 is exact for a linear field on each tetrahedron). Steps: sort the
 // cell's distinct vertex values u_0 < ... < u_m; bisect over that list (one evaluation per probe)
@@ -358,7 +358,7 @@ RootResult interval_cubic(const OrcMesh& m, int64_t cell, const double* phi, dou
 }
 
 // R3, fixed isovalue (the paper's own choice, Sec. 2.1: the iso-surface at a prescribed
-// alpha_iso, typically 0.5; the next row N3 of the scope): no volume matching, c = alpha_iso. A
+// alpha_iso, typically 0.5): no volume matching, c = alpha_iso. A
 // cell whose vertex values all lie on one side of it has no interface there (its area is 0).
 RootResult fixed_iso(const OrcMesh& m, int64_t cell, const double* phi, double iso) {
   const std::vector<int32_t> vs = cell_vertices(m, cell);
@@ -560,7 +560,7 @@ void orc_liquid_volume(const OrcMesh* m, int64_t cell, const double* phi, double
 // R0 + R3 + geometry at the root for every cell with eps < alpha < 1 - eps (other cells get
 // iso = nan, status 0, evals 0, zero geometry). Arrays are [n_cells] or [3 n_cells].
 // `cells`, when non-null, restricts the work to the listed cells (n_list of them).
-// method 0: bisection (R3); 1: interval cubic (R3, next row N1); 2: fixed isovalue iso_fixed (N3).
+// method 0: bisection (R3); 1: interval cubic (R3); 2: fixed isovalue iso_fixed.
 void orc_reconstruct_m(const OrcMesh* mp, const double* alpha, const double* phi, const double* cell_vol, double eps,
                        double tol, int max_iter, const int64_t* cells, int64_t n_list, int method, double iso_fixed,
                        double* iso,
@@ -649,7 +649,7 @@ double extrap_dtau(const OrcMesh& m, const double* cell_cen, const double* face_
   return d;
 }
 
-// N2: Eq. (extrapolation) in pseudo-time, once per side and per gradient component. The field phi
+// Eq. (extrapolation) in pseudo-time, once per side and per gradient component. The field phi
 // starts as the modified LSQ gradient component of every cell. Information travels from the bulk
 // of a side towards and across the interface (the text's direction): the liquid side moves along
 // -n_int, the vapour side along +n_int. The unknowns of a side are the interface cells (A_int > 0)
@@ -720,7 +720,7 @@ void extrapolate(const OrcMesh& m, const double* face_area, const double* cell_v
 // R4-R8. Inputs: geometry (from orc_geometry), alpha, reconstruction (iso/status/A_int/n_int/
 // x_gamma arrays from orc_reconstruct), T at cells, T at boundary faces (may be null: boundary
 // faces then stay out of the stencil), properties; ex = null for R5's single sweep, else the
-// options of the pseudo-time solve (N2), whose iteration counts it returns.
+// options of the pseudo-time solve, whose iteration counts it returns.
 // Outputs ([n_cells] or [3 n_cells]): band flag, grad (modified LSQ) on band cells, grad_l,
 // grad_v, q_l, q_v, mdot, Q on interface cells, status bits (ORed into `status`);
 // per face: crossing flag, x_f, d_own, d_neigh, A_int_f; totals[0..1] = sum mdot V, sum Q V.
@@ -824,7 +824,7 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
     Gi[2][1] = Gi[1][2];
     for (int i = 0; i < 3; ++i) grad[3 * c + i] = Gi[i][0] * b[0] + Gi[i][1] * b[1] + Gi[i][2] * b[2];
   }
-  // N2 (when asked): the other side's gradient of every interface cell from the pseudo-time solve
+  // the pseudo-time solve (when asked): the other side's gradient of every interface cell from the pseudo-time solve
   std::vector<double> g_n2;
   if (ex) {
     g_n2.assign(3 * nc, 0.0);
@@ -876,7 +876,7 @@ void orc_phase_change(const OrcMesh* mp, const double* face_area, const double* 
   totals[1] = pairwise_sum(qv);
 }
 
-// Eq. interface_htc (the next row N3 of the scope): on each side of a crossing face the interface
+// Eq. interface_htc: on each side of a crossing face the interface
 // heat-transfer coefficient a_f = k_phi A_int,f / d_f, k_phi the conductivity of the phase the cell
 // resides in (liquid when alpha > 1/2) and d_f the cell centre's distance to the crossing point;
 // 0 on other faces. The cell adds a_f to its energy-matrix diagonal and a_f T_sat to its
@@ -895,7 +895,7 @@ void orc_interface_htc(const OrcMesh* mp, const double* alpha, const uint8_t* cr
   }
 }
 
-// Eq. interface_htc's place in the energy equation (next row N3): a cell whose face f is detached
+// Eq. interface_htc's place in the energy equation: a cell whose face f is detached
 // from the diffusive coupling by the interface adds a_f to its matrix diagonal and a_f T_sat to its
 // right-hand side. Per cell, over its faces in the cell's face order: diag = sum a_f, rhs =
 // sum a_f T_sat, with a_f the coefficient of the cell's own side of the face.
@@ -916,7 +916,7 @@ void orc_htc_cell_sums(const OrcMesh* mp, const uint8_t* crossing, const double*
   }
 }
 
-// N2 alone, on a given gradient field: g_other [3 n_cells] receives the other side's gradient of
+// The pseudo-time solve alone, on a given gradient field: g_other [3 n_cells] receives the other side's gradient of
 // every interface cell (iface[c] != 0; its phase: liquid when alpha > 1/2), iters[6] the counts.
 void orc_extrapolate(const OrcMesh* m, const double* face_area, const double* cell_vol, const double* alpha,
                      const uint8_t* iface, const double* n_int, const double* grad, double dtau, int max_iter,

@@ -232,7 +232,7 @@ def test_P3_exact_at_vertex_values():
 
 
 def test_P11_interval_cubic_matches_closed_form_root():
-    """P11 (NEXT row N1, interval cubic): on tetrahedra with a linear field the interval-cubic root
+    """P11 (interval cubic): on tetrahedra with a linear field the interval-cubic root
     equals the closed-form root of the tetrahedron's cut-volume cubic, with |V_L(c)/V - alpha| <=
     1e-12, after at most one bisection step over the four vertex values and two interior samples
     (plus the final check)."""
@@ -449,7 +449,7 @@ def test_P7_stefan_flux(frac):
 
 @pytest.mark.parametrize("frac", [0.23, 0.81])
 def test_P12_interface_htc_stefan(frac):
-    """P12 (next row N3, Eq. interface_htc): on the planar Stefan layer the one crossing face per row
+    """P12 (Eq. interface_htc): on the planar Stefan layer the one crossing face per row
     of cells is the face next to the interface cell; its interface area projected onto the face is
     the face area h^2, and each side's coefficient is k_phi h^2 / d with d the distance from that
     cell's centre to the plane x = x_g; every other face has none."""
@@ -472,7 +472,7 @@ def test_P12_interface_htc_stefan(frac):
 
 @pytest.mark.parametrize("frac", [0.23, 0.81])
 def test_P12_energy_matrix_terms_stefan(frac):
-    """P12 (next row N3, Eq. interface_htc in the energy equation): on the planar Stefan layer each
+    """P12 (Eq. interface_htc in the energy equation): on the planar Stefan layer each
     cell next to the interface has exactly one detached face, so its diagonal term is k_phi h^2 / d
     (d its centre's distance to the plane x = x_g) and its right-hand side that times T_sat; every
     other cell has none."""
@@ -520,7 +520,7 @@ def test_P12_energy_matrix_terms_two_faces():
 
 
 def test_P12_fixed_isovalue_planar():
-    """P12 (next row N3): with the vertex field linear in x the alpha_iso = 0.5 surface is the plane
+    """P12: with the vertex field linear in x the alpha_iso = 0.5 surface is the plane
     where that field is 0.5; its area in each cut cell is the cell's cross-section (1/3)^2, its
     normal -x (vapour at high x), and the cells it misses have no interface."""
     m = synth.hex_box(6, 3, 3)
