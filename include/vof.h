@@ -84,12 +84,11 @@ typedef enum {
  * the cell split into tetrahedra of its own vertices); an FP32 refinement (from the MLP guess when
  * the mesh has an MLP, else from 1 - alpha) picks the interval, one
  * FP64 pass sums the straddling tetrahedra's pieces into that cubic, and its root follows from
- * the polynomial alone (bisection fallback, counted). The paper has no such mode: it is the
- * scope's next step for the root search. */
+ * the polynomial alone (bisection fallback, counted). The paper has no such mode. */
 #define VOF_ROOT_CUBIC 2
 /* Fixed isovalue: the iso-surface at alpha_iso (Sec. 2.1, typically 0.5), the paper's own
  * reconstruction, without volume matching; a cell whose vertex values do not straddle it has no
- * interface there. The scope's next step N3. */
+ * interface there. */
 #define VOF_ROOT_FIXED 3
 
 typedef struct vof_mesh vof_mesh; /* opaque, library-owned */

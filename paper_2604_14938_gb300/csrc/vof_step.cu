@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
         // every FP64 evaluation of V_L is P, exactly.
         //  - Learned: an evaluation at the refined point, one at a Newton point with the FP32
         //    slope, at most max_secant secant steps (the guess + secant steps of the learned path).
-        //  - Interval cubic (the next row N1 of the scope): safeguarded Newton steps on P.
+        //  - Interval cubic: safeguarded Newton steps on P.
         // A miss of the tolerance ends in bisection on P inside the bracket (the counted
         // fallback); if no interval brackets the target, in bisection over [phi_min, phi_max]
         // with every tetrahedron evaluated directly.

@@ -1,4 +1,4 @@
-"""The interval-cubic root mode (the scope's next step for the root search) on the GPU: the cut
+"""The interval-cubic root mode (the exact cubic of the root's vertex interval) on the GPU: the cut
 volume at its isovalue matches alpha (checked by the oracle), the isovalue agrees with the oracle's
 own interval-cubic root where the interface has area, the downstream steps from it agree with the
 oracle, and it takes one or two FP64 passes per cell."""
@@ -81,7 +81,7 @@ def test_interval_cubic_takes_the_mlp_guess():
 
 @pytest.mark.parametrize("name", ["hex_sphere", "voronoi_film", "tet_sphere", "pipe_film"])
 def test_fixed_isovalue_mode(name):
-    """The paper's own reconstruction (iso-surface at alpha_iso = 0.5, the scope's next row N3):
+    """The paper's own reconstruction (iso-surface at alpha_iso = 0.5):
     the geometry at 0.5 and the downstream steps match the oracle's, and the interface
     heat-transfer coefficients a_f = k_phi A_int,f / d_f of both sides of every crossing face next
     to the band match too."""
