@@ -198,7 +198,7 @@ def run_ours(args, rank, world, dev):
                 tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
                 M.set_group_sizes(tuned[mode])
             else:
-                tuned[mode] = M.autotune(ta_k[0], opt, reps=30)  # lanes per cell of each bin, for this mode
+                tuned[mode] = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
 
             def one(k):
                 ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]

@@ -228,9 +228,8 @@ vof_status vof_step_graph(vof_mesh* mesh, const double* d_alpha, const double* d
 
 /* Interface cells are binned by tetrahedron count ([1,4], [5,8], [9,24], [25,64], [65,192]); each
  * bin's root search runs with its own lanes per cell G. vof_autotune reconstructs with d_alpha,
- * then, bin by bin (largest first, two sweeps over the bins), times reps whole reconstructions
- * (CUDA events) for each of G = 1, 2, 4, 8, 16, 32, the other bins at their current choice, and
- * keeps the fastest;
+ * then, bin by bin (largest first), times reps whole reconstructions (CUDA events) for each of
+ * G = 1, 2, 4, 8, 16, 32, the other bins at their current choice, and keeps the fastest;
  * synchronises; h_G_out [5] (may be NULL) gets the choice (0 for bins without interface cells).
  * The choice applies when opt->group_size is 0.
  * vof_set_group_sizes sets it directly (0 = the built-in default for that bin). A choice whose lane

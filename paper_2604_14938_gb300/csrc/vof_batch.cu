@@ -173,7 +173,7 @@ vof_status vof_autotune(vof_mesh* m, const double* d_alpha, const vof_options* o
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // Coordinate descent over the populated bins, largest first, two sweeps: each candidate G of a bin is timed
+  // Coordinate descent over the populated bins, largest first: each candidate G of a bin is timed
   // as reps whole reconstructions (selection, learned guess, every bin's root search as parallel
   // branches), the other bins at their current choice, so that the choice accounts for the bins
   // sharing the GPU.
@@ -186,10 +186,8 @@ vof_status vof_autotune(vof_mesh* m, const double* d_alpha, const vof_options* o
     for (int j = i; j > 0 && cn.bin_count[order[j]] > cn.bin_count[order[j - 1]]; --j) std::swap(order[j], order[j - 1]);
   for (int b = 0; b < kBins; ++b)
     if (!m->bin_cells[b] || !cn.bin_count[b]) m->bin_G[b] = 0;
-  // two sweeps: the second revisits each bin with the others at their tuned choice (a small bin's
-  // timing depends on what the large bins, running beside it, were set to in the first sweep)
-  for (int i = 0; i < 2 * nb; ++i) {
-    const int b = order[i % nb];
+  for (int i = 0; i < nb; ++i) {
+    const int b = order[i];
     float best = 1e30f;
     int best_G = m->bin_G[b];
     for (int G = 1; G <= 32; G *= 2) {
