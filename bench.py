@@ -191,14 +191,6 @@ def run_ours(args, rank, world, dev):
         tuned = {}
         for mode in modes:
             opt = path_options(vof, mode)
-            if mode == "learned_extrap" and "learned" in tuned:  # the same root search as the learned path
-                tuned[mode] = tuned["learned"]
-                M.set_group_sizes(tuned[mode])
-            elif args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
-                tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
-                M.set_group_sizes(tuned[mode])
-            else:
-                tuned[mode] = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
 
             def one(k):
                 ta, tT = ta_k[k % len(ta_k)], tT_k[k % len(tT_k)]
@@ -208,6 +200,16 @@ def run_ours(args, rank, world, dev):
                     M.step_graph(ta, tT, tTb, synth.PROPS, mdot, Q, tot, opt, stream=stream)
                 if batch:
                     B.totals(btot, stream=stream)
+
+            if mode == "learned_extrap" and "learned" in tuned:  # the same root search as the learned path
+                tuned[mode] = tuned["learned"]
+                M.set_group_sizes(tuned[mode])
+            elif args.group_sizes:  # a fixed choice, e.g. one tuned without a profiler's serialised launches
+                tuned[mode] = [int(x) for x in args.group_sizes.split(",")]
+                M.set_group_sizes(tuned[mode])
+            else:
+                G0 = M.autotune(ta_k[0], opt, reps=10)  # lanes per cell of each bin, for this mode
+                tuned[mode] = step_tune(M, G0, one, flush, stream)
 
             for k in range(args.warmup):
                 one(k)
@@ -270,6 +272,39 @@ def run_ours(args, rank, world, dev):
     info = dict(n_cells=nc, batch=batch, pipe=pipe, tuned=tuned, extra=extra, e2e_units=e2e_units, fp64=fp64,
                 h2d=8 * (2 * nc + (0 if pipe else n_bnd)), d2h=8 * (nc + 2))
     return M, (meshes, a, T, Tb), desc, results, e2e_s, info
+
+
+def step_tune(M, G0, one, flush, stream, steps=8) -> list:
+    """The library's autotuner times reconstructions alone; in the step the crossing-face list and
+    the zeroing of mdot and Q run beside them, which can change a small bin's best lanes per cell.
+    Starting from its choice, coordinate descent over the populated bins with `steps` whole timed
+    steps per candidate (L2 flushed between steps, outside the events) keeps the fastest."""
+    import torch
+
+    def cost(G):
+        M.set_group_sizes(G)
+        one(0)  # a graph path captures its graph here
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k, (s0, e0) in enumerate(ev):
+            flush.fill_(k & 0xFF)
+            s0.record(stream)
+            one(k)
+            e0.record(stream)
+        stream.synchronize()
+        return sum(s0.elapsed_time(e0) for s0, e0 in ev)
+
+    best, best_t = list(G0), cost(list(G0))
+    for b in [b for b in range(len(G0)) if G0[b]]:
+        for G in (1, 2, 4, 8, 16, 32):
+            if G == best[b]:
+                continue
+            cand = list(best)
+            cand[b] = G
+            t = cost(cand)
+            if t < best_t:
+                best, best_t = cand, t
+    M.set_group_sizes(best)
+    return best
 
 
 def headline_mode(results) -> str:
