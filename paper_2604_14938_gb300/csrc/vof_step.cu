@@ -1124,10 +1124,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_root(MeshView M, const double* 
 // The learned and interval-cubic modes for small cells (tetrahedra, prisms, hexahedra, the pipe's
 // extruded polygons): every lane of a warp owns one cell and runs the same steps, so the warp's
 // instructions serve 32 cells and no lane group drifts out of step with the others.
-//  - FP32 refinement from the start value (the MLP guess, or 1 - alpha), regula falsi with the
-//    Illinois modification on FP32 wet fractions formed from the tetrahedra's corner values in one
-//    pass each (tet_wet32: nothing per tetrahedron is kept in shared memory). It stops as soon as
-//    its bracket holds no vertex value, i.e. once it has found the vertex interval of the root.
+//  - FP32 bracketing of the root by vertex values, from the start value (the MLP guess, or
+//    1 - alpha): the wet fraction at the vertex values next to the start, then next to the regula
+//    falsi point of the narrowed bracket, until no vertex value lies inside the bracket: it is then
+//    the root's vertex interval. Each FP32 evaluation forms the tetrahedra's wet fractions from
+//    their corner values in one pass (tet_wet32: nothing per tetrahedron is kept in shared memory).
+//  - Each block takes kCellThreads entries of the bin at a time, sorted by tetrahedron count, so
+//    that a warp's lanes hold cells of similar size.
 //  - One pass over the tetrahedra for that interval sums the interval's cubic in FP32-pair
 //    arithmetic (tet_piece_roles_ff) on values normalised by the cell's range (on this part an
 //    FP64 warp instruction costs 64 issue slots of its sub-partition). The vertices' wet/dry roles
