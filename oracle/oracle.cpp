@@ -25,9 +25,10 @@
 //   S   stencil variants of R7 for the stencil-anisotropy study:
 //       standard (unmodified) stencil, inverse-distance weights, vertex neighbours; cond(G_P)
 //
-// Pinned only in special cases (invariants otherwise): R1 (the plain mean on a uniform hex mesh),
-// R5, a reading of the extrapolation step (equal neighbour gradients), R4 (a point on the common
-// plane); R4's choice between two different planes has no independent pin ("parity unpinned").
+// Pinned only in special cases: R5, a reading of the extrapolation step (closed forms when the
+// neighbour gradients are equal; its weights also enter the pseudo-time solve, whose first step at a
+// Courant number of 1 reproduces it). R1 (inverse distances to cells of different sizes) and R4's
+// choice between two different planes are pinned by cases worked by hand.
 #include <algorithm>
 #include <array>
 #include <cmath>
