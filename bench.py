@@ -293,17 +293,26 @@ def step_tune(M, G0, one, flush, stream, steps=8) -> list:
         stream.synchronize()
         return sum(s0.elapsed_time(e0) for s0, e0 in ev)
 
+    best = coordinate_descent(G0, cost)
+    M.set_group_sizes(best)
+    return best
+
+
+def coordinate_descent(G0, cost) -> list:
+    """Lanes per cell of the populated bins (G0[b] != 0), one bin at a time in bin order: each of
+    1, 2, 4, 8, 16, 32 is tried with the other bins at their current best, and the cheapest kept.
+    Empty bins stay 0."""
     best, best_t = list(G0), cost(list(G0))
     for b in [b for b in range(len(G0)) if G0[b]]:
+        g_start = best[b]  # measured already, with the other bins as they are now
         for G in (1, 2, 4, 8, 16, 32):
-            if G == best[b]:
+            if G == g_start:
                 continue
             cand = list(best)
             cand[b] = G
             t = cost(cand)
             if t < best_t:
                 best, best_t = cand, t
-    M.set_group_sizes(best)
     return best
 
 
