@@ -43,9 +43,18 @@ RESIDENT_STEPS = 100  # device-resident input pairs of the moving-film workload 
 # tetrahedra at ~20 flops). The roofline's own basis is the FP64-equivalent work the kernel counts
 # on the device (pieces prepared and expanded, per-pass scaling).
 CLIP_FLOPS_PER_EVAL = 2000
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per root-search launch, from ncu
-# captures of the workload (and layers), path and lanes per cell given; null for anything else
-ROOT_TRAFFIC: dict = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per root-search launch record (one per
+# populated bin and step, as in the roofline's launch count), from ncu captures of the workload
+# (and layers), path and lanes per cell given; null for anything else. The pipe's root search was
+# captured on 100- and 200-layer cuts (3 launches per step: k_root<8> for the 5-8 tetrahedra bin,
+# k_root_cell and its hand-over k_root<4> for the 9-24 bin): 48.16 and 99.10 MB per step for
+# 48,384 and 96,768 interface cells, in proportion to within 3 %, so the 600-layer case
+# (290,304 interface cells, 3x the 200-layer cut) takes 3 x 99.10 MB per step.
+ROOT_TRAFFIC: dict = {
+    ("pipe8m", 100, "learned", (0, 8, 1, 0, 0)): 48.16e6 / 2,
+    ("pipe8m", 200, "learned", (0, 8, 1, 0, 0)): 99.10e6 / 2,
+    ("pipe8m", 600, "learned", (0, 8, 1, 0, 0)): 3 * 99.10e6 / 2,
+}
 # path name -> (root mode, pseudo-time extrapolation, guess option)
 PATHS = {"bisect": (0, 0, 0), "learned": (1, 0, 0), "learned_nomlp": (1, 0, 1), "cubic": (2, 0, 1),
          "learned_extrap": (1, 1, 0)}
@@ -496,6 +505,7 @@ def main():
     # bin; MLP features and forward; the pseudo-time extrapolation; batch totals
     per_step = (6 + nbins + (2 if mlp_used else 0) + (1 if best == "learned_extrap" else 0)
                 + (1 if info["batch"] else 0))
+    traffic = ROOT_TRAFFIC.get((args.workload, args.layers, best, tuple(info["tuned"][best])))
     config = bench_config(args, desc, info["n_cells"], fields[1], info["extra"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -518,7 +528,11 @@ def main():
         "roofline": {"kernel": "k_root (isovalue root search)", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None,
-                     "traffic": ROOT_TRAFFIC.get((args.workload, args.layers, best, tuple(info["tuned"][best]))),
+                     "traffic": traffic,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the root-search "
+                                        "launches per launch record, captured on 100- and 200-layer cuts of the pipe "
+                                        "in this lane choice and scaled by interface cells" if traffic else
+                                        "no ncu capture of this workload, path and lane choice"),
                      "flops_per_launch": counted / max(root_launches, 1),
                      "flops_per_iface_cell": counted / max(ks["n_iface"], 1),
                      "launches": root_launches, "ms_per_launch": root_ms / max(root_launches, 1),
