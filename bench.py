@@ -140,6 +140,19 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
+def hbm_peak_gbs(path=os.path.join(ROOT, "MEASURED_PEAKS.json")) -> tuple[float, str]:
+    """(HBM copy rate in GB/s, where it comes from): the measured copy rate of the GB300s
+    when the peaks file is present, else an earlier GB300 measurement of 6.8 TB/s."""
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            return v, f"measured copy rate (read + write bytes) on this GPU type: {v:.1f} GB/s of measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6800.0, "6800 GB/s of fallback (an earlier GB300 copy measurement)"
+
+
 def n_interface(a) -> int:
     return int(np.count_nonzero((a > 1e-12) & (a < 1 - 1e-12)))
 
@@ -506,6 +519,8 @@ def main():
     per_step = (6 + nbins + (2 if mlp_used else 0) + (1 if best == "learned_extrap" else 0)
                 + (1 if info["batch"] else 0))
     traffic = ROOT_TRAFFIC.get((args.workload, args.layers, best, tuple(info["tuned"][best])))
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    root_gbs = traffic / (root_ms / max(root_launches, 1) / 1e3) / 1e9 if traffic and root_ms else None
     config = bench_config(args, desc, info["n_cells"], fields[1], info["extra"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -543,6 +558,10 @@ def main():
                      "peak_source": (f"FP64 FMA-chain probe in this run (vof_probe_fp64_fma: 8 independent chains per "
                                      f"thread, every SM at full occupancy, best of 3): {peak:.4f} TFLOP/s of measured; "
                                      f"nominal 152 SMs x 2070 MHz x 4 flop/clk = {FP64_NOMINAL_TFLOPS:.4f}"),
+                     "hbm": {"achieved": root_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": root_gbs / hbm_peak if root_gbs else None, "peak_source": hbm_src,
+                             "note": "the root search's DRAM bytes per launch record over its mean launch time: "
+                                     "context beside the binding FP64 figure"},
                      "clip_estimate": {"flops_per_eval": CLIP_FLOPS_PER_EVAL, "achieved": clip_tf,
                                        "frac": clip_tf / peak if clip_tf else None,
                                        "note": "a clipping-based 2 kFLOP per FP64 cut-volume evaluation of a ~14-face "

@@ -1,5 +1,6 @@
 """Host logic of the benchmark that needs no GPU: the coordinate descent that refines the lanes
-per cell of each tetrahedron-count bin by whole-step timings."""
+per cell of each tetrahedron-count bin by whole-step timings, the HBM peak lookup, and the table
+of the root search's captured DRAM traffic."""
 import bench
 
 
@@ -26,3 +27,22 @@ def test_coordinate_descent_follows_the_coupling_in_bin_order():
         return abs(G[1] - 4) * 10 + abs(G[2] - G[1])
 
     assert bench.coordinate_descent([0, 32, 32, 0, 0], cost) == [0, 4, 4, 0, 0]
+
+
+def test_hbm_peak_reads_the_measured_rate_else_falls_back(tmp_path):
+    p = tmp_path / "peaks.json"
+    p.write_text('{"hbm_gbs": 6785.5, "bf16_tflops": 1906.3}')
+    v, src = bench.hbm_peak_gbs(str(p))
+    assert v == 6785.5 and "of measured" in src
+    v, src = bench.hbm_peak_gbs(str(tmp_path / "absent.json"))
+    assert v == 6800.0 and "of fallback" in src
+    p.write_text('{"bf16_tflops": 1906.3}')
+    assert bench.hbm_peak_gbs(str(p))[0] == 6800.0
+
+
+def test_root_traffic_entries_scale_with_the_interface():
+    # the full pipe's entry is three 200-layer cuts; the 200-layer cut about twice the 100-layer one
+    key = lambda L: ("pipe8m", L, "learned", (0, 8, 1, 0, 0))
+    t = bench.ROOT_TRAFFIC
+    assert t[key(600)] == 3 * t[key(200)]
+    assert 2.0 <= t[key(200)] / t[key(100)] <= 2.1
