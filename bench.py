@@ -46,15 +46,17 @@ CLIP_FLOPS_PER_EVAL = 2000
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per root-search launch record (one per
 # populated bin and step, as in the roofline's launch count), from ncu captures of the workload
 # (and layers), path and lanes per cell given; null for anything else. The pipe's root search was
-# captured on 100- and 200-layer cuts (3 launches per step: k_root<8> for the 5-8 tetrahedra bin,
-# k_root_cell and its hand-over k_root<4> for the 9-24 bin): 48.16 and 99.10 MB per step for
-# 48,384 and 96,768 interface cells, in proportion to within 3 %, so the 600-layer case
-# (290,304 interface cells, 3x the 200-layer cut) takes 3 x 99.10 MB per step.
-ROOT_TRAFFIC: dict = {
-    ("pipe8m", 100, "learned", (0, 8, 1, 0, 0)): 48.16e6 / 2,
-    ("pipe8m", 200, "learned", (0, 8, 1, 0, 0)): 99.10e6 / 2,
-    ("pipe8m", 600, "learned", (0, 8, 1, 0, 0)): 3 * 99.10e6 / 2,
-}
+# captured with the 9-24 tetrahedra bin on the thread-per-cell kernel (k_root_cell and its
+# hand-over launch) and 4, 8, 16 or 32 lanes per cell in the 5-8 bin (3 launches per step). At
+# 8 lanes: 48.16 and 99.10 MB per step on 100- and 200-layer cuts (48,384 and 96,768 interface
+# cells), in proportion to within 3 %; on the 200-layer cut 4, 16 and 32 lanes move 99.16, 99.05
+# and 99.08 MB (the 5-8 bin reads 6.75 MB whatever its lanes). The 600-layer case has three times
+# the 200-layer cut's interface cells (290,304) and is taken to move three times its bytes.
+_PIPE200_STEP_BYTES = {4: 99.16e6, 8: 99.10e6, 16: 99.05e6, 32: 99.08e6}
+ROOT_TRAFFIC: dict = {("pipe8m", 100, "learned", (0, 8, 1, 0, 0)): 48.16e6 / 2}
+for _g, _b in _PIPE200_STEP_BYTES.items():
+    ROOT_TRAFFIC[("pipe8m", 200, "learned", (0, _g, 1, 0, 0))] = _b / 2
+    ROOT_TRAFFIC[("pipe8m", 600, "learned", (0, _g, 1, 0, 0))] = 3 * _b / 2
 # path name -> (root mode, pseudo-time extrapolation, guess option)
 PATHS = {"bisect": (0, 0, 0), "learned": (1, 0, 0), "learned_nomlp": (1, 0, 1), "cubic": (2, 0, 1),
          "learned_extrap": (1, 1, 0)}

@@ -46,3 +46,7 @@ def test_root_traffic_entries_scale_with_the_interface():
     t = bench.ROOT_TRAFFIC
     assert t[key(600)] == 3 * t[key(200)]
     assert 2.0 <= t[key(200)] / t[key(100)] <= 2.1
+    # the 5-8 bin's lane count changes the captured bytes by well under 1 %
+    for G in (4, 16, 32):
+        k = ("pipe8m", 600, "learned", (0, G, 1, 0, 0))
+        assert abs(t[k] / t[key(600)] - 1) < 0.01
