@@ -1,8 +1,10 @@
 """GB300 (sm_103a) sharp-interface VOF phase-change hot path — Python binding.
 
 Argument marshalling over the C ABI of ``libvof_gb300.so`` (include/vof.h): every step of the
-path runs in the library's CUDA kernels; PyTorch supplies device memory and the stream. If the
-library is missing this module raises instead of falling back to anything else.
+path runs in the library's CUDA kernels; PyTorch supplies device memory and the stream. Each
+tensor argument of the hot-path calls is checked before the call (float64, contiguous, on the
+stated memory side, long enough for the mesh; ValueError otherwise). If the library is missing
+this module raises instead of falling back to anything else.
 """
 from __future__ import annotations
 
@@ -125,6 +127,30 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _arg(t, n: int, name: str, what: str, cuda: bool = True, optional: bool = False):
+    """The address of a float64 tensor argument, after the checks the C ABI cannot make on a bare
+    pointer: a contiguous torch tensor of dtype float64 with at least n elements, in CUDA device
+    memory (cuda=True) or in host memory (cuda=False). None passes as NULL where the argument is
+    optional. A wrong argument raises ValueError before any call into the library, where it would
+    otherwise be read or written out of bounds."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{what}: {name} is required")
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what}: {name} must be a torch tensor, not {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{what}: {name} must be float64, not {t.dtype}")
+    if bool(t.is_cuda) != cuda:
+        raise ValueError(f"{what}: {name} must be in {'CUDA device' if cuda else 'host'} memory")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: {name} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{what}: {name} holds {t.numel()} values, {n} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 class Mesh:
     """A mesh uploaded to the GPU (library-owned). `m` is any object with the primitive arrays
     of the mesh format (vx, vy, vz, face_vert_off, face_vert, face_owner, face_neigh,
@@ -161,31 +187,45 @@ class Mesh:
     def reconstruct(self, alpha, opt: Options | None = None, stream=None):
         """vof_reconstruct: alpha is a CUDA float64 tensor [n_cells]."""
         o = opt or default_options()
-        _check(lib().vof_reconstruct(self.h, _ptr(alpha), ctypes.byref(o), _stream(stream)), "vof_reconstruct")
+        pa = _arg(alpha, self.n_cells, "alpha", "vof_reconstruct")
+        _check(lib().vof_reconstruct(self.h, pa, ctypes.byref(o), _stream(stream)), "vof_reconstruct")
 
     def phase_change_source(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: Options | None = None,
                             stream=None):
         """vof_phase_change_source: all tensors CUDA float64 (T_bnd may be None)."""
         o = opt or default_options()
         p = props_of(props)
-        _check(lib().vof_phase_change_source(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p),
-                                             ctypes.byref(o), _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)),
-               "vof_phase_change_source")
+        a = self._step_args("vof_phase_change_source", alpha, T, T_bnd, mdot, Q, totals)
+        _check(lib().vof_phase_change_source(self.h, a[0], a[1], a[2], ctypes.byref(p), ctypes.byref(o), a[3], a[4],
+                                             a[5], _stream(stream)), "vof_phase_change_source")
 
     def step(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: Options | None = None, stream=None):
         """vof_step: reconstruct + phase-change source in one call."""
         o = opt or default_options()
         p = props_of(props)
-        _check(lib().vof_step(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p), ctypes.byref(o),
-                              _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)), "vof_step")
+        a = self._step_args("vof_step", alpha, T, T_bnd, mdot, Q, totals)
+        _check(lib().vof_step(self.h, a[0], a[1], a[2], ctypes.byref(p), ctypes.byref(o), a[3], a[4], a[5],
+                              _stream(stream)), "vof_step")
 
     def step_host(self, h_alpha, h_T, h_T_bnd, props: dict, h_mdot, h_totals, opt: Options | None = None,
                   stream=None):
         """vof_step_host: host tensors (pinned for asynchronous copies); synchronises."""
         o = opt or default_options()
         p = props_of(props)
-        _check(lib().vof_step_host(self.h, _ptr(h_alpha), _ptr(h_T), _ptr(h_T_bnd), ctypes.byref(p), ctypes.byref(o),
-                                   _ptr(h_mdot), _ptr(h_totals), _stream(stream)), "vof_step_host")
+        w = "vof_step_host"
+        nc, nf = self.n_cells, self.n_faces
+        a = (_arg(h_alpha, nc, "h_alpha", w, cuda=False), _arg(h_T, nc, "h_T", w, cuda=False),
+             _arg(h_T_bnd, nf, "h_T_bnd", w, cuda=False, optional=True), _arg(h_mdot, nc, "h_mdot", w, cuda=False),
+             _arg(h_totals, 2, "h_totals", w, cuda=False))
+        _check(lib().vof_step_host(self.h, a[0], a[1], a[2], ctypes.byref(p), ctypes.byref(o), a[3], a[4],
+                                   _stream(stream)), w)
+
+    def _step_args(self, what, alpha, T, T_bnd, mdot, Q, totals):
+        """Checked device addresses of a step's tensors: alpha, T, mdot, Q [n_cells], T_bnd
+        [n_faces] or None, totals [2]."""
+        nc, nf = self.n_cells, self.n_faces
+        return (_arg(alpha, nc, "alpha", what), _arg(T, nc, "T", what), _arg(T_bnd, nf, "T_bnd", what, optional=True),
+                _arg(mdot, nc, "mdot", what), _arg(Q, nc, "Q", what), _arg(totals, 2, "totals", what))
 
     # ---- results
     def field(self, name: str, stream=None):
@@ -328,10 +368,11 @@ def _mesh_mlp_features(self, alpha, stream=None):
     """(features [n_iface, 40] float32, ok [n_iface] int32) of the last reconstruction, which was
     made with the CUDA float64 tensor `alpha`."""
     import torch
+    pa = _arg(alpha, self.n_cells, "alpha", "vof_mlp_features")
     n = self.counts()["n_iface"]
     X = torch.empty((max(n, 1), N_MLP_FEATURES), dtype=torch.float32, device="cuda")
     ok = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
-    _check(_mlp_sig().vof_mlp_features(self.h, _ptr(alpha), _ptr(X), _ptr(ok), _stream(stream)), "vof_mlp_features")
+    _check(_mlp_sig().vof_mlp_features(self.h, pa, _ptr(X), _ptr(ok), _stream(stream)), "vof_mlp_features")
     return X[:n], ok[:n]
 
 
@@ -369,15 +410,17 @@ def _mesh_step_graph(self, alpha, T, T_bnd, props: dict, mdot, Q, totals, opt: O
     """vof_step_graph: the step captured once into a CUDA graph and replayed (non-default stream)."""
     o = opt or default_options()
     p = props_of(props)
-    _check(_ext_sig().vof_step_graph(self.h, _ptr(alpha), _ptr(T), _ptr(T_bnd), ctypes.byref(p), ctypes.byref(o),
-                                     _ptr(mdot), _ptr(Q), _ptr(totals), _stream(stream)), "vof_step_graph")
+    a = self._step_args("vof_step_graph", alpha, T, T_bnd, mdot, Q, totals)
+    _check(_ext_sig().vof_step_graph(self.h, a[0], a[1], a[2], ctypes.byref(p), ctypes.byref(o), a[3], a[4], a[5],
+                                     _stream(stream)), "vof_step_graph")
 
 
 def _mesh_autotune(self, alpha, opt: Options | None = None, reps: int = 5, stream=None) -> list:
     """vof_autotune: lanes per cell of every tetrahedron-count bin, timed on `alpha`."""
     o = opt or default_options()
     G = (ctypes.c_int * 5)()
-    _check(_ext_sig().vof_autotune(self.h, _ptr(alpha), ctypes.byref(o), reps, G, _stream(stream)), "vof_autotune")
+    pa = _arg(alpha, self.n_cells, "alpha", "vof_autotune")
+    _check(_ext_sig().vof_autotune(self.h, pa, ctypes.byref(o), reps, G, _stream(stream)), "vof_autotune")
     return list(G)
 
 
